@@ -1,0 +1,354 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every expected value is a
+quadrature, a closed form, a conservation law, a continuum limit of the SPH
+operators, or a brute-force enumeration.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_2104_00537_gb300 import cases
+from tests.lattice import centre_index, lattice_case, random_cloud
+
+
+# ---- Eq 11: Wendland C2 kernel -------------------------------------------
+
+@pytest.mark.parametrize("h", [0.01, 0.0346, 1.0])
+def test_wendland_normalises_to_one(h):
+    """Eq 3: the 3-D kernel integrates to 1 over its support (quadrature)."""
+    val, err = integrate.quad(lambda r: 4 * math.pi * r * r * oracle.wendland_w(r, h),
+                              0.0, 2 * h, epsabs=1e-13, epsrel=1e-12)
+    assert abs(val - 1.0) < 1e-10
+
+
+def test_wendland_compact_support_and_monotone():
+    """Eq 4 with k = 2: W = 0 for |r| >= 2h, and W decreases monotonically."""
+    h = 0.05
+    assert oracle.wendland_w(2 * h, h) == 0.0
+    assert oracle.wendland_w(2.5 * h, h) == 0.0
+    assert oracle.wendland_gradfac(2 * h, h) == 0.0
+    r = np.linspace(0, 2 * h, 200)
+    w = np.array([oracle.wendland_w(x, h) for x in r])
+    assert np.all(np.diff(w) < 0)
+
+
+@pytest.mark.parametrize("q", [0.05, 0.3, 0.9, 1.0, 1.5, 1.95])
+def test_wendland_gradient_matches_finite_difference(q):
+    """grad W = F r_ab must equal the radial derivative of W (central FD)."""
+    h = 0.0346
+    r = q * h
+    eps = 1e-6 * h
+    dwdr = (oracle.wendland_w(r + eps, h) - oracle.wendland_w(r - eps, h)) / (2 * eps)
+    F = oracle.wendland_gradfac(r, h)
+    assert F < 0
+    assert F * r == pytest.approx(dwdr, rel=1e-7)
+
+
+def test_wendland_second_moment_by_quadrature():
+    """The lattice pins below rely on int F(r) x_i x_j d^3r = -delta_ij."""
+    h = 0.03
+    val, _ = integrate.quad(lambda r: 4 * math.pi / 3 * r ** 4 * oracle.wendland_gradfac(r, h),
+                            0.0, 2 * h, epsabs=1e-14)
+    assert val == pytest.approx(-1.0, rel=1e-9)
+
+
+# ---- Eq 28: Tait equation of state ----------------------------------------
+
+def test_tait_reference_state_and_sound_speed():
+    """P(rho0) = 0 and dP/drho at rho0 = cs0^2 (c_s = sqrt(dP/drho), Sect. 2.4)."""
+    p = cases.default_params(0.02, 0.4, (0, 0, 0), (1, 1, 1))
+    assert oracle.tait(p, p["rho0"]) == 0.0
+    e = 1e-4
+    d = (oracle.tait(p, p["rho0"] + e) - oracle.tait(p, p["rho0"] - e)) / (2 * e)
+    assert d == pytest.approx(p["cs0"] ** 2, rel=1e-8)
+
+
+def test_tait_isothermal_special_case():
+    """gamma = 1 reduces Eq 28 to the linear law P = cs0^2 (rho - rho0)."""
+    p = cases.default_params(0.02, 0.4, (0, 0, 0), (1, 1, 1), gamma=1.0)
+    for rho in (990.0, 1000.5, 1012.25):
+        assert oracle.tait(p, rho) == pytest.approx(p["cs0"] ** 2 * (rho - 1000.0), rel=1e-12)
+
+
+def test_tait_exact_rational_value():
+    """rho/rho0 = 101/100, gamma = 7: compare with exact rational arithmetic."""
+    from fractions import Fraction
+    p = cases.default_params(0.02, 0.4, (0, 0, 0), (1, 1, 1), cs0=20.0)
+    B = Fraction(400) * 1000 / 7
+    exact = B * (Fraction(101, 100) ** 7 - 1)
+    assert oracle.tait(p, 1010.0) == pytest.approx(float(exact), rel=1e-13)
+
+
+# ---- Sect. 5.1: neighbour list ---------------------------------------------
+
+@pytest.mark.parametrize("cell_mode", [0, 1])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_cell_list_pairs_equal_brute_force(cell_mode, seed):
+    """The cell list finds exactly the O(N^2) pair set."""
+    c = random_cloud(N=500, L=0.15, seed=seed, cell_mode=cell_mode)
+    tb, cb, hb, pb = oracle.pairs(c.params, c.pos, use_cells=False, want_list=True)
+    tc, cc, hc, pc = oracle.pairs(c.params, c.pos, use_cells=True, want_list=True)
+    assert tb == tc and tb > 1000
+    assert np.array_equal(pb, pc)
+    assert np.array_equal(cb, cc) and np.array_equal(hb, hc)
+
+
+def test_pairs_are_symmetric_and_strict():
+    """(a,b) is a pair iff (b,a) is; lattice points exactly at 2h are excluded."""
+    # spacing chosen so that neighbours at exactly 2h = 2 dp exist
+    c = lattice_case(n=5, dp=0.02)
+    c.params["h"] = 0.02  # 2h = 2 dp: the second lattice neighbours sit on the cut-off
+    t, cnt, _, pl = oracle.pairs(c.params, c.pos, use_cells=True, want_list=True)
+    s = set(map(tuple, pl.tolist()))
+    assert all((b, a) in s for a, b in s)
+    ic = centre_index(5)
+    # inside 2h = 2dp strictly: offsets with |d|^2 < 4 -> 6 (|d|=1) + 12 (sqrt2) + 8 (sqrt3)
+    assert cnt[ic] == 26
+
+
+def test_sort_is_stable_by_cell_then_type():
+    """Neighbour-list order: by cell, fluid before boundary, ties in prior order."""
+    p = cases.default_params(0.02, 0.4, (0, 0, 0), (1, 1, 1))
+    cs = 2 * p["h"]
+    pos = np.array([[0.5 * cs, 0.5 * cs, 0.5 * cs],   # cell A
+                    [1.5 * cs, 0.5 * cs, 0.5 * cs],   # cell A+1 (x)
+                    [0.6 * cs, 0.4 * cs, 0.5 * cs],   # cell A, boundary
+                    [0.7 * cs, 0.7 * cs, 0.2 * cs],   # cell A
+                    [0.1 * cs, 1.5 * cs, 0.5 * cs],   # cell A + nx (y)
+                    [5.0, 5.0, 5.0]])                 # outside
+    ptype = np.array([0, 0, 1, 0, 0, 0], np.uint8)
+    order, inside = oracle.sort_order(p, pos, ptype)
+    assert inside == 5
+    assert order.tolist() == [0, 3, 2, 1, 4, 5]
+    order2, _ = oracle.sort_order(p, pos, ptype, prev_order=np.array([3, 0, 1, 2, 4, 5]))
+    assert order2.tolist() == [3, 0, 2, 1, 4, 5]
+
+
+# ---- PI: Eq 15-18, 21-22, 36 -----------------------------------------------
+
+def test_cell_list_interaction_equals_brute_force():
+    c = random_cloud(N=300, L=0.1, seed=5)
+    c.ptype[::7] = 1
+    a1, d1, m1, n1 = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype, use_cells=False)
+    a2, d2, m2, n2 = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype, use_cells=True)
+    assert n1 == n2
+    np.testing.assert_allclose(a2, a1, rtol=1e-12, atol=1e-12 * np.abs(a1).max())
+    np.testing.assert_allclose(d2, d1, rtol=1e-12, atol=1e-12 * np.abs(d1).max())
+    np.testing.assert_allclose(m2, m1, rtol=1e-12)
+
+
+def test_momentum_is_conserved():
+    """Eq 16/22 use a symmetric operator: sum_a m a_a = 0 for an all-fluid set."""
+    c = random_cloud(N=400, L=0.12, seed=7)
+    acc, _, _, npairs = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)
+    assert npairs > 10000
+    total = acc.sum(axis=0)
+    scale = np.abs(acc).sum()
+    assert np.all(np.abs(total) < 1e-12 * scale)
+
+
+@pytest.mark.parametrize("alpha", [0.01, 0.1])
+def test_artificial_viscosity_dissipates(alpha):
+    """With P = 0 only Pi_ab acts: kinetic energy must decrease (dKE/dt < 0),
+    momentum stays conserved, and the force is linear in alpha."""
+    c = random_cloud(N=400, L=0.12, seed=11, alpha=alpha)
+    c.rho[:] = c.params["rho0"]
+    acc, _, _, _ = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)
+    m = c.params["rho0"] * c.params["dp"] ** 3
+    dke = m * np.sum(c.vel * acc)
+    assert dke < 0
+    assert np.all(np.abs(acc.sum(0)) < 1e-12 * np.abs(acc).sum())
+    p2 = dict(c.params, alpha=2 * alpha)
+    acc2, _, _, _ = oracle.interact(p2, c.pos, c.vel, c.rho, c.ptype)
+    np.testing.assert_allclose(acc2, 2 * acc, rtol=1e-12, atol=1e-14)
+    p0 = dict(c.params, alpha=0.0)
+    acc0, _, _, _ = oracle.interact(p0, c.pos, c.vel, c.rho, c.ptype)
+    assert np.abs(acc0).max() < 1e-9 * np.abs(acc).max()
+
+
+def test_viscosity_vanishes_for_receding_pairs():
+    """Eq 21: Pi_ab = 0 when v_ab . r_ab >= 0 (two receding particles, P = 0)."""
+    c = random_cloud(N=2, L=0.01, seed=1)
+    c.pos[:] = [[0.05, 0.05, 0.05], [0.07, 0.05, 0.05]]
+    c.vel[:] = [[-0.3, 0.0, 0.0], [0.3, 0.0, 0.0]]
+    c.rho[:] = c.params["rho0"]
+    acc, _, mu, n = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)
+    assert n == 2 and np.all(acc == 0.0)
+    # Eq 35 still sees the pair: mu -> h |v_ab| / r when eta << r (eta^2/r^2 = 0.3 %)
+    h = c.params["h"]
+    assert mu[0] == pytest.approx(h * 0.6 / 0.02, rel=4e-3)
+
+
+def test_continuity_uniform_dilation():
+    """Eq 15 on a lattice with v = eps r: drho/dt -> -rho div v = -3 eps rho."""
+    n = 11
+    c = lattice_case(n=n, ddt_mode=0)
+    ic = centre_index(n)
+    eps = 0.5
+    c.vel[:] = eps * (c.pos - c.pos[ic])
+    _, drho, _, _ = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)
+    assert drho[ic] == pytest.approx(-3 * eps * c.params["rho0"], rel=1e-2)
+
+
+def test_pressure_gradient_linear_field():
+    """Eq 16 on a lattice with P = P0 + k z: a -> -(1/rho) dP/dz (g = 0)."""
+    n = 11
+    c = lattice_case(n=n)
+    p = c.params
+    ic = centre_index(n)
+    B = p["cs0"] ** 2 * p["rho0"] / p["gamma"]
+    k = 2000.0
+    P = 500.0 + k * (c.pos[:, 2] - c.pos[ic, 2])
+    c.rho[:] = p["rho0"] * (1 + P / B) ** (1 / p["gamma"])
+    acc, _, _, _ = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
+    expect = -k / c.rho[ic]
+    assert acc[ic, 2] == pytest.approx(expect, rel=2e-2)
+    assert abs(acc[ic, 0]) < 1e-6 * abs(expect) and abs(acc[ic, 1]) < 1e-6 * abs(expect)
+
+
+def test_density_diffusion_is_a_laplacian():
+    """Eq 17-18 (diffusive reading): D_a -> delta h c laplacian(rho) for a
+    quadratic density field (Brookshaw form of the SPH Laplacian)."""
+    n = 11
+    c = lattice_case(n=n)
+    p = c.params
+    ic = centre_index(n)
+    kappa = 0.5
+    x = c.pos[:, 0] - c.pos[ic, 0]
+    c.rho[:] = p["rho0"] * (1 + kappa * x * x)
+    _, drho, _, _ = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
+    lap = 2 * kappa * p["rho0"]
+    assert drho[ic] == pytest.approx(p["delta"] * p["h"] * p["cs0"] * lap, rel=2e-2)
+
+
+def test_density_diffusion_bump_sign_and_conservation():
+    """Uniform rho gives D = 0; a denser particle loses density to its
+    neighbours; sum_a V_a D_a = 0 (antisymmetric exchange)."""
+    n = 9
+    c = lattice_case(n=n)
+    p = c.params
+    _, drho, _, _ = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
+    assert np.all(drho == 0.0)
+    ic = centre_index(n)
+    c.rho[ic] *= 1.001
+    _, drho, _, _ = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
+    assert drho[ic] < 0
+    d = np.linalg.norm(c.pos - c.pos[ic], axis=1)
+    nb = (d > 0) & (d < 2 * p["h"])
+    assert np.all(drho[nb] > 0) and np.all(drho[~nb & (d > 0)] == 0)
+    cl = random_cloud(N=300, L=0.1, seed=9)
+    cl.vel[:] = 0
+    _, drho, _, _ = oracle.interact(cl.params, cl.pos, cl.vel, cl.rho, cl.ptype)
+    vol = (cl.params["rho0"] * cl.params["dp"] ** 3) / cl.rho
+    assert abs(np.sum(vol * drho)) < 1e-12 * np.sum(np.abs(vol * drho))
+
+
+def test_boundary_particles_dbc():
+    """Eq 36: boundary particles get no acceleration, and their density only
+    changes through fluid neighbours; fluid-boundary pairs push the fluid."""
+    n = 9
+    c = lattice_case(n=n)
+    p = c.params
+    c.ptype[:] = 1
+    c.vel[:] = 0.1
+    acc, drho, _, _ = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
+    assert np.all(acc == 0) and np.all(drho == 0)
+    # one fluid particle moving down towards a boundary lattice
+    c.ptype[:] = 1
+    c.vel[:] = 0
+    ic = centre_index(n)
+    c.ptype[ic] = 0
+    c.vel[ic] = (0.0, 0.0, -1.0)
+    c.rho[:] = 1001.0
+    acc, drho, _, _ = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
+    below = (np.linalg.norm(c.pos - c.pos[ic], axis=1) < 2 * p["h"]) & (c.pos[:, 2] < c.pos[ic, 2])
+    above = (np.linalg.norm(c.pos - c.pos[ic], axis=1) < 2 * p["h"]) & (c.pos[:, 2] > c.pos[ic, 2])
+    assert np.all(drho[below] > 0) and np.all(drho[above] < 0)
+    others = np.ones(len(c.pos), bool)
+    others[ic] = False
+    assert np.all(acc[others] == 0)
+
+
+# ---- Eq 33-35: time step and Symplectic integrator ------------------------
+
+def test_time_step_isolated_particle_closed_form():
+    """Eq 35 for an isolated particle: C_CFL min(sqrt(h/g), h/cs0)."""
+    c = cases.free_particle()
+    p = c.params
+    acc, drho, mu, n = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
+    assert n == 0 and mu[0] == 0
+    dt = oracle.time_step(p, acc, mu, c.ptype)
+    assert dt == pytest.approx(p["cfl"] * min(math.sqrt(p["h"] / 9.81), p["h"] / p["cs0"]),
+                               rel=1e-14)
+
+
+def test_free_fall_is_exact():
+    """Eq 33 integrates constant acceleration exactly: r = r0 + v0 t + g t^2/2."""
+    c = cases.free_particle()
+    s = oracle.OracleState(c)
+    ts = []
+    for _ in range(50):
+        s.step(1)
+        ts.append(s.t.value)
+    t = s.t.value
+    g = np.array(c.params["gravity"])
+    np.testing.assert_allclose(s.pos[0], c.pos[0] + c.vel[0] * t + 0.5 * g * t * t,
+                               rtol=0, atol=1e-13)
+    np.testing.assert_allclose(s.vel[0], c.vel[0] + g * t, rtol=0, atol=1e-13)
+    assert s.rho[0] == c.rho[0]
+    assert np.allclose(np.diff(ts), s.last_dt.value)
+
+
+def test_imposed_motion_follows_law():
+    """Eq 37: a moving boundary particle is placed by its motion law."""
+    c = cases.sloshing_tank(3000, 0.3, 0.03, 1.2)
+    s = oracle.OracleState(c)
+    s.step(5)
+    m = c.motions[0]
+    t = s.t.value
+    disp = m["amp"] * math.sin(m["omega"] * t)
+    b = np.where(c.ptype == 1)[0]
+    np.testing.assert_allclose(s.pos[b, 0] - c.pos[b, 0], disp, atol=1e-12)
+    np.testing.assert_allclose(s.vel[b, 0], m["amp"] * m["omega"] * math.cos(m["omega"] * t),
+                               atol=1e-12)
+    np.testing.assert_allclose(s.pos[b, 1:], c.pos[b, 1:], atol=0)
+
+
+def test_dam_break_steps_conserve_mass_and_stay_finite():
+    """Eq 14: mass exactly constant; state finite; the column starts to move."""
+    c = cases.dam_break(0.02)
+    s = oracle.OracleState(c)
+    m0 = s.diag()["mass"]
+    s.step(10)
+    d = s.diag()
+    assert d["mass"] == m0
+    assert d["n_out"] == 0
+    assert np.all(np.isfinite(s.pos)) and np.all(np.isfinite(s.rho))
+    assert d["ke"] > 0
+    assert s.last_dt.value > 0
+
+
+@pytest.mark.slow
+def test_still_tank_is_hydrostatic():
+    """Eq 28 + DBC: after 1 s at rest, pressure in horizontal slabs is within
+    2 % of rho0 g (H - z) (slabs at least 2h from the bottom and surface)."""
+    c = cases.still_tank(0.02, size=(0.16, 0.16), depth=0.3, height=0.34)
+    s = oracle.OracleState(c)
+    while s.t.value < 1.0:
+        s.step(50)
+    f = c.ptype == 0
+    P = s.pressure()[f]
+    z = s.pos[f, 2]
+    H = c.meta["surface"]
+    h = c.params["h"]
+    edges = np.arange(2 * h, H - 2 * h, 0.04)
+    for z0 in edges:
+        sel = (z >= z0) & (z < z0 + 0.04)
+        if sel.sum() < 10:
+            continue
+        expect = 1000.0 * 9.81 * (H - z[sel].mean())
+        assert P[sel].mean() == pytest.approx(expect, rel=0.02), z0
