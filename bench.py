@@ -1,0 +1,319 @@
+"""Benchmark of the WCSPH hot path on GB300 (one JSON line on rank 0).
+
+Default workload: the 3-D dam break at dp = 0.004 m (1,000,000 fluid +
+479,826 boundary particles, cells of 2h), stepped with the Symplectic scheme.
+A "step" is one full Symplectic step: NL -> PI -> dt -> predictor -> NL ->
+PI -> corrector.  The metric is particle interactions per second (ordered
+pairs evaluated by the two PI evaluations of each step, the paper's PIPS);
+steps/s is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload dam_break|dam_break_small|wave_flume|batched|served]
+
+Under torchrun each rank runs its own replica of the workload (independent
+cases, no data-path collective): "scaling": "weak".
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Algorithmic FLOPs per evaluated pair (each +, -, *, comparison, sqrt and
+# reciprocal counts 1; a fused multiply-add counts 2), counted on the pair
+# formula of Eq 11, 15, 17-18, 21-22 and 35 as written out in the design doc:
+F_PAIR_FF = 48   # a in F, b in F: momentum + viscosity + continuity + DDT + Eq 35 max
+F_PAIR_FB = 45   # a in F, b in B: as above without density diffusion
+F_PAIR_BF = 25   # a in B, b in F: continuity of Eq 36 only
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def workload(name, rank=0):
+    from paper_2104_00537_gb300 import cases
+    if name == "dam_break":
+        return [cases.dam_break(0.004, seed=rank)], "3-D dam break dp=0.004 (1.48M particles)"
+    if name == "dam_break_small":
+        return [cases.dam_break(0.02, seed=rank)], "3-D dam break dp=0.02 (28k particles)"
+    if name == "wave_flume":
+        return [cases.wave_flume(0.008, seed=rank)], "wave flume 25x1x1.2 m dp=0.008 (32M particles)"
+    if name == "batched":
+        return cases.batch_dam_breaks(256, seed=rank), "256 dam breaks, 5k-200k fluid each"
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        if not sm:
+            return None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world <= 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    import torch
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend)
+    return rank, world, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(case, seconds_budget=20.0):
+    """The FP64 oracle timed on the host cores over a bounded sample of the same
+    workload: one interaction evaluation (neighbour list over all particles)
+    for a contiguous block of target particles."""
+    import oracle
+    n = case.n
+    cores = os.cpu_count()
+    # calibrate on a small block, then size the sample for ~seconds_budget
+    t0 = time.perf_counter()
+    _, _, _, p0 = oracle.interact_range(case.params, case.pos, case.vel, case.rho, case.ptype,
+                                        0, min(n, 20000))
+    t_cal = time.perf_counter() - t0
+    block = min(n, max(20000, int(20000 * seconds_budget / max(t_cal, 1e-3) / 2)))
+    t0 = time.perf_counter()
+    _, _, _, pairs = oracle.interact_range(case.params, case.pos, case.vel, case.rho,
+                                           case.ptype, 0, block)
+    dt = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+            "sample": "FP64 oracle: neighbour list of all %d particles + interaction of "
+                      "particles [0, %d) of the dam break at t=0 (%d pairs, %.1f s)"
+                      % (n, block, pairs, dt)}
+
+
+def run_reference(args, rank, world, dist):
+    """Reference arm: the FP64 oracle on the host cores, same metric and workload;
+    each step is a bounded sample (interaction of a block of target particles)."""
+    import oracle
+    if rank != 0:
+        return
+    cs, desc = workload(args.workload, 0)
+    case = cs[0]
+    n = case.n
+    block = max(1, min(n, args.ref_block))
+
+    def one(k):
+        a0 = (k * block) % max(1, n - block)
+        _, _, _, p = oracle.interact_range(case.params, case.pos, case.vel, case.rho,
+                                           case.ptype, a0, a0 + block)
+        return p
+
+    for k in range(args.warmup):
+        one(k)
+    pairs = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        pairs += one(args.warmup + k)
+    dt = time.perf_counter() - t0
+    v = pairs / dt
+    out = {"metric": "particle_interactions_per_s", "value": v, "unit": "interactions/s",
+           "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": desc, "sample_particles_per_step": block},
+           "cpu_baseline": {"value": v, "unit": "interactions/s", "cores": os.cpu_count(),
+                            "kind": "oracle",
+                            "sample": "each step: neighbour list of all %d particles + "
+                                      "interaction of %d target particles" % (n, block)},
+           "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="dam_break")
+    ap.add_argument("--cell-mode", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-block", type=int, default=20000)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank, world, local, dist = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world, dist)
+        return
+
+    import torch
+    from paper_2104_00537_gb300 import sph
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    cs, desc = workload(args.workload, rank)
+    for c in cs:
+        c.params["cell_mode"] = args.cell_mode
+    with torch.cuda.stream(stream):
+        eng = sph.Engine.batch(cs, stream=stream) if len(cs) > 1 else \
+            sph.Engine.create(cs[0], stream=stream)
+    n_particles = sum(c.n for c in cs)
+
+    # warm-up
+    eng.step(args.warmup)
+    eng.set_options(timing=1)
+    eng.timing(reset=True)
+
+    def totals():
+        s = [eng.stats(i) for i in range(len(cs))]
+        return (sum(x["interactions"] for x in s), sum(x["interactions_fb"] for x in s),
+                sum(x["interactions_bf"] for x in s))
+
+    p0 = totals()
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    eng.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    p1 = totals()
+    tm = eng.timing(reset=True)
+    pairs = p1[0] - p0[0]
+    fb = p1[1] - p0[1]
+    bf = p1[2] - p0[2]
+    ff = pairs - fb - bf
+    ms_max = max_over_ranks(ms, dist)
+    pairs_all = sum_over_ranks(pairs, dist)
+    value = pairs_all / (ms_max / 1000.0)
+    steps_per_s = args.steps / (ms_max / 1000.0) * world
+
+    # roofline of the dominant kernel (the interaction): algorithmic FLOPs per
+    # launch / average launch duration (CUDA events on the engine's stream)
+    flops = F_PAIR_FF * ff + F_PAIR_FB * fb + F_PAIR_BF * bf
+    launches = max(1, tm["pi_launches"])
+    pi_avg_s = tm["pi_ms"] / 1000.0 / launches
+    achieved = flops / launches / pi_avg_s / 1e12
+    peak = fp32_peak_tflops()
+    roofline = {"bound": "alu", "kernel": "k_interact", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
+                "pi_ms_per_launch": 1000 * pi_avg_s,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal max clock)"}
+
+    out = {"metric": "particle_interactions_per_s", "value": value, "unit": "interactions/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": desc, "particles": n_particles, "cases": len(cs),
+                      "cell_mode": "2h" if args.cell_mode == 0 else "h",
+                      "l2": "state (%.0f MB) larger than L2 (129 MB), no flush" %
+                            (n_particles * 177 / 1e6),
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "steps_per_s": steps_per_s, "interactions_per_step": pairs / args.steps,
+           "gpu_launches": tm["kernel_launches"], "roofline": roofline, "clocks": clk}
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the public API from pinned host memory: create
+        # (H2D copy of the case), K steps, state read-back (D2H) per run
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2 = sph.Engine.create(cs[0], stream=stream, pinned=True) if len(cs) == 1 else \
+            sph.Engine.batch(cs, stream=stream)
+        e2.step(args.steps)
+        st = [e2.get_state(i) for i in range(len(cs))]
+        e2pairs = sum(e2.stats(i)["interactions"] for i in range(len(cs)))
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        h2d = sum(c.n * (24 + 12 + 4 + 1 + 4) for c in cs)
+        d2h = sum(c.n * (24 + 12 + 4 + 4) for c in cs)
+        out["e2e"] = {"value": e2pairs / t_e2e, "unit": "interactions/s",
+                      "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                      "note": "create from pinned host arrays + %d steps + get_state, "
+                              "wall clock" % args.steps}
+        e2.destroy()
+        del st
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(cs[0])
+    eng.destroy()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

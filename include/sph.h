@@ -1,0 +1,217 @@
+/*
+ * sph.h -- C ABI of libsph.so, the GB300 (sm_103a) hot path of the weakly
+ * compressible SPH method of the DualSPHysics paper (arXiv 2104.00537).
+ *
+ * One "engine" holds one or more independent SPH cases resident in device
+ * memory and advances them together, one Symplectic step at a time (Sect. 5.1:
+ * neighbour list NL -> particle interaction PI -> system update SU, Fig. 7).
+ * A single case is an engine with one case (sph_create); a batch is an
+ * engine created with many (sph_batch_create); a serving pool is an engine
+ * whose cases are admitted and released while it runs (sph_pool_*).
+ *
+ * Conventions for every call:
+ *  - Return SPH_OK (0) on success or a negative SPH_ERR_* code; the message
+ *    of the last error of the calling thread is in sph_last_error().
+ *  - Host pointers are caller-owned and only read (inputs) or written
+ *    (outputs) during the call; the library keeps no reference to them.
+ *  - Device memory is allocated at creation / admission only, through the
+ *    caller's allocator callback when one is given, else cudaMalloc, and is
+ *    released by the matching destroy call.
+ *  - All device work runs on the CUDA stream given at creation; calls that
+ *    return host data synchronise that stream.  One engine must not be used
+ *    from two threads at once; different engines are independent.
+ *  - Arrays of particles are in the caller's (generator) order on input and
+ *    on output; the device order (sorted by cell) is internal.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPH_OK 0
+#define SPH_ERR_ARG (-1)      /* invalid argument or parameter            */
+#define SPH_ERR_OOM (-2)      /* allocation failed / capacity exhausted   */
+#define SPH_ERR_CUDA (-3)     /* a CUDA runtime call failed               */
+#define SPH_ERR_UNSTABLE (-4) /* NaN/Inf in the state or dt < dt_min      */
+#define SPH_ERR_DOMAIN (-5)   /* more particles left the domain than allowed */
+#define SPH_ERR_TIMEOUT (-6)  /* a bounded device wait gave up            */
+#define SPH_ERR_BUSY (-7)     /* pool: no free slot or not enough memory  */
+#define SPH_ERR_STATE (-8)    /* call not valid in the engine's state     */
+
+typedef struct { double x, y, z; } sph_d3;
+
+/* Constants of one case.  Paper references: h, the Wendland C2 kernel with
+ * support 2h (Eq 11); rho0, cs0, gamma of the Tait equation of state (Eq 28);
+ * alpha of the artificial viscosity (Eq 21); delta of the density diffusion
+ * term (Eq 17-18); cfl = C_CFL of Eq 35; eta2 = eta^2 of Eq 21 and 35. */
+typedef struct {
+  double dp;        /* initial particle spacing; particle mass m = rho0 dp^3 */
+  double h, rho0, cs0, gamma, alpha, delta, cfl, eta2;
+  sph_d3 gravity;   /* body force f of Eq 13 (m/s^2)                        */
+  sph_d3 domain_min, domain_max; /* particles outside are frozen ("out")    */
+  double dt_fixed;  /* > 0: fixed time step instead of Eq 35                */
+  double dt_min;    /* a step with dt < dt_min fails with SPH_ERR_UNSTABLE  */
+  int32_t cell_mode;          /* 0: cells of size 2h (Sect. 5.1); 1: size h (Sect. 5.3) */
+  int32_t ddt_mode;           /* 0: no density diffusion; 1: Eq 17 with Eq 18 */
+  int32_t clamp_boundary_rho; /* 1: boundary density kept >= rho0           */
+  int32_t max_out;            /* out-of-domain quota; < 0: unlimited        */
+} sph_case_params;
+
+/* Imposed translation of a group of boundary particles (Eq 37):
+ * displacement D(t) = amplitude (sin(omega t + phase) - sin(phase)) along
+ * axis, velocity D'(t) axis. */
+typedef struct {
+  sph_d3 axis;
+  double amplitude, omega, phase;
+} sph_motion;
+
+/* Initial particles of one case (the sets P = F u B of Sect. 2.1). */
+typedef struct {
+  int64_t n;                    /* number of particles                         */
+  const double *pos;            /* [3n] x,y,z (m)                              */
+  const float *vel;             /* [3n] or NULL for zero                       */
+  const float *rho;             /* [n] density (kg/m^3)                        */
+  const uint8_t *type;          /* [n] 0 fluid (F), 1 boundary (B)             */
+  const int32_t *motion_group;  /* [n] index into motions, -1 fixed; or NULL   */
+  const sph_motion *motions;    /* [n_motions] (at most 8 per case)            */
+  int32_t n_motions;
+} sph_particles;
+
+/* Counters and diagnostics of one case (FP64 reductions on the device). */
+typedef struct {
+  double t;              /* simulated time                                  */
+  double last_dt;        /* last Eq 35 time step                            */
+  int64_t step;          /* completed Symplectic steps                      */
+  int64_t interactions;  /* evaluated ordered pairs (a,b), both PI evaluations */
+  int64_t interactions_fb; /* ... of which a in F, b in B                    */
+  int64_t interactions_bf; /* ... of which a in B (b in F, Eq 36)             */
+  double mass;           /* sum of particle masses (Eq 14)                  */
+  double kinetic_energy; /* sum over F of m |v|^2 / 2                       */
+  double momentum[3];    /* sum over F of m v                               */
+  double front;          /* max x over in-domain fluid particles            */
+  int64_t n_out;         /* particles frozen outside the domain             */
+  int32_t flags;         /* bit 0 NaN/Inf, bit 1 dt < dt_min, bit 2 quota   */
+  int32_t n_fluid;
+  int64_t n;
+} sph_stats;
+
+typedef struct sph_engine_t *sph_engine;
+
+/* Device allocator callback (e.g. the PyTorch caching allocator); must
+ * return memory usable on `stream`, aligned to at least 256 bytes. */
+typedef void *(*sph_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*sph_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+/* Engine-wide launch options (the autotuner's knobs). */
+typedef struct {
+  int32_t pi_block;   /* threads per block of the interaction kernel (0: default) */
+  int32_t pi_variant; /* interaction kernel variant (0: default)               */
+  int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
+  int32_t timing;     /* 1: time every PI launch with CUDA events              */
+} sph_options;
+
+/* Last error message of the calling thread ("" if none). */
+const char *sph_last_error(void);
+
+/* ---- single case -------------------------------------------------------
+ * sph_create: copy one case to the device (Sect. 5.1: data are copied once
+ * and stay resident) and build its cell grid.  stream: cudaStream_t or NULL
+ * for the default stream.  alloc/free: optional allocator, ctx passed back. */
+int sph_create(const sph_case_params *params, const sph_particles *parts,
+               void *stream, sph_alloc_fn alloc, sph_free_fn free_fn,
+               void *alloc_ctx, sph_engine *out);
+
+/* sph_step: advance every case of the engine by nsteps Symplectic steps
+ * (Eq 33-34), each: NL -> PI (state n) -> dt (Eq 35) -> predictor -> NL ->
+ * PI (state n+1/2) -> corrector.  Work is queued on the engine's stream;
+ * the call returns after synchronising and checking the failure flags. */
+int sph_step(sph_engine e, int64_t nsteps);
+
+/* sph_get_state: copy case `icase` (0 for a single case) to host arrays in
+ * the caller's original particle order.  Any output pointer may be NULL.
+ * pos [3n] double, vel [3n] float, rho [n] float, press [n] float (Eq 28). */
+int sph_get_state(sph_engine e, int32_t icase, double *pos, float *vel,
+                  float *rho, float *press, double *t, int64_t *step,
+                  double *last_dt);
+
+/* sph_get_stats: counters and FP64 diagnostics of case icase. */
+int sph_get_stats(sph_engine e, int32_t icase, sph_stats *out);
+
+/* sph_set_options / sph_get_timing: launch options; with timing on, the
+ * accumulated device time of the interaction kernel (ms, CUDA events on the
+ * engine's stream), its number of launches, the device time of whole
+ * sph_step calls, and the number of kernels launched by sph_step since the
+ * last reset (reset = 1 clears all after reading). */
+int sph_set_options(sph_engine e, const sph_options *opt);
+int sph_get_timing(sph_engine e, double *pi_ms, int64_t *pi_launches,
+                   double *step_ms, int64_t *kernel_launches, int32_t reset);
+
+/* ---- checkpoint ----------------------------------------------------------
+ * sph_get_raw: bit-exact snapshot of case icase (device storage format:
+ * integer cell + float offset, float velocity/density, time, step, dt).
+ * With buf == NULL only *bytes is set.  sph_create_from_raw rebuilds a
+ * single-case engine that continues bit-identically. */
+int sph_get_raw(sph_engine e, int32_t icase, void *buf, size_t *bytes);
+int sph_create_from_raw(const sph_case_params *params, const sph_particles *parts,
+                        const void *buf, size_t bytes, void *stream,
+                        sph_alloc_fn alloc, sph_free_fn free_fn, void *alloc_ctx,
+                        sph_engine *out);
+
+/* ---- parity / diagnostic entry points -----------------------------------
+ * sph_eval_forces: rebuild the neighbour list and evaluate the particle
+ * interaction once on the current state of case icase, without advancing
+ * it.  Outputs in original order: acc [3n] (dv/dt of Eq 22 + f, zero for
+ * B), drho [n] (Eq 15 with D_a, Eq 36 for B), mumax [n] (inner max of Eq 35);
+ * *dt = the Eq 35 step from this evaluation.  Any output may be NULL. */
+int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho,
+                    float *mumax, double *dt, int64_t *pairs);
+
+/* sph_get_order: rebuild the neighbour list and return, for case icase, the
+ * original ids in device (cell-sorted) order and their cell ids (-1 out). */
+int sph_get_order(sph_engine e, int32_t icase, int64_t *ids, int64_t *cells,
+                  int64_t *n_inside);
+
+/* sph_pair_stats: per particle (original order) the number of neighbours b
+ * with 0 < |r_ab|^2 < (2h)^2 and the sum mod 2^64 of SplitMix64-finalised
+ * neighbour ids (an order-independent fingerprint of the pair set). */
+int sph_pair_stats(sph_engine e, int32_t icase, int64_t *count, uint64_t *hash);
+
+/* ---- batches -------------------------------------------------------------
+ * sph_batch_create: ncases independent cases in one engine: their particles
+ * are concatenated and their cell grids laid out at segment offsets of one
+ * table, so each stage is one launch over all cases; each case keeps its
+ * own dt and t.  Step with sph_step, read with the icase argument. */
+int sph_batch_create(const sph_case_params *params, const sph_particles *parts,
+                     int32_t ncases, void *stream, sph_alloc_fn alloc,
+                     sph_free_fn free_fn, void *alloc_ctx, sph_engine *out);
+
+/* ---- serving pool ----------------------------------------------------------
+ * sph_pool_create: an engine with room for max_particles particles, max_cells
+ * grid cells and max_cases cases, allocated once.  sph_pool_admit copies a
+ * new case in (SPH_ERR_BUSY if it does not fit) and returns its slot; the
+ * case runs until its simulated time reaches t_end.  sph_pool_step advances
+ * all admitted cases and reports the slots that reached t_end;
+ * sph_pool_release frees a slot (its particles leave at the next step). */
+int sph_pool_create(int64_t max_particles, int64_t max_cells, int32_t max_cases,
+                    void *stream, sph_alloc_fn alloc, sph_free_fn free_fn,
+                    void *alloc_ctx, sph_engine *out);
+int sph_pool_admit(sph_engine e, const sph_case_params *params,
+                   const sph_particles *parts, double t_end, int32_t *slot);
+int sph_pool_step(sph_engine e, int64_t nsteps, int32_t *finished,
+                  int32_t *n_finished);
+int sph_pool_release(sph_engine e, int32_t slot);
+int sph_pool_usage(sph_engine e, int64_t *particles_used, int64_t *cells_used,
+                   int32_t *cases_used);
+
+/* sph_destroy: release all device memory of the engine. */
+void sph_destroy(sph_engine e);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

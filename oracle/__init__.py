@@ -66,6 +66,9 @@ def lib():
         L.orc_interact.restype = C.c_int64
         L.orc_interact.argtypes = [P, C.c_int64, _D, _D, _D, _U8, C.c_void_p, C.c_int,
                                    _D, _D, _D]
+        L.orc_interact_range.restype = C.c_int64
+        L.orc_interact_range.argtypes = [P, C.c_int64, _D, _D, _D, _U8, C.c_void_p, C.c_int,
+                                         C.c_int64, C.c_int64, _D, _D, _D]
         L.orc_dt.restype = C.c_double
         L.orc_dt.argtypes = [P, C.c_int64, _D, _D, _U8, C.c_void_p]
         L.orc_step.restype = C.c_int64
@@ -180,6 +183,23 @@ def interact(params: dict, pos, vel, rho, ptype, out=None, use_cells=True):
     out_ = None if out is None else np.ascontiguousarray(out, np.uint8)
     npairs = lib().orc_interact(C.byref(make_params(params)), n, pos, vel, rho, ptype,
                                 _ptr(out_), int(use_cells), acc, drho, mu)
+    if npairs < 0:
+        raise ValueError("oracle interaction failed")
+    return acc, drho, mu, int(npairs)
+
+
+def interact_range(params: dict, pos, vel, rho, ptype, a0, a1):
+    """PI for the particles a in [a0, a1) only: returns (acc, drho, mumax, npairs)."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    vel = np.ascontiguousarray(vel, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    ptype = np.ascontiguousarray(ptype, np.uint8)
+    n = len(pos)
+    acc = np.zeros((n, 3))
+    drho = np.zeros(n)
+    mu = np.zeros(n)
+    npairs = lib().orc_interact_range(C.byref(make_params(params)), n, pos, vel, rho, ptype,
+                                      None, 1, int(a0), int(a1), acc, drho, mu)
     if npairs < 0:
         raise ValueError("oracle interaction failed")
     return acc, drho, mu, int(npairs)

@@ -326,6 +326,17 @@ int64_t orc_interact(const orc_params *p, int64_t n, const double *pos,
                      const double *vel, const double *rho, const uint8_t *type,
                      const uint8_t *out, int use_cells, double *acc,
                      double *drho, double *mumax) {
+  return orc_interact_range(p, n, pos, vel, rho, type, out, use_cells, 0, n,
+                            acc, drho, mumax);
+}
+
+int64_t orc_interact_range(const orc_params *p, int64_t n, const double *pos,
+                           const double *vel, const double *rho,
+                           const uint8_t *type, const uint8_t *out,
+                           int use_cells, int64_t a0, int64_t a1, double *acc,
+                           double *drho, double *mumax) {
+  if (a0 < 0) a0 = 0;
+  if (a1 > n) a1 = n;
   cell_list cl;
   if (use_cells && cl_build(p, n, pos, type, out, &cl)) {
     cl_free(&cl);
@@ -336,7 +347,7 @@ int64_t orc_interact(const orc_params *p, int64_t n, const double *pos,
   int64_t total = 0;
 
 #pragma omp parallel for schedule(dynamic, 256) reduction(+ : total)
-  for (int64_t a = 0; a < n; a++) {
+  for (int64_t a = a0; a < a1; a++) {
     double ac[3] = {0.0, 0.0, 0.0}, dr = 0.0, mu = 0.0;
     int a_fluid = type[a] == 0;
     int active = !(out && out[a]) && (!use_cells || cl.cellof[a] >= 0);
@@ -540,10 +551,11 @@ int orc_diag(const orc_params *p, int64_t n, const double *pos,
              const double *vel, const uint8_t *type, const uint8_t *out,
              double res[7]) {
   double m = p->rho0 * p->dp * p->dp * p->dp;
-  double mass = 0.0, ke = 0.0, px = 0.0, py = 0.0, pz = 0.0, front = -INFINITY;
+  double ke = 0.0, px = 0.0, py = 0.0, pz = 0.0, front = -INFINITY;
   double nout = 0.0;
+  /* Eq 14: every particle keeps its mass m, so the total is exactly n m */
+  double mass = (double)n * m;
   for (int64_t a = 0; a < n; a++) {
-    mass += m;
     if (out && out[a]) {
       nout += 1.0;
       continue;

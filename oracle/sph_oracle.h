@@ -76,6 +76,15 @@ int64_t orc_interact(const orc_params *p, int64_t n, const double *pos,
                      const uint8_t *out, int use_cells, double *acc,
                      double *drho, double *mumax);
 
+/* The same evaluation restricted to the particles a in [a0, a1) (their
+ * neighbours range over all particles); outputs of other particles are not
+ * written.  Used to time bounded samples of a large case. */
+int64_t orc_interact_range(const orc_params *p, int64_t n, const double *pos,
+                           const double *vel, const double *rho,
+                           const uint8_t *type, const uint8_t *out,
+                           int use_cells, int64_t a0, int64_t a1, double *acc,
+                           double *drho, double *mumax);
+
 /* Variable time step, Eq 35. */
 double orc_dt(const orc_params *p, int64_t n, const double *acc,
               const double *mumax, const uint8_t *type, const uint8_t *out);

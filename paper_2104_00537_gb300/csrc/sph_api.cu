@@ -1,0 +1,994 @@
+// sph_api.cu -- host engine behind the C ABI of include/sph.h.
+//
+// An engine owns the device arrays of one or more cases (capacity fixed at
+// creation), the per-case constant/dynamic tables and the work stream.  One
+// Symplectic step (Eq 33-34) is enqueued as
+//   NL(state n): sort keys -> reorder + Tait (Eq 28) -> cell table
+//   PI(state n) -> dt (Eq 35) + motion (Eq 37) -> predictor
+//   NL(state n+1/2) -> PI(state n+1/2) -> corrector -> t += dt
+// with three state buffers: X holds the current state (and the half-step
+// state in cell order during PI 2), Y the cell-sorted state n, Z the
+// half-step state in Y's order.  The corrector writes state n+1 into X in
+// place, so every step has the same buffer roles and can be replayed from
+// one captured CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/sph.h"
+#include "sph_internal.cuh"
+#include "sph_kernels.cuh"
+
+using namespace sph;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                              \
+  do {                                                                              \
+    cudaError_t err_ = (expr);                                                      \
+    if (err_ != cudaSuccess)                                                        \
+      return fail(SPH_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(err_)); \
+  } while (0)
+
+struct Grid {
+  double origin[3], cs;
+  int nc[3], margin;
+  int64_t ncells;
+};
+
+int make_grid(const sph_case_params &p, Grid &g) {
+  if (!(p.h > 0) || !(p.dp > 0) || !(p.rho0 > 0) || !(p.cs0 > 0) || !(p.gamma > 0))
+    return fail(SPH_ERR_ARG, "h, dp, rho0, cs0 and gamma must be positive");
+  if (p.cell_mode != 0 && p.cell_mode != 1) return fail(SPH_ERR_ARG, "cell_mode must be 0 or 1");
+  const double dmin[3] = {p.domain_min.x, p.domain_min.y, p.domain_min.z};
+  const double dmax[3] = {p.domain_max.x, p.domain_max.y, p.domain_max.z};
+  g.cs = p.cell_mode == 1 ? p.h : 2.0 * p.h;
+  g.margin = p.cell_mode == 1 ? 2 : 1;
+  g.ncells = 1;
+  for (int k = 0; k < 3; k++) {
+    if (!(dmax[k] > dmin[k])) return fail(SPH_ERR_ARG, "domain_max must exceed domain_min");
+    g.origin[k] = dmin[k] - g.margin * g.cs;
+    double c = std::ceil((dmax[k] - dmin[k]) / g.cs);
+    if (c > 1e7) return fail(SPH_ERR_ARG, "domain too large for the cell grid");
+    g.nc[k] = 2 * g.margin + (int)c;
+    g.ncells *= g.nc[k];
+  }
+  if (g.ncells > (int64_t(1) << 30)) return fail(SPH_ERR_ARG, "too many cells");
+  return SPH_OK;
+}
+
+void fill_const(const sph_case_params &p, const sph_particles &parts, const Grid &g,
+                uint32_t cellbase, double t_end, int64_t n_fluid, CaseConst &C) {
+  std::memset(&C, 0, sizeof(C));
+  for (int k = 0; k < 3; k++) C.origin[k] = g.origin[k];
+  C.cs = g.cs;
+  C.inv_cs = 1.0 / g.cs;
+  C.h_d = p.h;
+  C.cs0_d = p.cs0;
+  C.cfl = p.cfl;
+  C.dt_fixed = p.dt_fixed;
+  C.dt_min = p.dt_min;
+  C.t_end = t_end;
+  C.nmot = parts.n_motions;
+  for (int m = 0; m < parts.n_motions; m++) {
+    const sph_motion &mo = parts.motions[m];
+    C.mot_amp[m] = mo.amplitude;
+    C.mot_omega[m] = mo.omega;
+    C.mot_phase[m] = mo.phase;
+    C.mot_axis[m][0] = (float)mo.axis.x;
+    C.mot_axis[m][1] = (float)mo.axis.y;
+    C.mot_axis[m][2] = (float)mo.axis.z;
+  }
+  C.nx = g.nc[0];
+  C.ny = g.nc[1];
+  C.nz = g.nc[2];
+  C.margin = g.margin;
+  C.cellbase = cellbase;
+  C.ddt = p.ddt_mode == 1;
+  C.clamp = p.clamp_boundary_rho != 0;
+  C.max_out = p.max_out;
+  C.active = 1;
+  C.n_fluid = (int32_t)n_fluid;
+  C.h = (float)p.h;
+  C.csf = (float)g.cs;
+  C.r2max = (float)(4.0 * p.h * p.h);
+  C.eta2 = (float)p.eta2;
+  const double m = p.rho0 * p.dp * p.dp * p.dp;
+  C.m_d = m;
+  C.m = (float)m;
+  C.rho0 = (float)p.rho0;
+  C.inv_rho0 = (float)(1.0 / p.rho0);
+  C.btait = (float)(p.cs0 * p.cs0 * p.rho0 / p.gamma);
+  C.gamma = (float)p.gamma;
+  const double kPi = 3.14159265358979323846;
+  const double aD = 21.0 / (16.0 * kPi * p.h * p.h * p.h);  // Eq 11, 3-D
+  C.cw = (float)(-5.0 * aD / (p.h * p.h));
+  C.half_inv_h = (float)(0.5 / p.h);
+  C.kvisc = (float)(-2.0 * p.alpha * p.cs0 * p.h);
+  C.kddt = p.ddt_mode == 1 ? (float)(2.0 * p.delta * p.h * p.cs0) : 0.f;
+  C.g[0] = (float)p.gravity.x;
+  C.g[1] = (float)p.gravity.y;
+  C.g[2] = (float)p.gravity.z;
+  C.cs0f = (float)p.cs0;
+}
+
+struct Slot {
+  bool used = false;
+  sph_case_params params{};
+  int64_t n = 0, n_fluid = 0;
+  uint32_t cellbase = 0;
+  int64_t ncells = 0;
+  double t_end = 0;
+};
+
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+struct sph_engine_t {
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  sph_alloc_fn alloc = nullptr;
+  sph_free_fn freefn = nullptr;
+  void *ctx = nullptr;
+  std::vector<std::pair<void *, size_t>> allocs;
+  int64_t cap_p = 0, cap_cells = 0;
+  int cap_cases = 0;
+  int nbits = 0;
+  int margin = 0;  // shared by all cases (0: not set yet)
+  bool pool = false;
+  std::vector<Slot> slots;
+  std::vector<CaseConst> hconst;
+  std::vector<std::pair<int64_t, int64_t>> free_cells;  // [begin, end) ranges
+  int64_t n_phys = 0, n_dead = 0;
+  // device
+  CaseConst *dconst = nullptr;
+  CaseDyn *ddyn = nullptr;
+  State S[3]{};
+  uint32_t *keysA = nullptr, *keysB = nullptr, *keysC = nullptr, *keysD = nullptr;
+  uint32_t *perm1 = nullptr, *perm2 = nullptr;
+  float4 *ace = nullptr;
+  float *mu = nullptr;
+  uint4 *ctab = nullptr;
+  int *nvalid = nullptr;
+  void *sort_tmp = nullptr;
+  double *diag = nullptr;
+  char *io = nullptr;
+  size_t io_bytes = 0;
+  // options, graph, timing
+  sph_options opt{};
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_n = -1, graph_dead = -1;
+  std::vector<cudaEvent_t> evs;
+  double pi_ms = 0, step_ms = 0;
+  int64_t pi_launches = 0, kernel_launches = 0;
+
+  void *dalloc(size_t bytes) {
+    bytes = align256(bytes ? bytes : 256);
+    void *p = nullptr;
+    if (alloc) {
+      p = alloc(bytes, (void *)s, ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) allocs.push_back({p, bytes});
+    return p;
+  }
+  void release_all() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    for (auto &e : evs) cudaEventDestroy(e);
+    evs.clear();
+    if (s) cudaStreamSynchronize(s);
+    for (auto &a : allocs) {
+      if (freefn)
+        freefn(a.first, a.second, (void *)s, ctx);
+      else
+        cudaFree(a.first);
+    }
+    allocs.clear();
+    if (own_stream && s) cudaStreamDestroy(s);
+    s = nullptr;
+  }
+};
+
+namespace {
+
+int bits_for(int64_t cap_cells) {
+  int b = 1;
+  while (((int64_t(1) << b) - 2) < 2 * cap_cells) b++;
+  return b;
+}
+
+int allocate(sph_engine e) {
+  const int64_t N = e->cap_p > 0 ? e->cap_p : 1;
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void *p = e->dalloc(bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  e->dconst = (CaseConst *)A(sizeof(CaseConst) * e->cap_cases);
+  e->ddyn = (CaseDyn *)A(sizeof(CaseDyn) * e->cap_cases);
+  for (int b = 0; b < 3; b++) {
+    e->S[b].posc = (float4 *)A(16 * N);
+    e->S[b].velrho = (float4 *)A(16 * N);
+    e->S[b].id = (uint32_t *)A(4 * N);
+    e->S[b].cid = (uint16_t *)A(2 * N);
+    e->S[b].code = (uint8_t *)A(N);
+  }
+  e->keysA = (uint32_t *)A(4 * N);
+  e->keysB = (uint32_t *)A(4 * N);
+  e->keysC = (uint32_t *)A(4 * N);
+  e->keysD = (uint32_t *)A(4 * N);
+  e->perm1 = (uint32_t *)A(4 * N);
+  e->perm2 = (uint32_t *)A(4 * N);
+  e->ace = (float4 *)A(16 * N);
+  e->mu = (float *)A(4 * N);
+  e->ctab = (uint4 *)A(16 * e->cap_cells);
+  e->nvalid = (int *)A(16);
+  e->sort_tmp = A(radix_sort_temp_bytes(N));
+  e->diag = (double *)A(sizeof(double) * (8 * 1024 + 8));
+  e->io_bytes = align256(48 * (size_t)N) + 4096;
+  e->io = (char *)A(e->io_bytes);
+  if (!ok) return fail(SPH_ERR_OOM, "device allocation failed");
+  CUDA_TRY(cudaMemsetAsync(e->ddyn, 0, sizeof(CaseDyn) * e->cap_cases, e->s));
+  CUDA_TRY(cudaMemsetAsync(e->dconst, 0, sizeof(CaseConst) * e->cap_cases, e->s));
+  return SPH_OK;
+}
+
+int init_engine(sph_engine e, void *stream, sph_alloc_fn alloc, sph_free_fn freefn, void *ctx) {
+  e->alloc = alloc;
+  e->freefn = freefn;
+  e->ctx = ctx;
+  if (stream) {
+    e->s = (cudaStream_t)stream;
+  } else {
+    CUDA_TRY(cudaStreamCreateWithFlags(&e->s, cudaStreamNonBlocking));
+    e->own_stream = true;
+  }
+  return SPH_OK;
+}
+
+int check_particles(const sph_case_params *p, const sph_particles *parts) {
+  if (!p || !parts) return fail(SPH_ERR_ARG, "null params or particles");
+  if (parts->n < 0 || parts->n > (int64_t(1) << 30)) return fail(SPH_ERR_ARG, "bad particle count");
+  if (parts->n > 0 && (!parts->pos || !parts->rho || !parts->type))
+    return fail(SPH_ERR_ARG, "pos, rho and type are required");
+  if (parts->n_motions < 0 || parts->n_motions > kMaxMotions)
+    return fail(SPH_ERR_ARG, "at most 8 motions per case");
+  if (parts->n_motions > 0 && !parts->motions) return fail(SPH_ERR_ARG, "motions pointer is null");
+  if (parts->motion_group)
+    for (int64_t i = 0; i < parts->n; i++)
+      if (parts->motion_group[i] >= parts->n_motions)
+        return fail(SPH_ERR_ARG, "motion_group index out of range");
+  if (!(p->cfl > 0) && !(p->dt_fixed > 0)) return fail(SPH_ERR_ARG, "cfl or dt_fixed must be > 0");
+  return SPH_OK;
+}
+
+// Copy one case's particles into the device arrays at offset dst0 (slot).
+int upload_case(sph_engine e, int slot, const sph_particles *parts, int64_t dst0) {
+  const int64_t n = parts->n;
+  if (n == 0) return SPH_OK;
+  char *p = e->io;
+  double *d_pos = (double *)p;
+  p += align256(24 * n);
+  float *d_vel = (float *)p;
+  p += align256(12 * n);
+  float *d_rho = (float *)p;
+  p += align256(4 * n);
+  uint8_t *d_type = (uint8_t *)p;
+  p += align256(n);
+  int32_t *d_group = (int32_t *)p;
+  CUDA_TRY(cudaMemcpyAsync(d_pos, parts->pos, 24 * n, cudaMemcpyHostToDevice, e->s));
+  if (parts->vel) CUDA_TRY(cudaMemcpyAsync(d_vel, parts->vel, 12 * n, cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaMemcpyAsync(d_rho, parts->rho, 4 * n, cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaMemcpyAsync(d_type, parts->type, n, cudaMemcpyHostToDevice, e->s));
+  if (parts->motion_group)
+    CUDA_TRY(cudaMemcpyAsync(d_group, parts->motion_group, 4 * n, cudaMemcpyHostToDevice, e->s));
+  launch_upload((int)n, d_pos, parts->vel ? d_vel : nullptr, d_rho, d_type,
+                parts->motion_group ? d_group : nullptr, slot, 0, e->dconst, e->ddyn, e->nbits,
+                e->S[0], e->keysA, (int)dst0, e->s);
+  CUDA_TRY(cudaGetLastError());
+  // the io buffer is reused by the next call: wait for the copies
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  return SPH_OK;
+}
+
+int set_slot(sph_engine e, int slot, const sph_case_params *p, const sph_particles *parts,
+             const Grid &g, uint32_t cellbase, double t_end) {
+  int64_t nf = 0;
+  for (int64_t i = 0; i < parts->n; i++) nf += parts->type[i] == 0;
+  Slot &S = e->slots[slot];
+  S.used = true;
+  S.params = *p;
+  S.n = parts->n;
+  S.n_fluid = nf;
+  S.cellbase = cellbase;
+  S.ncells = g.ncells;
+  S.t_end = t_end;
+  fill_const(*p, *parts, g, cellbase, t_end, nf, e->hconst[slot]);
+  CUDA_TRY(cudaMemcpyAsync(e->dconst + slot, &e->hconst[slot], sizeof(CaseConst),
+                           cudaMemcpyHostToDevice, e->s));
+  CaseDyn d;
+  std::memset(&d, 0, sizeof(d));
+  d.dtmin_bits = kFloatInfBits;
+  CUDA_TRY(cudaMemcpyAsync(e->ddyn + slot, &d, sizeof(CaseDyn), cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  return SPH_OK;
+}
+
+// Build an engine holding ncases cases back to back.
+int create_engine(const sph_case_params *params, const sph_particles *parts, int ncases,
+                  void *stream, sph_alloc_fn alloc, sph_free_fn freefn, void *ctx,
+                  sph_engine *out) {
+  if (!out) return fail(SPH_ERR_ARG, "null output handle");
+  *out = nullptr;
+  if (ncases <= 0 || ncases > 65535) return fail(SPH_ERR_ARG, "ncases must be in [1, 65535]");
+  std::vector<Grid> grids(ncases);
+  int64_t np = 0, nc = 0;
+  int margin = 0;
+  for (int c = 0; c < ncases; c++) {
+    int rc = check_particles(params + c, parts + c);
+    if (rc) return rc;
+    rc = make_grid(params[c], grids[c]);
+    if (rc) return rc;
+    if (margin && grids[c].margin != margin)
+      return fail(SPH_ERR_ARG, "all cases of an engine must use the same cell_mode");
+    margin = grids[c].margin;
+    np += parts[c].n;
+    nc += grids[c].ncells;
+  }
+  if (np > (int64_t(1) << 31) - 1) return fail(SPH_ERR_ARG, "too many particles");
+  if (nc > (int64_t(1) << 30)) return fail(SPH_ERR_ARG, "too many cells");
+  sph_engine e = new sph_engine_t();
+  int rc = init_engine(e, stream, alloc, freefn, ctx);
+  if (rc) {
+    delete e;
+    return rc;
+  }
+  e->cap_p = np;
+  e->cap_cells = nc;
+  e->cap_cases = ncases;
+  e->nbits = bits_for(nc);
+  e->margin = margin;
+  e->slots.resize(ncases);
+  e->hconst.resize(ncases);
+  rc = allocate(e);
+  int64_t cell0 = 0, p0 = 0;
+  for (int c = 0; c < ncases && rc == SPH_OK; c++) {
+    rc = set_slot(e, c, params + c, parts + c, grids[c], (uint32_t)cell0, 0.0);
+    if (rc == SPH_OK) rc = upload_case(e, c, parts + c, p0);
+    cell0 += grids[c].ncells;
+    p0 += parts[c].n;
+  }
+  if (rc) {
+    e->release_all();
+    delete e;
+    return rc;
+  }
+  e->n_phys = np;
+  *out = e;
+  return SPH_OK;
+}
+
+// One Symplectic step (all cases).  ev: 4 events around the two PI launches.
+void enqueue_step(sph_engine e, cudaEvent_t *ev) {
+  const int n = (int)e->n_phys;
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &X = e->S[0], &Y = e->S[1], &Z = e->S[2];
+  const uint32_t kout = key_out(e->nbits);
+  cudaStream_t s = e->s;
+  // NL on state n
+  radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
+  launch_reorder(nl, e->perm1, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->dconst, s);
+  launch_mark(nl, e->keysB, e->ctab, e->cap_cells, kout, e->nvalid, s);
+  // PI on state n, time step, predictor
+  if (ev) cudaEventRecord(ev[0], s);
+  launch_interact(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, Y.cid, e->ctab,
+                  e->dconst, e->ddyn, e->ace, nullptr, 1, e->opt.pi_block, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
+  launch_predictor(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
+                   e->keysC, s);
+  // NL on state n+1/2 (id/cid/code of Z are those of Y)
+  radix_sort(e->keysC, e->keysD, e->perm2, nl, e->nbits, e->sort_tmp, s);
+  launch_reorder(nl, e->perm2, Z.posc, Z.velrho, Y.id, Y.cid, Y.code, X, e->dconst, s);
+  launch_mark(nl, e->keysD, e->ctab, e->cap_cells, kout, e->nvalid + 1, s);
+  if (ev) cudaEventRecord(ev[2], s);
+  launch_interact(e->margin, nl, e->nvalid + 1, e->keysD, X.posc, X.velrho, X.cid, e->ctab,
+                  e->dconst, e->ddyn, e->ace, nullptr, 0, e->opt.pi_block, s);
+  if (ev) cudaEventRecord(ev[3], s);
+  launch_corrector(nl, e->perm2, e->keysD, e->keysB, Y, X, e->ace, e->dconst, e->ddyn, e->nbits,
+                   e->keysA, s);
+  launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
+}
+
+// NL only, on the current state: keysA/X -> keysB/Y + cell table.
+void enqueue_nl(sph_engine e) {
+  const int n = (int)e->n_phys;
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &X = e->S[0], &Y = e->S[1];
+  radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, e->s);
+  launch_reorder(nl, e->perm1, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->dconst, e->s);
+  launch_mark(nl, e->keysB, e->ctab, e->cap_cells, key_out(e->nbits), e->nvalid, e->s);
+}
+
+int check_flags(sph_engine e) {
+  std::vector<CaseDyn> d(e->cap_cases);
+  CUDA_TRY(cudaMemcpyAsync(d.data(), e->ddyn, sizeof(CaseDyn) * e->cap_cases,
+                           cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  for (int c = 0; c < e->cap_cases; c++) {
+    if (!e->slots[c].used) continue;
+    if (d[c].flags & kFlagNaN)
+      return fail(SPH_ERR_UNSTABLE, "case " + std::to_string(c) + ": NaN/Inf in the interaction");
+    if (d[c].flags & kFlagDtMin)
+      return fail(SPH_ERR_UNSTABLE, "case " + std::to_string(c) + ": dt below dt_min");
+    int mo = e->hconst[c].max_out;
+    if (mo >= 0 && d[c].n_out > mo)
+      return fail(SPH_ERR_DOMAIN, "case " + std::to_string(c) + ": " +
+                                      std::to_string(d[c].n_out) + " particles left the domain");
+  }
+  return SPH_OK;
+}
+
+int valid_case(sph_engine e, int icase) {
+  if (!e) return fail(SPH_ERR_ARG, "null engine");
+  if (icase < 0 || icase >= e->cap_cases || !e->slots[icase].used)
+    return fail(SPH_ERR_ARG, "no such case");
+  return SPH_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char *sph_last_error(void) { return g_err.c_str(); }
+
+int sph_create(const sph_case_params *params, const sph_particles *parts, void *stream,
+               sph_alloc_fn alloc, sph_free_fn free_fn, void *alloc_ctx, sph_engine *out) {
+  return create_engine(params, parts, 1, stream, alloc, free_fn, alloc_ctx, out);
+}
+
+int sph_batch_create(const sph_case_params *params, const sph_particles *parts, int32_t ncases,
+                     void *stream, sph_alloc_fn alloc, sph_free_fn free_fn, void *alloc_ctx,
+                     sph_engine *out) {
+  if (!params || !parts) return fail(SPH_ERR_ARG, "null params or particles");
+  return create_engine(params, parts, ncases, stream, alloc, free_fn, alloc_ctx, out);
+}
+
+int sph_set_options(sph_engine e, const sph_options *opt) {
+  if (!e || !opt) return fail(SPH_ERR_ARG, "null argument");
+  if (opt->pi_block != 0 && (opt->pi_block < 32 || opt->pi_block > 1024 || opt->pi_block % 32))
+    return fail(SPH_ERR_ARG, "pi_block must be a multiple of 32 in [32, 1024]");
+  e->opt = *opt;
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  e->gexec = nullptr;
+  return SPH_OK;
+}
+
+int sph_step(sph_engine e, int64_t nsteps) {
+  if (!e) return fail(SPH_ERR_ARG, "null engine");
+  if (nsteps < 0) return fail(SPH_ERR_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return SPH_OK;
+  if (e->n_phys == 0) return SPH_OK;
+  const bool timing = e->opt.timing != 0;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (timing) {
+    size_t need = 4 * (size_t)nsteps + 2;
+    while (e->evs.size() < need) {
+      cudaEvent_t ev;
+      CUDA_TRY(cudaEventCreate(&ev));
+      e->evs.push_back(ev);
+    }
+    t0 = e->evs[4 * nsteps];
+    t1 = e->evs[4 * nsteps + 1];
+    CUDA_TRY(cudaEventRecord(t0, e->s));
+  }
+  int64_t k = 0;
+  if (!timing && e->opt.use_graph && e->n_dead == 0) {
+    if (!e->gexec || e->graph_n != e->n_phys) {
+      if (e->gexec) cudaGraphExecDestroy(e->gexec);
+      e->gexec = nullptr;
+      cudaGraph_t g;
+      CUDA_TRY(cudaStreamBeginCapture(e->s, cudaStreamCaptureModeThreadLocal));
+      enqueue_step(e, nullptr);
+      CUDA_TRY(cudaStreamEndCapture(e->s, &g));
+      cudaError_t err = cudaGraphInstantiate(&e->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (err != cudaSuccess) return fail(SPH_ERR_CUDA, cudaGetErrorString(err));
+      e->graph_n = e->n_phys;
+    }
+    for (; k < nsteps; k++) CUDA_TRY(cudaGraphLaunch(e->gexec, e->s));
+  }
+  const int64_t per_step = 6 * std::max(1, (e->nbits + 7) / 8) + 10;
+  e->kernel_launches += per_step * nsteps;
+  for (; k < nsteps; k++) {
+    enqueue_step(e, timing ? &e->evs[4 * k] : nullptr);
+    e->n_phys -= e->n_dead;
+    e->n_dead = 0;
+  }
+  if (timing) CUDA_TRY(cudaEventRecord(t1, e->s));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  if (timing) {
+    for (int64_t j = 0; j < nsteps; j++) {
+      float a = 0.f, b = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&a, e->evs[4 * j], e->evs[4 * j + 1]));
+      CUDA_TRY(cudaEventElapsedTime(&b, e->evs[4 * j + 2], e->evs[4 * j + 3]));
+      e->pi_ms += a + b;
+      e->pi_launches += 2;
+    }
+    float tot = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&tot, t0, t1));
+    e->step_ms += tot;
+  }
+  return check_flags(e);
+}
+
+int sph_get_timing(sph_engine e, double *pi_ms, int64_t *pi_launches, double *step_ms,
+                   int64_t *kernel_launches, int32_t reset) {
+  if (!e) return fail(SPH_ERR_ARG, "null engine");
+  if (pi_ms) *pi_ms = e->pi_ms;
+  if (pi_launches) *pi_launches = e->pi_launches;
+  if (step_ms) *step_ms = e->step_ms;
+  if (kernel_launches) *kernel_launches = e->kernel_launches;
+  if (reset) {
+    e->pi_ms = e->step_ms = 0;
+    e->pi_launches = 0;
+    e->kernel_launches = 0;
+  }
+  return SPH_OK;
+}
+
+int sph_get_state(sph_engine e, int32_t icase, double *pos, float *vel, float *rho, float *press,
+                  double *t, int64_t *step, double *last_dt) {
+  int rc = valid_case(e, icase);
+  if (rc) return rc;
+  const int64_t n = e->slots[icase].n;
+  char *p = e->io;
+  double *d_pos = (double *)p;
+  p += align256(24 * n);
+  float *d_vel = (float *)p;
+  p += align256(12 * n);
+  float *d_rho = (float *)p;
+  p += align256(4 * n);
+  float *d_press = (float *)p;
+  launch_export((int)e->n_phys, e->keysA, e->S[0], e->dconst, icase, 0, e->nbits,
+                pos ? d_pos : nullptr, vel ? d_vel : nullptr, rho ? d_rho : nullptr,
+                press ? d_press : nullptr, e->s);
+  CUDA_TRY(cudaGetLastError());
+  if (pos) CUDA_TRY(cudaMemcpyAsync(pos, d_pos, 24 * n, cudaMemcpyDeviceToHost, e->s));
+  if (vel) CUDA_TRY(cudaMemcpyAsync(vel, d_vel, 12 * n, cudaMemcpyDeviceToHost, e->s));
+  if (rho) CUDA_TRY(cudaMemcpyAsync(rho, d_rho, 4 * n, cudaMemcpyDeviceToHost, e->s));
+  if (press) CUDA_TRY(cudaMemcpyAsync(press, d_press, 4 * n, cudaMemcpyDeviceToHost, e->s));
+  CaseDyn d;
+  CUDA_TRY(cudaMemcpyAsync(&d, e->ddyn + icase, sizeof(d), cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  if (t) *t = d.t;
+  if (step) *step = d.step;
+  if (last_dt) *last_dt = d.dt;
+  return SPH_OK;
+}
+
+int sph_get_stats(sph_engine e, int32_t icase, sph_stats *out) {
+  int rc = valid_case(e, icase);
+  if (rc) return rc;
+  if (!out) return fail(SPH_ERR_ARG, "null output");
+  const int nparts = 512;
+  launch_diag((int)e->n_phys, e->keysA, e->S[0], e->dconst, icase, e->nbits, e->diag + 8, nparts,
+              e->diag, e->s);
+  CUDA_TRY(cudaGetLastError());
+  double v[8];
+  CaseDyn d;
+  CUDA_TRY(cudaMemcpyAsync(v, e->diag, sizeof(v), cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaMemcpyAsync(&d, e->ddyn + icase, sizeof(d), cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  out->t = d.t;
+  out->last_dt = d.dt;
+  out->step = d.step;
+  out->interactions = (int64_t)d.pairs;
+  out->interactions_fb = (int64_t)d.pairs_fb;
+  out->interactions_bf = (int64_t)d.pairs_bf;
+  out->mass = v[0] * e->hconst[icase].m_d;
+  out->kinetic_energy = v[1];
+  out->momentum[0] = v[2];
+  out->momentum[1] = v[3];
+  out->momentum[2] = v[4];
+  out->front = v[6];
+  out->n_out = (int64_t)v[7];
+  out->flags = (int32_t)d.flags;
+  out->n_fluid = (int32_t)e->slots[icase].n_fluid;
+  out->n = e->slots[icase].n;
+  return SPH_OK;
+}
+
+// ---- checkpoint ----------------------------------------------------------------
+
+namespace {
+struct RawHeader {
+  uint32_t magic, version;
+  int64_t n;
+  double t, dt;
+  int64_t step;
+  uint64_t pairs;
+  int32_t n_out, flags;
+};
+constexpr uint32_t kRawMagic = 0x52485053u;  // "SPHR"
+}  // namespace
+
+int sph_get_raw(sph_engine e, int32_t icase, void *buf, size_t *bytes) {
+  int rc = valid_case(e, icase);
+  if (rc) return rc;
+  if (!bytes) return fail(SPH_ERR_ARG, "null size pointer");
+  const int64_t n = e->slots[icase].n;
+  const size_t need = sizeof(RawHeader) + (size_t)n * (4 + 4 + 16 + 16);
+  if (!buf) {
+    *bytes = need;
+    return SPH_OK;
+  }
+  if (*bytes < need) return fail(SPH_ERR_ARG, "raw buffer too small");
+  *bytes = need;
+  // device order of the case = order in X, filtered by slot (host-side)
+  const int64_t np = e->n_phys;
+  std::vector<uint32_t> keys(np), ids(np);
+  std::vector<uint16_t> cid(np);
+  std::vector<float4> pc(np), vr(np);
+  CUDA_TRY(cudaMemcpyAsync(keys.data(), e->keysA, 4 * np, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaMemcpyAsync(ids.data(), e->S[0].id, 4 * np, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaMemcpyAsync(cid.data(), e->S[0].cid, 2 * np, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaMemcpyAsync(pc.data(), e->S[0].posc, 16 * np, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaMemcpyAsync(vr.data(), e->S[0].velrho, 16 * np, cudaMemcpyDeviceToHost, e->s));
+  CaseDyn d;
+  CUDA_TRY(cudaMemcpyAsync(&d, e->ddyn + icase, sizeof(d), cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  RawHeader hd{kRawMagic, 1, n, d.t, d.dt, d.step, d.pairs, d.n_out, (int32_t)d.flags};
+  char *o = (char *)buf;
+  std::memcpy(o, &hd, sizeof(hd));
+  uint32_t *oid = (uint32_t *)(o + sizeof(hd));
+  int32_t *ocell = (int32_t *)(oid + n);
+  float4 *opc = (float4 *)(ocell + n);
+  float4 *ovr = opc + n;
+  const uint32_t kdead = key_dead(e->nbits), kout = key_out(e->nbits);
+  const uint32_t cb = e->slots[icase].cellbase;
+  int64_t j = 0;
+  for (int64_t i = 0; i < np && j < n; i++) {
+    if (cid[i] != icase || keys[i] == kdead) continue;
+    oid[j] = ids[i];
+    ocell[j] = keys[i] >= kout ? -1 : (int32_t)((keys[i] >> 1) - cb);
+    std::memcpy(opc + j, &pc[i], 16);
+    std::memcpy(ovr + j, &vr[i], 16);
+    j++;
+  }
+  if (j != n) return fail(SPH_ERR_STATE, "raw export found the wrong particle count");
+  return SPH_OK;
+}
+
+int sph_create_from_raw(const sph_case_params *params, const sph_particles *parts,
+                        const void *buf, size_t bytes, void *stream, sph_alloc_fn alloc,
+                        sph_free_fn free_fn, void *alloc_ctx, sph_engine *out) {
+  if (!buf || bytes < sizeof(RawHeader)) return fail(SPH_ERR_ARG, "bad raw buffer");
+  RawHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kRawMagic || hd.version != 1) return fail(SPH_ERR_ARG, "not a raw snapshot");
+  if (!parts || parts->n != hd.n) return fail(SPH_ERR_ARG, "particle count does not match snapshot");
+  if (bytes < sizeof(RawHeader) + (size_t)hd.n * 40) return fail(SPH_ERR_ARG, "truncated snapshot");
+  int rc = create_engine(params, parts, 1, stream, alloc, free_fn, alloc_ctx, out);
+  if (rc) return rc;
+  sph_engine e = *out;
+  const int64_t n = hd.n;
+  const char *o = (const char *)buf + sizeof(hd);
+  const uint32_t *ids = (const uint32_t *)o;
+  const int32_t *cell = (const int32_t *)(ids + n);
+  const float4 *pc = (const float4 *)(cell + n);
+  const float4 *vr = pc + n;
+  // reorder type/group into snapshot order on the host, then import
+  std::vector<uint8_t> type(n);
+  std::vector<int32_t> group(n, -1);
+  for (int64_t j = 0; j < n; j++) {
+    if (ids[j] >= (uint32_t)n) {
+      sph_destroy(e);
+      *out = nullptr;
+      return fail(SPH_ERR_ARG, "bad id in snapshot");
+    }
+    type[j] = parts->type[ids[j]];
+    if (parts->motion_group) group[j] = parts->motion_group[ids[j]];
+  }
+  char *p = e->io;
+  int32_t *d_cell = (int32_t *)p;
+  p += align256(4 * n);
+  float4 *d_pc = (float4 *)p;
+  p += align256(16 * n);
+  float4 *d_vr = (float4 *)p;
+  p += align256(16 * n);
+  uint8_t *d_type = (uint8_t *)p;
+  p += align256(n);
+  int32_t *d_group = (int32_t *)p;
+  CUDA_TRY(cudaMemcpyAsync(d_cell, cell, 4 * n, cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaMemcpyAsync(d_pc, pc, 16 * n, cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaMemcpyAsync(d_vr, vr, 16 * n, cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaMemcpyAsync(d_type, type.data(), n, cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaMemcpyAsync(d_group, group.data(), 4 * n, cudaMemcpyHostToDevice, e->s));
+  launch_import_raw((int)n, d_cell, d_pc, d_vr, d_type, d_group, 0, 0, e->dconst, e->nbits,
+                    e->S[0], e->keysA, 0, e->s);
+  // ids: the import wrote 0..n-1; restore the snapshot ids
+  CUDA_TRY(cudaMemcpyAsync(e->S[0].id, ids, 4 * n, cudaMemcpyHostToDevice, e->s));
+  CaseDyn d;
+  std::memset(&d, 0, sizeof(d));
+  d.t = hd.t;
+  d.dt = hd.dt;
+  d.step = hd.step;
+  d.pairs = hd.pairs;
+  d.n_out = hd.n_out;
+  d.flags = (unsigned)hd.flags;
+  d.dtmin_bits = kFloatInfBits;
+  CUDA_TRY(cudaMemcpyAsync(e->ddyn, &d, sizeof(d), cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  return SPH_OK;
+}
+
+// ---- parity / diagnostics ------------------------------------------------------
+
+int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho, float *mumax,
+                    double *dt, int64_t *pairs) {
+  int rc = valid_case(e, icase);
+  if (rc) return rc;
+  const int64_t n = e->slots[icase].n;
+  std::vector<CaseDyn> saved(e->cap_cases);
+  CUDA_TRY(cudaMemcpyAsync(saved.data(), e->ddyn, sizeof(CaseDyn) * e->cap_cases,
+                           cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  std::vector<CaseDyn> fresh = saved;
+  for (auto &d : fresh) {
+    d.dtmin_bits = kFloatInfBits;
+    d.pairs = 0;
+  }
+  CUDA_TRY(cudaMemcpyAsync(e->ddyn, fresh.data(), sizeof(CaseDyn) * e->cap_cases,
+                           cudaMemcpyHostToDevice, e->s));
+  enqueue_nl(e);
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &Y = e->S[1];
+  launch_interact(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, Y.cid, e->ctab,
+                  e->dconst, e->ddyn, e->ace, e->mu, 1, e->opt.pi_block, e->s);
+  char *p = e->io;
+  float *d_acc = (float *)p;
+  p += align256(12 * n);
+  float *d_drho = (float *)p;
+  p += align256(4 * n);
+  float *d_mu = (float *)p;
+  launch_scatter_forces(nl, Y.cid, Y.id, icase, 0, e->nvalid, e->ace, e->mu, d_acc, d_drho, d_mu,
+                        e->s);
+  CUDA_TRY(cudaGetLastError());
+  if (acc) CUDA_TRY(cudaMemcpyAsync(acc, d_acc, 12 * n, cudaMemcpyDeviceToHost, e->s));
+  if (drho) CUDA_TRY(cudaMemcpyAsync(drho, d_drho, 4 * n, cudaMemcpyDeviceToHost, e->s));
+  if (mumax) CUDA_TRY(cudaMemcpyAsync(mumax, d_mu, 4 * n, cudaMemcpyDeviceToHost, e->s));
+  CaseDyn d;
+  CUDA_TRY(cudaMemcpyAsync(&d, e->ddyn + icase, sizeof(d), cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  CUDA_TRY(cudaMemcpyAsync(e->ddyn, saved.data(), sizeof(CaseDyn) * e->cap_cases,
+                           cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  const CaseConst &C = e->hconst[icase];
+  if (dt) {
+    if (C.dt_fixed > 0)
+      *dt = C.dt_fixed;
+    else if (d.dtmin_bits >= kFloatInfBits)
+      *dt = C.cfl * C.h_d / C.cs0_d;
+    else {
+      float m;
+      std::memcpy(&m, &d.dtmin_bits, 4);
+      *dt = C.cfl * (double)m;
+    }
+  }
+  if (pairs) *pairs = (int64_t)d.pairs;
+  return SPH_OK;
+}
+
+int sph_get_order(sph_engine e, int32_t icase, int64_t *ids, int64_t *cells, int64_t *n_inside) {
+  int rc = valid_case(e, icase);
+  if (rc) return rc;
+  enqueue_nl(e);
+  const int64_t np = e->n_phys;
+  std::vector<uint32_t> keys(np), id(np);
+  std::vector<uint16_t> cid(np);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(keys.data(), e->keysB, 4 * np, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaMemcpyAsync(id.data(), e->S[1].id, 4 * np, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaMemcpyAsync(cid.data(), e->S[1].cid, 2 * np, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  const uint32_t kout = key_out(e->nbits), kdead = key_dead(e->nbits);
+  const uint32_t cb = e->slots[icase].cellbase;
+  int64_t j = 0, inside = 0;
+  for (int64_t i = 0; i < np - e->n_dead; i++) {
+    if (cid[i] != icase || keys[i] == kdead) continue;
+    if (ids) ids[j] = id[i];
+    if (cells) cells[j] = keys[i] >= kout ? -1 : (int64_t)((keys[i] >> 1) - cb);
+    inside += keys[i] < kout;
+    j++;
+  }
+  if (n_inside) *n_inside = inside;
+  return SPH_OK;
+}
+
+int sph_pair_stats(sph_engine e, int32_t icase, int64_t *count, uint64_t *hash) {
+  int rc = valid_case(e, icase);
+  if (rc) return rc;
+  const int64_t n = e->slots[icase].n;
+  enqueue_nl(e);
+  char *p = e->io;
+  long long *d_count = (long long *)p;
+  p += align256(8 * n);
+  unsigned long long *d_hash = (unsigned long long *)p;
+  CUDA_TRY(cudaMemsetAsync(d_count, 0, 8 * n, e->s));
+  CUDA_TRY(cudaMemsetAsync(d_hash, 0, 8 * n, e->s));
+  launch_pair_stats((int)(e->n_phys - e->n_dead), e->nvalid, e->keysB, e->S[1], e->ctab,
+                    e->dconst, icase, 0, d_count, d_hash, e->s);
+  CUDA_TRY(cudaGetLastError());
+  if (count) CUDA_TRY(cudaMemcpyAsync(count, d_count, 8 * n, cudaMemcpyDeviceToHost, e->s));
+  if (hash) CUDA_TRY(cudaMemcpyAsync(hash, d_hash, 8 * n, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  return SPH_OK;
+}
+
+// ---- serving pool --------------------------------------------------------------
+
+int sph_pool_create(int64_t max_particles, int64_t max_cells, int32_t max_cases, void *stream,
+                    sph_alloc_fn alloc, sph_free_fn free_fn, void *alloc_ctx, sph_engine *out) {
+  if (!out) return fail(SPH_ERR_ARG, "null output handle");
+  *out = nullptr;
+  if (max_particles <= 0 || max_particles > (int64_t(1) << 31) - 1 || max_cells <= 0 ||
+      max_cells > (int64_t(1) << 30) || max_cases <= 0 || max_cases > 65535)
+    return fail(SPH_ERR_ARG, "bad pool capacity");
+  sph_engine e = new sph_engine_t();
+  int rc = init_engine(e, stream, alloc, free_fn, alloc_ctx);
+  if (rc) {
+    delete e;
+    return rc;
+  }
+  e->pool = true;
+  e->cap_p = max_particles;
+  e->cap_cells = max_cells;
+  e->cap_cases = max_cases;
+  e->nbits = bits_for(max_cells);
+  e->slots.resize(max_cases);
+  e->hconst.resize(max_cases);
+  e->free_cells.push_back({0, max_cells});
+  rc = allocate(e);
+  if (rc == SPH_OK) {
+    cudaError_t err = cudaStreamSynchronize(e->s);
+    if (err != cudaSuccess) rc = fail(SPH_ERR_CUDA, cudaGetErrorString(err));
+  }
+  if (rc) {
+    e->release_all();
+    delete e;
+    return rc;
+  }
+  *out = e;
+  return SPH_OK;
+}
+
+int sph_pool_admit(sph_engine e, const sph_case_params *params, const sph_particles *parts,
+                   double t_end, int32_t *slot) {
+  if (!e || !e->pool) return fail(SPH_ERR_STATE, "not a pool engine");
+  if (!slot) return fail(SPH_ERR_ARG, "null slot pointer");
+  int rc = check_particles(params, parts);
+  if (rc) return rc;
+  Grid g;
+  rc = make_grid(*params, g);
+  if (rc) return rc;
+  int used = 0;
+  for (auto &s : e->slots) used += s.used;
+  if (used == 0) e->margin = g.margin;
+  if (g.margin != e->margin) return fail(SPH_ERR_ARG, "cell_mode differs from the pool's cases");
+  int free_slot = -1;
+  for (int c = 0; c < e->cap_cases; c++)
+    if (!e->slots[c].used) {
+      free_slot = c;
+      break;
+    }
+  if (free_slot < 0) return fail(SPH_ERR_BUSY, "no free case slot");
+  if (e->n_phys + parts->n > e->cap_p) return fail(SPH_ERR_BUSY, "not enough particle memory");
+  int fr = -1;
+  for (size_t r = 0; r < e->free_cells.size(); r++)
+    if (e->free_cells[r].second - e->free_cells[r].first >= g.ncells) {
+      fr = (int)r;
+      break;
+    }
+  if (fr < 0) return fail(SPH_ERR_BUSY, "not enough cell-table memory");
+  const int64_t cb = e->free_cells[fr].first;
+  e->free_cells[fr].first += g.ncells;
+  if (e->free_cells[fr].first == e->free_cells[fr].second)
+    e->free_cells.erase(e->free_cells.begin() + fr);
+  rc = set_slot(e, free_slot, params, parts, g, (uint32_t)cb, t_end);
+  if (rc == SPH_OK) rc = upload_case(e, free_slot, parts, e->n_phys);
+  if (rc) return rc;
+  e->n_phys += parts->n;
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  e->gexec = nullptr;
+  *slot = free_slot;
+  return SPH_OK;
+}
+
+int sph_pool_step(sph_engine e, int64_t nsteps, int32_t *finished, int32_t *n_finished) {
+  if (!e || !e->pool) return fail(SPH_ERR_STATE, "not a pool engine");
+  int rc = sph_step(e, nsteps);
+  if (rc) return rc;
+  std::vector<CaseDyn> d(e->cap_cases);
+  CUDA_TRY(cudaMemcpyAsync(d.data(), e->ddyn, sizeof(CaseDyn) * e->cap_cases,
+                           cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  int k = 0;
+  for (int c = 0; c < e->cap_cases; c++)
+    if (e->slots[c].used && e->slots[c].t_end > 0 && d[c].t >= e->slots[c].t_end) {
+      if (finished) finished[k] = c;
+      k++;
+    }
+  if (n_finished) *n_finished = k;
+  return SPH_OK;
+}
+
+int sph_pool_release(sph_engine e, int32_t slot) {
+  if (!e || !e->pool) return fail(SPH_ERR_STATE, "not a pool engine");
+  int rc = valid_case(e, slot);
+  if (rc) return rc;
+  launch_release((int)e->n_phys, e->S[0].cid, slot, e->nbits, e->keysA, e->s);
+  e->hconst[slot].active = 0;
+  CUDA_TRY(cudaMemcpyAsync(e->dconst + slot, &e->hconst[slot], sizeof(CaseConst),
+                           cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  Slot &S = e->slots[slot];
+  e->n_dead += S.n;
+  // return the cell range (merge neighbours)
+  e->free_cells.push_back({S.cellbase, S.cellbase + S.ncells});
+  std::sort(e->free_cells.begin(), e->free_cells.end());
+  std::vector<std::pair<int64_t, int64_t>> merged;
+  for (auto &r : e->free_cells) {
+    if (!merged.empty() && merged.back().second == r.first)
+      merged.back().second = r.second;
+    else
+      merged.push_back(r);
+  }
+  e->free_cells.swap(merged);
+  S = Slot();
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  e->gexec = nullptr;
+  return SPH_OK;
+}
+
+int sph_pool_usage(sph_engine e, int64_t *particles_used, int64_t *cells_used,
+                   int32_t *cases_used) {
+  if (!e) return fail(SPH_ERR_ARG, "null engine");
+  int64_t cells = 0;
+  int cases = 0;
+  for (auto &s : e->slots)
+    if (s.used) {
+      cells += s.ncells;
+      cases++;
+    }
+  if (particles_used) *particles_used = e->n_phys - e->n_dead;
+  if (cells_used) *cells_used = cells;
+  if (cases_used) *cases_used = cases;
+  return SPH_OK;
+}
+
+void sph_destroy(sph_engine e) {
+  if (!e) return;
+  e->release_all();
+  delete e;
+}
+
+}  // extern "C"

@@ -1,0 +1,847 @@
+// sph_kernels.cu -- the per-step kernels of the WCSPH hot path (DualSPHysics
+// paper, arXiv 2104.00537) for sm_103a:
+//   k_upload      host particles -> (cell, float offset) state + keys
+//   k_reorder     gather the state into cell order, Tait pressure (Eq 28)
+//   k_mark        cell begin/end table (Sect. 5.1)
+//   k_interact    Wendland C2 pair loop: momentum with artificial viscosity
+//                 (Eq 21-22), continuity with density diffusion (Eq 15,
+//                 17-18), dynamic boundaries (Eq 36), Eq 35 reductions
+//   k_dt          time step (Eq 35) and imposed-motion increments (Eq 37)
+//   k_predictor   Symplectic half step (Eq 33-34)
+//   k_corrector   Symplectic full step (Eq 33-34)
+//   k_end_step    t += dt in FP64
+//   k_export / k_diag / k_pair_stats   read-out and parity helpers
+#include <cfloat>
+
+#include "sph_internal.cuh"
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+// ---- small helpers ----------------------------------------------------------
+
+__device__ __forceinline__ float tait_pressure(const CaseConst &C, float rho) {
+  // P = B ((rho/rho0)^gamma - 1), evaluated as B expm1(gamma log1p(e)) with
+  // e = (rho - rho0)/rho0 so that no digits cancel near rho0.
+  float e = (rho - C.rho0) * C.inv_rho0;
+  return C.btait * expm1f(C.gamma * log1pf(e));
+}
+
+__device__ __forceinline__ void decode_cell(uint32_t lin, int nx, int ny, int &cx, int &cy,
+                                            int &cz) {
+  int t = (int)(lin / (uint32_t)nx);
+  cx = (int)lin - t * nx;
+  cz = t / ny;
+  cy = t - cz * ny;
+}
+
+__device__ __forceinline__ float below(float cs) {  // largest float < cs
+  return __int_as_float(__float_as_int(cs) - 1);
+}
+
+// New (cell, offset) after adding disp (FP64) to the offset of axis k.
+// Returns the cell shift; off_out is the new float offset in [0, cs).
+__device__ __forceinline__ int shift_axis(float off, double disp, const CaseConst &C,
+                                          float &off_out) {
+  double x = (double)off + disp;
+  double k = floor(x * C.inv_cs);
+  x = fma(-k, C.cs, x);
+  if (x < 0.0) {
+    x += C.cs;
+    k -= 1.0;
+  } else if (x >= C.cs) {
+    x -= C.cs;
+    k += 1.0;
+  }
+  float f = (float)x;
+  if (f >= C.csf) f = below(C.csf);
+  if (f < 0.f) f = 0.f;
+  off_out = f;
+  return (int)k;
+}
+
+// ---- upload ------------------------------------------------------------------
+
+__global__ void k_upload(int n, const double *__restrict__ pos, const float *__restrict__ vel,
+                         const float *__restrict__ rho, const uint8_t *__restrict__ type,
+                         const int32_t *__restrict__ group, int slot, uint32_t id_base,
+                         const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
+                         int nbits, State st, uint32_t *__restrict__ keys, int dst0) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const CaseConst &C = cc[slot];
+  int c[3];
+  float off[3];
+  bool inside = true;
+  for (int k = 0; k < 3; k++) {
+    // same cell rule as the oracle: floor((r - origin) / cs) in FP64
+    double rel = pos[3 * i + k] - C.origin[k];
+    double f = floor(rel / C.cs);
+    int nk = k == 0 ? C.nx : (k == 1 ? C.ny : C.nz);
+    if (!(f >= C.margin && f < nk - C.margin)) inside = false;
+    c[k] = (int)f;
+    float o = (float)(rel - f * C.cs);
+    if (o >= C.csf) o = below(C.csf);
+    if (o < 0.f) o = 0.f;
+    off[k] = o;
+  }
+  int d = dst0 + i;
+  uint8_t code = type[i] == 0 ? 0 : (group && group[i] >= 0 ? (uint8_t)(2 + group[i]) : 1);
+  float4 vr = make_float4(vel ? vel[3 * i] : 0.f, vel ? vel[3 * i + 1] : 0.f,
+                          vel ? vel[3 * i + 2] : 0.f, rho[i]);
+  uint32_t key;
+  if (inside) {
+    uint32_t lin = ((uint32_t)c[2] * C.ny + c[1]) * C.nx + c[0];
+    key = 2u * (C.cellbase + lin) + (code ? 1u : 0u);
+    st.posc[d] = make_float4(off[0], off[1], off[2], 0.f);
+  } else {
+    key = key_out(nbits);
+    // frozen particles keep a float position relative to the grid origin
+    st.posc[d] = make_float4((float)(pos[3 * i] - C.origin[0]),
+                             (float)(pos[3 * i + 1] - C.origin[1]),
+                             (float)(pos[3 * i + 2] - C.origin[2]), 0.f);
+    atomicAdd(&dyn[slot].n_out, 1);
+  }
+  st.velrho[d] = vr;
+  st.id[d] = id_base + (uint32_t)i;
+  st.cid[d] = (uint16_t)slot;
+  st.code[d] = code;
+  keys[d] = key;
+}
+
+// ---- reorder + equation of state ------------------------------------------
+
+__global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
+                          const float4 *__restrict__ posc_src,
+                          const float4 *__restrict__ velrho_src,
+                          const uint32_t *__restrict__ id_src,
+                          const uint16_t *__restrict__ cid_src,
+                          const uint8_t *__restrict__ code_src, State dst,
+                          const CaseConst *__restrict__ cc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t p = perm[i];
+  float4 pc = posc_src[p];
+  float4 vr = velrho_src[p];
+  uint16_t cidx = cid_src[p];
+  pc.w = tait_pressure(cc[cidx], vr.w);
+  dst.posc[i] = pc;
+  dst.velrho[i] = vr;
+  dst.id[i] = id_src[p];
+  dst.cid[i] = cidx;
+  dst.code[i] = code_src[p];
+}
+
+// ---- cell table --------------------------------------------------------------
+
+// ctab[c] = {first fluid, end fluid, first boundary, end boundary} of cell c
+// (global cell index); empty ranges stay {0,0}.  nvalid = first out/dead key.
+__global__ void k_mark(int n, const uint32_t *__restrict__ keys, uint4 *__restrict__ ctab,
+                       uint32_t kout, int *__restrict__ nvalid) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t k = keys[i];
+  if (k >= kout) {
+    if (i == 0 || keys[i - 1] < kout) *nvalid = i;
+    return;
+  }
+  if (i == n - 1) *nvalid = n;
+  uint32_t c = k >> 1;
+  unsigned *e = reinterpret_cast<unsigned *>(ctab + c) + ((k & 1u) ? 2 : 0);
+  if (i == 0 || keys[i - 1] != k) e[0] = (unsigned)i;
+  if (i == n - 1 || keys[i + 1] != k) e[1] = (unsigned)(i + 1);
+}
+
+// ---- particle interaction ----------------------------------------------------
+
+// Per-case warp-aggregated reductions: pair count (sum) and Eq 35 minimum.
+// npairs: all pairs of a; nfb: pairs with a in F, b in B; nbf: pairs with a in B.
+__device__ __forceinline__ void reduce_case(int cidx, bool has, unsigned npairs, unsigned nfb,
+                                            unsigned nbf, unsigned dtbits, bool bad,
+                                            CaseDyn *dyn) {
+  const unsigned full = 0xffffffffu;
+  int c0 = __shfl_sync(full, cidx, 0);
+  bool uniform = __all_sync(full, cidx == c0 && has);
+  if (uniform) {
+    unsigned p32 = __reduce_add_sync(full, npairs);
+    unsigned fb = __reduce_add_sync(full, nfb);
+    unsigned bf = __reduce_add_sync(full, nbf);
+    unsigned m = __reduce_min_sync(full, dtbits);
+    unsigned anybad = __any_sync(full, bad);
+    if ((threadIdx.x & 31) == 0) {
+      if (p32) atomicAdd(&dyn[c0].pairs, (unsigned long long)p32);
+      if (fb) atomicAdd(&dyn[c0].pairs_fb, (unsigned long long)fb);
+      if (bf) atomicAdd(&dyn[c0].pairs_bf, (unsigned long long)bf);
+      if (m < kFloatInfBits) atomicMin(&dyn[c0].dtmin_bits, m);
+      if (anybad) atomicOr(&dyn[c0].flags, kFlagNaN);
+    }
+  } else if (has) {
+    if (npairs) atomicAdd(&dyn[cidx].pairs, (unsigned long long)npairs);
+    if (nfb) atomicAdd(&dyn[cidx].pairs_fb, (unsigned long long)nfb);
+    if (nbf) atomicAdd(&dyn[cidx].pairs_bf, (unsigned long long)nbf);
+    if (dtbits < kFloatInfBits) atomicMin(&dyn[cidx].dtmin_bits, dtbits);
+    if (bad) atomicOr(&dyn[cidx].flags, kFlagNaN);
+  }
+}
+
+// One thread per particle a in cell order; the 27 (cells of 2h) or 125
+// (cells of h) neighbour cells are visited cell by cell, fluid range first.
+// r_ab = (offset_a - offset_b) - (cell shift) * cs, all in FP32.
+template <int M>
+__global__ void __launch_bounds__(128)
+k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
+           const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
+           const uint16_t *__restrict__ cid, const uint4 *__restrict__ ctab,
+           const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
+           float4 *__restrict__ ace, float *__restrict__ mu_out, int want_dt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int nvalid = *nvalid_p;
+  bool has = i < nvalid;
+  int cidx = i < n ? (int)cid[i] : -1;
+  unsigned npairs = 0, nfb = 0, nbf = 0;
+  unsigned dtbits = kFloatInfBits;
+  bool bad = false;
+  if (has) {
+    const CaseConst &C = cc[cidx];
+    const uint32_t key = keys[i];
+    const bool afluid = (key & 1u) == 0;
+    const int gc = (int)(key >> 1);
+    const int nx = C.nx, nxy = C.nx * C.ny;
+    const float csf = C.csf, r2max = C.r2max, eta2 = C.eta2, hih = C.half_inv_h;
+    const float4 pa = posc[i];
+    const float4 va = velrho[i];
+    const float kv = C.kvisc * va.w;
+    const bool ddt = C.ddt != 0;
+    float ax = 0.f, ay = 0.f, az = 0.f, s1 = 0.f, s2 = 0.f, mur = 0.f;
+    unsigned cnt = 0, cntb = 0;
+#pragma unroll 1
+    for (int dz = -M; dz <= M; dz++) {
+#pragma unroll 1
+      for (int dy = -M; dy <= M; dy++) {
+        const int row = gc + dz * nxy + dy * nx;
+        const float sy = pa.y - (float)dy * csf;
+        const float sz = pa.z - (float)dz * csf;
+#pragma unroll 1
+        for (int dx = -M; dx <= M; dx++) {
+          const uint4 r = ctab[row + dx];
+          const float sx = pa.x - (float)dx * csf;
+          // fluid neighbours
+#pragma unroll 1
+          for (unsigned j = r.x; j < r.y; j++) {
+            const float4 pb = posc[j];
+            const float rx = sx - pb.x, ry = sy - pb.y, rz = sz - pb.z;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            if (r2 < r2max && r2 > 0.f) {
+              const float4 vb = velrho[j];
+              const float rr = r2 * rsqrtf(r2);
+              const float t = fmaf(-hih, rr, 1.f);
+              const float t3 = t * t * t;
+              const float vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
+              const float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
+              const float ib = __fdividef(1.f, vb.w);
+              const float w = t3 * ib;
+              s1 = fmaf(w, vr, s1);
+              cnt++;
+              if (afluid) {
+                if (ddt) s2 = fmaf(w, vb.w - va.w, s2);
+                const float e = r2 + eta2;
+                const float sab = va.w + vb.w;
+                const float ie = __fdividef(1.f, e * sab);
+                const float mu = vr * ie * sab;  // v_ab.r_ab / (r^2 + eta^2)
+                mur = fmaxf(mur, fabsf(mu));
+                const float pi = fminf(vr, 0.f) * ie;
+                const float u = fmaf(kv, pi, (pa.w + pb.w) * ib);
+                const float s = t3 * u;
+                ax = fmaf(s, rx, ax);
+                ay = fmaf(s, ry, ay);
+                az = fmaf(s, rz, az);
+              }
+            }
+          }
+          if (afluid) {
+            // boundary neighbours (no density diffusion, Eq 17 sums over F)
+#pragma unroll 1
+            for (unsigned j = r.z; j < r.w; j++) {
+              const float4 pb = posc[j];
+              const float rx = sx - pb.x, ry = sy - pb.y, rz = sz - pb.z;
+              const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+              if (r2 < r2max && r2 > 0.f) {
+                const float4 vb = velrho[j];
+                const float rr = r2 * rsqrtf(r2);
+                const float t = fmaf(-hih, rr, 1.f);
+                const float t3 = t * t * t;
+                const float vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
+                const float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
+                const float ib = __fdividef(1.f, vb.w);
+                const float w = t3 * ib;
+                s1 = fmaf(w, vr, s1);
+                cntb++;
+                const float e = r2 + eta2;
+                const float sab = va.w + vb.w;
+                const float ie = __fdividef(1.f, e * sab);
+                const float mu = vr * ie * sab;
+                mur = fmaxf(mur, fabsf(mu));
+                const float pi = fminf(vr, 0.f) * ie;
+                const float u = fmaf(kv, pi, (pa.w + pb.w) * ib);
+                const float s = t3 * u;
+                ax = fmaf(s, rx, ax);
+                ay = fmaf(s, ry, ay);
+                az = fmaf(s, rz, az);
+              }
+            }
+          }
+        }
+      }
+    }
+    npairs = cnt + cntb;
+    nfb = afluid ? cntb : 0u;
+    nbf = afluid ? 0u : cnt;
+    const float mcw = C.m * C.cw;
+    float4 out;
+    float mumax = C.h * mur;
+    if (afluid) {
+      const float ca = -mcw / va.w;
+      out.x = fmaf(ca, ax, C.g[0]);
+      out.y = fmaf(ca, ay, C.g[1]);
+      out.z = fmaf(ca, az, C.g[2]);
+      out.w = mcw * (va.w * s1 - C.kddt * s2);
+      const float f = sqrtf(out.x * out.x + out.y * out.y + out.z * out.z);
+      const float dtf = f > 0.f ? sqrtf(C.h / f) : INFINITY;
+      const float dtcv = C.h / (C.cs0f + mumax);
+      float dta = fminf(dtf, dtcv);
+      bad = !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) && isfinite(out.w));
+      if (want_dt) dtbits = __float_as_uint(dta);
+    } else {
+      out = make_float4(0.f, 0.f, 0.f, mcw * va.w * s1);
+      mumax = 0.f;
+      bad = !isfinite(out.w);
+    }
+    ace[i] = out;
+    if (mu_out) mu_out[i] = mumax;
+  }
+  reduce_case(cidx, has, npairs, nfb, nbf, dtbits, bad, dyn);
+}
+
+// ---- time step and motion ----------------------------------------------------
+
+__device__ __forceinline__ double motion_disp(const CaseConst &C, int g, double t) {
+  return C.mot_amp[g] * (sin(C.mot_omega[g] * t + C.mot_phase[g]) - sin(C.mot_phase[g]));
+}
+__device__ __forceinline__ double motion_vel(const CaseConst &C, int g, double t) {
+  return C.mot_amp[g] * C.mot_omega[g] * cos(C.mot_omega[g] * t + C.mot_phase[g]);
+}
+
+__global__ void k_dt(int ncases, const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncases) return;
+  const CaseConst &C = cc[c];
+  CaseDyn &D = dyn[c];
+  if (!C.active) return;
+  unsigned bits = D.dtmin_bits;
+  double dt;
+  if (C.dt_fixed > 0.0) {
+    dt = C.dt_fixed;
+  } else if (bits >= kFloatInfBits) {
+    dt = C.cfl * C.h_d / C.cs0_d;  // no fluid: dt_f = inf, dt_cv = h / cs0
+  } else {
+    dt = C.cfl * (double)__uint_as_float(bits);
+  }
+  if (dt < C.dt_min) D.flags |= kFlagDtMin;
+  if (C.t_end > 0.0 && D.t >= C.t_end) dt = 0.0;  // finished cases stay put
+  D.dt = dt;
+  D.dtmin_bits = kFloatInfBits;
+  for (int g = 0; g < C.nmot; g++) {
+    double d0 = motion_disp(C, g, D.t);
+    D.mot[g][0] = motion_disp(C, g, D.t + 0.5 * dt) - d0;
+    D.mot[g][1] = motion_vel(C, g, D.t + 0.5 * dt);
+    D.mot[g][2] = motion_disp(C, g, D.t + dt) - d0;
+    D.mot[g][3] = motion_vel(C, g, D.t + dt);
+  }
+}
+
+__global__ void k_end_step(int ncases, const CaseConst *__restrict__ cc,
+                           CaseDyn *__restrict__ dyn) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncases || !cc[c].active) return;
+  CaseDyn &D = dyn[c];
+  if (D.dt > 0.0) {
+    D.t += D.dt;
+    D.step += 1;
+  }
+}
+
+// ---- Symplectic predictor / corrector ------------------------------------------
+
+// Moves a particle by disp (FP64, per axis) from cell key k; returns the new
+// key (or key_out) and writes the new offsets.
+__device__ __forceinline__ uint32_t move_particle(uint32_t k, const float4 &p, const double disp[3],
+                                                  const CaseConst &C, bool boundary, int nbits,
+                                                  float4 &pout, bool &left) {
+  int cx, cy, cz;
+  decode_cell((k >> 1) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+  float ox, oy, oz;
+  cx += shift_axis(p.x, disp[0], C, ox);
+  cy += shift_axis(p.y, disp[1], C, oy);
+  cz += shift_axis(p.z, disp[2], C, oz);
+  const int M = C.margin;
+  left = !(cx >= M && cx < C.nx - M && cy >= M && cy < C.ny - M && cz >= M && cz < C.nz - M);
+  if (left) {
+    // frozen: keep a float position relative to the grid origin
+    pout = make_float4((float)(cx * C.cs + ox), (float)(cy * C.cs + oy),
+                       (float)(cz * C.cs + oz), 0.f);
+    return key_out(nbits);
+  }
+  pout = make_float4(ox, oy, oz, 0.f);
+  uint32_t lin = ((uint32_t)cz * C.ny + cy) * C.nx + cx;
+  return 2u * (C.cellbase + lin) + (boundary ? 1u : 0u);
+}
+
+__global__ void k_predictor(int n, const uint32_t *__restrict__ keys_in, State src,
+                            const float4 *__restrict__ ace, const CaseConst *__restrict__ cc,
+                            CaseDyn *__restrict__ dyn, int nbits, float4 *__restrict__ posc_out,
+                            float4 *__restrict__ velrho_out, uint32_t *__restrict__ keys_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys_in[i];
+  const float4 p = src.posc[i];
+  const float4 v = src.velrho[i];
+  if (k >= key_out(nbits)) {  // frozen or released: unchanged
+    posc_out[i] = p;
+    velrho_out[i] = v;
+    keys_out[i] = k;
+    return;
+  }
+  const int cidx = src.cid[i];
+  const uint8_t code = src.code[i];
+  const CaseConst &C = cc[cidx];
+  const CaseDyn &D = dyn[cidx];
+  const double hdt = 0.5 * D.dt;
+  const float hdtf = (float)hdt;
+  const float4 a = ace[i];
+  double disp[3];
+  float4 vn;
+  if (code == 0) {
+    disp[0] = hdt * (double)v.x;
+    disp[1] = hdt * (double)v.y;
+    disp[2] = hdt * (double)v.z;
+    vn = make_float4(fmaf(hdtf, a.x, v.x), fmaf(hdtf, a.y, v.y), fmaf(hdtf, a.z, v.z),
+                     fmaf(hdtf, a.w, v.w));
+  } else {
+    float rho = fmaf(hdtf, a.w, v.w);
+    if (C.clamp && rho < C.rho0) rho = C.rho0;
+    if (code >= 2) {
+      const int g = code - 2;
+      const double d = D.mot[g][0];
+      const float vm = (float)D.mot[g][1];
+      disp[0] = d * C.mot_axis[g][0];
+      disp[1] = d * C.mot_axis[g][1];
+      disp[2] = d * C.mot_axis[g][2];
+      vn = make_float4(vm * C.mot_axis[g][0], vm * C.mot_axis[g][1], vm * C.mot_axis[g][2], rho);
+    } else {
+      disp[0] = disp[1] = disp[2] = 0.0;
+      vn = make_float4(v.x, v.y, v.z, rho);
+    }
+  }
+  float4 pn;
+  bool left;
+  uint32_t kn = move_particle(k, p, disp, C, code != 0, nbits, pn, left);
+  if (left) {
+    // left the domain at the half step: frozen at state n
+    int cx, cy, cz;
+    decode_cell((k >> 1) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+    pn = make_float4((float)(cx * C.cs + p.x), (float)(cy * C.cs + p.y),
+                     (float)(cz * C.cs + p.z), 0.f);
+    vn = v;
+    atomicAdd(&dyn[cidx].n_out, 1);
+  }
+  posc_out[i] = pn;
+  velrho_out[i] = vn;
+  keys_out[i] = kn;
+}
+
+__global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
+                            const uint32_t *__restrict__ keys_half,
+                            const uint32_t *__restrict__ keys_n, State sn, State x,
+                            const float4 *__restrict__ ace, const CaseConst *__restrict__ cc,
+                            CaseDyn *__restrict__ dyn, int nbits,
+                            uint32_t *__restrict__ keys_next) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t p = perm2[i];
+  const uint32_t kh = keys_half[i];
+  if (kh >= key_out(nbits)) {  // frozen (already in x) or released
+    keys_next[i] = kh;
+    return;
+  }
+  const float4 pn = sn.posc[p];
+  const float4 vn = sn.velrho[p];
+  const uint32_t k = keys_n[p];
+  const int cidx = x.cid[i];
+  const uint8_t code = x.code[i];
+  const CaseConst &C = cc[cidx];
+  const CaseDyn &D = dyn[cidx];
+  const double dt = D.dt;
+  const float dtf = (float)dt;
+  const float4 a = ace[i];
+  const float rhoh = x.velrho[i].w;
+  // Eq 34: rho^{n+1} = rho^n (2 - eps) / (2 + eps), eps = -(R / rho^{n+1/2}) dt
+  const float eps = -(a.w / rhoh) * dtf;
+  float rho = vn.w * (2.f - eps) / (2.f + eps);
+  double disp[3];
+  float4 vnew;
+  if (code == 0) {
+    vnew = make_float4(fmaf(dtf, a.x, vn.x), fmaf(dtf, a.y, vn.y), fmaf(dtf, a.z, vn.z), rho);
+    disp[0] = dt * (0.5 * ((double)vnew.x + (double)vn.x));
+    disp[1] = dt * (0.5 * ((double)vnew.y + (double)vn.y));
+    disp[2] = dt * (0.5 * ((double)vnew.z + (double)vn.z));
+  } else {
+    if (C.clamp && rho < C.rho0) rho = C.rho0;
+    if (code >= 2) {
+      const int g = code - 2;
+      const double d = D.mot[g][2];
+      const float vm = (float)D.mot[g][3];
+      disp[0] = d * C.mot_axis[g][0];
+      disp[1] = d * C.mot_axis[g][1];
+      disp[2] = d * C.mot_axis[g][2];
+      vnew = make_float4(vm * C.mot_axis[g][0], vm * C.mot_axis[g][1], vm * C.mot_axis[g][2],
+                         rho);
+    } else {
+      disp[0] = disp[1] = disp[2] = 0.0;
+      vnew = make_float4(vn.x, vn.y, vn.z, rho);
+    }
+  }
+  float4 pnew;
+  bool left;
+  uint32_t kn = move_particle(k, pn, disp, C, code != 0, nbits, pnew, left);
+  if (left) atomicAdd(&dyn[cidx].n_out, 1);  // frozen at state n+1
+  x.posc[i] = pnew;
+  x.velrho[i] = vnew;
+  keys_next[i] = kn;
+}
+
+// ---- read-out ------------------------------------------------------------------
+
+__global__ void k_export(int n, const uint32_t *__restrict__ keys, State st,
+                         const CaseConst *__restrict__ cc, int slot, uint32_t id_base,
+                         int nbits, double *__restrict__ pos, float *__restrict__ vel,
+                         float *__restrict__ rho, float *__restrict__ press) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || st.cid[i] != slot) return;
+  const uint32_t k = keys[i];
+  if (k == key_dead(nbits)) return;
+  const CaseConst &C = cc[slot];
+  const uint32_t lid = st.id[i] - id_base;
+  const float4 p = st.posc[i];
+  const float4 v = st.velrho[i];
+  double x, y, z;
+  if (k >= key_out(nbits)) {
+    x = (double)p.x;
+    y = (double)p.y;
+    z = (double)p.z;
+  } else {
+    int cx, cy, cz;
+    decode_cell((k >> 1) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+    x = cx * C.cs + (double)p.x;
+    y = cy * C.cs + (double)p.y;
+    z = cz * C.cs + (double)p.z;
+  }
+  if (pos) {
+    pos[3 * lid] = C.origin[0] + x;
+    pos[3 * lid + 1] = C.origin[1] + y;
+    pos[3 * lid + 2] = C.origin[2] + z;
+  }
+  if (vel) {
+    vel[3 * lid] = v.x;
+    vel[3 * lid + 1] = v.y;
+    vel[3 * lid + 2] = v.z;
+  }
+  if (rho) rho[lid] = v.w;
+  if (press) press[lid] = tait_pressure(C, v.w);
+}
+
+// Raw export: cell (or -1) and the float4 pair, in original order.
+__global__ void k_export_raw(int n, const uint32_t *__restrict__ keys, State st,
+                             const CaseConst *__restrict__ cc, int slot, uint32_t id_base,
+                             int nbits, int32_t *__restrict__ cell, float4 *__restrict__ posc,
+                             float4 *__restrict__ velrho) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || st.cid[i] != slot) return;
+  const uint32_t k = keys[i];
+  if (k == key_dead(nbits)) return;
+  const uint32_t lid = st.id[i] - id_base;
+  cell[lid] = k >= key_out(nbits) ? -1 : (int32_t)((k >> 1) - cc[slot].cellbase);
+  posc[lid] = st.posc[i];
+  velrho[lid] = st.velrho[i];
+}
+
+// Raw import (checkpoint restore): inverse of k_export_raw.
+__global__ void k_import_raw(int n, const int32_t *__restrict__ cell,
+                             const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
+                             const uint8_t *__restrict__ type, const int32_t *__restrict__ group,
+                             int slot, uint32_t id_base, const CaseConst *__restrict__ cc,
+                             int nbits, State st, uint32_t *__restrict__ keys, int dst0) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const CaseConst &C = cc[slot];
+  uint8_t code = type[i] == 0 ? 0 : (group && group[i] >= 0 ? (uint8_t)(2 + group[i]) : 1);
+  int d = dst0 + i;
+  keys[d] = cell[i] < 0 ? key_out(nbits) : 2u * (C.cellbase + (uint32_t)cell[i]) + (code ? 1u : 0u);
+  st.posc[d] = posc[i];
+  st.velrho[d] = velrho[i];
+  st.id[d] = id_base + (uint32_t)i;
+  st.cid[d] = (uint16_t)slot;
+  st.code[d] = code;
+}
+
+// Scatter per-particle float4/float results of the sorted order to original order.
+__global__ void k_scatter_forces(int n, const uint16_t *__restrict__ cid,
+                                 const uint32_t *__restrict__ id, int slot, uint32_t id_base,
+                                 const int *__restrict__ nvalid_p, const float4 *__restrict__ ace,
+                                 const float *__restrict__ mu, float *__restrict__ acc_out,
+                                 float *__restrict__ drho_out, float *__restrict__ mu_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cid[i] != slot) return;
+  const uint32_t lid = id[i] - id_base;
+  const bool valid = i < *nvalid_p;
+  const float4 a = valid ? ace[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (acc_out) {
+    acc_out[3 * lid] = a.x;
+    acc_out[3 * lid + 1] = a.y;
+    acc_out[3 * lid + 2] = a.z;
+  }
+  if (drho_out) drho_out[lid] = a.w;
+  if (mu_out) mu_out[lid] = valid ? mu[i] : 0.f;
+}
+
+// Neighbour count and id fingerprint over the pairs that the interaction
+// evaluates (a in F: b in P; a in B: b in F), same FP32 distance test.
+__device__ __forceinline__ unsigned long long splitmix64_fin(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_pair_stats(int n, const int *__restrict__ nvalid_p,
+                             const uint32_t *__restrict__ keys, State st,
+                             const uint4 *__restrict__ ctab, const CaseConst *__restrict__ cc,
+                             int slot, uint32_t id_base, long long *__restrict__ count,
+                             unsigned long long *__restrict__ hash) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *nvalid_p || st.cid[i] != slot) return;
+  const CaseConst &C = cc[slot];
+  const uint32_t key = keys[i];
+  const bool afluid = (key & 1u) == 0;
+  const int gc = (int)(key >> 1), nx = C.nx, nxy = C.nx * C.ny, M = C.margin;
+  const float4 pa = st.posc[i];
+  long long cnt = 0;
+  unsigned long long h = 0;
+  for (int dz = -M; dz <= M; dz++)
+    for (int dy = -M; dy <= M; dy++)
+      for (int dx = -M; dx <= M; dx++) {
+        const uint4 r = ctab[gc + dz * nxy + dy * nx + dx];
+        const float sx = pa.x - (float)dx * C.csf, sy = pa.y - (float)dy * C.csf,
+                    sz = pa.z - (float)dz * C.csf;
+        for (int part = 0; part < (afluid ? 2 : 1); part++) {
+          const unsigned j0 = part ? r.z : r.x, j1 = part ? r.w : r.y;
+          for (unsigned j = j0; j < j1; j++) {
+            const float4 pb = st.posc[j];
+            const float rx = sx - pb.x, ry = sy - pb.y, rz = sz - pb.z;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            if (r2 < C.r2max && r2 > 0.f) {
+              cnt++;
+              h += splitmix64_fin((unsigned long long)(st.id[j] - id_base));
+            }
+          }
+        }
+      }
+  const uint32_t lid = st.id[i] - id_base;
+  count[lid] = cnt;
+  hash[lid] = h;
+}
+
+// FP64 diagnostics of one case: per-block partials (fixed order), then a
+// single block sums the partials in block order: deterministic.
+__global__ void k_diag_partial(int n, const uint32_t *__restrict__ keys, State st,
+                               const CaseConst *__restrict__ cc, int slot, int nbits,
+                               double *__restrict__ part) {
+  __shared__ double sh[8][256];
+  const CaseConst &C = cc[slot];
+  double v[8] = {0, 0, 0, 0, 0, 0, -1e300, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (st.cid[i] != slot) continue;
+    const uint32_t k = keys[i];
+    if (k == key_dead(nbits)) continue;
+    v[0] += 1.0;  // particle count; total mass = count * m (Eq 14)
+    if (k >= key_out(nbits)) {
+      v[7] += 1.0;
+      continue;
+    }
+    if (st.code[i] != 0) continue;
+    const float4 q = st.velrho[i];
+    const double m = C.m_d;
+    v[1] += 0.5 * m * ((double)q.x * q.x + (double)q.y * q.y + (double)q.z * q.z);
+    v[2] += m * q.x;
+    v[3] += m * q.y;
+    v[4] += m * q.z;
+    v[5] += 1.0;
+    int cx, cy, cz;
+    decode_cell((k >> 1) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+    double x = C.origin[0] + cx * C.cs + (double)st.posc[i].x;
+    if (x > v[6]) v[6] = x;
+  }
+  for (int q = 0; q < 8; q++) sh[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 8; q++) {
+        if (q == 6)
+          sh[q][threadIdx.x] = fmax(sh[q][threadIdx.x], sh[q][threadIdx.x + s]);
+        else
+          sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) part[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_diag_final(int nparts, const double *__restrict__ part, double *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double v[8] = {0, 0, 0, 0, 0, 0, -1e300, 0};
+  for (int b = 0; b < nparts; b++)
+    for (int q = 0; q < 8; q++) {
+      if (q == 6)
+        v[q] = fmax(v[q], part[b * 8 + q]);
+      else
+        v[q] += part[b * 8 + q];
+    }
+  for (int q = 0; q < 8; q++) out[q] = v[q];
+}
+
+// Release: particles of a slot get the dead key and leave at the next sort.
+__global__ void k_release(int n, const uint16_t *__restrict__ cid, int slot, int nbits,
+                          uint32_t *__restrict__ keys) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && cid[i] == slot) keys[i] = key_dead(nbits);
+}
+
+// ---- launchers ---------------------------------------------------------------
+
+static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+void launch_upload(int n, const double *pos, const float *vel, const float *rho,
+                   const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
+                   const CaseConst *cc, CaseDyn *dyn, int nbits, State st, uint32_t *keys,
+                   int dst0, cudaStream_t s) {
+  if (n > 0)
+    k_upload<<<nblk(n, 256), 256, 0, s>>>(n, pos, vel, rho, type, group, slot, id_base, cc,
+                                          dyn, nbits, st, keys, dst0);
+}
+
+void launch_reorder(int n, const uint32_t *perm, const float4 *posc, const float4 *velrho,
+                    const uint32_t *id, const uint16_t *cid, const uint8_t *code, State dst,
+                    const CaseConst *cc, cudaStream_t s) {
+  if (n > 0)
+    k_reorder<<<nblk(n, 256), 256, 0, s>>>(n, perm, posc, velrho, id, cid, code, dst, cc);
+}
+
+void launch_mark(int n, const uint32_t *keys, uint4 *ctab, int64_t ncells, uint32_t kout,
+                 int *nvalid, cudaStream_t s) {
+  cudaMemsetAsync(ctab, 0, sizeof(uint4) * (size_t)ncells, s);
+  cudaMemsetAsync(nvalid, 0, sizeof(int), s);
+  if (n > 0) k_mark<<<nblk(n, 256), 256, 0, s>>>(n, keys, ctab, kout, nvalid);
+}
+
+void launch_interact(int margin, int n, const int *nvalid, const uint32_t *keys,
+                     const float4 *posc, const float4 *velrho, const uint16_t *cid,
+                     const uint4 *ctab, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
+                     float *mu, int want_dt, int block, cudaStream_t s) {
+  if (n <= 0) return;
+  (void)block;
+  const int b = 128;
+  if (margin == 1)
+    k_interact<1><<<nblk(n, b), b, 0, s>>>(n, nvalid, keys, posc, velrho, cid, ctab, cc, dyn,
+                                           ace, mu, want_dt);
+  else
+    k_interact<2><<<nblk(n, b), b, 0, s>>>(n, nvalid, keys, posc, velrho, cid, ctab, cc, dyn,
+                                           ace, mu, want_dt);
+}
+
+void launch_dt(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t s) {
+  k_dt<<<nblk(ncases, 64), 64, 0, s>>>(ncases, cc, dyn);
+}
+
+void launch_end_step(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t s) {
+  k_end_step<<<nblk(ncases, 64), 64, 0, s>>>(ncases, cc, dyn);
+}
+
+void launch_predictor(int n, const uint32_t *keys_in, State src, const float4 *ace,
+                      const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
+                      float4 *velrho_out, uint32_t *keys_out, cudaStream_t s) {
+  if (n > 0)
+    k_predictor<<<nblk(n, 256), 256, 0, s>>>(n, keys_in, src, ace, cc, dyn, nbits, posc_out,
+                                             velrho_out, keys_out);
+}
+
+void launch_corrector(int n, const uint32_t *perm2, const uint32_t *keys_half,
+                      const uint32_t *keys_n, State sn, State x, const float4 *ace,
+                      const CaseConst *cc, CaseDyn *dyn, int nbits, uint32_t *keys_next,
+                      cudaStream_t s) {
+  if (n > 0)
+    k_corrector<<<nblk(n, 256), 256, 0, s>>>(n, perm2, keys_half, keys_n, sn, x, ace, cc, dyn,
+                                             nbits, keys_next);
+}
+
+void launch_export(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
+                   uint32_t id_base, int nbits, double *pos, float *vel, float *rho,
+                   float *press, cudaStream_t s) {
+  if (n > 0)
+    k_export<<<nblk(n, 256), 256, 0, s>>>(n, keys, st, cc, slot, id_base, nbits, pos, vel, rho,
+                                          press);
+}
+
+void launch_export_raw(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
+                       uint32_t id_base, int nbits, int32_t *cell, float4 *posc,
+                       float4 *velrho, cudaStream_t s) {
+  if (n > 0)
+    k_export_raw<<<nblk(n, 256), 256, 0, s>>>(n, keys, st, cc, slot, id_base, nbits, cell, posc,
+                                              velrho);
+}
+
+void launch_import_raw(int n, const int32_t *cell, const float4 *posc, const float4 *velrho,
+                       const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
+                       const CaseConst *cc, int nbits, State st, uint32_t *keys, int dst0,
+                       cudaStream_t s) {
+  if (n > 0)
+    k_import_raw<<<nblk(n, 256), 256, 0, s>>>(n, cell, posc, velrho, type, group, slot, id_base,
+                                              cc, nbits, st, keys, dst0);
+}
+
+void launch_scatter_forces(int n, const uint16_t *cid, const uint32_t *id, int slot,
+                           uint32_t id_base, const int *nvalid, const float4 *ace,
+                           const float *mu, float *acc_out, float *drho_out, float *mu_out,
+                           cudaStream_t s) {
+  if (n > 0)
+    k_scatter_forces<<<nblk(n, 256), 256, 0, s>>>(n, cid, id, slot, id_base, nvalid, ace, mu,
+                                                  acc_out, drho_out, mu_out);
+}
+
+void launch_pair_stats(int n, const int *nvalid, const uint32_t *keys, State st,
+                       const uint4 *ctab, const CaseConst *cc, int slot, uint32_t id_base,
+                       long long *count, unsigned long long *hash, cudaStream_t s) {
+  if (n > 0)
+    k_pair_stats<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, ctab, cc, slot, id_base,
+                                              count, hash);
+}
+
+void launch_diag(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
+                 int nbits, double *part, int nparts, double *out, cudaStream_t s) {
+  k_diag_partial<<<nparts, 256, 0, s>>>(n, keys, st, cc, slot, nbits, part);
+  k_diag_final<<<1, 32, 0, s>>>(nparts, part, out);
+}
+
+void launch_release(int n, const uint16_t *cid, int slot, int nbits, uint32_t *keys,
+                    cudaStream_t s) {
+  if (n > 0) k_release<<<nblk(n, 256), 256, 0, s>>>(n, cid, slot, nbits, keys);
+}
+
+}  // namespace sph

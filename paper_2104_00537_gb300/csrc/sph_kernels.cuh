@@ -1,0 +1,51 @@
+// sph_kernels.cuh -- host launchers of the kernels in sph_kernels.cu.
+#pragma once
+#include "sph_internal.cuh"
+
+namespace sph {
+
+void launch_upload(int n, const double *pos, const float *vel, const float *rho,
+                   const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
+                   const CaseConst *cc, CaseDyn *dyn, int nbits, State st, uint32_t *keys,
+                   int dst0, cudaStream_t s);
+void launch_reorder(int n, const uint32_t *perm, const float4 *posc, const float4 *velrho,
+                    const uint32_t *id, const uint16_t *cid, const uint8_t *code, State dst,
+                    const CaseConst *cc, cudaStream_t s);
+void launch_mark(int n, const uint32_t *keys, uint4 *ctab, int64_t ncells, uint32_t kout,
+                 int *nvalid, cudaStream_t s);
+void launch_interact(int margin, int n, const int *nvalid, const uint32_t *keys,
+                     const float4 *posc, const float4 *velrho, const uint16_t *cid,
+                     const uint4 *ctab, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
+                     float *mu, int want_dt, int block, cudaStream_t s);
+void launch_dt(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t s);
+void launch_end_step(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t s);
+void launch_predictor(int n, const uint32_t *keys_in, State src, const float4 *ace,
+                      const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
+                      float4 *velrho_out, uint32_t *keys_out, cudaStream_t s);
+void launch_corrector(int n, const uint32_t *perm2, const uint32_t *keys_half,
+                      const uint32_t *keys_n, State sn, State x, const float4 *ace,
+                      const CaseConst *cc, CaseDyn *dyn, int nbits, uint32_t *keys_next,
+                      cudaStream_t s);
+void launch_export(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
+                   uint32_t id_base, int nbits, double *pos, float *vel, float *rho,
+                   float *press, cudaStream_t s);
+void launch_export_raw(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
+                       uint32_t id_base, int nbits, int32_t *cell, float4 *posc,
+                       float4 *velrho, cudaStream_t s);
+void launch_import_raw(int n, const int32_t *cell, const float4 *posc, const float4 *velrho,
+                       const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
+                       const CaseConst *cc, int nbits, State st, uint32_t *keys, int dst0,
+                       cudaStream_t s);
+void launch_scatter_forces(int n, const uint16_t *cid, const uint32_t *id, int slot,
+                           uint32_t id_base, const int *nvalid, const float4 *ace,
+                           const float *mu, float *acc_out, float *drho_out, float *mu_out,
+                           cudaStream_t s);
+void launch_pair_stats(int n, const int *nvalid, const uint32_t *keys, State st,
+                       const uint4 *ctab, const CaseConst *cc, int slot, uint32_t id_base,
+                       long long *count, unsigned long long *hash, cudaStream_t s);
+void launch_diag(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
+                 int nbits, double *part, int nparts, double *out, cudaStream_t s);
+void launch_release(int n, const uint16_t *cid, int slot, int nbits, uint32_t *keys,
+                    cudaStream_t s);
+
+}  // namespace sph

@@ -1,0 +1,331 @@
+"""GPU (sm_103a, through the C ABI) versus the FP64 oracle, element by element.
+
+Tolerances (FP32 path against FP64): cell order and neighbour pair sets
+bit-exact; one interaction evaluation within 1e-4 of max|.| per result; after
+100 Symplectic steps of the 8,000-particle dam break the front within 0.5 dp
+and the kinetic energy within 1 %; mass exactly constant.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_00537_gb300 import cases, sph
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def c0():
+    return cases.dam_break(0.02)
+
+
+def rel_err(gpu, ref):
+    scale = np.abs(ref).max()
+    return float(np.abs(np.asarray(gpu, np.float64) - ref).max() / max(scale, 1e-300))
+
+
+def oracle_eval(case, st):
+    """Oracle interaction on the GPU's own state (same input numbers)."""
+    return oracle.interact(case.params, st["pos"], st["vel"].astype(np.float64),
+                           st["rho"].astype(np.float64), case.ptype)
+
+
+def n_ambiguous(case, pos):
+    """Evaluated pairs within 1e-6 (relative) of the cut-off: FP32 and FP64
+    may legitimately disagree on these (their kernel weight is ~1e-18)."""
+    both, inside, amb = pi_pair_sets(case, pos)
+    return int(amb.sum())
+
+
+def check_eval(case, eng, icase=0):
+    st = eng.get_state(icase)
+    g = eng.eval_forces(icase)
+    acc, drho, mu, npairs = oracle_eval(case, st)
+    f = case.ptype == 0
+    assert abs(g["pairs"] - npairs) <= n_ambiguous(case, st["pos"])
+    assert rel_err(g["acc"][f], acc[f]) < TOL
+    assert rel_err(g["drho"], drho) < TOL
+    assert rel_err(g["mumax"][f], mu[f]) < TOL
+    assert np.all(g["acc"][~f] == 0)
+    dt = oracle.time_step(case.params, acc, mu, case.ptype)
+    assert abs(g["dt"] - dt) < TOL * dt
+    return g, (acc, drho, mu)
+
+
+# ---- neighbour list ------------------------------------------------------------
+
+@pytest.mark.parametrize("cell_mode", [0, 1])
+def test_sorted_order_is_bit_exact(c0, cell_mode):
+    case = cases.dam_break(0.02, cell_mode=cell_mode)
+    eng = sph.Engine.create(case)
+    ids, cells, ninside = eng.order()
+    order, inside = oracle.sort_order(case.params, case.pos, case.ptype)
+    assert ninside == inside == case.n
+    assert np.array_equal(ids, order)
+    ocell = oracle.cells(case.params, case.pos)
+    assert np.array_equal(cells, ocell[order])
+    eng.destroy()
+
+
+def pi_pair_sets(case, pos):
+    """Per particle: pairs evaluated by the interaction (a in F: b in P; a in B:
+    b in F), and the pairs within 1e-6 (relative) of the cut-off."""
+    from scipy.spatial import cKDTree
+    h = case.params["h"]
+    R2 = 4 * h * h
+    tree = cKDTree(pos)
+    pairs = tree.query_pairs(2 * h * (1 + 1e-5), output_type="ndarray")
+    d = pos[pairs[:, 0]] - pos[pairs[:, 1]]
+    r2 = np.einsum("ij,ij->i", d, d)
+    both = np.concatenate([pairs, pairs[:, ::-1]])
+    r2b = np.concatenate([r2, r2])
+    fa = case.ptype[both[:, 0]] == 0
+    fb = case.ptype[both[:, 1]] == 0
+    evaluated = fa | fb
+    both, r2b = both[evaluated], r2b[evaluated]
+    amb = np.abs(r2b - R2) < 1e-6 * R2
+    inside = (r2b < R2) & (r2b > 0)
+    return both, inside, amb
+
+
+def mix(z):
+    z = np.asarray(z, np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+@pytest.mark.parametrize("cell_mode", [0, 1])
+def test_pair_sets_are_bit_exact(cell_mode):
+    case = cases.dam_break(0.02, cell_mode=cell_mode)
+    eng = sph.Engine.create(case)
+    cnt, hsh = eng.pair_stats()
+    pos = eng.get_state()["pos"]
+    both, inside, amb = pi_pair_sets(case, pos)
+    n = case.n
+    sure = inside & ~amb
+    ref_cnt = np.bincount(both[sure, 0], minlength=n)
+    ref_hash = np.zeros(n, np.uint64)
+    with np.errstate(over="ignore"):
+        np.add.at(ref_hash, both[sure, 0], mix(both[sure, 1]))
+    namb = np.bincount(both[amb, 0], minlength=n)
+    clean = namb == 0
+    assert np.array_equal(cnt[clean], ref_cnt[clean])
+    assert np.array_equal(hsh[clean], ref_hash[clean])
+    # particles with a neighbour within 1e-6 of the cut-off: the GPU set must be
+    # the sure set plus a subset of the ambiguous pairs
+    for a in np.where(~clean)[0]:
+        extra = both[amb & (both[:, 0] == a), 1]
+        ok = False
+        for m in range(1 << len(extra)):
+            sel = [extra[k] for k in range(len(extra)) if m >> k & 1]
+            with np.errstate(over="ignore"):
+                hh = ref_hash[a] + (mix(np.array(sel)).sum(dtype=np.uint64) if sel else np.uint64(0))
+            if cnt[a] == ref_cnt[a] + len(sel) and hsh[a] == hh:
+                ok = True
+                break
+        assert ok, a
+    print("ambiguous pairs: %d of %d" % (int(amb.sum()), int(inside.sum())))
+    eng.destroy()
+
+
+# ---- particle interaction ----------------------------------------------------
+
+@pytest.mark.parametrize("cell_mode", [0, 1])
+def test_one_evaluation_at_rest(c0, cell_mode):
+    case = cases.dam_break(0.02, cell_mode=cell_mode)
+    eng = sph.Engine.create(case)
+    check_eval(case, eng)
+    eng.destroy()
+
+
+def test_one_evaluation_in_motion(c0):
+    """After 60 steps the column moves: viscosity and DDT terms are active."""
+    eng = sph.Engine.create(c0)
+    eng.step(60)
+    g, (acc, drho, mu) = check_eval(c0, eng)
+    assert np.abs(mu).max() > 0
+    eng.destroy()
+
+
+def test_one_evaluation_ragged_sizes():
+    """Random clouds of awkward sizes (not multiples of any tile)."""
+    from tests.lattice import random_cloud
+    for n, seed in ((1, 1), (31, 2), (257, 3), (2049, 4)):
+        c = random_cloud(N=n, L=0.08 * (n / 257) ** (1 / 3) + 0.01, seed=seed)
+        c.ptype[::5] = 1
+        c.vel = c.vel.astype(np.float32).astype(np.float64)
+        c.rho = c.rho.astype(np.float32).astype(np.float64)
+        eng = sph.Engine.create(c)
+        st = eng.get_state()
+        g = eng.eval_forces()
+        acc, drho, mu, npairs = oracle_eval(c, st)
+        assert abs(g["pairs"] - npairs) <= n_ambiguous(c, st["pos"])
+        if npairs:
+            f = c.ptype == 0
+            assert rel_err(g["acc"][f], acc[f]) < TOL
+            assert rel_err(g["drho"], drho) < TOL
+        eng.destroy()
+
+
+# ---- whole steps -----------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def c0_100(c0):
+    o = oracle.OracleState(c0)
+    o.step(100)
+    return o
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_dam_break_100_steps(c0, c0_100, use_graph):
+    eng = sph.Engine.create(c0)
+    eng.set_options(use_graph=use_graph)
+    m0 = eng.stats()["mass"]
+    eng.step(100)
+    s = eng.stats()
+    st = eng.get_state()
+    o = c0_100
+    od = o.diag()
+    dp = c0.params["dp"]
+    assert s["step"] == 100
+    assert abs(s["t"] - o.t.value) < 1e-3 * o.t.value
+    assert abs(s["front"] - od["front"]) < 0.5 * dp
+    assert abs(s["ke"] - od["ke"]) < 0.01 * od["ke"]
+    assert s["mass"] == m0 == od["mass"]
+    assert np.abs(st["pos"] - o.pos).max() < 0.5 * dp
+    assert s["n_out"] == 0 and s["flags"] == 0
+    eng.destroy()
+
+
+def test_determinism(c0):
+    a = sph.Engine.create(c0)
+    b = sph.Engine.create(c0)
+    a.step(30)
+    b.step(30)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("pos", "vel", "rho"):
+        assert np.array_equal(sa[k], sb[k])
+    assert a.stats()["interactions"] == b.stats()["interactions"]
+
+
+def test_free_fall_gpu():
+    c = cases.free_particle()
+    eng = sph.Engine.create(c)
+    eng.step(40)
+    st = eng.get_state()
+    t = st["t"]
+    g = np.array(c.params["gravity"])
+    exact = c.pos[0] + c.vel[0] * t + 0.5 * g * t * t
+    assert np.abs(st["pos"][0] - exact).max() < 1e-7
+    assert np.abs(st["vel"][0] - (c.vel[0] + g * t)).max() < 1e-5
+    dt = c.params["cfl"] * min(np.sqrt(c.params["h"] / 9.81), c.params["h"] / c.params["cs0"])
+    assert abs(st["last_dt"] - dt) < 1e-6 * dt
+
+
+def test_moving_boundary_and_sloshing_parity():
+    c = cases.sloshing_tank(3000, 0.3, 0.03, 1.2)
+    eng = sph.Engine.create(c)
+    eng.step(20)
+    st = eng.get_state()
+    o = oracle.OracleState(c)
+    o.step(20)
+    b = c.ptype == 1
+    m = c.motions[0]
+    t = st["t"]
+    assert abs(t - o.t.value) < 1e-4 * t
+    np.testing.assert_allclose(st["pos"][b, 0] - c.pos[b, 0], m["amp"] * np.sin(m["omega"] * t),
+                               atol=1e-6)
+    assert np.abs(st["pos"] - o.pos).max() < 0.01 * c.params["dp"]
+    eng.destroy()
+
+
+def test_out_of_domain_particle_is_frozen():
+    """A particle shot out of the domain is frozen, keeps its mass, and the
+    quota error fires when max_out is exceeded."""
+    c = cases.dam_break(0.04)
+    f = np.where(c.ptype == 0)[0][-1]
+    c.pos[f] = (0.8, 0.3, c.params["domain_max"][2] - 0.004)   # alone, near the top
+    c.vel[f] = (0.0, 0.0, 5.0)
+    eng = sph.Engine.create(c)
+    eng.step(3)
+    s = eng.stats()
+    o = oracle.OracleState(c)
+    o.step(3)
+    assert s["n_out"] == o.diag()["n_out"] >= 1
+    assert s["mass"] == o.diag()["mass"]
+    c.params["max_out"] = 0
+    eng2 = sph.Engine.create(c)
+    with pytest.raises(sph.SphError) as ei:
+        eng2.step(3)
+    assert ei.value.code == -5
+
+
+def test_nan_input_is_reported():
+    c = cases.dam_break(0.04)
+    c.rho[3] = np.nan
+    eng = sph.Engine.create(c)
+    with pytest.raises(sph.SphError) as ei:
+        eng.step(1)
+    assert ei.value.code == -4
+
+
+def test_dt_min_is_reported():
+    c = cases.dam_break(0.04, dt_min=1.0)
+    eng = sph.Engine.create(c)
+    with pytest.raises(sph.SphError) as ei:
+        eng.step(1)
+    assert ei.value.code == -4
+
+
+def test_raw_checkpoint_resume_is_bit_exact(c0):
+    a = sph.Engine.create(c0)
+    a.step(10)
+    raw = a.get_raw()
+    b = sph.Engine.from_raw(c0, raw)
+    a.step(15)
+    b.step(15)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("pos", "vel", "rho"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert sa["t"] == sb["t"] and sa["step"] == sb["step"] == 25
+
+
+def test_batch_equals_alone():
+    cs = [cases.dam_break(0.04, seed=1), cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
+          cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
+    bat = sph.Engine.batch(cs)
+    bat.step(12)
+    for i, c in enumerate(cs):
+        e = sph.Engine.create(c)
+        e.step(12)
+        sa, sb = e.get_state(), bat.get_state(i)
+        for k in ("pos", "vel", "rho"):
+            assert np.array_equal(sa[k], sb[k]), (i, k)
+        assert sa["t"] == sb["t"]
+        assert e.stats()["interactions"] == bat.stats(i)["interactions"]
+        e.destroy()
+
+
+def test_pool_mix_equals_alone():
+    ca = cases.dam_break(0.04, seed=5)
+    cb = cases.sloshing_tank(2500, 0.3, 0.03, 1.1, seed=6)
+    pool = sph.Engine.pool(200000, 2000000, 8)
+    sa = pool.admit(ca, t_end=1.0)
+    pool.pool_step(5)
+    sb = pool.admit(cb, t_end=1.0)   # admitted while case a runs
+    pool.pool_step(7)
+    pool.release(sa)                  # a leaves; b keeps running
+    pool.pool_step(3)
+    ea = sph.Engine.create(ca)
+    ea.step(12)
+    eb = sph.Engine.create(cb)
+    eb.step(10)
+    st = pool.get_state(sb)
+    ref = eb.get_state()
+    for k in ("pos", "vel", "rho"):
+        assert np.array_equal(st[k], ref[k]), k
+    assert pool.usage()["cases"] == 1
