@@ -248,7 +248,9 @@ def test_out_of_domain_particle_is_frozen():
     quota error fires when max_out is exceeded."""
     c = cases.dam_break(0.04)
     f = np.where(c.ptype == 0)[0][-1]
-    c.pos[f] = (0.8, 0.3, c.params["domain_max"][2] - 0.004)   # alone, near the top
+    origin, cs, nc, margin = oracle.grid(c.params)
+    ztop = origin[2] + (nc[2] - margin) * cs          # upper edge of the in-domain cells
+    c.pos[f] = (0.8, 0.3, ztop - 0.004)               # alone, just below it
     c.vel[f] = (0.0, 0.0, 5.0)
     eng = sph.Engine.create(c)
     eng.step(3)
