@@ -211,6 +211,32 @@ int sph_pool_usage(sph_engine e, int64_t *particles_used, int64_t *cells_used,
 /* sph_destroy: release all device memory of the engine. */
 void sph_destroy(sph_engine e);
 
+/* ---- allocation-free cell-key sort ------------------------------------------
+ * The paper has no counterpart of this call; it exists for callers that may
+ * not let a library allocate device memory (a host program that owns the
+ * whole device-memory budget, or a loop that cannot accept the device
+ * synchronisation that cudaMalloc/cudaFree may cause).
+ *
+ * sph_sort_cell_keys_static: stable sort of n 32-bit keys (only the low nbits
+ * bits are significant) -- the sort the neighbour list uses.  keys_in [n]
+ * (read), keys_out [n] and perm_out [n] (written; perm_out[i] = index in
+ * keys_in of the i-th smallest key, ties in input order) are caller-owned
+ * DEVICE pointers; work is queued on `stream` (cudaStream_t, NULL = default
+ * stream) and the call returns without synchronising.
+ * It calls no cudaMalloc/cudaFree: its scratch is one fixed array of about
+ * 4.3 MB in the library's device data, present on every GPU that loads the
+ * library until the process exits.  n above SPH_SORT_STATIC_MAX_KEYS is
+ * rejected with SPH_ERR_ARG.  The first call on a device looks up that
+ * array's device address (with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array: two
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race and corrupt each other's results; serialise them.  No scratch
+ * content carries over between calls. */
+#define SPH_SORT_STATIC_MAX_KEYS 524288
+int sph_sort_cell_keys_static(const uint32_t *keys_in, uint32_t *keys_out,
+                              uint32_t *perm_out, int64_t n, int32_t nbits,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

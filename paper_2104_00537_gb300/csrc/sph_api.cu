@@ -135,6 +135,8 @@ inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
+void sph::set_last_error(const std::string &msg) { g_err = msg; }
+
 struct sph_engine_t {
   cudaStream_t s = nullptr;
   bool own_stream = false;

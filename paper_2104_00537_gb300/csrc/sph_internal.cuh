@@ -13,6 +13,8 @@
 // key yields the neighbour-list order of Sect. 5.1 for all cases at once.
 #pragma once
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace sph {
@@ -70,6 +72,9 @@ struct State {
   uint16_t *cid;
   uint8_t *code;
 };
+
+// Sets the message returned by sph_last_error() (defined in sph_api.cu).
+void set_last_error(const std::string &msg);
 
 // ---- launchers (defined in the .cu files) --------------------------------
 size_t radix_sort_temp_bytes(int64_t n);

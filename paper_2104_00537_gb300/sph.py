@@ -16,6 +16,7 @@ from . import build as _build
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 SPH_OK = 0
+SORT_STATIC_MAX_KEYS = 524288  # SPH_SORT_STATIC_MAX_KEYS of include/sph.h
 ERRORS = {-1: "SPH_ERR_ARG", -2: "SPH_ERR_OOM", -3: "SPH_ERR_CUDA", -4: "SPH_ERR_UNSTABLE",
           -5: "SPH_ERR_DOMAIN", -6: "SPH_ERR_TIMEOUT", -7: "SPH_ERR_BUSY", -8: "SPH_ERR_STATE"}
 
