@@ -140,7 +140,7 @@ def cells(params: dict, pos):
 
 
 def sort_order(params: dict, pos, ptype, out=None, prev_order=None):
-    """Neighbour-list order (stable by (cell, is_boundary)); returns (order, n_inside)."""
+    """Neighbour-list order (stable by (is_boundary, cell)); returns (order, n_inside)."""
     pos = np.ascontiguousarray(pos, np.float64)
     ptype = np.ascontiguousarray(ptype, np.uint8)
     n = len(pos)

@@ -20,6 +20,9 @@
  *  - V_b = m_b / rho_b; all particles have m = rho0 dp^3.
  *  - the neighbour list is rebuilt before both interaction evaluations of a
  *    Symplectic step; the step size comes from the first evaluation.
+ *  - neighbour-list order: fluid particles sorted by cell, then boundary
+ *    particles sorted by cell, ties in the previous order (Sect. 5.1 only
+ *    says particles are sorted by the cell they belong to).
  *  - |f_a| in Eq 35 is the full fluid acceleration (gravity included) and
  *    Eq 35's v.r is v_ab.r_ab over the same neighbours as the interaction.
  *  - boundary density is clamped to >= rho0 after each update (optional).
@@ -111,7 +114,7 @@ int orc_cells(const orc_params *p, int64_t n, const double *pos, int64_t *cell) 
 }
 
 typedef struct {
-  int64_t key;  /* 2 * cell + is_boundary, out-of-domain: INT64_MAX */
+  int64_t key;  /* is_boundary * 2^40 + cell, out-of-domain: INT64_MAX */
   int64_t rank; /* position in the previous order (makes the sort stable) */
   int64_t id;
 } sort_item;
@@ -141,7 +144,7 @@ int64_t orc_sort(const orc_params *p, int64_t n, const double *pos,
     if (cell[a] < 0 || (out && out[a])) {
       it[r].key = INT64_MAX;
     } else {
-      it[r].key = 2 * cell[a] + (type[a] ? 1 : 0);
+      it[r].key = (type[a] ? ((int64_t)1 << 40) : 0) + cell[a];
       inside++;
     }
   }
@@ -180,7 +183,11 @@ static int cl_build(const orc_params *p, int64_t n, const double *pos,
   orc_cells(p, n, pos, cl->cellof);
   for (int64_t a = 0; a < n; a++)
     if (out && out[a]) cl->cellof[a] = -1;
-  int64_t inside = orc_sort(p, n, pos, type, out, NULL, cl->order);
+  /* the lookup structure groups particles by cell only (type ignored) */
+  (void)type;
+  uint8_t *notype = (uint8_t *)calloc((size_t)(n ? n : 1), 1);
+  int64_t inside = notype ? orc_sort(p, n, pos, notype, out, NULL, cl->order) : -1;
+  free(notype);
   if (inside < 0) return -1;
   /* counting pass, then prefix sum gives the first index of every cell */
   for (int64_t r = 0; r < inside; r++) cl->start[cl->cellof[cl->order[r]] + 1]++;

@@ -53,8 +53,9 @@ int orc_grid(const orc_params *p, double origin[3], double *cs, int64_t nc[3],
              int32_t *margin);
 /* Linear cell id of each particle, -1 if outside the domain. */
 int orc_cells(const orc_params *p, int64_t n, const double *pos, int64_t *cell);
-/* Neighbour-list order: stable sort of prev_order by (cell, is_boundary);
- * out-of-domain particles last.  Returns the number of in-domain particles. */
+/* Neighbour-list order: stable sort of prev_order by (is_boundary, cell):
+ * fluid particles by cell, then boundary particles by cell, out-of-domain
+ * particles last.  Returns the number of in-domain particles. */
 int64_t orc_sort(const orc_params *p, int64_t n, const double *pos,
                  const uint8_t *type, const uint8_t *out,
                  const int64_t *prev_order, int64_t *order);

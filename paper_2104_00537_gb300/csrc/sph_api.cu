@@ -120,6 +120,7 @@ void fill_const(const sph_case_params &p, const sph_particles &parts, const Grid
   C.g[1] = (float)p.gravity.y;
   C.g[2] = (float)p.gravity.z;
   C.cs0f = (float)p.cs0;
+  C.inv_csf = (float)(1.0 / g.cs);
 }
 
 struct Slot {
@@ -161,7 +162,9 @@ struct sph_engine_t {
   uint32_t *perm1 = nullptr, *perm2 = nullptr;
   float4 *ace = nullptr;
   float *mu = nullptr;
-  uint4 *ctab = nullptr;
+  uint32_t *cstart = nullptr;  // cell start table, 2 * (cap_cells + 1) words
+  uint32_t *cells_tmp = nullptr;
+  float *press = nullptr;
   int *nvalid = nullptr;
   void *sort_tmp = nullptr;
   double *diag = nullptr;
@@ -206,11 +209,7 @@ struct sph_engine_t {
 
 namespace {
 
-int bits_for(int64_t cap_cells) {
-  int b = 1;
-  while (((int64_t(1) << b) - 2) < 2 * cap_cells) b++;
-  return b;
-}
+int bits_for(int64_t cap_cells) { return key_bits(cap_cells); }
 
 int allocate(sph_engine e) {
   const int64_t N = e->cap_p > 0 ? e->cap_p : 1;
@@ -237,7 +236,9 @@ int allocate(sph_engine e) {
   e->perm2 = (uint32_t *)A(4 * N);
   e->ace = (float4 *)A(16 * N);
   e->mu = (float *)A(4 * N);
-  e->ctab = (uint4 *)A(16 * e->cap_cells);
+  e->cstart = (uint32_t *)A(4 * (2 * e->cap_cells + 2));
+  e->cells_tmp = (uint32_t *)A(4 * cells_temp_words(e->cap_cells));
+  e->press = (float *)A(4 * N);
   e->nvalid = (int *)A(16);
   e->sort_tmp = A(radix_sort_temp_bytes(N));
   e->diag = (double *)A(sizeof(double) * (8 * 1024 + 8));
@@ -389,27 +390,30 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
   const int n = (int)e->n_phys;
   const int nl = (int)(e->n_phys - e->n_dead);
   State &X = e->S[0], &Y = e->S[1], &Z = e->S[2];
-  const uint32_t kout = key_out(e->nbits);
   cudaStream_t s = e->s;
   // NL on state n
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
-  launch_reorder(nl, e->perm1, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->dconst, s);
-  launch_mark(nl, e->keysB, e->ctab, e->cap_cells, kout, e->nvalid, s);
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->press,
+                 e->dconst, e->nbits, s);
+  launch_cells(nl, e->keysB, e->cstart, e->cap_cells, e->nbits, e->nvalid, e->cells_tmp, s);
   // PI on state n, time step, predictor
   if (ev) cudaEventRecord(ev[0], s);
-  launch_interact(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, Y.cid, e->ctab,
-                  e->dconst, e->ddyn, e->ace, nullptr, 1, e->opt.pi_block, s);
+  launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
+                  e->press, Y.cid, e->cstart, e->cap_cells, e->nbits, e->dconst, e->ddyn, e->ace,
+                  nullptr, 1, s);
   if (ev) cudaEventRecord(ev[1], s);
   launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
   launch_predictor(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
                    e->keysC, s);
   // NL on state n+1/2 (id/cid/code of Z are those of Y)
   radix_sort(e->keysC, e->keysD, e->perm2, nl, e->nbits, e->sort_tmp, s);
-  launch_reorder(nl, e->perm2, Z.posc, Z.velrho, Y.id, Y.cid, Y.code, X, e->dconst, s);
-  launch_mark(nl, e->keysD, e->ctab, e->cap_cells, kout, e->nvalid + 1, s);
+  launch_reorder(nl, e->perm2, e->keysD, Z.posc, Z.velrho, Y.id, Y.cid, Y.code, X, e->press,
+                 e->dconst, e->nbits, s);
+  launch_cells(nl, e->keysD, e->cstart, e->cap_cells, e->nbits, e->nvalid + 1, e->cells_tmp, s);
   if (ev) cudaEventRecord(ev[2], s);
-  launch_interact(e->margin, nl, e->nvalid + 1, e->keysD, X.posc, X.velrho, X.cid, e->ctab,
-                  e->dconst, e->ddyn, e->ace, nullptr, 0, e->opt.pi_block, s);
+  launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid + 1, e->keysD, X.posc, X.velrho,
+                  e->press, X.cid, e->cstart, e->cap_cells, e->nbits, e->dconst, e->ddyn, e->ace,
+                  nullptr, 0, s);
   if (ev) cudaEventRecord(ev[3], s);
   launch_corrector(nl, e->perm2, e->keysD, e->keysB, Y, X, e->ace, e->dconst, e->ddyn, e->nbits,
                    e->keysA, s);
@@ -422,8 +426,9 @@ void enqueue_nl(sph_engine e) {
   const int nl = (int)(e->n_phys - e->n_dead);
   State &X = e->S[0], &Y = e->S[1];
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, e->s);
-  launch_reorder(nl, e->perm1, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->dconst, e->s);
-  launch_mark(nl, e->keysB, e->ctab, e->cap_cells, key_out(e->nbits), e->nvalid, e->s);
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->press,
+                 e->dconst, e->nbits, e->s);
+  launch_cells(nl, e->keysB, e->cstart, e->cap_cells, e->nbits, e->nvalid, e->cells_tmp, e->s);
 }
 
 int check_flags(sph_engine e) {
@@ -473,8 +478,10 @@ int sph_batch_create(const sph_case_params *params, const sph_particles *parts, 
 
 int sph_set_options(sph_engine e, const sph_options *opt) {
   if (!e || !opt) return fail(SPH_ERR_ARG, "null argument");
-  if (opt->pi_block != 0 && (opt->pi_block < 32 || opt->pi_block > 1024 || opt->pi_block % 32))
-    return fail(SPH_ERR_ARG, "pi_block must be a multiple of 32 in [32, 1024]");
+  if (opt->pi_block != 0 && opt->pi_block != 128)
+    return fail(SPH_ERR_ARG, "pi_block must be 0 (default) or 128");
+  if (opt->pi_variant < 0 || opt->pi_variant > 1)
+    return fail(SPH_ERR_ARG, "pi_variant must be 0 (compacted) or 1 (inline)");
   e->opt = *opt;
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
   e->gexec = nullptr;
@@ -515,7 +522,9 @@ int sph_step(sph_engine e, int64_t nsteps) {
     }
     for (; k < nsteps; k++) CUDA_TRY(cudaGraphLaunch(e->gexec, e->s));
   }
-  const int64_t per_step = 6 * std::max(1, (e->nbits + 7) / 8) + 10;
+  // per step: 2 sorts (3 kernels per 8-bit pass), 2 reorders, 2 cell tables
+  // (4 kernels), 2 interactions, dt, predictor, corrector, end of step
+  const int64_t per_step = 6 * std::max(1, (e->nbits + 7) / 8) + 2 + 8 + 2 + 4;
   e->kernel_launches += per_step * nsteps;
   for (; k < nsteps; k++) {
     enqueue_step(e, timing ? &e->evs[4 * k] : nullptr);
@@ -669,7 +678,7 @@ int sph_get_raw(sph_engine e, int32_t icase, void *buf, size_t *bytes) {
   for (int64_t i = 0; i < np && j < n; i++) {
     if (cid[i] != icase || keys[i] == kdead) continue;
     oid[j] = ids[i];
-    ocell[j] = keys[i] >= kout ? -1 : (int32_t)((keys[i] >> 1) - cb);
+    ocell[j] = keys[i] >= kout ? -1 : (int32_t)(key_cell(keys[i], e->nbits) - cb);
     std::memcpy(opc + j, &pc[i], 16);
     std::memcpy(ovr + j, &vr[i], 16);
     j++;
@@ -763,8 +772,9 @@ int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho, float 
   enqueue_nl(e);
   const int nl = (int)(e->n_phys - e->n_dead);
   State &Y = e->S[1];
-  launch_interact(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, Y.cid, e->ctab,
-                  e->dconst, e->ddyn, e->ace, e->mu, 1, e->opt.pi_block, e->s);
+  launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
+                  e->press, Y.cid, e->cstart, e->cap_cells, e->nbits, e->dconst, e->ddyn, e->ace,
+                  e->mu, 1, e->s);
   char *p = e->io;
   float *d_acc = (float *)p;
   p += align256(12 * n);
@@ -817,7 +827,7 @@ int sph_get_order(sph_engine e, int32_t icase, int64_t *ids, int64_t *cells, int
   for (int64_t i = 0; i < np - e->n_dead; i++) {
     if (cid[i] != icase || keys[i] == kdead) continue;
     if (ids) ids[j] = id[i];
-    if (cells) cells[j] = keys[i] >= kout ? -1 : (int64_t)((keys[i] >> 1) - cb);
+    if (cells) cells[j] = keys[i] >= kout ? -1 : (int64_t)(key_cell(keys[i], e->nbits) - cb);
     inside += keys[i] < kout;
     j++;
   }
@@ -836,8 +846,8 @@ int sph_pair_stats(sph_engine e, int32_t icase, int64_t *count, uint64_t *hash) 
   unsigned long long *d_hash = (unsigned long long *)p;
   CUDA_TRY(cudaMemsetAsync(d_count, 0, 8 * n, e->s));
   CUDA_TRY(cudaMemsetAsync(d_hash, 0, 8 * n, e->s));
-  launch_pair_stats((int)(e->n_phys - e->n_dead), e->nvalid, e->keysB, e->S[1], e->ctab,
-                    e->dconst, icase, 0, d_count, d_hash, e->s);
+  launch_pair_stats((int)(e->n_phys - e->n_dead), e->nvalid, e->keysB, e->S[1], e->cstart,
+                    e->cap_cells, e->nbits, e->dconst, icase, 0, d_count, d_hash, e->s);
   CUDA_TRY(cudaGetLastError());
   if (count) CUDA_TRY(cudaMemcpyAsync(count, d_count, 8 * n, cudaMemcpyDeviceToHost, e->s));
   if (hash) CUDA_TRY(cudaMemcpyAsync(hash, d_hash, 8 * n, cudaMemcpyDeviceToHost, e->s));

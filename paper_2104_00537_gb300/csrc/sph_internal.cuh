@@ -2,15 +2,19 @@
 // libsph.so (not part of the public ABI).
 //
 // Particle state lives in structure-of-arrays form, sorted by cell key:
-//   posc   float4  {offset x, y, z inside the cell, pressure P (Eq 28)}
+//   posc   float4  {offset x, y, z inside the cell, cell x index (as float)}
 //   velrho float4  {v x, y, z, rho}
-//   id     uint32  particle index in upload order
+//   press  float   pressure P of Eq 28 (written by the reorder)
+//   id     uint32  particle index within its case (caller's order)
 //   cid    uint16  case slot of the particle
 //   code   uint8   0 fluid, 1 fixed boundary, 2 + g moving boundary group g
-// The key of a particle is 2 * (cellbase of its case + linear cell) + is_boundary,
-// with linear cell = (cz * ny + cy) * nx + cx; out-of-domain particles carry
-// key_out(nbits) and released particles key_dead(nbits), so a stable sort by
-// key yields the neighbour-list order of Sect. 5.1 for all cases at once.
+// The key of an in-domain particle is (is_boundary << (nbits-1)) | global cell,
+// global cell = cellbase of its case + (cz * ny + cy) * nx + cx, so a stable
+// sort by key puts all fluid particles first, in cell order, then all boundary
+// particles in cell order (Sect. 5.1: particles sorted by the cell they belong
+// to); out-of-domain particles carry key_out(nbits), released ones key_dead.
+// cstart[t * (cells + 1) + c] is the first sorted index of type t with cell
+// >= c, so every run of consecutive cells of one type is one index range.
 #pragma once
 #include <cstdint>
 #include <string>
@@ -42,6 +46,8 @@ struct CaseConst {
   float kddt;   // 2 delta h cs0
   float g[3];
   float cs0f;
+  float inv_csf;  // 1 / cs
+  float pad3_;
 };
 
 // Mutable per-case values, updated on the device during a step.
@@ -63,6 +69,18 @@ constexpr uint32_t kFloatInfBits = 0x7f800000u;
 
 __host__ __device__ inline uint32_t key_out(int nbits) { return (1u << nbits) - 2u; }
 __host__ __device__ inline uint32_t key_dead(int nbits) { return (1u << nbits) - 1u; }
+__host__ __device__ inline uint32_t key_bbit(int nbits) { return 1u << (nbits - 1); }
+__host__ __device__ inline uint32_t key_make(uint32_t gcell, bool boundary, int nbits) {
+  return gcell | (boundary ? key_bbit(nbits) : 0u);
+}
+__host__ __device__ inline uint32_t key_cell(uint32_t k, int nbits) { return k & (key_bbit(nbits) - 1u); }
+__host__ __device__ inline bool key_boundary(uint32_t k, int nbits) { return (k & key_bbit(nbits)) != 0u; }
+// smallest nbits with 2^(nbits-1) >= cells + 2, so that key_out exceeds every boundary key
+__host__ __device__ inline int key_bits(int64_t cells) {
+  int b = 2;
+  while ((int64_t(1) << (b - 1)) < cells + 2) b++;
+  return b;
+}
 
 // Device arrays of one state buffer.
 struct State {

@@ -2,7 +2,7 @@
 // paper, arXiv 2104.00537) for sm_103a:
 //   k_upload      host particles -> (cell, float offset) state + keys
 //   k_reorder     gather the state into cell order, Tait pressure (Eq 28)
-//   k_mark        cell begin/end table (Sect. 5.1)
+//   k_mark + k_fill_*   cell start table of the sorted order (Sect. 5.1)
 //   k_interact    Wendland C2 pair loop: momentum with artificial viscosity
 //                 (Eq 21-22), continuity with density diffusion (Eq 15,
 //                 17-18), dynamic boundaries (Eq 36), Eq 35 reductions
@@ -39,8 +39,8 @@ __device__ __forceinline__ float below(float cs) {  // largest float < cs
   return __int_as_float(__float_as_int(cs) - 1);
 }
 
-// New (cell, offset) after adding disp (FP64) to the offset of axis k.
-// Returns the cell shift; off_out is the new float offset in [0, cs).
+// New offset after adding disp (FP64) to a float offset in [0, cs); returns
+// the cell shift.
 __device__ __forceinline__ int shift_axis(float off, double disp, const CaseConst &C,
                                           float &off_out) {
   double x = (double)off + disp;
@@ -79,7 +79,7 @@ __global__ void k_upload(int n, const double *__restrict__ pos, const float *__r
     double f = floor(rel / C.cs);
     int nk = k == 0 ? C.nx : (k == 1 ? C.ny : C.nz);
     if (!(f >= C.margin && f < nk - C.margin)) inside = false;
-    c[k] = (int)f;
+    c[k] = inside ? (int)f : 0;
     float o = (float)(rel - f * C.cs);
     if (o >= C.csf) o = below(C.csf);
     if (o < 0.f) o = 0.f;
@@ -92,8 +92,8 @@ __global__ void k_upload(int n, const double *__restrict__ pos, const float *__r
   uint32_t key;
   if (inside) {
     uint32_t lin = ((uint32_t)c[2] * C.ny + c[1]) * C.nx + c[0];
-    key = 2u * (C.cellbase + lin) + (code ? 1u : 0u);
-    st.posc[d] = make_float4(off[0], off[1], off[2], 0.f);
+    key = key_make(C.cellbase + lin, code != 0, nbits);
+    st.posc[d] = make_float4(off[0], off[1], off[2], (float)c[0]);
   } else {
     key = key_out(nbits);
     // frozen particles keep a float position relative to the grid origin
@@ -111,50 +111,140 @@ __global__ void k_upload(int n, const double *__restrict__ pos, const float *__r
 
 // ---- reorder + equation of state ------------------------------------------
 
+// dst[i] = src[perm[i]]; the cell x index goes to posc.w and the Tait
+// pressure (Eq 28) to press[i].
 __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
+                          const uint32_t *__restrict__ keys_sorted,
                           const float4 *__restrict__ posc_src,
                           const float4 *__restrict__ velrho_src,
                           const uint32_t *__restrict__ id_src,
                           const uint16_t *__restrict__ cid_src,
                           const uint8_t *__restrict__ code_src, State dst,
-                          const CaseConst *__restrict__ cc) {
+                          float *__restrict__ press, const CaseConst *__restrict__ cc,
+                          int nbits) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t p = perm[i];
   float4 pc = posc_src[p];
   float4 vr = velrho_src[p];
   uint16_t cidx = cid_src[p];
-  pc.w = tait_pressure(cc[cidx], vr.w);
+  const CaseConst &C = cc[cidx];
+  const uint32_t k = keys_sorted[i];
+  if (k < key_out(nbits)) {
+    const uint32_t lin = key_cell(k, nbits) - C.cellbase;
+    pc.w = (float)(lin % (uint32_t)C.nx);
+  }
   dst.posc[i] = pc;
   dst.velrho[i] = vr;
   dst.id[i] = id_src[p];
   dst.cid[i] = cidx;
   dst.code[i] = code_src[p];
+  press[i] = tait_pressure(C, vr.w);
 }
 
-// ---- cell table --------------------------------------------------------------
+// ---- cell start table --------------------------------------------------------
 
-// ctab[c] = {first fluid, end fluid, first boundary, end boundary} of cell c
-// (global cell index); empty ranges stay {0,0}.  nvalid = first out/dead key.
-__global__ void k_mark(int n, const uint32_t *__restrict__ keys, uint4 *__restrict__ ctab,
-                       uint32_t kout, int *__restrict__ nvalid) {
+// cstart (pre-filled with 0xff): first sorted index of every non-empty
+// (type, cell); cstart[cap1-1] = end of the fluid segment, cstart[2 cap1-1] =
+// nvalid (first out-of-domain / released key).
+__global__ void k_mark(int n, const uint32_t *__restrict__ keys, uint32_t *__restrict__ cstart,
+                       uint32_t cap1, int nbits, int *__restrict__ nvalid) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  uint32_t k = keys[i];
-  if (k >= kout) {
-    if (i == 0 || keys[i - 1] < kout) *nvalid = i;
-    return;
+  const uint32_t k = keys[i], kout = key_out(nbits), bb = key_bbit(nbits);
+  const uint32_t prev = i > 0 ? keys[i - 1] : 0u;
+  if (k >= bb && (i == 0 || prev < bb)) cstart[cap1 - 1] = (uint32_t)i;
+  if (i == n - 1 && k < bb) cstart[cap1 - 1] = (uint32_t)n;
+  if (k >= kout && (i == 0 || prev < kout)) {
+    *nvalid = i;
+    cstart[2 * cap1 - 1] = (uint32_t)i;
   }
-  if (i == n - 1) *nvalid = n;
-  uint32_t c = k >> 1;
-  unsigned *e = reinterpret_cast<unsigned *>(ctab + c) + ((k & 1u) ? 2 : 0);
-  if (i == 0 || keys[i - 1] != k) e[0] = (unsigned)i;
-  if (i == n - 1 || keys[i + 1] != k) e[1] = (unsigned)(i + 1);
+  if (i == n - 1 && k < kout) {
+    *nvalid = n;
+    cstart[2 * cap1 - 1] = (uint32_t)n;
+  }
+  if (k < kout && (i == 0 || prev != k))
+    cstart[(key_boundary(k, nbits) ? cap1 : 0u) + key_cell(k, nbits)] = (uint32_t)i;
+}
+
+// Suffix minimum over cstart (empty cells take the start of the next
+// non-empty one): per-block pass, carry pass, apply pass.
+constexpr int kFillThreads = 1024, kFillItems = 4, kFillBlock = kFillThreads * kFillItems;
+
+__device__ __forceinline__ uint32_t warp_suffix_min(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane + o < 32) v = min(v, y);
+  }
+  return v;
+}
+
+// In place: each block turns its chunk into a chunk-local suffix minimum and
+// writes the chunk minimum to bmin.
+__global__ void __launch_bounds__(kFillThreads)
+k_fill_block(uint32_t *__restrict__ a, int64_t len, uint32_t *__restrict__ bmin) {
+  __shared__ uint32_t wmin[32];
+  const int64_t base = (int64_t)blockIdx.x * kFillBlock + (int64_t)threadIdx.x * kFillItems;
+  uint32_t v[kFillItems];
+  for (int q = 0; q < kFillItems; q++) v[q] = base + q < len ? a[base + q] : 0xffffffffu;
+  for (int q = kFillItems - 2; q >= 0; q--) v[q] = min(v[q], v[q + 1]);
+  const uint32_t s = warp_suffix_min(v[0]);  // inclusive suffix over the lanes of this warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wmin[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = wmin[lane];
+    w = warp_suffix_min(w);
+    wmin[lane] = w;  // inclusive suffix over warps
+  }
+  __syncthreads();
+  uint32_t after = 0xffffffffu;  // minimum of everything after this thread's items
+  const uint32_t nxt = __shfl_down_sync(0xffffffffu, s, 1);
+  if (lane < 31) after = nxt;
+  if (warp < 31) after = min(after, wmin[warp + 1]);
+  for (int q = 0; q < kFillItems; q++)
+    if (base + q < len) a[base + q] = min(v[q], after);
+  if (threadIdx.x == 0) bmin[blockIdx.x] = wmin[0];
+}
+
+// Single block: bmin[b] <- min over the blocks after b (exclusive suffix min).
+__global__ void __launch_bounds__(1024) k_fill_carry(uint32_t *__restrict__ bmin, int nb) {
+  __shared__ uint32_t wmin[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0xffffffffu;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int end = nb; end > 0; end -= 1024) {  // chunks of 1024 from the end
+    const int idx = end - 1024 + (int)threadIdx.x;
+    const uint32_t v = idx >= 0 ? bmin[idx] : 0xffffffffu;
+    const uint32_t s = warp_suffix_min(v);
+    if (lane == 0) wmin[warp] = s;
+    __syncthreads();
+    if (warp == 0) wmin[lane] = warp_suffix_min(wmin[lane]);
+    __syncthreads();
+    uint32_t after = carry;
+    const uint32_t nxt = __shfl_down_sync(0xffffffffu, s, 1);
+    if (lane < 31) after = min(after, nxt);
+    if (warp < 31) after = min(after, wmin[warp + 1]);
+    const uint32_t chunk_min = wmin[0];
+    __syncthreads();
+    if (idx >= 0) bmin[idx] = after;
+    if (threadIdx.x == 0) carry = min(carry, chunk_min);
+    __syncthreads();
+  }
+}
+
+__global__ void k_fill_apply(uint32_t *__restrict__ a, int64_t len,
+                             const uint32_t *__restrict__ carry) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  const uint32_t c = carry[i / kFillBlock];
+  if (c < a[i]) a[i] = c;
 }
 
 // ---- particle interaction ----------------------------------------------------
 
-// Per-case warp-aggregated reductions: pair count (sum) and Eq 35 minimum.
 // npairs: all pairs of a; nfb: pairs with a in F, b in B; nbf: pairs with a in B.
 __device__ __forceinline__ void reduce_case(int cidx, bool has, unsigned npairs, unsigned nfb,
                                             unsigned nbf, unsigned dtbits, bool bad,
@@ -184,142 +274,212 @@ __device__ __forceinline__ void reduce_case(int cidx, bool has, unsigned npairs,
   }
 }
 
-// One thread per particle a in cell order; the 27 (cells of 2h) or 125
-// (cells of h) neighbour cells are visited cell by cell, fluid range first.
-// r_ab = (offset_a - offset_b) - (cell shift) * cs, all in FP32.
-template <int M>
+// Gap between an offset o in [0, cs) and the slab of cells at relative index d.
+__device__ __forceinline__ float slab_gap(int d, float o, float cs) {
+  return d > 0 ? fmaf((float)d, cs, -o) : (d < 0 ? o - (float)(d + 1) * cs : 0.f);
+}
+
+// Per-particle accumulators of one interaction evaluation.
+struct Acc {
+  float ax, ay, az;  // sum t^3 [(Pa+Pb)/rho_b + kv min(v.r,0)/((r^2+eta^2)(rho_a+rho_b))] r_ab
+  float s1;          // sum t^3 / rho_b v_ab.r_ab            (continuity, Eq 15 / 36)
+  float s2;          // sum_{b in F} t^3 / rho_b (rho_b - rho_a)  (density diffusion, Eq 17-18)
+  float mur;         // max |v_ab.r_ab| / (r^2 + eta^2)      (Eq 35)
+  unsigned cnt, cntb;
+};
+
+// Pair terms for a fluid particle a and a neighbour b (ddt: b in F).
+// grad_a W_ab = cw t^3 r_ab with t = 1 - r/(2h) (derivative of Eq 11).
+__device__ __forceinline__ void pair_fluid(const float4 &va, float Pa, float kv, float hih,
+                                           float eta2, float rx, float ry, float rz, float r2,
+                                           const float4 &vb, float Pb, bool ddt, Acc &A) {
+  const float rr = r2 * rsqrtf(r2);
+  const float t = fmaf(-hih, rr, 1.f);
+  const float t3 = t * t * t;
+  const float vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
+  const float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
+  const float ib = __fdividef(1.f, vb.w);
+  const float w = t3 * ib;
+  A.s1 = fmaf(w, vr, A.s1);
+  if (ddt) A.s2 = fmaf(w, vb.w - va.w, A.s2);
+  const float sab = va.w + vb.w;
+  const float ie = __fdividef(1.f, (r2 + eta2) * sab);
+  const float mu = vr * ie * sab;  // v_ab.r_ab / (r^2 + eta^2)
+  A.mur = fmaxf(A.mur, fabsf(mu));
+  const float pi = fminf(vr, 0.f) * ie;
+  const float u = fmaf(kv, pi, (Pa + Pb) * ib);
+  const float s = t3 * u;
+  A.ax = fmaf(s, rx, A.ax);
+  A.ay = fmaf(s, ry, A.ay);
+  A.az = fmaf(s, rz, A.az);
+}
+
+// Boundary particle a: continuity over fluid neighbours only (Eq 36).
+__device__ __forceinline__ void pair_boundary(const float4 &va, float hih, float rx, float ry,
+                                              float rz, float r2, const float4 &vb, Acc &A) {
+  const float rr = r2 * rsqrtf(r2);
+  const float t = fmaf(-hih, rr, 1.f);
+  const float t3 = t * t * t;
+  const float vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
+  const float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
+  A.s1 = fmaf(t3 * __fdividef(1.f, vb.w), vr, A.s1);
+}
+
+// One thread per particle a in sorted order (all fluid targets first, then
+// boundary targets, so warps rarely mix the two).  The (2M+1)^2 rows of
+// neighbour cells (fixed dy, dz) are visited in lock-step by the warp; in a
+// row each lane keeps only the cells that its own sphere of radius 2h can
+// reach, which form one contiguous index range per particle type.
+//
+// VARIANT 0 (compacted): the candidates of a row are tested in chunks of 32
+//   (r^2 < (2h)^2 only); the hits form a 32-bit mask per lane and the pair
+//   terms then run over the set bits, so no lane idles on a rejected
+//   candidate while another computes a pair.
+// VARIANT 1 (inline): test and pair terms in one loop (divergent).
+template <int M, int VARIANT>
 __global__ void __launch_bounds__(128)
 k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
            const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
-           const uint16_t *__restrict__ cid, const uint4 *__restrict__ ctab,
+           const float *__restrict__ press, const uint16_t *__restrict__ cid,
+           const uint32_t *__restrict__ cstart, uint32_t cap1, int nbits,
            const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
            float4 *__restrict__ ace, float *__restrict__ mu_out, int want_dt) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int nvalid = *nvalid_p;
-  bool has = i < nvalid;
-  int cidx = i < n ? (int)cid[i] : -1;
-  unsigned npairs = 0, nfb = 0, nbf = 0;
-  unsigned dtbits = kFloatInfBits;
-  bool bad = false;
-  if (has) {
-    const CaseConst &C = cc[cidx];
-    const uint32_t key = keys[i];
-    const bool afluid = (key & 1u) == 0;
-    const int gc = (int)(key >> 1);
-    const int nx = C.nx, nxy = C.nx * C.ny;
-    const float csf = C.csf, r2max = C.r2max, eta2 = C.eta2, hih = C.half_inv_h;
-    const float4 pa = posc[i];
-    const float4 va = velrho[i];
-    const float kv = C.kvisc * va.w;
-    const bool ddt = C.ddt != 0;
-    float ax = 0.f, ay = 0.f, az = 0.f, s1 = 0.f, s2 = 0.f, mur = 0.f;
-    unsigned cnt = 0, cntb = 0;
+  const unsigned full = 0xffffffffu;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvalid = *nvalid_p;
+  const bool has = i < nvalid;
+  const int cidx = i < n ? (int)cid[i] : 0;
+  const CaseConst &C = cc[cidx];
+  const uint32_t key = has ? keys[i] : 0u;
+  const bool afluid = has && !key_boundary(key, nbits);
+  const int gc = (int)key_cell(key, nbits);
+  const int nx = C.nx, nxy = C.nx * C.ny;
+  const float cs = C.csf, ics = C.inv_csf, r2max = C.r2max, eta2 = C.eta2, hih = C.half_inv_h;
+  const float r2prune = r2max * 1.0001f;  // conservative: pruning never drops a pair
+  const float4 pa = has ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 va = has ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+  const float Pa = has ? press[i] : 0.f;
+  const float kv = C.kvisc * va.w;
+  const bool ddt_on = C.ddt != 0;
+  Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
+  constexpr int W = 2 * M + 1;
+
 #pragma unroll 1
-    for (int dz = -M; dz <= M; dz++) {
+  for (int row = 0; row < W * W; row++) {
+    const int dy = row % W - M, dz = row / W - M;
+    const float gy = slab_gap(dy, pa.y, cs), gz = slab_gap(dz, pa.z, cs);
+    const float d2 = fmaf(gy, gy, gz * gz);
+    int loF = 0, hiF = 0, loB = 0, hiB = 0;
+    if (has && d2 < r2prune) {
+      const float L = sqrtf(r2prune - d2);
+      const int kx0 = max(-M, (int)floorf((pa.x - L) * ics));
+      const int kx1 = min(M, (int)floorf((pa.x + L) * ics));
+      const int c0 = gc + dz * nxy + dy * nx + kx0;
+      const int c1 = gc + dz * nxy + dy * nx + kx1 + 1;
+      loF = (int)cstart[c0];
+      hiF = (int)cstart[c1];
+      if (afluid) {
+        loB = (int)cstart[cap1 + c0];
+        hiB = (int)cstart[cap1 + c1];
+      }
+    }
+    const float sy = fmaf(-(float)dy, cs, pa.y), sz = fmaf(-(float)dz, cs, pa.z);
 #pragma unroll 1
-      for (int dy = -M; dy <= M; dy++) {
-        const int row = gc + dz * nxy + dy * nx;
-        const float sy = pa.y - (float)dy * csf;
-        const float sz = pa.z - (float)dz * csf;
+    for (int part = 0; part < 2; part++) {  // fluid neighbours, then boundary neighbours
+      const int lo = part ? loB : loF;
+      const int len = (part ? hiB : hiF) - lo;
+      const int maxlen = (int)__reduce_max_sync(full, (unsigned)max(len, 0));
+      const bool ddt = ddt_on && part == 0;
 #pragma unroll 1
-        for (int dx = -M; dx <= M; dx++) {
-          const uint4 r = ctab[row + dx];
-          const float sx = pa.x - (float)dx * csf;
-          // fluid neighbours
-#pragma unroll 1
-          for (unsigned j = r.x; j < r.y; j++) {
-            const float4 pb = posc[j];
-            const float rx = sx - pb.x, ry = sy - pb.y, rz = sz - pb.z;
-            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            if (r2 < r2max && r2 > 0.f) {
+      for (int base = 0; base < maxlen; base += 32) {
+        if (VARIANT == 0) {
+          unsigned m = 0u;
+          const int nk = min(32, maxlen - base);
+#pragma unroll 4
+          for (int k = 0; k < nk; k++) {
+            if (base + k < len) {
+              const float4 pb = posc[lo + base + k];
+              const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+              const float ry = sy - pb.y, rz = sz - pb.z;
+              const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+              if (r2 < r2max && r2 > 0.f) m |= 1u << k;
+            }
+          }
+          while (__any_sync(full, m != 0u)) {
+            if (m) {
+              const int k = __ffs(m) - 1;
+              m &= m - 1u;
+              const int j = lo + base + k;
+              const float4 pb = posc[j];
               const float4 vb = velrho[j];
-              const float rr = r2 * rsqrtf(r2);
-              const float t = fmaf(-hih, rr, 1.f);
-              const float t3 = t * t * t;
-              const float vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
-              const float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
-              const float ib = __fdividef(1.f, vb.w);
-              const float w = t3 * ib;
-              s1 = fmaf(w, vr, s1);
-              cnt++;
+              const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+              const float ry = sy - pb.y, rz = sz - pb.z;
+              const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
               if (afluid) {
-                if (ddt) s2 = fmaf(w, vb.w - va.w, s2);
-                const float e = r2 + eta2;
-                const float sab = va.w + vb.w;
-                const float ie = __fdividef(1.f, e * sab);
-                const float mu = vr * ie * sab;  // v_ab.r_ab / (r^2 + eta^2)
-                mur = fmaxf(mur, fabsf(mu));
-                const float pi = fminf(vr, 0.f) * ie;
-                const float u = fmaf(kv, pi, (pa.w + pb.w) * ib);
-                const float s = t3 * u;
-                ax = fmaf(s, rx, ax);
-                ay = fmaf(s, ry, ay);
-                az = fmaf(s, rz, az);
+                pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt, A);
+                if (part) A.cntb++; else A.cnt++;
+              } else {
+                pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
+                A.cnt++;
               }
             }
           }
-          if (afluid) {
-            // boundary neighbours (no density diffusion, Eq 17 sums over F)
+        } else {
+          const int nk = min(32, maxlen - base);
 #pragma unroll 1
-            for (unsigned j = r.z; j < r.w; j++) {
+          for (int k = 0; k < nk; k++) {
+            if (base + k < len) {
+              const int j = lo + base + k;
               const float4 pb = posc[j];
-              const float rx = sx - pb.x, ry = sy - pb.y, rz = sz - pb.z;
+              const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+              const float ry = sy - pb.y, rz = sz - pb.z;
               const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
               if (r2 < r2max && r2 > 0.f) {
                 const float4 vb = velrho[j];
-                const float rr = r2 * rsqrtf(r2);
-                const float t = fmaf(-hih, rr, 1.f);
-                const float t3 = t * t * t;
-                const float vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
-                const float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
-                const float ib = __fdividef(1.f, vb.w);
-                const float w = t3 * ib;
-                s1 = fmaf(w, vr, s1);
-                cntb++;
-                const float e = r2 + eta2;
-                const float sab = va.w + vb.w;
-                const float ie = __fdividef(1.f, e * sab);
-                const float mu = vr * ie * sab;
-                mur = fmaxf(mur, fabsf(mu));
-                const float pi = fminf(vr, 0.f) * ie;
-                const float u = fmaf(kv, pi, (pa.w + pb.w) * ib);
-                const float s = t3 * u;
-                ax = fmaf(s, rx, ax);
-                ay = fmaf(s, ry, ay);
-                az = fmaf(s, rz, az);
+                if (afluid) {
+                  pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt, A);
+                  if (part) A.cntb++; else A.cnt++;
+                } else {
+                  pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
+                  A.cnt++;
+                }
               }
             }
           }
         }
       }
     }
-    npairs = cnt + cntb;
-    nfb = afluid ? cntb : 0u;
-    nbf = afluid ? 0u : cnt;
+  }
+
+  unsigned npairs = 0, nfb = 0, nbf = 0, dtbits = kFloatInfBits;
+  bool bad = false;
+  if (has) {
+    npairs = A.cnt + A.cntb;
+    nfb = afluid ? A.cntb : 0u;
+    nbf = afluid ? 0u : A.cnt;
     const float mcw = C.m * C.cw;
     float4 out;
-    float mumax = C.h * mur;
+    float mumax = C.h * A.mur;
     if (afluid) {
       const float ca = -mcw / va.w;
-      out.x = fmaf(ca, ax, C.g[0]);
-      out.y = fmaf(ca, ay, C.g[1]);
-      out.z = fmaf(ca, az, C.g[2]);
-      out.w = mcw * (va.w * s1 - C.kddt * s2);
+      out.x = fmaf(ca, A.ax, C.g[0]);
+      out.y = fmaf(ca, A.ay, C.g[1]);
+      out.z = fmaf(ca, A.az, C.g[2]);
+      out.w = mcw * (va.w * A.s1 - C.kddt * A.s2);
       const float f = sqrtf(out.x * out.x + out.y * out.y + out.z * out.z);
       const float dtf = f > 0.f ? sqrtf(C.h / f) : INFINITY;
       const float dtcv = C.h / (C.cs0f + mumax);
-      float dta = fminf(dtf, dtcv);
       bad = !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) && isfinite(out.w));
-      if (want_dt) dtbits = __float_as_uint(dta);
+      if (want_dt) dtbits = __float_as_uint(fminf(dtf, dtcv));
     } else {
-      out = make_float4(0.f, 0.f, 0.f, mcw * va.w * s1);
+      out = make_float4(0.f, 0.f, 0.f, mcw * va.w * A.s1);
       mumax = 0.f;
       bad = !isfinite(out.w);
     }
     ace[i] = out;
     if (mu_out) mu_out[i] = mumax;
   }
-  reduce_case(cidx, has, npairs, nfb, nbf, dtbits, bad, dyn);
+  reduce_case(i < n ? cidx : -1, has, npairs, nfb, nbf, dtbits, bad, dyn);
 }
 
 // ---- time step and motion ----------------------------------------------------
@@ -372,13 +532,13 @@ __global__ void k_end_step(int ncases, const CaseConst *__restrict__ cc,
 
 // ---- Symplectic predictor / corrector ------------------------------------------
 
-// Moves a particle by disp (FP64, per axis) from cell key k; returns the new
-// key (or key_out) and writes the new offsets.
+// Moves a particle by disp (FP64, per axis) from the cell of key k; returns
+// the new key (or key_out) and writes the new offsets.
 __device__ __forceinline__ uint32_t move_particle(uint32_t k, const float4 &p, const double disp[3],
                                                   const CaseConst &C, bool boundary, int nbits,
                                                   float4 &pout, bool &left) {
   int cx, cy, cz;
-  decode_cell((k >> 1) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+  decode_cell(key_cell(k, nbits) - C.cellbase, C.nx, C.ny, cx, cy, cz);
   float ox, oy, oz;
   cx += shift_axis(p.x, disp[0], C, ox);
   cy += shift_axis(p.y, disp[1], C, oy);
@@ -391,9 +551,9 @@ __device__ __forceinline__ uint32_t move_particle(uint32_t k, const float4 &p, c
                        (float)(cz * C.cs + oz), 0.f);
     return key_out(nbits);
   }
-  pout = make_float4(ox, oy, oz, 0.f);
+  pout = make_float4(ox, oy, oz, (float)cx);
   uint32_t lin = ((uint32_t)cz * C.ny + cy) * C.nx + cx;
-  return 2u * (C.cellbase + lin) + (boundary ? 1u : 0u);
+  return key_make(C.cellbase + lin, boundary, nbits);
 }
 
 __global__ void k_predictor(int n, const uint32_t *__restrict__ keys_in, State src,
@@ -448,7 +608,7 @@ __global__ void k_predictor(int n, const uint32_t *__restrict__ keys_in, State s
   if (left) {
     // left the domain at the half step: frozen at state n
     int cx, cy, cz;
-    decode_cell((k >> 1) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+    decode_cell(key_cell(k, nbits) - C.cellbase, C.nx, C.ny, cx, cy, cz);
     pn = make_float4((float)(cx * C.cs + p.x), (float)(cy * C.cs + p.y),
                      (float)(cz * C.cs + p.z), 0.f);
     vn = v;
@@ -521,6 +681,21 @@ __global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
 
 // ---- read-out ------------------------------------------------------------------
 
+__device__ __forceinline__ void cell_position(uint32_t k, const float4 &p, const CaseConst &C,
+                                              int nbits, double &x, double &y, double &z) {
+  if (k >= key_out(nbits)) {
+    x = (double)p.x;
+    y = (double)p.y;
+    z = (double)p.z;
+  } else {
+    int cx, cy, cz;
+    decode_cell(key_cell(k, nbits) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+    x = cx * C.cs + (double)p.x;
+    y = cy * C.cs + (double)p.y;
+    z = cz * C.cs + (double)p.z;
+  }
+}
+
 __global__ void k_export(int n, const uint32_t *__restrict__ keys, State st,
                          const CaseConst *__restrict__ cc, int slot, uint32_t id_base,
                          int nbits, double *__restrict__ pos, float *__restrict__ vel,
@@ -534,17 +709,7 @@ __global__ void k_export(int n, const uint32_t *__restrict__ keys, State st,
   const float4 p = st.posc[i];
   const float4 v = st.velrho[i];
   double x, y, z;
-  if (k >= key_out(nbits)) {
-    x = (double)p.x;
-    y = (double)p.y;
-    z = (double)p.z;
-  } else {
-    int cx, cy, cz;
-    decode_cell((k >> 1) - C.cellbase, C.nx, C.ny, cx, cy, cz);
-    x = cx * C.cs + (double)p.x;
-    y = cy * C.cs + (double)p.y;
-    z = cz * C.cs + (double)p.z;
-  }
+  cell_position(k, p, C, nbits, x, y, z);
   if (pos) {
     pos[3 * lid] = C.origin[0] + x;
     pos[3 * lid + 1] = C.origin[1] + y;
@@ -559,22 +724,7 @@ __global__ void k_export(int n, const uint32_t *__restrict__ keys, State st,
   if (press) press[lid] = tait_pressure(C, v.w);
 }
 
-// Raw export: cell (or -1) and the float4 pair, in original order.
-__global__ void k_export_raw(int n, const uint32_t *__restrict__ keys, State st,
-                             const CaseConst *__restrict__ cc, int slot, uint32_t id_base,
-                             int nbits, int32_t *__restrict__ cell, float4 *__restrict__ posc,
-                             float4 *__restrict__ velrho) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || st.cid[i] != slot) return;
-  const uint32_t k = keys[i];
-  if (k == key_dead(nbits)) return;
-  const uint32_t lid = st.id[i] - id_base;
-  cell[lid] = k >= key_out(nbits) ? -1 : (int32_t)((k >> 1) - cc[slot].cellbase);
-  posc[lid] = st.posc[i];
-  velrho[lid] = st.velrho[i];
-}
-
-// Raw import (checkpoint restore): inverse of k_export_raw.
+// Raw import (checkpoint restore).
 __global__ void k_import_raw(int n, const int32_t *__restrict__ cell,
                              const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
                              const uint8_t *__restrict__ type, const int32_t *__restrict__ group,
@@ -585,7 +735,8 @@ __global__ void k_import_raw(int n, const int32_t *__restrict__ cell,
   const CaseConst &C = cc[slot];
   uint8_t code = type[i] == 0 ? 0 : (group && group[i] >= 0 ? (uint8_t)(2 + group[i]) : 1);
   int d = dst0 + i;
-  keys[d] = cell[i] < 0 ? key_out(nbits) : 2u * (C.cellbase + (uint32_t)cell[i]) + (code ? 1u : 0u);
+  keys[d] = cell[i] < 0 ? key_out(nbits)
+                        : key_make(C.cellbase + (uint32_t)cell[i], code != 0, nbits);
   st.posc[d] = posc[i];
   st.velrho[d] = velrho[i];
   st.id[d] = id_base + (uint32_t)i;
@@ -593,7 +744,7 @@ __global__ void k_import_raw(int n, const int32_t *__restrict__ cell,
   st.code[d] = code;
 }
 
-// Scatter per-particle float4/float results of the sorted order to original order.
+// Scatter per-particle results of the sorted order to the original order.
 __global__ void k_scatter_forces(int n, const uint16_t *__restrict__ cid,
                                  const uint32_t *__restrict__ id, int slot, uint32_t id_base,
                                  const int *__restrict__ nvalid_p, const float4 *__restrict__ ace,
@@ -614,7 +765,8 @@ __global__ void k_scatter_forces(int n, const uint16_t *__restrict__ cid,
 }
 
 // Neighbour count and id fingerprint over the pairs that the interaction
-// evaluates (a in F: b in P; a in B: b in F), same FP32 distance test.
+// evaluates (a in F: b in P; a in B: b in F), with the same FP32 distance
+// test, visiting every cell of the (2M+1)^3 block.
 __device__ __forceinline__ unsigned long long splitmix64_fin(unsigned long long z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
@@ -623,37 +775,36 @@ __device__ __forceinline__ unsigned long long splitmix64_fin(unsigned long long 
 
 __global__ void k_pair_stats(int n, const int *__restrict__ nvalid_p,
                              const uint32_t *__restrict__ keys, State st,
-                             const uint4 *__restrict__ ctab, const CaseConst *__restrict__ cc,
-                             int slot, uint32_t id_base, long long *__restrict__ count,
-                             unsigned long long *__restrict__ hash) {
+                             const uint32_t *__restrict__ cstart, uint32_t cap1, int nbits,
+                             const CaseConst *__restrict__ cc, int slot, uint32_t id_base,
+                             long long *__restrict__ count, unsigned long long *__restrict__ hash) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *nvalid_p || st.cid[i] != slot) return;
   const CaseConst &C = cc[slot];
   const uint32_t key = keys[i];
-  const bool afluid = (key & 1u) == 0;
-  const int gc = (int)(key >> 1), nx = C.nx, nxy = C.nx * C.ny, M = C.margin;
+  const bool afluid = !key_boundary(key, nbits);
+  const int gc = (int)key_cell(key, nbits), nx = C.nx, nxy = C.nx * C.ny, M = C.margin;
   const float4 pa = st.posc[i];
   long long cnt = 0;
   unsigned long long h = 0;
   for (int dz = -M; dz <= M; dz++)
-    for (int dy = -M; dy <= M; dy++)
-      for (int dx = -M; dx <= M; dx++) {
-        const uint4 r = ctab[gc + dz * nxy + dy * nx + dx];
-        const float sx = pa.x - (float)dx * C.csf, sy = pa.y - (float)dy * C.csf,
-                    sz = pa.z - (float)dz * C.csf;
-        for (int part = 0; part < (afluid ? 2 : 1); part++) {
-          const unsigned j0 = part ? r.z : r.x, j1 = part ? r.w : r.y;
-          for (unsigned j = j0; j < j1; j++) {
-            const float4 pb = st.posc[j];
-            const float rx = sx - pb.x, ry = sy - pb.y, rz = sz - pb.z;
-            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            if (r2 < C.r2max && r2 > 0.f) {
-              cnt++;
-              h += splitmix64_fin((unsigned long long)(st.id[j] - id_base));
-            }
+    for (int dy = -M; dy <= M; dy++) {
+      const int c0 = gc + dz * nxy + dy * nx - M, c1 = c0 + 2 * M + 1;
+      const float sy = fmaf(-(float)dy, C.csf, pa.y), sz = fmaf(-(float)dz, C.csf, pa.z);
+      for (int part = 0; part < (afluid ? 2 : 1); part++) {
+        const unsigned j0 = cstart[part * cap1 + c0], j1 = cstart[part * cap1 + c1];
+        for (unsigned j = j0; j < j1; j++) {
+          const float4 pb = st.posc[j];
+          const float rx = fmaf(pa.w - pb.w, C.csf, pa.x - pb.x);
+          const float ry = sy - pb.y, rz = sz - pb.z;
+          const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+          if (r2 < C.r2max && r2 > 0.f) {
+            cnt++;
+            h += splitmix64_fin((unsigned long long)(st.id[j] - id_base));
           }
         }
       }
+    }
   const uint32_t lid = st.id[i] - id_base;
   count[lid] = cnt;
   hash[lid] = h;
@@ -684,9 +835,9 @@ __global__ void k_diag_partial(int n, const uint32_t *__restrict__ keys, State s
     v[3] += m * q.y;
     v[4] += m * q.z;
     v[5] += 1.0;
-    int cx, cy, cz;
-    decode_cell((k >> 1) - C.cellbase, C.nx, C.ny, cx, cy, cz);
-    double x = C.origin[0] + cx * C.cs + (double)st.posc[i].x;
+    double x, y, z;
+    cell_position(k, st.posc[i], C, nbits, x, y, z);
+    x += C.origin[0];
     if (x > v[6]) v[6] = x;
   }
   for (int q = 0; q < 8; q++) sh[q][threadIdx.x] = v[q];
@@ -737,33 +888,59 @@ void launch_upload(int n, const double *pos, const float *vel, const float *rho,
                                           dyn, nbits, st, keys, dst0);
 }
 
-void launch_reorder(int n, const uint32_t *perm, const float4 *posc, const float4 *velrho,
-                    const uint32_t *id, const uint16_t *cid, const uint8_t *code, State dst,
-                    const CaseConst *cc, cudaStream_t s) {
+void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
+                    const float4 *posc, const float4 *velrho, const uint32_t *id,
+                    const uint16_t *cid, const uint8_t *code, State dst, float *press,
+                    const CaseConst *cc, int nbits, cudaStream_t s) {
   if (n > 0)
-    k_reorder<<<nblk(n, 256), 256, 0, s>>>(n, perm, posc, velrho, id, cid, code, dst, cc);
+    k_reorder<<<nblk(n, 256), 256, 0, s>>>(n, perm, keys_sorted, posc, velrho, id, cid, code,
+                                           dst, press, cc, nbits);
 }
 
-void launch_mark(int n, const uint32_t *keys, uint4 *ctab, int64_t ncells, uint32_t kout,
-                 int *nvalid, cudaStream_t s) {
-  cudaMemsetAsync(ctab, 0, sizeof(uint4) * (size_t)ncells, s);
+size_t cells_temp_words(int64_t cap_cells) {
+  return (size_t)((2 * (cap_cells + 1) + kFillBlock - 1) / kFillBlock) + 1;
+}
+
+int launch_cells(int n, const uint32_t *keys, uint32_t *cstart, int64_t cap_cells, int nbits,
+                 int *nvalid, uint32_t *tmp, cudaStream_t s) {
+  const int64_t len = 2 * (cap_cells + 1);
+  const int nb = (int)((len + kFillBlock - 1) / kFillBlock);
   cudaMemsetAsync(nvalid, 0, sizeof(int), s);
-  if (n > 0) k_mark<<<nblk(n, 256), 256, 0, s>>>(n, keys, ctab, kout, nvalid);
+  if (n > 0) {
+    cudaMemsetAsync(cstart, 0xff, sizeof(uint32_t) * (size_t)len, s);
+    k_mark<<<nblk(n, 256), 256, 0, s>>>(n, keys, cstart, (uint32_t)(cap_cells + 1), nbits,
+                                        nvalid);
+  } else {
+    cudaMemsetAsync(cstart, 0, sizeof(uint32_t) * (size_t)len, s);
+  }
+  k_fill_block<<<nb, kFillThreads, 0, s>>>(cstart, len, tmp);
+  k_fill_carry<<<1, 1024, 0, s>>>(tmp, nb);
+  k_fill_apply<<<nblk(len, 256), 256, 0, s>>>(cstart, len, tmp);
+  return n > 0 ? 4 : 3;
 }
 
-void launch_interact(int margin, int n, const int *nvalid, const uint32_t *keys,
-                     const float4 *posc, const float4 *velrho, const uint16_t *cid,
-                     const uint4 *ctab, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
-                     float *mu, int want_dt, int block, cudaStream_t s) {
+void launch_interact(int margin, int variant, int n, const int *nvalid, const uint32_t *keys,
+                     const float4 *posc, const float4 *velrho, const float *press,
+                     const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
+                     const CaseConst *cc, CaseDyn *dyn, float4 *ace, float *mu, int want_dt,
+                     cudaStream_t s) {
   if (n <= 0) return;
-  (void)block;
   const int b = 128;
-  if (margin == 1)
-    k_interact<1><<<nblk(n, b), b, 0, s>>>(n, nvalid, keys, posc, velrho, cid, ctab, cc, dyn,
-                                           ace, mu, want_dt);
-  else
-    k_interact<2><<<nblk(n, b), b, 0, s>>>(n, nvalid, keys, posc, velrho, cid, ctab, cc, dyn,
-                                           ace, mu, want_dt);
+  const uint32_t cap1 = (uint32_t)(cap_cells + 1);
+#define SPH_PI_ARGS                                                                      \
+  n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, mu, want_dt
+  if (margin == 1) {
+    if (variant == 1)
+      k_interact<1, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+    else
+      k_interact<1, 0><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+  } else {
+    if (variant == 1)
+      k_interact<2, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+    else
+      k_interact<2, 0><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+  }
+#undef SPH_PI_ARGS
 }
 
 void launch_dt(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t s) {
@@ -799,14 +976,6 @@ void launch_export(int n, const uint32_t *keys, State st, const CaseConst *cc, i
                                           press);
 }
 
-void launch_export_raw(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
-                       uint32_t id_base, int nbits, int32_t *cell, float4 *posc,
-                       float4 *velrho, cudaStream_t s) {
-  if (n > 0)
-    k_export_raw<<<nblk(n, 256), 256, 0, s>>>(n, keys, st, cc, slot, id_base, nbits, cell, posc,
-                                              velrho);
-}
-
 void launch_import_raw(int n, const int32_t *cell, const float4 *posc, const float4 *velrho,
                        const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
                        const CaseConst *cc, int nbits, State st, uint32_t *keys, int dst0,
@@ -826,11 +995,13 @@ void launch_scatter_forces(int n, const uint16_t *cid, const uint32_t *id, int s
 }
 
 void launch_pair_stats(int n, const int *nvalid, const uint32_t *keys, State st,
-                       const uint4 *ctab, const CaseConst *cc, int slot, uint32_t id_base,
-                       long long *count, unsigned long long *hash, cudaStream_t s) {
+                       const uint32_t *cstart, int64_t cap_cells, int nbits, const CaseConst *cc,
+                       int slot, uint32_t id_base, long long *count, unsigned long long *hash,
+                       cudaStream_t s) {
   if (n > 0)
-    k_pair_stats<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, ctab, cc, slot, id_base,
-                                              count, hash);
+    k_pair_stats<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, cstart,
+                                              (uint32_t)(cap_cells + 1), nbits, cc, slot,
+                                              id_base, count, hash);
 }
 
 void launch_diag(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,

@@ -8,15 +8,20 @@ void launch_upload(int n, const double *pos, const float *vel, const float *rho,
                    const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
                    const CaseConst *cc, CaseDyn *dyn, int nbits, State st, uint32_t *keys,
                    int dst0, cudaStream_t s);
-void launch_reorder(int n, const uint32_t *perm, const float4 *posc, const float4 *velrho,
-                    const uint32_t *id, const uint16_t *cid, const uint8_t *code, State dst,
-                    const CaseConst *cc, cudaStream_t s);
-void launch_mark(int n, const uint32_t *keys, uint4 *ctab, int64_t ncells, uint32_t kout,
-                 int *nvalid, cudaStream_t s);
-void launch_interact(int margin, int n, const int *nvalid, const uint32_t *keys,
-                     const float4 *posc, const float4 *velrho, const uint16_t *cid,
-                     const uint4 *ctab, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
-                     float *mu, int want_dt, int block, cudaStream_t s);
+void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
+                    const float4 *posc, const float4 *velrho, const uint32_t *id,
+                    const uint16_t *cid, const uint8_t *code, State dst, float *press,
+                    const CaseConst *cc, int nbits, cudaStream_t s);
+// Words of temporary storage launch_cells needs for cap_cells cells.
+size_t cells_temp_words(int64_t cap_cells);
+// Cell start table of the sorted keys (and nvalid); returns kernels launched.
+int launch_cells(int n, const uint32_t *keys, uint32_t *cstart, int64_t cap_cells, int nbits,
+                 int *nvalid, uint32_t *tmp, cudaStream_t s);
+void launch_interact(int margin, int variant, int n, const int *nvalid, const uint32_t *keys,
+                     const float4 *posc, const float4 *velrho, const float *press,
+                     const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
+                     const CaseConst *cc, CaseDyn *dyn, float4 *ace, float *mu, int want_dt,
+                     cudaStream_t s);
 void launch_dt(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t s);
 void launch_end_step(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t s);
 void launch_predictor(int n, const uint32_t *keys_in, State src, const float4 *ace,
@@ -29,9 +34,6 @@ void launch_corrector(int n, const uint32_t *perm2, const uint32_t *keys_half,
 void launch_export(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
                    uint32_t id_base, int nbits, double *pos, float *vel, float *rho,
                    float *press, cudaStream_t s);
-void launch_export_raw(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
-                       uint32_t id_base, int nbits, int32_t *cell, float4 *posc,
-                       float4 *velrho, cudaStream_t s);
 void launch_import_raw(int n, const int32_t *cell, const float4 *posc, const float4 *velrho,
                        const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
                        const CaseConst *cc, int nbits, State st, uint32_t *keys, int dst0,
@@ -41,8 +43,9 @@ void launch_scatter_forces(int n, const uint16_t *cid, const uint32_t *id, int s
                            const float *mu, float *acc_out, float *drho_out, float *mu_out,
                            cudaStream_t s);
 void launch_pair_stats(int n, const int *nvalid, const uint32_t *keys, State st,
-                       const uint4 *ctab, const CaseConst *cc, int slot, uint32_t id_base,
-                       long long *count, unsigned long long *hash, cudaStream_t s);
+                       const uint32_t *cstart, int64_t cap_cells, int nbits, const CaseConst *cc,
+                       int slot, uint32_t id_base, long long *count, unsigned long long *hash,
+                       cudaStream_t s);
 void launch_diag(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
                  int nbits, double *part, int nparts, double *out, cudaStream_t s);
 void launch_release(int n, const uint16_t *cid, int slot, int nbits, uint32_t *keys,

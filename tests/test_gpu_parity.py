@@ -134,17 +134,21 @@ def test_pair_sets_are_bit_exact(cell_mode):
 
 # ---- particle interaction ----------------------------------------------------
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("cell_mode", [0, 1])
-def test_one_evaluation_at_rest(c0, cell_mode):
+def test_one_evaluation_at_rest(c0, cell_mode, variant):
     case = cases.dam_break(0.02, cell_mode=cell_mode)
     eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=variant)
     check_eval(case, eng)
     eng.destroy()
 
 
-def test_one_evaluation_in_motion(c0):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_one_evaluation_in_motion(c0, variant):
     """After 60 steps the column moves: viscosity and DDT terms are active."""
     eng = sph.Engine.create(c0)
+    eng.set_options(pi_variant=variant)
     eng.step(60)
     g, (acc, drho, mu) = check_eval(c0, eng)
     assert np.abs(mu).max() > 0

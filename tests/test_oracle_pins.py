@@ -110,8 +110,8 @@ def test_pairs_are_symmetric_and_strict():
     assert cnt[ic] == 26
 
 
-def test_sort_is_stable_by_cell_then_type():
-    """Neighbour-list order: by cell, fluid before boundary, ties in prior order."""
+def test_sort_is_stable_by_type_then_cell():
+    """Neighbour-list order: fluid by cell, then boundary by cell, ties in prior order."""
     p = cases.default_params(0.02, 0.4, (0, 0, 0), (1, 1, 1))
     cs = 2 * p["h"]
     pos = np.array([[0.5 * cs, 0.5 * cs, 0.5 * cs],   # cell A
@@ -123,9 +123,9 @@ def test_sort_is_stable_by_cell_then_type():
     ptype = np.array([0, 0, 1, 0, 0, 0], np.uint8)
     order, inside = oracle.sort_order(p, pos, ptype)
     assert inside == 5
-    assert order.tolist() == [0, 3, 2, 1, 4, 5]
+    assert order.tolist() == [0, 3, 1, 4, 2, 5]
     order2, _ = oracle.sort_order(p, pos, ptype, prev_order=np.array([3, 0, 1, 2, 4, 5]))
-    assert order2.tolist() == [3, 0, 2, 1, 4, 5]
+    assert order2.tolist() == [3, 0, 1, 4, 2, 5]
 
 
 # ---- PI: Eq 15-18, 21-22, 36 -----------------------------------------------

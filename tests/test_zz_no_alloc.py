@@ -35,10 +35,11 @@ def test_static_sort_matches_engine_neighbour_list():
     ids, cells, n_inside = eng.order()          # existing entry point (allocating path)
     eng.destroy()
     assert n_inside == case.n
-    # the engine's keys: 2 * cell + is_boundary, in the caller's particle order
+    # the engine's keys, in the caller's particle order: boundary bit above the cell
+    cbits = int(cells.max()).bit_length()
     keys = np.zeros(case.n, np.int64)
-    keys[ids] = 2 * cells + case.ptype[ids].astype(np.int64)
-    nbits = int(keys.max()).bit_length() + 1
+    keys[ids] = (case.ptype[ids].astype(np.int64) << cbits) | cells
+    nbits = cbits + 1
     stream = torch.cuda.current_stream()
     d_in = torch.from_numpy(keys.astype(np.int32)).cuda()
     f = _fn()
@@ -52,8 +53,8 @@ def test_static_sort_matches_engine_neighbour_list():
         perm = d_perm.cpu().numpy().astype(np.int64)
         skeys = d_keys.cpu().numpy().astype(np.int64)
         assert np.array_equal(perm, ids), call
-        assert np.array_equal(skeys >> 1, cells), call
-        assert np.array_equal(skeys & 1, case.ptype[ids]), call
+        assert np.array_equal(skeys & ((1 << cbits) - 1), cells), call
+        assert np.array_equal(skeys >> cbits, case.ptype[ids]), call
 
 
 def test_static_sort_rejects_oversize():
