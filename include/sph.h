@@ -56,7 +56,7 @@ typedef struct {
   sph_d3 domain_min, domain_max; /* particles outside are frozen ("out")    */
   double dt_fixed;  /* > 0: fixed time step instead of Eq 35                */
   double dt_min;    /* a step with dt < dt_min fails with SPH_ERR_UNSTABLE  */
-  int32_t cell_mode;          /* 0: cells of size 2h (Sect. 5.1); 1: size h (Sect. 5.3) */
+  int32_t cell_mode;          /* 0: cells of 2h (Sect. 5.1); 1: of h (Sect. 5.3); 2: of 2h/3 */
   int32_t ddt_mode;           /* 0: no density diffusion; 1: Eq 17 with Eq 18 */
   int32_t clamp_boundary_rho; /* 1: boundary density kept >= rho0           */
   int32_t max_out;            /* out-of-domain quota; < 0: unlimited        */

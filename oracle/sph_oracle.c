@@ -69,8 +69,9 @@ double orc_tait(const orc_params *p, double rho) {
 int orc_grid(const orc_params *p, double origin[3], double *cs, int64_t nc[3],
              int32_t *margin) {
   if (!(p->h > 0.0)) return -1;
-  double c = p->cell_mode == 1 ? p->h : 2.0 * p->h;
-  int32_t m = p->cell_mode == 1 ? 2 : 1; /* cells needed to cover 2h */
+  if (p->cell_mode < 0 || p->cell_mode > 2) return -1;
+  int32_t m = p->cell_mode + 1; /* cells needed to cover 2h */
+  double c = 2.0 * p->h / m;    /* cells of 2h, h or 2h/3 */
   for (int k = 0; k < 3; k++) {
     if (!(p->dmax[k] > p->dmin[k])) return -1;
     origin[k] = p->dmin[k] - m * c;

@@ -29,7 +29,7 @@ typedef struct {
   double dmin[3];   /* domain box: particles outside leave the simulation   */
   double dmax[3];
   double dt_fixed;  /* > 0: use this time step instead of Eq 35             */
-  int32_t cell_mode;          /* 0: cells of 2h (Sect. 5.1); 1: cells of h */
+  int32_t cell_mode;          /* 0: cells of 2h (Sect. 5.1); 1: of h; 2: of 2h/3 */
   int32_t ddt_mode;           /* 0: no density diffusion; 1: Eq 17 + Eq 18 */
   int32_t clamp_boundary_rho; /* 1: boundary density kept >= rho0          */
   int32_t pad_;

@@ -49,11 +49,12 @@ struct Grid {
 int make_grid(const sph_case_params &p, Grid &g) {
   if (!(p.h > 0) || !(p.dp > 0) || !(p.rho0 > 0) || !(p.cs0 > 0) || !(p.gamma > 0))
     return fail(SPH_ERR_ARG, "h, dp, rho0, cs0 and gamma must be positive");
-  if (p.cell_mode != 0 && p.cell_mode != 1) return fail(SPH_ERR_ARG, "cell_mode must be 0 or 1");
+  if (p.cell_mode < 0 || p.cell_mode > 2) return fail(SPH_ERR_ARG, "cell_mode must be 0, 1 or 2");
   const double dmin[3] = {p.domain_min.x, p.domain_min.y, p.domain_min.z};
   const double dmax[3] = {p.domain_max.x, p.domain_max.y, p.domain_max.z};
-  g.cs = p.cell_mode == 1 ? p.h : 2.0 * p.h;
-  g.margin = p.cell_mode == 1 ? 2 : 1;
+  // cells of 2h, h or 2h/3: the 2h support spans margin = 1, 2 or 3 cells
+  g.margin = p.cell_mode + 1;
+  g.cs = 2.0 * p.h / g.margin;
   g.ncells = 1;
   for (int k = 0; k < 3; k++) {
     if (!(dmax[k] > dmin[k])) return fail(SPH_ERR_ARG, "domain_max must exceed domain_min");

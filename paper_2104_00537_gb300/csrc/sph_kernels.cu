@@ -111,8 +111,8 @@ __global__ void k_upload(int n, const double *__restrict__ pos, const float *__r
 
 // ---- reorder + equation of state ------------------------------------------
 
-// dst[i] = src[perm[i]]; the cell x index goes to posc.w and the Tait
-// pressure (Eq 28) to press[i].
+// dst[i] = src[perm[i]]; the cell x index goes to posc.w and P/rho, with P
+// the Tait pressure of Eq 28, to press[i].
 __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
                           const uint32_t *__restrict__ keys_sorted,
                           const float4 *__restrict__ posc_src,
@@ -139,7 +139,7 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
   dst.id[i] = id_src[p];
   dst.cid[i] = cidx;
   dst.code[i] = code_src[p];
-  press[i] = tait_pressure(C, vr.w);
+  press[i] = tait_pressure(C, vr.w) / vr.w;
 }
 
 // ---- cell start table --------------------------------------------------------
@@ -290,9 +290,10 @@ struct Acc {
 
 // Pair terms for a fluid particle a and a neighbour b (ddt: b in F).
 // grad_a W_ab = cw t^3 r_ab with t = 1 - r/(2h) (derivative of Eq 11).
+// Qb = P_b / rho_b, so (P_a + P_b) / rho_b = P_a / rho_b + Qb.
 __device__ __forceinline__ void pair_fluid(const float4 &va, float Pa, float kv, float hih,
                                            float eta2, float rx, float ry, float rz, float r2,
-                                           const float4 &vb, float Pb, bool ddt, Acc &A) {
+                                           const float4 &vb, float Qb, bool ddt, Acc &A) {
   const float rr = r2 * rsqrtf(r2);
   const float t = fmaf(-hih, rr, 1.f);
   const float t3 = t * t * t;
@@ -307,7 +308,7 @@ __device__ __forceinline__ void pair_fluid(const float4 &va, float Pa, float kv,
   const float mu = vr * ie * sab;  // v_ab.r_ab / (r^2 + eta^2)
   A.mur = fmaxf(A.mur, fabsf(mu));
   const float pi = fminf(vr, 0.f) * ie;
-  const float u = fmaf(kv, pi, (Pa + Pb) * ib);
+  const float u = fmaf(kv, pi, fmaf(Pa, ib, Qb));
   const float s = t3 * u;
   A.ax = fmaf(s, rx, A.ax);
   A.ay = fmaf(s, ry, A.ay);
@@ -356,9 +357,11 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   const int nx = C.nx, nxy = C.nx * C.ny;
   const float cs = C.csf, ics = C.inv_csf, r2max = C.r2max, eta2 = C.eta2, hih = C.half_inv_h;
   const float r2prune = r2max * 1.0001f;  // conservative: pruning never drops a pair
+  // 0 < r2 < r2max as one unsigned compare (r2 >= 0; +0 wraps to UINT_MAX)
+  const unsigned r2max_u = __float_as_uint(r2max) - 1u;
   const float4 pa = has ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float4 va = has ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
-  const float Pa = has ? press[i] : 0.f;
+  const float Pa = has ? press[i] * va.w : 0.f;  // press holds P / rho
   const float kv = C.kvisc * va.w;
   const bool ddt_on = C.ddt != 0;
   Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
@@ -402,7 +405,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
               const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
               const float ry = sy - pb.y, rz = sz - pb.z;
               const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-              if (r2 < r2max && r2 > 0.f) m |= 1u << k;
+              if (__float_as_uint(r2) - 1u < r2max_u) m |= 1u << k;
             }
           }
           while (__any_sync(full, m != 0u)) {
@@ -434,7 +437,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
               const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
               const float ry = sy - pb.y, rz = sz - pb.z;
               const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-              if (r2 < r2max && r2 > 0.f) {
+              if (__float_as_uint(r2) - 1u < r2max_u) {
                 const float4 vb = velrho[j];
                 if (afluid) {
                   pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt, A);
@@ -934,6 +937,11 @@ void launch_interact(int margin, int variant, int n, const int *nvalid, const ui
       k_interact<1, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else
       k_interact<1, 0><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+  } else if (margin == 3) {
+    if (variant == 1)
+      k_interact<3, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+    else
+      k_interact<3, 0><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
   } else {
     if (variant == 1)
       k_interact<2, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);

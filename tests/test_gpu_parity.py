@@ -56,7 +56,7 @@ def check_eval(case, eng, icase=0):
 
 # ---- neighbour list ------------------------------------------------------------
 
-@pytest.mark.parametrize("cell_mode", [0, 1])
+@pytest.mark.parametrize("cell_mode", [0, 1, 2])
 def test_sorted_order_is_bit_exact(c0, cell_mode):
     case = cases.dam_break(0.02, cell_mode=cell_mode)
     eng = sph.Engine.create(case)
@@ -98,7 +98,7 @@ def mix(z):
         return z ^ (z >> np.uint64(31))
 
 
-@pytest.mark.parametrize("cell_mode", [0, 1])
+@pytest.mark.parametrize("cell_mode", [0, 1, 2])
 def test_pair_sets_are_bit_exact(cell_mode):
     case = cases.dam_break(0.02, cell_mode=cell_mode)
     eng = sph.Engine.create(case)
@@ -135,7 +135,7 @@ def test_pair_sets_are_bit_exact(cell_mode):
 # ---- particle interaction ----------------------------------------------------
 
 @pytest.mark.parametrize("variant", [0, 1])
-@pytest.mark.parametrize("cell_mode", [0, 1])
+@pytest.mark.parametrize("cell_mode", [0, 1, 2])
 def test_one_evaluation_at_rest(c0, cell_mode, variant):
     case = cases.dam_break(0.02, cell_mode=cell_mode)
     eng = sph.Engine.create(case)

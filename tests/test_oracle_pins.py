@@ -85,7 +85,7 @@ def test_tait_exact_rational_value():
 
 # ---- Sect. 5.1: neighbour list ---------------------------------------------
 
-@pytest.mark.parametrize("cell_mode", [0, 1])
+@pytest.mark.parametrize("cell_mode", [0, 1, 2])
 @pytest.mark.parametrize("seed", [1, 2])
 def test_cell_list_pairs_equal_brute_force(cell_mode, seed):
     """The cell list finds exactly the O(N^2) pair set."""
