@@ -196,6 +196,112 @@ def run_reference(args, rank, world, dist):
     print(json.dumps(out), flush=True)
 
 
+def timed_steps(eng, stream, steps):
+    """Device time (ms) of `steps` Symplectic steps on the engine's stream."""
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    eng.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def run_batched(args):
+    """256 uneven dam breaks: one batched engine (one launch per stage for all
+    cases, CUDA-graph replay, autotuned cell size / kernel variant) against the
+    plain path that steps each case alone in its own engine (also replayed
+    from a CUDA graph).  Reports aggregate case-steps/s of both."""
+    import torch
+    from paper_2104_00537_gb300 import autotune, cases, sph
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    cs = cases.batch_dam_breaks(args.ncases, seed=0)
+    gpu = torch.cuda.get_device_name(0)
+    mk = lambda cc: sph.Engine.batch(cc, stream=stream)
+    (cm, var), tune_ms = autotune.tune(cs, mk, gpu)
+    for c in cs:
+        c.params["cell_mode"] = cm
+    eng = sph.Engine.batch(cs, stream=stream)
+    eng.set_options(pi_variant=var, use_graph=1)
+    eng.step(args.warmup)
+    p0 = sum(eng.stats(i)["interactions"] for i in range(len(cs)))
+    clocks = ClockSampler(0)
+    ms_b = timed_steps(eng, stream, args.steps)
+    clk = clocks.stop()
+    p1 = sum(eng.stats(i)["interactions"] for i in range(len(cs)))
+    eng.destroy()
+    # plain: one case at a time, each in its own engine
+    ms_p = 0.0
+    pp = 0
+    for c in cs:
+        e = sph.Engine.create(c, stream=stream)
+        e.set_options(pi_variant=var, use_graph=1)
+        e.step(args.warmup)
+        q0 = e.stats()["interactions"]
+        ms_p += timed_steps(e, stream, args.steps)
+        pp += e.stats()["interactions"] - q0
+        e.destroy()
+    nb = len(cs) * args.steps
+    out = {"metric": "case_steps_per_s", "value": nb / (ms_b / 1e3), "unit": "case-steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "%d dam breaks, fluid 5k-200k log-uniform" % len(cs),
+                      "particles": sum(c.n for c in cs), "cell_mode": cm, "pi_variant": var},
+           "batched": {"case_steps_per_s": nb / (ms_b / 1e3),
+                       "interactions_per_s": (p1 - p0) / (ms_b / 1e3)},
+           "plain": {"case_steps_per_s": nb / (ms_p / 1e3),
+                     "interactions_per_s": pp / (ms_p / 1e3)},
+           "speedup_vs_plain": ms_p / ms_b, "autotune_ms_per_step": tune_ms, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
+def run_served(args):
+    """Poisson arrivals of sloshing-tank requests served by continuous batching
+    on one pool engine, against the same trace served one request at a time."""
+    import torch
+    from paper_2104_00537_gb300 import cases, serve, sph
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    trace = cases.sloshing_trace(args.requests, rate=args.rate, seed=0, n_min=10000,
+                                 n_max=args.max_fluid, t_end=args.t_end)
+    for _, c, _ in trace:
+        c.params["cell_mode"] = args.cell_mode
+    free, _ = torch.cuda.mem_get_info()
+    max_p = int(min(free * 0.3 / 200, 64_000_000))   # about 200 B per particle slot
+    max_cells = int(min(free * 0.05 / 8, 200_000_000))
+    results = {}
+    for name, slots in (("served", 64), ("plain", 1)):
+        pool = sph.Engine.pool(max_p, max_cells, slots, stream=stream)
+        pool.set_options(use_graph=1)
+        reqs = [serve.Request(i, a, c, te) for i, (a, c, te) in enumerate(trace)]
+        srv = serve.Server(pool, chunk=args.chunk)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        srv.run(reqs)
+        wall = time.perf_counter() - t0
+        s = serve.summary(reqs, wall)
+        s["case_steps_per_s"] = srv.case_steps / wall
+        results[name] = s
+        pool.destroy()
+    out = {"metric": "served_p50_time_to_result_s", "value": results["served"]["p50_s"],
+           "unit": "s", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "sloshing tanks, Poisson %.0f req/s, %d requests, fluid "
+                                  "10k-%d log-uniform, t_end %.3g s"
+                                  % (args.rate, args.requests, args.max_fluid, args.t_end),
+                      "chunk_steps": args.chunk, "cell_mode": args.cell_mode},
+           "served": results["served"], "plain": results["plain"],
+           "throughput_ratio": results["served"]["throughput_req_s"] /
+           results["plain"]["throughput_req_s"],
+           "case_steps_ratio": results["served"]["case_steps_per_s"] /
+           results["plain"]["case_steps_per_s"]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,12 +309,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_break")
-    ap.add_argument("--cell-mode", type=int, default=0)
+    ap.add_argument("--cell-mode", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-block", type=int, default=20000)
+    ap.add_argument("--ncases", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--max-fluid", type=int, default=200000)
+    ap.add_argument("--t-end", type=float, default=0.05)
+    ap.add_argument("--chunk", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.impl != "reference" and args.workload == "batched":
+        return run_batched(args)
+    if args.impl != "reference" and args.workload == "served":
+        return run_served(args)
 
     rank, world, local, dist = dist_init()
     if args.impl == "reference":
@@ -279,7 +395,7 @@ def main():
            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": desc, "particles": n_particles, "cases": len(cs),
-                      "cell_mode": "2h" if args.cell_mode == 0 else "h",
+                      "cell_mode": ["2h", "h", "2h/3"][args.cell_mode],
                       "l2": "state (%.0f MB) larger than L2 (129 MB), no flush" %
                             (n_particles * 177 / 1e6),
                       "parallelism": "replicas" if world > 1 else "single"},

@@ -247,3 +247,24 @@ def free_particle(dp: float = 0.02, pos=(0.5, 0.5, 0.5), vel=(0.3, -0.2, 0.1), *
     rho = np.array([params["rho0"]])
     return Case("free_particle", params, p, v, rho, np.zeros(1, np.uint8),
                 np.full(1, -1, np.int32), [], {})
+
+
+def sloshing_trace(n_requests: int = 100, rate: float = 20.0, seed: int = 0,
+                   n_min: int = 10000, n_max: int = 2000000, t_end: float = 1.0):
+    """Seeded serving trace: Poisson arrivals (mean `rate` per second) of
+    sloshing-tank cases, fill depth U(0.2, 0.4) m, excitation amplitude
+    U(0.01, 0.05) m and frequency U(0.5, 1.5) Hz, fluid count log-uniform in
+    [n_min, n_max].  Returns a list of (arrival_s, case, t_end)."""
+    u = uniform01(seed ^ 0x7E5A, 5 * n_requests).reshape(n_requests, 5)
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += -math.log(1.0 - u[i, 0]) / rate
+        n = math.exp(math.log(n_min) + u[i, 1] * (math.log(n_max) - math.log(n_min)))
+        depth = 0.2 + 0.2 * u[i, 2]
+        amp = 0.01 + 0.04 * u[i, 3]
+        freq = 0.5 + 1.0 * u[i, 4]
+        c = sloshing_tank(int(n), depth, amp, freq, seed=seed + 1 + i)
+        c.meta.update(request=i)
+        out.append((t, c, t_end))
+    return out

@@ -155,6 +155,7 @@ struct sph_engine_t {
   std::vector<CaseConst> hconst;
   std::vector<std::pair<int64_t, int64_t>> free_cells;  // [begin, end) ranges
   int64_t n_phys = 0, n_dead = 0;
+  int64_t cells_hw = 0;  // cells in use: [0, cells_hw) holds every live case's grid
   // device
   CaseConst *dconst = nullptr;
   CaseDyn *ddyn = nullptr;
@@ -174,7 +175,7 @@ struct sph_engine_t {
   // options, graph, timing
   sph_options opt{};
   cudaGraphExec_t gexec = nullptr;
-  int64_t graph_n = -1, graph_dead = -1;
+  int64_t graph_n = -1, graph_dead = -1;  // n_phys and cells_hw of the captured graph
   std::vector<cudaEvent_t> evs;
   double pi_ms = 0, step_ms = 0;
   int64_t pi_launches = 0, kernel_launches = 0;
@@ -382,6 +383,7 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     return rc;
   }
   e->n_phys = np;
+  e->cells_hw = nc;
   *out = e;
   return SPH_OK;
 }
@@ -396,11 +398,11 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
   launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->press,
                  e->dconst, e->nbits, s);
-  launch_cells(nl, e->keysB, e->cstart, e->cap_cells, e->nbits, e->nvalid, e->cells_tmp, s);
+  launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
   // PI on state n, time step, predictor
   if (ev) cudaEventRecord(ev[0], s);
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
-                  e->press, Y.cid, e->cstart, e->cap_cells, e->nbits, e->dconst, e->ddyn, e->ace,
+                  e->press, Y.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
                   nullptr, 1, s);
   if (ev) cudaEventRecord(ev[1], s);
   launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
@@ -410,10 +412,10 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
   radix_sort(e->keysC, e->keysD, e->perm2, nl, e->nbits, e->sort_tmp, s);
   launch_reorder(nl, e->perm2, e->keysD, Z.posc, Z.velrho, Y.id, Y.cid, Y.code, X, e->press,
                  e->dconst, e->nbits, s);
-  launch_cells(nl, e->keysD, e->cstart, e->cap_cells, e->nbits, e->nvalid + 1, e->cells_tmp, s);
+  launch_cells(nl, e->keysD, e->cstart, e->cells_hw, e->nbits, e->nvalid + 1, e->cells_tmp, s);
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid + 1, e->keysD, X.posc, X.velrho,
-                  e->press, X.cid, e->cstart, e->cap_cells, e->nbits, e->dconst, e->ddyn, e->ace,
+                  e->press, X.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
                   nullptr, 0, s);
   if (ev) cudaEventRecord(ev[3], s);
   launch_corrector(nl, e->perm2, e->keysD, e->keysB, Y, X, e->ace, e->dconst, e->ddyn, e->nbits,
@@ -429,7 +431,7 @@ void enqueue_nl(sph_engine e) {
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, e->s);
   launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->press,
                  e->dconst, e->nbits, e->s);
-  launch_cells(nl, e->keysB, e->cstart, e->cap_cells, e->nbits, e->nvalid, e->cells_tmp, e->s);
+  launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, e->s);
 }
 
 int check_flags(sph_engine e) {
@@ -509,7 +511,7 @@ int sph_step(sph_engine e, int64_t nsteps) {
   }
   int64_t k = 0;
   if (!timing && e->opt.use_graph && e->n_dead == 0) {
-    if (!e->gexec || e->graph_n != e->n_phys) {
+    if (!e->gexec || e->graph_n != e->n_phys || e->graph_dead != e->cells_hw) {
       if (e->gexec) cudaGraphExecDestroy(e->gexec);
       e->gexec = nullptr;
       cudaGraph_t g;
@@ -520,6 +522,7 @@ int sph_step(sph_engine e, int64_t nsteps) {
       cudaGraphDestroy(g);
       if (err != cudaSuccess) return fail(SPH_ERR_CUDA, cudaGetErrorString(err));
       e->graph_n = e->n_phys;
+      e->graph_dead = e->cells_hw;  // cells in use at capture
     }
     for (; k < nsteps; k++) CUDA_TRY(cudaGraphLaunch(e->gexec, e->s));
   }
@@ -774,7 +777,7 @@ int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho, float 
   const int nl = (int)(e->n_phys - e->n_dead);
   State &Y = e->S[1];
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
-                  e->press, Y.cid, e->cstart, e->cap_cells, e->nbits, e->dconst, e->ddyn, e->ace,
+                  e->press, Y.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
                   e->mu, 1, e->s);
   char *p = e->io;
   float *d_acc = (float *)p;
@@ -848,7 +851,7 @@ int sph_pair_stats(sph_engine e, int32_t icase, int64_t *count, uint64_t *hash) 
   CUDA_TRY(cudaMemsetAsync(d_count, 0, 8 * n, e->s));
   CUDA_TRY(cudaMemsetAsync(d_hash, 0, 8 * n, e->s));
   launch_pair_stats((int)(e->n_phys - e->n_dead), e->nvalid, e->keysB, e->S[1], e->cstart,
-                    e->cap_cells, e->nbits, e->dconst, icase, 0, d_count, d_hash, e->s);
+                    e->cells_hw, e->nbits, e->dconst, icase, 0, d_count, d_hash, e->s);
   CUDA_TRY(cudaGetLastError());
   if (count) CUDA_TRY(cudaMemcpyAsync(count, d_count, 8 * n, cudaMemcpyDeviceToHost, e->s));
   if (hash) CUDA_TRY(cudaMemcpyAsync(hash, d_hash, 8 * n, cudaMemcpyDeviceToHost, e->s));
@@ -929,6 +932,7 @@ int sph_pool_admit(sph_engine e, const sph_case_params *params, const sph_partic
   if (rc == SPH_OK) rc = upload_case(e, free_slot, parts, e->n_phys);
   if (rc) return rc;
   e->n_phys += parts->n;
+  e->cells_hw = std::max<int64_t>(e->cells_hw, cb + g.ncells);
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
   e->gexec = nullptr;
   *slot = free_slot;
@@ -977,6 +981,9 @@ int sph_pool_release(sph_engine e, int32_t slot) {
   }
   e->free_cells.swap(merged);
   S = Slot();
+  e->cells_hw = 0;
+  for (auto &s : e->slots)
+    if (s.used) e->cells_hw = std::max<int64_t>(e->cells_hw, (int64_t)s.cellbase + s.ncells);
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
   e->gexec = nullptr;
   return SPH_OK;
