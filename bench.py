@@ -314,10 +314,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-block", type=int, default=20000)
     ap.add_argument("--ncases", type=int, default=256)
-    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--max-fluid", type=int, default=200000)
-    ap.add_argument("--t-end", type=float, default=0.05)
+    ap.add_argument("--t-end", type=float, default=0.1)
     ap.add_argument("--chunk", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

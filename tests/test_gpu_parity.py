@@ -335,3 +335,27 @@ def test_pool_mix_equals_alone():
     for k in ("pos", "vel", "rho"):
         assert np.array_equal(st[k], ref[k]), k
     assert pool.usage()["cases"] == 1
+
+
+def test_wave_flume_fiftieth_scale():
+    """The 25 m piston-wavemaker flume on a 1/50-particle-count copy (dp =
+    0.008 * 50^(1/3) m, 768k particles): 3 Symplectic steps against the oracle,
+    and the piston placed by its motion law (Eq 37)."""
+    c = cases.wave_flume(0.008 * 50 ** (1 / 3))
+    eng = sph.Engine.create(c)
+    eng.step(3)
+    st = eng.get_state()
+    o = oracle.OracleState(c)
+    o.step(3)
+    dp = c.params["dp"]
+    assert abs(st["t"] - o.t.value) < 1e-4 * o.t.value
+    assert np.abs(st["pos"] - o.pos).max() < 1e-3 * dp
+    f = c.ptype == 0
+    assert rel_err(st["vel"][f], o.vel[f]) < 1e-3
+    piston = c.group >= 0
+    m = c.motions[0]
+    disp = m["amp"] * np.sin(m["omega"] * st["t"])
+    np.testing.assert_allclose(st["pos"][piston, 0] - c.pos[piston, 0], disp, atol=1e-6)
+    s = eng.stats()
+    assert s["mass"] == o.diag()["mass"] and s["n_out"] == 0
+    eng.destroy()
