@@ -40,10 +40,17 @@ __device__ __forceinline__ float below(float cs) {  // largest float < cs
 }
 
 // New offset after adding disp (FP64) to a float offset in [0, cs); returns
-// the cell shift.
+// the cell shift.  The sum is formed in FP64; when its float rounding stays
+// inside the cell (the common case) that rounding is the new offset, and
+// only a particle that changes cell takes the FP64 floor / shift path.
 __device__ __forceinline__ int shift_axis(float off, double disp, const CaseConst &C,
                                           float &off_out) {
   double x = (double)off + disp;
+  const float xf = (float)x;
+  if (xf >= 0.f && xf < C.csf) {
+    off_out = xf;
+    return 0;
+  }
   double k = floor(x * C.inv_cs);
   x = fma(-k, C.cs, x);
   if (x < 0.0) {
@@ -654,9 +661,12 @@ __global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
   float4 vnew;
   if (code == 0) {
     vnew = make_float4(fmaf(dtf, a.x, vn.x), fmaf(dtf, a.y, vn.y), fmaf(dtf, a.z, vn.z), rho);
-    disp[0] = dt * (0.5 * ((double)vnew.x + (double)vn.x));
-    disp[1] = dt * (0.5 * ((double)vnew.y + (double)vn.y));
-    disp[2] = dt * (0.5 * ((double)vnew.z + (double)vn.z));
+    // r^{n+1} = r^n + dt (v^{n+1} + v^n) / 2: the FP32 sum of two FP32
+    // velocities is exact to within one rounding; dt multiplies in FP64
+    const double hdt = 0.5 * dt;
+    disp[0] = hdt * (double)(vnew.x + vn.x);
+    disp[1] = hdt * (double)(vnew.y + vn.y);
+    disp[2] = hdt * (double)(vnew.z + vn.z);
   } else {
     if (C.clamp && rho < C.rho0) rho = C.rho0;
     if (code >= 2) {
