@@ -223,9 +223,11 @@ int allocate(sph_engine e) {
   };
   e->dconst = (CaseConst *)A(sizeof(CaseConst) * e->cap_cases);
   e->ddyn = (CaseDyn *)A(sizeof(CaseDyn) * e->cap_cases);
+  // kReadPad readable entries past the last particle (interaction reads)
+  const int64_t NP = N + kReadPad;
   for (int b = 0; b < 3; b++) {
-    e->S[b].posc = (float4 *)A(16 * N);
-    e->S[b].velrho = (float4 *)A(16 * N);
+    e->S[b].posc = (float4 *)A(16 * NP);
+    e->S[b].velrho = (float4 *)A(16 * NP);
     e->S[b].id = (uint32_t *)A(4 * N);
     e->S[b].cid = (uint16_t *)A(2 * N);
     e->S[b].code = (uint8_t *)A(N);
@@ -240,13 +242,18 @@ int allocate(sph_engine e) {
   e->mu = (float *)A(4 * N);
   e->cstart = (uint32_t *)A(4 * (2 * e->cap_cells + 2));
   e->cells_tmp = (uint32_t *)A(4 * cells_temp_words(e->cap_cells));
-  e->press = (float *)A(4 * N);
+  e->press = (float *)A(4 * NP);
   e->nvalid = (int *)A(16);
   e->sort_tmp = A(radix_sort_temp_bytes(N));
   e->diag = (double *)A(sizeof(double) * (8 * 1024 + 8));
   e->io_bytes = align256(48 * (size_t)N) + 4096;
   e->io = (char *)A(e->io_bytes);
   if (!ok) return fail(SPH_ERR_OOM, "device allocation failed");
+  for (int b = 0; b < 3; b++) {  // defined contents for the padding
+    CUDA_TRY(cudaMemsetAsync(e->S[b].posc, 0, 16 * NP, e->s));
+    CUDA_TRY(cudaMemsetAsync(e->S[b].velrho, 0, 16 * NP, e->s));
+  }
+  CUDA_TRY(cudaMemsetAsync(e->press, 0, 4 * NP, e->s));
   CUDA_TRY(cudaMemsetAsync(e->ddyn, 0, sizeof(CaseDyn) * e->cap_cases, e->s));
   CUDA_TRY(cudaMemsetAsync(e->dconst, 0, sizeof(CaseConst) * e->cap_cases, e->s));
   return SPH_OK;

@@ -65,6 +65,9 @@ struct CaseDyn {
 };
 
 constexpr unsigned kFlagNaN = 1u, kFlagDtMin = 2u, kFlagQuota = 4u;
+// Readable entries of posc/velrho/press past the last particle, so that a
+// warp may test 32 candidates at a time without per-candidate bounds checks.
+constexpr int64_t kReadPad = 1024;
 constexpr uint32_t kFloatInfBits = 0x7f800000u;
 
 __host__ __device__ inline uint32_t key_out(int nbits) { return (1u << nbits) - 2u; }

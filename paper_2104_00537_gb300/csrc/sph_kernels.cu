@@ -415,22 +415,36 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
               if (__float_as_uint(r2) - 1u < r2max_u) m |= 1u << k;
             }
           }
-          while (__any_sync(full, m != 0u)) {
-            if (m) {
-              const int k = __ffs(m) - 1;
-              m &= m - 1u;
-              const int j = lo + base + k;
-              const float4 pb = posc[j];
-              const float4 vb = velrho[j];
-              const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
-              const float ry = sy - pb.y, rz = sz - pb.z;
-              const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-              if (afluid) {
+          if (part) A.cntb += __popc(m); else A.cnt += __popc(m);
+          if (__all_sync(full, afluid || !has)) {  // fluid targets only
+            while (__any_sync(full, m != 0u)) {
+              if (m) {
+                const int k = 31 - __clz(m);
+                m ^= 1u << k;
+                const int j = lo + base + k;
+                const float4 pb = posc[j];
+                const float4 vb = velrho[j];
+                const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+                const float ry = sy - pb.y, rz = sz - pb.z;
+                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
                 pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt, A);
-                if (part) A.cntb++; else A.cnt++;
-              } else {
-                pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
-                A.cnt++;
+              }
+            }
+          } else {
+            while (__any_sync(full, m != 0u)) {
+              if (m) {
+                const int k = 31 - __clz(m);
+                m ^= 1u << k;
+                const int j = lo + base + k;
+                const float4 pb = posc[j];
+                const float4 vb = velrho[j];
+                const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+                const float ry = sy - pb.y, rz = sz - pb.z;
+                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                if (afluid)
+                  pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt, A);
+                else
+                  pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
               }
             }
           }
