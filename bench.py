@@ -42,6 +42,23 @@ def fp32_peak_tflops(mhz=SM_MAX_MHZ):
     return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
+def measured_traffic(cell_mode, workload_name):
+    """DRAM bytes per interaction launch from the committed ncu capture, or None
+    when the capture does not match (other workload / cell size, or the kernel
+    source changed since the counters were taken)."""
+    import hashlib
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "k_interact_traffic.json")))
+        src = open(os.path.join(ROOT, d["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+        return None
+    if workload_name != "dam_break" or cell_mode != 1:
+        return None
+    return d["dram_bytes_read"] + d["dram_bytes_write"]
+
+
 def workload(name, rank=0):
     from paper_2104_00537_gb300 import cases
     if name == "dam_break":
@@ -390,7 +407,8 @@ def main():
     achieved = flops / launches / pi_avg_s / 1e12
     peak = fp32_peak_tflops()
     roofline = {"bound": "alu", "kernel": "k_interact", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": measured_traffic(args.cell_mode, args.workload),
                 "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
                 "pi_ms_per_launch": 1000 * pi_avg_s,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal max clock)"}
