@@ -110,7 +110,9 @@ typedef void (*sph_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 /* Engine-wide launch options (the autotuner's knobs). */
 typedef struct {
   int32_t pi_block;   /* threads per block of the interaction kernel (0: default) */
-  int32_t pi_variant; /* interaction kernel variant (0: default)               */
+  int32_t pi_variant; /* interaction pair loop: 0 compacted hit masks (default),
+                       * 1 test and evaluate inline, 2 hit masks queued per
+                       * lane across rows (same sums as 0, bit for bit)       */
   int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
   int32_t timing;     /* 1: time every PI launch with CUDA events              */
 } sph_options;

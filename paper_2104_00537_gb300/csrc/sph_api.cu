@@ -490,8 +490,8 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
   if (!e || !opt) return fail(SPH_ERR_ARG, "null argument");
   if (opt->pi_block != 0 && opt->pi_block != 128)
     return fail(SPH_ERR_ARG, "pi_block must be 0 (default) or 128");
-  if (opt->pi_variant < 0 || opt->pi_variant > 1)
-    return fail(SPH_ERR_ARG, "pi_variant must be 0 (compacted) or 1 (inline)");
+  if (opt->pi_variant < 0 || opt->pi_variant > 2)
+    return fail(SPH_ERR_ARG, "pi_variant must be 0 (compacted), 1 (inline) or 2 (queued)");
   e->opt = *opt;
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
   e->gexec = nullptr;

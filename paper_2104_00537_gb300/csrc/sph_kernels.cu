@@ -333,6 +333,44 @@ __device__ __forceinline__ void pair_boundary(const float4 &va, float hih, float
   A.s1 = fmaf(t3 * __fdividef(1.f, vb.w), vr, A.s1);
 }
 
+// Final values of target a from its accumulators: dv/dt (Eq 22 with g), drho/dt
+// (Eq 15 with the Eq 17-18 term, or Eq 36), mu_max and the Eq 35 candidate
+// time step; then the warp's per-case reduction of counts, dt and flags.
+__device__ __forceinline__ void finish_target(const CaseConst &C, int i, int n, int cidx, bool has,
+                                              bool afluid, const float4 &va, const Acc &A,
+                                              int want_dt, float4 *__restrict__ ace,
+                                              float *__restrict__ mu_out, CaseDyn *dyn) {
+  unsigned npairs = 0, nfb = 0, nbf = 0, dtbits = kFloatInfBits;
+  bool bad = false;
+  if (has) {
+    npairs = A.cnt + A.cntb;
+    nfb = afluid ? A.cntb : 0u;
+    nbf = afluid ? 0u : A.cnt;
+    const float mcw = C.m * C.cw;
+    float4 out;
+    float mumax = C.h * A.mur;
+    if (afluid) {
+      const float ca = -mcw / va.w;
+      out.x = fmaf(ca, A.ax, C.g[0]);
+      out.y = fmaf(ca, A.ay, C.g[1]);
+      out.z = fmaf(ca, A.az, C.g[2]);
+      out.w = mcw * (va.w * A.s1 - C.kddt * A.s2);
+      const float f = sqrtf(out.x * out.x + out.y * out.y + out.z * out.z);
+      const float dtf = f > 0.f ? sqrtf(C.h / f) : INFINITY;
+      const float dtcv = C.h / (C.cs0f + mumax);
+      bad = !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) && isfinite(out.w));
+      if (want_dt) dtbits = __float_as_uint(fminf(dtf, dtcv));
+    } else {
+      out = make_float4(0.f, 0.f, 0.f, mcw * va.w * A.s1);
+      mumax = 0.f;
+      bad = !isfinite(out.w);
+    }
+    ace[i] = out;
+    if (mu_out) mu_out[i] = mumax;
+  }
+  reduce_case(i < n ? cidx : -1, has, npairs, nfb, nbf, dtbits, bad, dyn);
+}
+
 // One thread per particle a in sorted order (all fluid targets first, then
 // boundary targets, so warps rarely mix the two).  The (2M+1)^2 rows of
 // neighbour cells (fixed dy, dz) are visited in lock-step by the warp; in a
@@ -344,6 +382,7 @@ __device__ __forceinline__ void pair_boundary(const float4 &va, float hih, float
 //   terms then run over the set bits, so no lane idles on a rejected
 //   candidate while another computes a pair.
 // VARIANT 1 (inline): test and pair terms in one loop (divergent).
+// (VARIANT 2, the queued pair loop, is k_interact_q below.)
 template <int M, int VARIANT>
 __global__ void __launch_bounds__(128)
 k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
@@ -405,7 +444,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
         if (VARIANT == 0) {
           unsigned m = 0u;
           const int nk = min(32, maxlen - base);
-#pragma unroll 4
+#pragma unroll 8
           for (int k = 0; k < nk; k++) {
             if (base + k < len) {
               const float4 pb = posc[lo + base + k];
@@ -475,35 +514,150 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
     }
   }
 
-  unsigned npairs = 0, nfb = 0, nbf = 0, dtbits = kFloatInfBits;
-  bool bad = false;
-  if (has) {
-    npairs = A.cnt + A.cntb;
-    nfb = afluid ? A.cntb : 0u;
-    nbf = afluid ? 0u : A.cnt;
-    const float mcw = C.m * C.cw;
-    float4 out;
-    float mumax = C.h * A.mur;
-    if (afluid) {
-      const float ca = -mcw / va.w;
-      out.x = fmaf(ca, A.ax, C.g[0]);
-      out.y = fmaf(ca, A.ay, C.g[1]);
-      out.z = fmaf(ca, A.az, C.g[2]);
-      out.w = mcw * (va.w * A.s1 - C.kddt * A.s2);
-      const float f = sqrtf(out.x * out.x + out.y * out.y + out.z * out.z);
-      const float dtf = f > 0.f ? sqrtf(C.h / f) : INFINITY;
-      const float dtcv = C.h / (C.cs0f + mumax);
-      bad = !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) && isfinite(out.w));
-      if (want_dt) dtbits = __float_as_uint(fminf(dtf, dtcv));
-    } else {
-      out = make_float4(0.f, 0.f, 0.f, mcw * va.w * A.s1);
-      mumax = 0.f;
-      bad = !isfinite(out.w);
+  finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
+}
+
+// Queued pair loop (VARIANT 2).  Same rows, pruning and 32-candidate test as
+// VARIANT 0, but a chunk's hits are not evaluated at once: each lane appends
+// (first index, hit mask, row, part) to its own FIFO in shared memory, and the
+// warp evaluates one pair per lane per iteration only while every active lane
+// has a queued hit.  A lane's hits from many rows are thus evaluated back to
+// back, so the warp's lock-step waste follows the imbalance of whole neighbour
+// counts rather than that of every row.  Each lane still takes its pairs in the
+// same order as VARIANT 0, so the sums are bit-identical to it.
+constexpr int kQCap = 16;  // FIFO slots per lane (power of two)
+
+template <int M>
+__global__ void __launch_bounds__(128, 6)
+k_interact_q(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
+             const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
+             const float *__restrict__ press, const uint16_t *__restrict__ cid,
+             const uint32_t *__restrict__ cstart, uint32_t cap1, int nbits,
+             const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
+             float4 *__restrict__ ace, float *__restrict__ mu_out, int want_dt) {
+  __shared__ uint32_t q_base[kQCap * 128];
+  __shared__ uint32_t q_mask[kQCap * 128];
+  __shared__ uint8_t q_row[kQCap * 128];  // row | part << 7
+  const unsigned full = 0xffffffffu;
+  const int tid = threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + tid;
+  const int nvalid = *nvalid_p;
+  const bool has = i < nvalid;
+  const int cidx = i < n ? (int)cid[i] : 0;
+  const CaseConst &C = cc[cidx];
+  const uint32_t key = has ? keys[i] : 0u;
+  const bool afluid = has && !key_boundary(key, nbits);
+  const int gc = (int)key_cell(key, nbits);
+  const int nx = C.nx, nxy = C.nx * C.ny;
+  const float cs = C.csf, ics = C.inv_csf, r2max = C.r2max, eta2 = C.eta2, hih = C.half_inv_h;
+  const float r2prune = r2max * 1.0001f;
+  const unsigned r2max_u = __float_as_uint(r2max) - 1u;
+  const float4 pa = has ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 va = has ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+  const float Pa = has ? press[i] * va.w : 0.f;
+  const float kv = C.kvisc * va.w;
+  const bool ddt_on = C.ddt != 0;
+  const bool warp_fluid = __all_sync(full, afluid || !has);
+  const unsigned active = __ballot_sync(full, has);
+  Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
+  constexpr int W = 2 * M + 1;
+
+  // FIFO state of this lane and the entry being evaluated
+  unsigned head = 0, tail = 0;
+  unsigned cur = 0u;
+  int cbase = 0;
+  float csy = 0.f, csz = 0.f;
+  bool cddt = false;
+
+  // one pair of this lane (if it has one): pop an entry when the current is done
+  auto pair_step = [&]() {
+    if (cur == 0u && head != tail) {
+      const int s = (int)(head & (kQCap - 1)) * 128 + tid;
+      cur = q_mask[s];
+      cbase = (int)q_base[s];
+      const int rw = q_row[s];
+      head++;
+      const int r = rw & 0x7f;
+      csy = fmaf(-(float)(r % W - M), cs, pa.y);
+      csz = fmaf(-(float)(r / W - M), cs, pa.z);
+      cddt = ddt_on && !(rw & 0x80);
     }
-    ace[i] = out;
-    if (mu_out) mu_out[i] = mumax;
+    if (cur) {
+      const int k = 31 - __clz(cur);
+      cur ^= 1u << k;
+      const int j = cbase + k;
+      const float4 pb = posc[j];
+      const float4 vb = velrho[j];
+      const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+      const float ry = csy - pb.y, rz = csz - pb.z;
+      const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      if (warp_fluid || afluid)
+        pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], cddt, A);
+      else
+        pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
+    }
+  };
+
+#pragma unroll 1
+  for (int row = 0; row < W * W; row++) {
+    const int dy = row % W - M, dz = row / W - M;
+    const float gy = slab_gap(dy, pa.y, cs), gz = slab_gap(dz, pa.z, cs);
+    const float d2 = fmaf(gy, gy, gz * gz);
+    int loF = 0, hiF = 0, loB = 0, hiB = 0;
+    if (has && d2 < r2prune) {
+      const float L = sqrtf(r2prune - d2);
+      const int kx0 = max(-M, (int)floorf((pa.x - L) * ics));
+      const int kx1 = min(M, (int)floorf((pa.x + L) * ics));
+      const int c0 = gc + dz * nxy + dy * nx + kx0;
+      const int c1 = gc + dz * nxy + dy * nx + kx1 + 1;
+      loF = (int)cstart[c0];
+      hiF = (int)cstart[c1];
+      if (afluid) {
+        loB = (int)cstart[cap1 + c0];
+        hiB = (int)cstart[cap1 + c1];
+      }
+    }
+    const float sy = fmaf(-(float)dy, cs, pa.y), sz = fmaf(-(float)dz, cs, pa.z);
+#pragma unroll 1
+    for (int part = 0; part < 2; part++) {
+      const int lo = part ? loB : loF;
+      const int len = (part ? hiB : hiF) - lo;
+      const int maxlen = (int)__reduce_max_sync(full, (unsigned)max(len, 0));
+#pragma unroll 1
+      for (int base = 0; base < maxlen; base += 32) {
+        unsigned m = 0u;
+        const int nk = min(32, maxlen - base);
+#pragma unroll 8
+        for (int k = 0; k < nk; k++) {
+          if (base + k < len) {
+            const float4 pb = posc[lo + base + k];
+            const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+            const float ry = sy - pb.y, rz = sz - pb.z;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            if (__float_as_uint(r2) - 1u < r2max_u) m |= 1u << k;
+          }
+        }
+        if (part) A.cntb += __popc(m); else A.cnt += __popc(m);
+        // make room for this entry: a lane with a full FIFO evaluates (rare)
+        while (__any_sync(full, m != 0u && tail - head >= (unsigned)kQCap)) pair_step();
+        if (m) {
+          const int s = (int)(tail & (kQCap - 1)) * 128 + tid;
+          q_base[s] = (uint32_t)(lo + base);
+          q_mask[s] = m;
+          q_row[s] = (uint8_t)(row | (part << 7));
+          tail++;
+        }
+        // balanced evaluation: one pair per lane while every active lane has one
+        for (;;) {
+          const unsigned busy = __ballot_sync(full, cur != 0u || head != tail);
+          if (busy == 0u || (active & ~busy) != 0u) break;
+          pair_step();
+        }
+      }
+    }
   }
-  reduce_case(i < n ? cidx : -1, has, npairs, nfb, nbf, dtbits, bad, dyn);
+  while (__any_sync(full, cur != 0u || head != tail)) pair_step();
+  finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
 }
 
 // ---- time step and motion ----------------------------------------------------
@@ -957,17 +1111,23 @@ void launch_interact(int margin, int variant, int n, const int *nvalid, const ui
 #define SPH_PI_ARGS                                                                      \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, mu, want_dt
   if (margin == 1) {
-    if (variant == 1)
+    if (variant == 2)
+      k_interact_q<1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+    else if (variant == 1)
       k_interact<1, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else
       k_interact<1, 0><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
   } else if (margin == 3) {
-    if (variant == 1)
+    if (variant == 2)
+      k_interact_q<3><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+    else if (variant == 1)
       k_interact<3, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else
       k_interact<3, 0><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
   } else {
-    if (variant == 1)
+    if (variant == 2)
+      k_interact_q<2><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+    else if (variant == 1)
       k_interact<2, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else
       k_interact<2, 0><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);

@@ -134,7 +134,7 @@ def test_pair_sets_are_bit_exact(cell_mode):
 
 # ---- particle interaction ----------------------------------------------------
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("cell_mode", [0, 1, 2])
 def test_one_evaluation_at_rest(c0, cell_mode, variant):
     case = cases.dam_break(0.02, cell_mode=cell_mode)
@@ -144,7 +144,7 @@ def test_one_evaluation_at_rest(c0, cell_mode, variant):
     eng.destroy()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_one_evaluation_in_motion(c0, variant):
     """After 60 steps the column moves: viscosity and DDT terms are active."""
     eng = sph.Engine.create(c0)
@@ -155,15 +155,17 @@ def test_one_evaluation_in_motion(c0, variant):
     eng.destroy()
 
 
-def test_one_evaluation_ragged_sizes():
+@pytest.mark.parametrize("variant", [0, 2])
+def test_one_evaluation_ragged_sizes(variant):
     """Random clouds of awkward sizes (not multiples of any tile)."""
     from tests.lattice import random_cloud
-    for n, seed in ((1, 1), (31, 2), (257, 3), (2049, 4)):
+    for n, seed in ((1, 1), (2, 5), (31, 2), (257, 3), (2049, 4)):
         c = random_cloud(N=n, L=0.08 * (n / 257) ** (1 / 3) + 0.01, seed=seed)
         c.ptype[::5] = 1
         c.vel = c.vel.astype(np.float32).astype(np.float64)
         c.rho = c.rho.astype(np.float32).astype(np.float64)
         eng = sph.Engine.create(c)
+        eng.set_options(pi_variant=variant)
         st = eng.get_state()
         g = eng.eval_forces()
         acc, drho, mu, npairs = oracle_eval(c, st)
@@ -203,6 +205,27 @@ def test_dam_break_100_steps(c0, c0_100, use_graph):
     assert np.abs(st["pos"] - o.pos).max() < 0.5 * dp
     assert s["n_out"] == 0 and s["flags"] == 0
     eng.destroy()
+
+
+@pytest.mark.parametrize("cell_mode", [0, 1])
+def test_queued_pair_loop_is_bit_identical(cell_mode):
+    """The queued pair loop takes each particle's pairs in the same order as
+    the compacted one, so whole steps agree bit for bit (a batch of uneven
+    cases, so that warps straddle cases and particle types)."""
+    cs = [cases.dam_break(0.04, seed=1, cell_mode=cell_mode),
+          cases.sloshing_tank(2001, 0.25, 0.02, 1.0, seed=2, cell_mode=cell_mode)]
+    res = []
+    for var in (0, 2):
+        e = sph.Engine.batch(cs)
+        e.set_options(pi_variant=var)
+        e.step(15)
+        res.append([e.get_state(i) for i in range(len(cs))] + [e.stats(0), e.stats(1)])
+        e.destroy()
+    for a, b in zip(res[0][:2], res[1][:2]):
+        for k in ("pos", "vel", "rho"):
+            assert np.array_equal(a[k], b[k]), k
+    assert res[0][2]["interactions"] == res[1][2]["interactions"]
+    assert res[0][3]["interactions"] == res[1][3]["interactions"]
 
 
 def test_determinism(c0):
