@@ -26,7 +26,8 @@ class OrcParams(C.Structure):
                 ("g", C.c_double * 3), ("dmin", C.c_double * 3),
                 ("dmax", C.c_double * 3), ("dt_fixed", C.c_double),
                 ("cell_mode", C.c_int32), ("ddt_mode", C.c_int32),
-                ("clamp_boundary_rho", C.c_int32), ("pad_", C.c_int32)]
+                ("clamp_boundary_rho", C.c_int32), ("visc_mode", C.c_int32),
+                ("nu0", C.c_double)]
 
 
 class OrcMotion(C.Structure):
@@ -54,6 +55,10 @@ def lib():
         L.orc_wendland_gradfac.argtypes = [C.c_double, C.c_double]
         L.orc_tait.restype = C.c_double
         L.orc_tait.argtypes = [P, C.c_double]
+        L.orc_sps_tau.restype = C.c_int
+        L.orc_sps_tau.argtypes = [P, C.c_int64, _D, _D, _D, _U8, C.c_void_p, _D]
+        L.orc_rho_hydro.restype = C.c_double
+        L.orc_rho_hydro.argtypes = [P, C.POINTER(C.c_double)]
         L.orc_grid.restype = C.c_int
         L.orc_grid.argtypes = [P, _D, C.POINTER(C.c_double), _I64, C.POINTER(C.c_int32)]
         L.orc_cells.restype = C.c_int
@@ -75,6 +80,11 @@ def lib():
         L.orc_step.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _U8,
                                _I32, _U8, C.c_void_p, C.POINTER(C.c_double),
                                C.POINTER(C.c_double), C.c_int64]
+        L.orc_step_verlet.restype = C.c_int64
+        L.orc_step_verlet.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _D, _D,
+                                      _U8, _I32, _U8, C.c_void_p, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32,
+                                      C.c_int64]
         L.orc_diag.restype = C.c_int
         L.orc_diag.argtypes = [P, C.c_int64, _D, _D, _U8, C.c_void_p, _D]
         _lib = L
@@ -93,6 +103,8 @@ def make_params(p: dict) -> OrcParams:
     o.cell_mode = int(p.get("cell_mode", 0))
     o.ddt_mode = int(p.get("ddt_mode", 1))
     o.clamp_boundary_rho = int(p.get("clamp_boundary_rho", 1))
+    o.visc_mode = int(p.get("visc_mode", 0))
+    o.nu0 = float(p.get("nu0", 1e-6))
     return o
 
 
@@ -120,6 +132,26 @@ def wendland_gradfac(r, h):
 
 def tait(params: dict, rho):
     return lib().orc_tait(C.byref(make_params(params)), float(rho))
+
+
+def sps_tau(params: dict, pos, vel, rho, ptype, out=None):
+    """tau / rho of Eq 25 per particle: columns xx, yy, zz, xy, xz, yz."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    vel = np.ascontiguousarray(vel, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    ptype = np.ascontiguousarray(ptype, np.uint8)
+    out_ = None if out is None else np.ascontiguousarray(out, np.uint8)
+    tau = np.zeros((len(ptype), 6))
+    if lib().orc_sps_tau(C.byref(make_params(params)), len(ptype), pos, vel, rho, ptype,
+                         _ptr(out_), tau) != 0:
+        raise ValueError("oracle sps_tau failed")
+    return tau
+
+
+def rho_hydro(params: dict, rab):
+    """Hydrostatic density difference rho^H_ab of Eq 19-20 for r_ab."""
+    r = (C.c_double * 3)(*[float(x) for x in rab])
+    return lib().orc_rho_hydro(C.byref(make_params(params)), r)
 
 
 def grid(params: dict):
@@ -215,7 +247,9 @@ def time_step(params: dict, acc, mumax, ptype, out=None):
 
 
 class OracleState:
-    """Mutable FP64 state of one case, advanced by Symplectic steps."""
+    """Mutable FP64 state of one case, advanced by Symplectic steps (Eq 33-34)
+    or, when the case's params say integrator = 1, by Verlet steps (Eq 30-31,
+    with an Eq 31 step every verlet_steps steps)."""
 
     def __init__(self, case):
         self.params = dict(case.params)
@@ -231,10 +265,28 @@ class OracleState:
         self.last_dt = C.c_double(0.0)
         self.steps = 0
         self.pairs = 0
+        self.verlet = int(self.params.get("integrator", 0)) == 1
+        self.vel_prev = self.vel.copy()
+        self.rho_prev = self.rho.copy()
+        self.step_count = C.c_int64(0)
 
     def step(self, nsteps=1):
         L = lib()
         mot = make_motions(self.motions)
+        if self.verlet:
+            ns = int(self.params.get("verlet_steps", 40)) or 40
+            npairs = L.orc_step_verlet(C.byref(make_params(self.params)),
+                                       C.cast(mot, C.c_void_p), len(self.motions),
+                                       len(self.pos), self.pos, self.vel, self.rho,
+                                       self.vel_prev, self.rho_prev, self.ptype, self.group,
+                                       self.out, self.order.ctypes.data_as(C.c_void_p),
+                                       C.byref(self.t), C.byref(self.last_dt),
+                                       C.byref(self.step_count), ns, int(nsteps))
+            if npairs < 0:
+                raise ValueError("oracle step failed")
+            self.steps += nsteps
+            self.pairs += npairs
+            return npairs
         npairs = L.orc_step(C.byref(make_params(self.params)), C.cast(mot, C.c_void_p),
                             len(self.motions), len(self.pos), self.pos, self.vel,
                             self.rho, self.ptype, self.group, self.out,

@@ -64,6 +64,12 @@ double orc_tait(const orc_params *p, double rho) {
   return B * (pow(rho / p->rho0, p->gamma) - 1.0);
 }
 
+double orc_rho_hydro(const orc_params *p, const double rab[3]) {
+  double B = p->cs0 * p->cs0 * p->rho0 / p->gamma;
+  double PH = -p->rho0 * (p->g[0] * rab[0] + p->g[1] * rab[1] + p->g[2] * rab[2]);
+  return p->rho0 * pow(1.0 + PH / B, 1.0 / p->gamma) - p->rho0;
+}
+
 /* ---- grid and neighbour list (Sect. 5.1) ------------------------------ */
 
 int orc_grid(const orc_params *p, double origin[3], double *cs, int64_t nc[3],
@@ -290,6 +296,7 @@ static int pair_interaction(const orc_params *p, int a, int b_fluid,
                             const double *ra, const double *rb,
                             const double *va, const double *vb, double rhoa,
                             double rhob, double Pa, double Pb, int a_fluid,
+                            const double *tau_a, const double *tau_b,
                             double *acc, double *drho, double *mu) {
   (void)a;
   double rab[3] = {ra[0] - rb[0], ra[1] - rb[1], ra[2] - rb[2]};
@@ -305,29 +312,146 @@ static int pair_interaction(const orc_params *p, int a, int b_fluid,
   /* continuity, Eq 15 (fluid a) and Eq 36 (boundary a) */
   *drho += rhoa * Vb * vdotgw;
   if (!a_fluid) return 1;
-  /* density diffusion D_a, Eq 17-18, over fluid neighbours only */
-  if (p->ddt_mode == 1 && b_fluid) {
-    double psi_dot_gradW = -2.0 * (rhob - rhoa) * F;
+  /* density diffusion D_a, Eq 17, over fluid neighbours only; psi_ab from
+   * Eq 18 (mode 1) or Eq 19-20 (mode 2), in the diffusive sign (drho > 0
+   * where the neighbours are denser than the hydrostatic difference) */
+  if ((p->ddt_mode == 1 || p->ddt_mode == 2) && b_fluid) {
+    double drho_ba = rhob - rhoa;
+    if (p->ddt_mode == 2) drho_ba -= orc_rho_hydro(p, rab);
+    double psi_dot_gradW = -2.0 * drho_ba * F;
     *drho += p->delta * p->h * p->cs0 * psi_dot_gradW * Vb;
   }
-  /* artificial viscosity, Eq 21 */
   double vr = vab[0] * rab[0] + vab[1] * rab[1] + vab[2] * rab[2];
   double muab = p->h * vr / (r2 + p->eta2);
   double Pi = 0.0;
-  if (vr < 0.0) {
+  if (p->visc_mode == 0 && vr < 0.0) {
+    /* artificial viscosity, Eq 21 */
     double cbar = p->cs0;
     double rhobar = 0.5 * (rhoa + rhob);
     Pi = -p->alpha * cbar * muab / rhobar;
   }
-  /* momentum, Eq 22 */
+  /* momentum, Eq 22 (Eq 16 with Pi) */
   double s = m * ((Pa + Pb) / (rhoa * rhob) + Pi);
   acc[0] -= s * gradW[0];
   acc[1] -= s * gradW[1];
   acc[2] -= s * gradW[2];
+  if (p->visc_mode == 1) {
+    /* laminar viscosity, Eq 23: m_b 4 nu0 (r_ab . grad W) v_ab / ((rho_a + rho_b)(r^2 + eta^2)) */
+    double rgw = rab[0] * gradW[0] + rab[1] * gradW[1] + rab[2] * gradW[2];
+    double cl = m * 4.0 * p->nu0 * rgw / ((rhoa + rhob) * (r2 + p->eta2));
+    for (int i = 0; i < 3; i++) acc[i] += cl * vab[i];
+    /* SPS stress, Eq 26: m_b (tau_a + tau_b)^{ij} / (rho_a rho_b) grad^j W, with
+     * tau = rho (tau / rho) from Eq 25 */
+    double T[3][3];
+    const int ix[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++)
+        T[i][j] = (rhoa * tau_a[ix[i][j]] + rhob * tau_b[ix[i][j]]) / (rhoa * rhob);
+    for (int i = 0; i < 3; i++)
+      acc[i] += m * (T[i][0] * gradW[0] + T[i][1] * gradW[1] + T[i][2] * gradW[2]);
+  }
   /* Eq 35 inner maximum */
   double mu_abs = fabs(muab);
   if (mu_abs > *mu) *mu = mu_abs;
   return 1;
+}
+
+/* Candidate neighbours of particle a: every other in-domain particle (brute
+ * force, index order) or every particle of the (2M+1)^3 cells around a's
+ * cell (cell-list order).  The caller tests the support and the types. */
+static int64_t candidates(int use_cells, const cell_list *cl, int64_t n, const uint8_t *out,
+                          int64_t a, int64_t **buf, int64_t *cap) {
+  int64_t k = 0;
+#define ORC_PUSH(b)                                                   \
+  do {                                                                \
+    if (k == *cap) {                                                  \
+      *cap = *cap ? 2 * *cap : 1024;                                  \
+      *buf = (int64_t *)realloc(*buf, sizeof(int64_t) * (size_t)*cap); \
+    }                                                                 \
+    (*buf)[k++] = (b);                                                \
+  } while (0)
+  if (!use_cells) {
+    for (int64_t b = 0; b < n; b++)
+      if (b != a && !(out && out[b])) ORC_PUSH(b);
+  } else {
+    int64_t c = cl->cellof[a];
+    int64_t cx = c % cl->nc[0], cy = (c / cl->nc[0]) % cl->nc[1], cz = c / (cl->nc[0] * cl->nc[1]);
+    int32_t M = cl->margin;
+    for (int64_t z = cz - M; z <= cz + M; z++)
+      for (int64_t y = cy - M; y <= cy + M; y++)
+        for (int64_t x = cx - M; x <= cx + M; x++) {
+          int64_t cc = (z * cl->nc[1] + y) * cl->nc[0] + x;
+          for (int64_t q = cl->start[cc]; q < cl->start[cc + 1]; q++)
+            if (cl->order[q] != a) ORC_PUSH(cl->order[q]);
+        }
+  }
+#undef ORC_PUSH
+  return k;
+}
+
+/* Eq 24-25 for every active fluid particle (tau6 = tau / rho, 6 per particle). */
+static void sps_tau_all(const orc_params *p, int64_t n, const double *pos, const double *vel,
+                        const double *rho, const uint8_t *type, const uint8_t *out,
+                        int use_cells, const cell_list *cl, double *tau6) {
+  const double m = p->rho0 * p->dp * p->dp * p->dp;
+  const double R2 = 4.0 * p->h * p->h;
+#pragma omp parallel
+  {
+    int64_t *buf = NULL, cap = 0;
+#pragma omp for schedule(dynamic, 256)
+    for (int64_t a = 0; a < n; a++) {
+      double *T = tau6 + 6 * a;
+      for (int i = 0; i < 6; i++) T[i] = 0.0;
+      int active = !(out && out[a]) && (!use_cells || cl->cellof[a] >= 0);
+      if (!active || type[a] != 0) continue;
+      /* SPH velocity gradient G^{ij} = sum_b V_b (v_b - v_a)^i grad^j_a W_ab */
+      double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      const double *ra = pos + 3 * a, *va = vel + 3 * a;
+      int64_t nc = candidates(use_cells, cl, n, out, a, &buf, &cap);
+      for (int64_t k = 0; k < nc; k++) {
+        int64_t b = buf[k];
+        double rab[3] = {ra[0] - pos[3 * b], ra[1] - pos[3 * b + 1], ra[2] - pos[3 * b + 2]};
+        double r2 = rab[0] * rab[0] + rab[1] * rab[1] + rab[2] * rab[2];
+        if (!(r2 > 0.0 && r2 < R2)) continue;
+        double F = orc_wendland_gradfac(sqrt(r2), p->h);
+        double Vb = m / rho[b];
+        for (int i = 0; i < 3; i++)
+          for (int j = 0; j < 3; j++) G[i][j] += Vb * (vel[3 * b + i] - va[i]) * F * rab[j];
+      }
+      /* strain rate S = (G + G^T) / 2 and |S| = (2 S:S)^(1/2) / 2 as printed
+       * with Eq 25; nu_SPS = (C_S Delta)^2 |S| (dimensionally consistent
+       * reading of the printed square); Delta = dp */
+      double S[3][3], SS = 0.0;
+      for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+          S[i][j] = 0.5 * (G[i][j] + G[j][i]);
+          SS += S[i][j] * S[i][j];
+        }
+      double Smag = 0.5 * sqrt(2.0 * SS);
+      double tr = S[0][0] + S[1][1] + S[2][2];
+      double nu = ORC_SPS_CS * p->dp * ORC_SPS_CS * p->dp * Smag;
+      double iso = -(2.0 / 3.0) * ORC_SPS_CL * p->dp * p->dp * Smag * Smag;
+      T[0] = 2.0 * nu * (S[0][0] - tr / 3.0) + iso;
+      T[1] = 2.0 * nu * (S[1][1] - tr / 3.0) + iso;
+      T[2] = 2.0 * nu * (S[2][2] - tr / 3.0) + iso;
+      T[3] = 2.0 * nu * S[0][1];
+      T[4] = 2.0 * nu * S[0][2];
+      T[5] = 2.0 * nu * S[1][2];
+    }
+    free(buf);
+  }
+}
+
+int orc_sps_tau(const orc_params *p, int64_t n, const double *pos, const double *vel,
+                const double *rho, const uint8_t *type, const uint8_t *out, double *tau6) {
+  cell_list cl;
+  if (cl_build(p, n, pos, type, out, &cl)) {
+    cl_free(&cl);
+    return -1;
+  }
+  sps_tau_all(p, n, pos, vel, rho, type, out, 1, &cl, tau6);
+  cl_free(&cl);
+  return 0;
 }
 
 int64_t orc_interact(const orc_params *p, int64_t n, const double *pos,
@@ -352,57 +476,49 @@ int64_t orc_interact_range(const orc_params *p, int64_t n, const double *pos,
   }
   double *press = (double *)malloc(sizeof(double) * (n ? n : 1));
   for (int64_t a = 0; a < n; a++) press[a] = orc_tait(p, rho[a]);
+  double *tau6 = NULL;
+  if (p->visc_mode == 1) {
+    tau6 = (double *)malloc(sizeof(double) * 6 * (size_t)(n ? n : 1));
+    sps_tau_all(p, n, pos, vel, rho, type, out, use_cells, &cl, tau6);
+  }
+  static const double zero6[6] = {0, 0, 0, 0, 0, 0};
   int64_t total = 0;
 
-#pragma omp parallel for schedule(dynamic, 256) reduction(+ : total)
-  for (int64_t a = a0; a < a1; a++) {
-    double ac[3] = {0.0, 0.0, 0.0}, dr = 0.0, mu = 0.0;
-    int a_fluid = type[a] == 0;
-    int active = !(out && out[a]) && (!use_cells || cl.cellof[a] >= 0);
-    if (active) {
-      const double *ra = pos + 3 * a;
-      if (!use_cells) {
-        for (int64_t b = 0; b < n; b++) {
-          if (b == a || (out && out[b])) continue;
+#pragma omp parallel reduction(+ : total)
+  {
+    int64_t *buf = NULL, cap = 0;
+#pragma omp for schedule(dynamic, 256)
+    for (int64_t a = a0; a < a1; a++) {
+      double ac[3] = {0.0, 0.0, 0.0}, dr = 0.0, mu = 0.0;
+      int a_fluid = type[a] == 0;
+      int active = !(out && out[a]) && (!use_cells || cl.cellof[a] >= 0);
+      if (active) {
+        const double *ra = pos + 3 * a;
+        int64_t nc = candidates(use_cells, &cl, n, out, a, &buf, &cap);
+        for (int64_t k = 0; k < nc; k++) {
+          int64_t b = buf[k];
           int b_fluid = type[b] == 0;
           if (!a_fluid && !b_fluid) continue; /* Eq 36: b in F only */
-          total += pair_interaction(p, (int)a, b_fluid, ra, pos + 3 * b,
-                                    vel + 3 * a, vel + 3 * b, rho[a], rho[b],
-                                    press[a], press[b], a_fluid, ac, &dr, &mu);
+          total += pair_interaction(p, (int)a, b_fluid, ra, pos + 3 * b, vel + 3 * a,
+                                    vel + 3 * b, rho[a], rho[b], press[a], press[b], a_fluid,
+                                    tau6 ? tau6 + 6 * a : zero6, tau6 ? tau6 + 6 * b : zero6,
+                                    ac, &dr, &mu);
         }
-      } else {
-        int64_t c = cl.cellof[a];
-        int64_t cx = c % cl.nc[0], cy = (c / cl.nc[0]) % cl.nc[1],
-                cz = c / (cl.nc[0] * cl.nc[1]);
-        int32_t M = cl.margin;
-        for (int64_t z = cz - M; z <= cz + M; z++)
-          for (int64_t y = cy - M; y <= cy + M; y++)
-            for (int64_t x = cx - M; x <= cx + M; x++) {
-              int64_t cc = (z * cl.nc[1] + y) * cl.nc[0] + x;
-              for (int64_t k = cl.start[cc]; k < cl.start[cc + 1]; k++) {
-                int64_t b = cl.order[k];
-                if (b == a) continue;
-                int b_fluid = type[b] == 0;
-                if (!a_fluid && !b_fluid) continue;
-                total += pair_interaction(p, (int)a, b_fluid, ra, pos + 3 * b,
-                                          vel + 3 * a, vel + 3 * b, rho[a],
-                                          rho[b], press[a], press[b], a_fluid,
-                                          ac, &dr, &mu);
-              }
-            }
+        if (a_fluid) {
+          ac[0] += p->g[0];
+          ac[1] += p->g[1];
+          ac[2] += p->g[2];
+        }
       }
-      if (a_fluid) {
-        ac[0] += p->g[0];
-        ac[1] += p->g[1];
-        ac[2] += p->g[2];
-      }
+      acc[3 * a] = ac[0];
+      acc[3 * a + 1] = ac[1];
+      acc[3 * a + 2] = ac[2];
+      drho[a] = dr;
+      mumax[a] = mu;
     }
-    acc[3 * a] = ac[0];
-    acc[3 * a + 1] = ac[1];
-    acc[3 * a + 2] = ac[2];
-    drho[a] = dr;
-    mumax[a] = mu;
+    free(buf);
   }
+  free(tau6);
   free(press);
   if (use_cells) cl_free(&cl);
   return total;
@@ -549,6 +665,73 @@ int64_t orc_step(const orc_params *p, const orc_motion *motions, int32_t nmot,
   free(pos0);
   free(vel0);
   free(rho0);
+  free(tmp);
+  return pairs;
+}
+
+/* ---- Verlet scheme (Sect. 2.5.1) ---------------------------------------- */
+
+int64_t orc_step_verlet(const orc_params *p, const orc_motion *motions, int32_t nmot,
+                        int64_t n, double *pos, double *vel, double *rho,
+                        double *vel_prev, double *rho_prev, const uint8_t *type,
+                        const int32_t *group, uint8_t *out, int64_t *order, double *t,
+                        double *last_dt, int64_t *step, int32_t ns, int64_t nsteps) {
+  if (ns < 1) return -1;
+  size_t N = (size_t)(n ? n : 1);
+  double *acc = (double *)malloc(sizeof(double) * 3 * N);
+  double *drho = (double *)malloc(sizeof(double) * N);
+  double *mu = (double *)malloc(sizeof(double) * N);
+  int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * N);
+  int64_t pairs = 0;
+  for (int64_t s = 0; s < nsteps; s++) {
+    /* NL + PI on state n: F^n, R^n */
+    if (order) {
+      orc_sort(p, n, pos, type, out, order, tmp);
+      memcpy(order, tmp, sizeof(int64_t) * (size_t)n);
+    }
+    int64_t np = orc_interact(p, n, pos, vel, rho, type, out, 1, acc, drho, mu);
+    if (np < 0) { pairs = -1; break; }
+    pairs += np;
+    double dt = orc_dt(p, n, acc, mu, type, out);
+    double t0 = *t;
+    int eq31 = (*step % ns) == 0;
+    for (int64_t a = 0; a < n; a++) {
+      if (out[a]) continue;
+      /* density: Eq 30 (from rho^{n-1}, twice the step) or Eq 31 */
+      double rnew = eq31 ? rho[a] + dt * drho[a] : rho_prev[a] + 2.0 * dt * drho[a];
+      if (type[a] == 0) {
+        for (int k = 0; k < 3; k++) {
+          double vn = vel[3 * a + k], F = acc[3 * a + k];
+          pos[3 * a + k] += dt * vn + 0.5 * dt * dt * F;
+          double vnew = eq31 ? vn + dt * F : vel_prev[3 * a + k] + 2.0 * dt * F;
+          vel_prev[3 * a + k] = vn;
+          vel[3 * a + k] = vnew;
+        }
+      } else {
+        if (p->clamp_boundary_rho && rnew < p->rho0) rnew = p->rho0;
+        for (int k = 0; k < 3; k++) vel_prev[3 * a + k] = vel[3 * a + k];
+        int g = group ? group[a] : -1;
+        if (g >= 0 && g < nmot) {
+          const orc_motion *m = motions + g;
+          double d = motion_disp(m, t0 + dt) - motion_disp(m, t0);
+          double v = motion_vel(m, t0 + dt);
+          for (int k = 0; k < 3; k++) {
+            pos[3 * a + k] += d * m->axis[k];
+            vel[3 * a + k] = v * m->axis[k];
+          }
+        }
+      }
+      rho_prev[a] = rho[a];
+      rho[a] = rnew;
+      if (!inside_domain(p, pos + 3 * a)) out[a] = 1; /* frozen at n+1 */
+    }
+    *t = t0 + dt;
+    *last_dt = dt;
+    *step += 1;
+  }
+  free(acc);
+  free(drho);
+  free(mu);
   free(tmp);
   return pairs;
 }

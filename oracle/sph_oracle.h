@@ -30,10 +30,17 @@ typedef struct {
   double dmax[3];
   double dt_fixed;  /* > 0: use this time step instead of Eq 35             */
   int32_t cell_mode;          /* 0: cells of 2h (Sect. 5.1); 1: of h; 2: of 2h/3 */
-  int32_t ddt_mode;           /* 0: no density diffusion; 1: Eq 17 + Eq 18 */
+  int32_t ddt_mode;           /* 0: no density diffusion; 1: Eq 17 + Eq 18;
+                               * 2: Eq 17 + Eq 19-20 (dynamic density)     */
   int32_t clamp_boundary_rho; /* 1: boundary density kept >= rho0          */
-  int32_t pad_;
+  int32_t visc_mode;          /* 0: artificial viscosity, Eq 21-22;
+                               * 1: laminar viscosity + SPS, Eq 23-27      */
+  double nu0;                 /* kinematic viscosity of Eq 23 (m^2/s)      */
 } orc_params;
+
+/* SPS constants of Eq 25: Smagorinsky C_S and C_l; Delta = dp. */
+#define ORC_SPS_CS 0.12
+#define ORC_SPS_CL 0.0066
 
 /* Imposed sinusoidal translation of a group of boundary particles (Eq 37):
  * displacement D(t) = amp * (sin(omega t + phase) - sin(phase)) along axis. */
@@ -47,6 +54,17 @@ double orc_wendland_w(double r, double h);
 double orc_wendland_gradfac(double r, double h);
 /* Tait equation of state, Eq 28. */
 double orc_tait(const orc_params *p, double rho);
+/* SPS stress of Eq 25 divided by rho, for fluid particle a, from the SPH
+ * velocity gradient over its neighbours b in P (Eq 24-25):
+ * out = {xx, yy, zz, xy, xz, yz}.  Zero for boundary and frozen particles. */
+int orc_sps_tau(const orc_params *p, int64_t n, const double *pos, const double *vel,
+                const double *rho, const uint8_t *type, const uint8_t *out, double *tau6);
+
+/* Hydrostatic density difference of Eq 19: the density that Eq 28, solved
+ * for rho, gives at the pressure P^H_ab = rho0 g z_ab of Eq 20, minus rho0.
+ * With a gravity vector g, rho0 g z_ab reads -rho0 (g . r_ab), which is
+ * rho0 |g| (z_a - z_b) when g points down z. */
+double orc_rho_hydro(const orc_params *p, const double rab[3]);
 
 /* Cell grid: origin, cell size, cell counts and margin (in cells). */
 int orc_grid(const orc_params *p, double origin[3], double *cs, int64_t nc[3],
@@ -98,6 +116,18 @@ int64_t orc_step(const orc_params *p, const orc_motion *motions, int32_t nmot,
                  int64_t n, double *pos, double *vel, double *rho,
                  const uint8_t *type, const int32_t *group, uint8_t *out,
                  int64_t *order, double *t, double *last_dt, int64_t nsteps);
+
+/* nsteps Verlet steps (Eq 30, with the Eq 31 step whenever the count of
+ * completed steps *step is a multiple of ns; so the first step, which has
+ * no state n-1, is an Eq 31 step).  vel_prev / rho_prev hold v^{n-1} and
+ * rho^{n-1} and are updated with the state.  One PI per step, the time step
+ * of Eq 35 from it, boundary conditions as in orc_step.  Returns the number
+ * of evaluated pairs. */
+int64_t orc_step_verlet(const orc_params *p, const orc_motion *motions, int32_t nmot,
+                        int64_t n, double *pos, double *vel, double *rho,
+                        double *vel_prev, double *rho_prev, const uint8_t *type,
+                        const int32_t *group, uint8_t *out, int64_t *order, double *t,
+                        double *last_dt, int64_t *step, int32_t ns, int64_t nsteps);
 
 /* Diagnostics: res = {total mass, fluid kinetic energy, fluid momentum x, y,
  * z, front (max x of in-domain fluid), number out of domain}. */

@@ -70,7 +70,8 @@ def default_params(dp: float, depth: float, domain_min, domain_max, **kw) -> dic
              alpha=0.01, delta=0.1, cfl=0.2, eta2=0.001 * h * h,
              gravity=(0.0, 0.0, -G), domain_min=tuple(float(x) for x in domain_min),
              domain_max=tuple(float(x) for x in domain_max), cell_mode=0, ddt_mode=1,
-             clamp_boundary_rho=1, dt_fixed=0.0, dt_min=0.0)
+             clamp_boundary_rho=1, dt_fixed=0.0, dt_min=0.0, integrator=0, verlet_steps=40,
+             visc_mode=0, nu0=1e-6)
     p.update(kw)
     return p
 

@@ -141,9 +141,11 @@ def test_cell_list_interaction_equals_brute_force():
     np.testing.assert_allclose(m2, m1, rtol=1e-12)
 
 
-def test_momentum_is_conserved():
-    """Eq 16/22 use a symmetric operator: sum_a m a_a = 0 for an all-fluid set."""
-    c = random_cloud(N=400, L=0.12, seed=7)
+@pytest.mark.parametrize("visc_mode", [0, 1])
+def test_momentum_is_conserved(visc_mode):
+    """Eq 16/22 (and Eq 23, 26 for visc_mode 1) use antisymmetric pair terms:
+    sum_a m a_a = 0 for an all-fluid set."""
+    c = random_cloud(N=400, L=0.12, seed=7, visc_mode=visc_mode, nu0=1e-2)
     acc, _, _, npairs = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)
     assert npairs > 10000
     total = acc.sum(axis=0)
@@ -210,6 +212,58 @@ def test_pressure_gradient_linear_field():
     assert abs(acc[ic, 0]) < 1e-6 * abs(expect) and abs(acc[ic, 1]) < 1e-6 * abs(expect)
 
 
+def test_laminar_viscosity_is_a_laplacian():
+    """Eq 23 (Lo and Shao): Gamma_a -> nu0 laplacian(v) for v_x = kappa y^2 on
+    a lattice at rest density (P = 0); the SPS term vanishes at y = 0."""
+    n = 11
+    c = lattice_case(n=n, visc_mode=1, nu0=1e-3)
+    p = c.params
+    ic = centre_index(n)
+    kappa = 3.0
+    y = c.pos[:, 1] - c.pos[ic, 1]
+    c.vel[:] = 0
+    c.vel[:, 0] = kappa * y * y
+    acc, _, _, _ = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
+    assert acc[ic, 0] == pytest.approx(2 * kappa * p["nu0"], rel=2e-2)
+    assert abs(acc[ic, 1]) < 1e-9 and abs(acc[ic, 2]) < 1e-9
+
+
+def test_sps_stress_of_a_simple_shear():
+    """Eq 24-25 for v_x = gamma y: S_xy = gamma/2, |S| = gamma/2 (the printed
+    |S| = (2 S:S)^(1/2) / 2), nu_SPS = (C_S dp)^2 |S|, so tau_xy/rho =
+    (C_S dp)^2 gamma^2 / 2 and the diagonal -(2/3) C_l dp^2 gamma^2 / 4."""
+    n = 11
+    c = lattice_case(n=n, visc_mode=1, nu0=0.0)
+    ic = centre_index(n)
+    gam = 5.0
+    c.vel[:] = 0
+    c.vel[:, 0] = gam * (c.pos[:, 1] - c.pos[ic, 1])
+    T = oracle.sps_tau(c.params, c.pos, c.vel, c.rho, c.ptype)[ic]
+    dp = c.params["dp"]
+    assert T[3] == pytest.approx((0.12 * dp) ** 2 * gam ** 2 / 2, rel=2e-2)
+    for k in range(3):
+        assert T[k] == pytest.approx(-(2 / 3) * 0.0066 * dp ** 2 * gam ** 2 / 4, rel=4e-2)
+    assert abs(T[4]) < 1e-6 * T[3] and abs(T[5]) < 1e-6 * T[3]
+
+
+def test_sps_force_is_the_stress_divergence():
+    """Eq 26 -> div(tau)/rho.  For v_x = kappa (y - y0)^2 (nu0 = 0), with
+    Y = y - y0 at the centre: tau_xy/rho = 2 (C_S dp)^2 kappa^2 |Y| Y and
+    tau_ii/rho = -(2/3) C_l dp^2 kappa^2 Y^2, so a_x = 4 (C_S dp)^2 kappa^2 |Y|
+    and a_y = -(4/3) C_l dp^2 kappa^2 Y."""
+    n = 13
+    c = lattice_case(n=n, visc_mode=1, nu0=0.0)
+    ic = centre_index(n)
+    dp = c.params["dp"]
+    kappa, Y = 50.0, 0.3
+    y = c.pos[:, 1] - c.pos[ic, 1] + Y
+    c.vel[:] = 0
+    c.vel[:, 0] = kappa * y * y
+    acc, _, _, _ = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)
+    assert acc[ic, 0] == pytest.approx(4 * (0.12 * dp) ** 2 * kappa ** 2 * Y, rel=3e-2)
+    assert acc[ic, 1] == pytest.approx(-(4 / 3) * 0.0066 * dp ** 2 * kappa ** 2 * Y, rel=3e-2)
+
+
 def test_density_diffusion_is_a_laplacian():
     """Eq 17-18 (diffusive reading): D_a -> delta h c laplacian(rho) for a
     quadratic density field (Brookshaw form of the SPH Laplacian)."""
@@ -245,6 +299,55 @@ def test_density_diffusion_bump_sign_and_conservation():
     _, drho, _, _ = oracle.interact(cl.params, cl.pos, cl.vel, cl.rho, cl.ptype)
     vol = (cl.params["rho0"] * cl.params["dp"] ** 3) / cl.rho
     assert abs(np.sum(vol * drho)) < 1e-12 * np.sum(np.abs(vol * drho))
+
+
+def test_hydrostatic_density_difference_inverts_tait():
+    """Eq 19-20: rho^H_ab is the density at which Eq 28 gives the pressure
+    rho0 g z_ab (b below a: positive; horizontal: zero; no gravity: zero)."""
+    p = cases.default_params(0.02, 0.4, (0, 0, 0), (1, 1, 1))
+    rho0, g = p["rho0"], 9.81
+    for dz in (0.05, -0.03, 0.0):
+        rH = oracle.rho_hydro(p, (0.01, -0.02, dz))
+        assert oracle.tait(p, rho0 + rH) == pytest.approx(rho0 * g * dz, rel=1e-9, abs=1e-9)
+        assert (rH > 0) == (dz > 0)
+    p0 = dict(p, gravity=(0.0, 0.0, 0.0))
+    assert oracle.rho_hydro(p0, (0.0, 0.0, 0.05)) == 0.0
+
+
+def hydrostatic_lattice(ddt_mode, cs0):
+    """11^3 lattice under gravity, density from Eq 28 with P = rho0 g (H - z)."""
+    c = lattice_case(n=11, gravity=(0.0, 0.0, -9.81), ddt_mode=ddt_mode, cs0=cs0)
+    p = c.params
+    B = p["cs0"] ** 2 * p["rho0"] / p["gamma"]
+    H = c.pos[:, 2].max() + p["dp"]
+    c.rho[:] = p["rho0"] * (1 + p["rho0"] * 9.81 * (H - c.pos[:, 2]) / B) ** (1 / p["gamma"])
+    return c
+
+
+def test_fourtakas_ddt_vanishes_on_a_hydrostatic_column():
+    """Eq 19: psi acts on the dynamic density only.  On a column at rest in
+    hydrostatic balance the Eq 18 term is large where the support is cut (top
+    and bottom layers: b runs over fluid only), while the Eq 19 term is ~0
+    there (its residue is the curvature of Eq 28, ~1e-5 here)."""
+    Dm = {}
+    for mode in (1, 2):
+        c = hydrostatic_lattice(mode, cs0=1000.0)
+        c.vel[:] = 0
+        _, drho, _, _ = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)
+        Dm[mode] = drho
+    z = c.pos[:, 2]
+    edge = (z <= z.min() + 1e-9) | (z >= z.max() - 1e-9)
+    assert np.abs(Dm[1][edge]).min() > 0
+    assert np.abs(Dm[2]).max() < 1e-4 * np.abs(Dm[1][edge]).max()
+
+
+def test_fourtakas_ddt_without_gravity_is_eq18():
+    """With g = 0, P^H = 0 and Eq 19 reduces to Eq 18 exactly."""
+    out = []
+    for mode in (1, 2):
+        c = random_cloud(N=300, L=0.1, seed=9, ddt_mode=mode)
+        out.append(oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)[1])
+    assert np.array_equal(out[0], out[1])
 
 
 def test_boundary_particles_dbc():
@@ -316,6 +419,41 @@ def test_imposed_motion_follows_law():
     np.testing.assert_allclose(s.vel[b, 0], m["amp"] * m["omega"] * math.cos(m["omega"] * t),
                                atol=1e-12)
     np.testing.assert_allclose(s.pos[b, 1:], c.pos[b, 1:], atol=0)
+
+
+# ---- Eq 30-31: Verlet scheme ------------------------------------------------
+
+@pytest.mark.parametrize("ns", [1, 3, 40])
+def test_verlet_free_fall_is_exact(ns):
+    """Eq 30 (v^{n+1} = v^{n-1} + 2 dt F^n, r^{n+1} = r^n + dt v^n + dt^2 F^n / 2)
+    and Eq 31 both integrate a constant acceleration exactly at constant dt:
+    a dropped factor 2, v^n in place of v^{n-1}, or a missing dt^2 term breaks
+    this."""
+    c = cases.free_particle(integrator=1, verlet_steps=ns)
+    s = oracle.OracleState(c)
+    s.step(50)
+    t = s.t.value
+    g = np.array(c.params["gravity"])
+    np.testing.assert_allclose(s.pos[0], c.pos[0] + c.vel[0] * t + 0.5 * g * t * t,
+                               rtol=0, atol=1e-13)
+    np.testing.assert_allclose(s.vel[0], c.vel[0] + g * t, rtol=0, atol=1e-13)
+    assert s.step_count.value == 50
+
+
+def test_verlet_agrees_with_symplectic_on_dam_break():
+    """Both schemes are second order for the same equations (Sect. 2.5): after
+    100 steps of the dam break the two states agree far inside a particle
+    spacing, and the densities within 1e-3 relative."""
+    a = oracle.OracleState(cases.dam_break(0.02))
+    b = oracle.OracleState(cases.dam_break(0.02, integrator=1, verlet_steps=40))
+    a.step(100)
+    b.step(100)
+    assert b.t.value == pytest.approx(a.t.value, rel=1e-3)
+    assert np.abs(a.pos - b.pos).max() < 0.01 * 0.02
+    assert np.abs(a.rho - b.rho).max() < 1.0
+    da, db = a.diag(), b.diag()
+    assert db["ke"] == pytest.approx(da["ke"], rel=1e-2)
+    assert db["mass"] == da["mass"]
 
 
 def test_dam_break_steps_conserve_mass_and_stay_finite():
