@@ -30,11 +30,17 @@ import numpy as np  # noqa: E402
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Algorithmic FLOPs per evaluated pair (each +, -, *, comparison, sqrt and
-# reciprocal counts 1; a fused multiply-add counts 2), counted on the pair
-# formula of Eq 11, 15, 17-18, 21-22 and 35 as written out in the design doc:
+# reciprocal counts 1; a fused multiply-add counts 2), counted operation by
+# operation on the pair formula of Eq 11, 15, 17-18, 21-22 and 35:
 F_PAIR_FF = 48   # a in F, b in F: momentum + viscosity + continuity + DDT + Eq 35 max
 F_PAIR_FB = 45   # a in F, b in B: as above without density diffusion
 F_PAIR_BF = 25   # a in B, b in F: continuity of Eq 36 only
+# Eq 19-20 adds, per fluid-fluid pair: g . r_ab (5), P^H / B -> (1 + x)^(1/gamma)
+# as log, multiply, exp (3), times rho0 minus rho0 (2), minus from rho_b - rho_a (1)
+F_PAIR_FF_HYD = F_PAIR_FF + 11
+# Laminar + SPS (Eq 23-27) adds, per pair with a in F: Eq 23 (9), Eq 26 with
+# the stored tau (33) and the strain pass of Eq 24-25 (33); Eq 21 drops (4)
+F_PAIR_VISC = 9 + 33 + 33 - 4
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -332,6 +338,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_break")
     ap.add_argument("--cell-mode", type=int, default=1)
+    ap.add_argument("--ddt-mode", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--pi-variant", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "verlet"])
+    ap.add_argument("--visc-mode", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--nu0", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-block", type=int, default=20000)
@@ -360,14 +371,19 @@ def main():
     cs, desc = workload(args.workload, rank)
     for c in cs:
         c.params["cell_mode"] = args.cell_mode
+        c.params["ddt_mode"] = args.ddt_mode
+        c.params["integrator"] = 1 if args.integrator == "verlet" else 0
+        c.params["visc_mode"] = args.visc_mode
+        c.params["nu0"] = args.nu0
     with torch.cuda.stream(stream):
         eng = sph.Engine.batch(cs, stream=stream) if len(cs) > 1 else \
             sph.Engine.create(cs[0], stream=stream)
+    eng.set_options(pi_variant=args.pi_variant)
     n_particles = sum(c.n for c in cs)
 
     # warm-up
     eng.step(args.warmup)
-    eng.set_options(timing=1)
+    eng.set_options(pi_variant=args.pi_variant, timing=1)
     eng.timing(reset=True)
 
     def totals():
@@ -401,14 +417,22 @@ def main():
 
     # roofline of the dominant kernel (the interaction): algorithmic FLOPs per
     # launch / average launch duration (CUDA events on the engine's stream)
-    flops = F_PAIR_FF * ff + F_PAIR_FB * fb + F_PAIR_BF * bf
+    f_ff = {0: F_PAIR_FB, 1: F_PAIR_FF, 2: F_PAIR_FF_HYD}[args.ddt_mode]
+    f_fb = F_PAIR_FB
+    if args.visc_mode == 1:
+        f_ff += F_PAIR_VISC
+        f_fb += F_PAIR_VISC
+    flops = f_ff * ff + f_fb * fb + F_PAIR_BF * bf
     launches = max(1, tm["pi_launches"])
     pi_avg_s = tm["pi_ms"] / 1000.0 / launches
     achieved = flops / launches / pi_avg_s / 1e12
     peak = fp32_peak_tflops()
     roofline = {"bound": "alu", "kernel": "k_interact", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": measured_traffic(args.cell_mode, args.workload),
+                "traffic": measured_traffic(args.cell_mode, args.workload)
+                if (args.ddt_mode, args.pi_variant, args.integrator, args.visc_mode) ==
+                (1, 0, "symplectic", 0)
+                else None,
                 "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
                 "pi_ms_per_launch": 1000 * pi_avg_s,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal max clock)"}
@@ -419,6 +443,13 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": desc, "particles": n_particles, "cases": len(cs),
                       "cell_mode": ["2h", "h", "2h/3"][args.cell_mode],
+                      "density_diffusion": ["none", "Eq 18", "Eq 19-20"][args.ddt_mode],
+                      "viscosity": ["artificial, Eq 21", "laminar + SPS, Eq 23-27 (nu0 %g)"
+                                    % args.nu0][args.visc_mode],
+                      "integrator": {"symplectic": "Symplectic, Eq 33-34 (2 PI per step)",
+                                     "verlet": "Verlet, Eq 30-31, N_S = 40 (1 PI per step)"}[
+                          args.integrator],
+                      "pi_variant": args.pi_variant,
                       "l2": "state (%.0f MB) larger than L2 (129 MB), no flush" %
                             (n_particles * 177 / 1e6),
                       "parallelism": "replicas" if world > 1 else "single"},
@@ -432,6 +463,7 @@ def main():
         t0 = time.perf_counter()
         e2 = sph.Engine.create(cs[0], stream=stream, pinned=True) if len(cs) == 1 else \
             sph.Engine.batch(cs, stream=stream)
+        e2.set_options(pi_variant=args.pi_variant)
         e2.step(args.steps)
         st = [e2.get_state(i) for i in range(len(cs))]
         e2pairs = sum(e2.stats(i)["interactions"] for i in range(len(cs)))

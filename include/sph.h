@@ -57,9 +57,24 @@ typedef struct {
   double dt_fixed;  /* > 0: fixed time step instead of Eq 35                */
   double dt_min;    /* a step with dt < dt_min fails with SPH_ERR_UNSTABLE  */
   int32_t cell_mode;          /* 0: cells of 2h (Sect. 5.1); 1: of h (Sect. 5.3); 2: of 2h/3 */
-  int32_t ddt_mode;           /* 0: no density diffusion; 1: Eq 17 with Eq 18 */
+  int32_t ddt_mode;           /* 0: no density diffusion; 1: Eq 17 with Eq 18;
+                               * 2: Eq 17 with Eq 19-20 (dynamic density)  */
   int32_t clamp_boundary_rho; /* 1: boundary density kept >= rho0           */
   int32_t max_out;            /* out-of-domain quota; < 0: unlimited        */
+  int32_t integrator;         /* 0: Symplectic, Eq 33-34 (two PI per step);
+                               * 1: Verlet, Eq 30-31 (one PI per step).  All
+                               * cases of one engine use the same scheme;
+                               * pools run the Symplectic scheme only.     */
+  int32_t verlet_steps;       /* N_S of Eq 31: a step whose count of completed
+                               * steps is a multiple of N_S (the first step
+                               * included) is an Eq 31 step; 0 means 40    */
+  int32_t visc_mode;          /* 0: artificial viscosity (Eq 21-22, alpha);
+                               * 1: laminar viscosity (Eq 23, nu0) + SPS
+                               * turbulence (Eq 24-27, C_S = 0.12, C_l =
+                               * 0.0066, Delta = dp); needs one more
+                               * neighbour pass per interaction             */
+  int32_t pad_;
+  double nu0;                 /* kinematic viscosity of Eq 23 (m^2/s)       */
 } sph_case_params;
 
 /* Imposed translation of a group of boundary particles (Eq 37):
@@ -86,8 +101,8 @@ typedef struct {
 typedef struct {
   double t;              /* simulated time                                  */
   double last_dt;        /* last Eq 35 time step                            */
-  int64_t step;          /* completed Symplectic steps                      */
-  int64_t interactions;  /* evaluated ordered pairs (a,b), both PI evaluations */
+  int64_t step;          /* completed time steps                            */
+  int64_t interactions;  /* evaluated ordered pairs (a,b), all PI evaluations */
   int64_t interactions_fb; /* ... of which a in F, b in B                    */
   int64_t interactions_bf; /* ... of which a in B (b in F, Eq 36)             */
   double mass;           /* sum of particle masses (Eq 14)                  */
@@ -155,9 +170,10 @@ int sph_get_timing(sph_engine e, double *pi_ms, int64_t *pi_launches,
 
 /* ---- checkpoint ----------------------------------------------------------
  * sph_get_raw: bit-exact snapshot of case icase (device storage format:
- * integer cell + float offset, float velocity/density, time, step, dt).
- * With buf == NULL only *bytes is set.  sph_create_from_raw rebuilds a
- * single-case engine that continues bit-identically. */
+ * integer cell + float offset, float velocity/density, time, step, dt; for
+ * the Verlet scheme also v^{n-1} and rho^{n-1} of Eq 30).  With buf == NULL
+ * only *bytes is set.  sph_create_from_raw rebuilds a single-case engine
+ * that continues bit-identically (a Verlet engine needs a Verlet snapshot). */
 int sph_get_raw(sph_engine e, int32_t icase, void *buf, size_t *bytes);
 int sph_create_from_raw(const sph_case_params *params, const sph_particles *parts,
                         const void *buf, size_t bytes, void *stream,
@@ -173,6 +189,15 @@ int sph_create_from_raw(const sph_case_params *params, const sph_particles *part
 int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho,
                     float *mumax, double *dt, int64_t *pairs);
 
+
+/* sph_eval_sps: tau / rho of Eq 25 (the SPS stress of Eq 24-25 with the
+ * velocity gradient of the SPH estimate over b in P) for every particle of
+ * case icase, on its current state and without advancing it.  tau6 [6n]
+ * caller-owned host buffer, original particle order, per particle xx, yy,
+ * zz, xy, xz, yz; zero for boundary particles, frozen particles and cases
+ * with visc_mode 0.  SPH_ERR_STATE if no case of the engine uses
+ * visc_mode 1. */
+int sph_eval_sps(sph_engine e, int32_t icase, float *tau6);
 /* sph_get_order: rebuild the neighbour list and return, for case icase, the
  * original ids in device (cell-sorted) order and their cell ids (-1 out). */
 int sph_get_order(sph_engine e, int32_t icase, int64_t *ids, int64_t *cells,

@@ -50,6 +50,13 @@ int make_grid(const sph_case_params &p, Grid &g) {
   if (!(p.h > 0) || !(p.dp > 0) || !(p.rho0 > 0) || !(p.cs0 > 0) || !(p.gamma > 0))
     return fail(SPH_ERR_ARG, "h, dp, rho0, cs0 and gamma must be positive");
   if (p.cell_mode < 0 || p.cell_mode > 2) return fail(SPH_ERR_ARG, "cell_mode must be 0, 1 or 2");
+  if (p.ddt_mode < 0 || p.ddt_mode > 2) return fail(SPH_ERR_ARG, "ddt_mode must be 0, 1 or 2");
+  if (p.integrator < 0 || p.integrator > 1)
+    return fail(SPH_ERR_ARG, "integrator must be 0 (Symplectic) or 1 (Verlet)");
+  if (p.verlet_steps < 0) return fail(SPH_ERR_ARG, "verlet_steps must be >= 0");
+  if (p.visc_mode < 0 || p.visc_mode > 1)
+    return fail(SPH_ERR_ARG, "visc_mode must be 0 (artificial) or 1 (laminar + SPS)");
+  if (!(p.nu0 >= 0)) return fail(SPH_ERR_ARG, "nu0 must be >= 0");
   const double dmin[3] = {p.domain_min.x, p.domain_min.y, p.domain_min.z};
   const double dmax[3] = {p.domain_max.x, p.domain_max.y, p.domain_max.z};
   // cells of 2h, h or 2h/3: the 2h support spans margin = 1, 2 or 3 cells
@@ -95,9 +102,10 @@ void fill_const(const sph_case_params &p, const sph_particles &parts, const Grid
   C.nz = g.nc[2];
   C.margin = g.margin;
   C.cellbase = cellbase;
-  C.ddt = p.ddt_mode == 1;
+  C.ddt = p.ddt_mode;
   C.clamp = p.clamp_boundary_rho != 0;
   C.max_out = p.max_out;
+  C.verlet_steps = p.verlet_steps > 0 ? p.verlet_steps : 40;
   C.active = 1;
   C.n_fluid = (int32_t)n_fluid;
   C.h = (float)p.h;
@@ -115,13 +123,27 @@ void fill_const(const sph_case_params &p, const sph_particles &parts, const Grid
   const double aD = 21.0 / (16.0 * kPi * p.h * p.h * p.h);  // Eq 11, 3-D
   C.cw = (float)(-5.0 * aD / (p.h * p.h));
   C.half_inv_h = (float)(0.5 / p.h);
-  C.kvisc = (float)(-2.0 * p.alpha * p.cs0 * p.h);
-  C.kddt = p.ddt_mode == 1 ? (float)(2.0 * p.delta * p.h * p.cs0) : 0.f;
+  // artificial viscosity only in visc_mode 0; laminar + SPS constants otherwise
+  C.kvisc = p.visc_mode == 0 ? (float)(-2.0 * p.alpha * p.cs0 * p.h) : 0.f;
+  C.visc = p.visc_mode;
+  C.nu0 = (float)p.nu0;
+  C.sps_cs2 = (float)(0.12 * p.dp * 0.12 * p.dp);
+  C.sps_cl2 = (float)(0.0066 * p.dp * p.dp);
+  C.kddt = p.ddt_mode != 0 ? (float)(2.0 * p.delta * p.h * p.cs0) : 0.f;
   C.g[0] = (float)p.gravity.x;
   C.g[1] = (float)p.gravity.y;
   C.g[2] = (float)p.gravity.z;
   C.cs0f = (float)p.cs0;
   C.inv_csf = (float)(1.0 / g.cs);
+  C.inv_gamma = (float)(1.0 / p.gamma);
+  const double kB = -p.gamma / (p.cs0 * p.cs0);  // -rho0 / B
+  C.khyd[0] = (float)(kB * p.gravity.x);
+  C.khyd[1] = (float)(kB * p.gravity.y);
+  C.khyd[2] = (float)(kB * p.gravity.z);
+  const double k = 1.0 / p.gamma;
+  C.hyd_c[0] = (float)((k - 1.0) / 2.0);
+  C.hyd_c[1] = (float)((k - 2.0) / 3.0);
+  C.hyd_c[2] = (float)((k - 3.0) / 4.0);
 }
 
 struct Slot {
@@ -150,6 +172,11 @@ struct sph_engine_t {
   int cap_cases = 0;
   int nbits = 0;
   int margin = 0;  // shared by all cases (0: not set yet)
+  int integrator = 0;  // 0 Symplectic (Eq 33-34), 1 Verlet (Eq 30-31), all cases
+  bool ext = false;    // a case uses Eq 19-20 diffusion or laminar + SPS viscosity
+  bool sps = false;    // a case uses laminar + SPS viscosity (tau buffers below)
+  float4 *tau4 = nullptr;  // (tau/rho) of Eq 25 in sorted order: xx, yy, zz, xy
+  float2 *tau2 = nullptr;  //   xz, yz
   bool pool = false;
   std::vector<Slot> slots;
   std::vector<CaseConst> hconst;
@@ -176,6 +203,7 @@ struct sph_engine_t {
   sph_options opt{};
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_n = -1, graph_dead = -1;  // n_phys and cells_hw of the captured graph
+  int graph_ext = 0;                       // ext + 2 sps of the captured graph
   std::vector<cudaEvent_t> evs;
   double pi_ms = 0, step_ms = 0;
   int64_t pi_launches = 0, kernel_launches = 0;
@@ -231,6 +259,7 @@ int allocate(sph_engine e) {
     e->S[b].id = (uint32_t *)A(4 * N);
     e->S[b].cid = (uint16_t *)A(2 * N);
     e->S[b].code = (uint8_t *)A(N);
+    e->S[b].vrprev = e->integrator == 1 && b < 2 ? (float4 *)A(16 * N) : nullptr;
   }
   e->keysA = (uint32_t *)A(4 * N);
   e->keysB = (uint32_t *)A(4 * N);
@@ -243,6 +272,10 @@ int allocate(sph_engine e) {
   e->cstart = (uint32_t *)A(4 * (2 * e->cap_cells + 2));
   e->cells_tmp = (uint32_t *)A(4 * cells_temp_words(e->cap_cells));
   e->press = (float *)A(4 * NP);
+  if (e->sps || e->pool) {
+    e->tau4 = (float4 *)A(16 * N);
+    e->tau2 = (float2 *)A(8 * N);
+  }
   e->nvalid = (int *)A(16);
   e->sort_tmp = A(radix_sort_temp_bytes(N));
   e->diag = (double *)A(sizeof(double) * (8 * 1024 + 8));
@@ -357,6 +390,8 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     if (rc) return rc;
     if (margin && grids[c].margin != margin)
       return fail(SPH_ERR_ARG, "all cases of an engine must use the same cell_mode");
+    if (params[c].integrator != params[0].integrator)
+      return fail(SPH_ERR_ARG, "all cases of an engine must use the same integrator");
     margin = grids[c].margin;
     np += parts[c].n;
     nc += grids[c].ncells;
@@ -376,6 +411,11 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
   e->margin = margin;
   e->slots.resize(ncases);
   e->hconst.resize(ncases);
+  e->integrator = params[0].integrator;
+  for (int c = 0; c < ncases; c++) {
+    e->ext = e->ext || params[c].ddt_mode == 2 || params[c].visc_mode == 1;
+    e->sps = e->sps || params[c].visc_mode == 1;
+  }
   rc = allocate(e);
   int64_t cell0 = 0, p0 = 0;
   for (int c = 0; c < ncases && rc == SPH_OK; c++) {
@@ -395,35 +435,62 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
   return SPH_OK;
 }
 
+// One Verlet step (all cases): NL and PI on state n, time step, update to
+// n+1 written back in X (sorted order).  ev: 2 events around the PI launch.
+void enqueue_step_verlet(sph_engine e, cudaEvent_t *ev) {
+  const int n = (int)e->n_phys;
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &X = e->S[0], &Y = e->S[1];
+  cudaStream_t s = e->s;
+  radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev, Y,
+                 e->press, e->dconst, e->nbits, s);
+  launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
+  if (ev) cudaEventRecord(ev[0], s);
+  launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
+                  e->press, Y.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
+                  nullptr, 1, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
+  launch_verlet(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, X, e->keysA, s);
+  launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
+}
+
 // One Symplectic step (all cases).  ev: 4 events around the two PI launches.
 void enqueue_step(sph_engine e, cudaEvent_t *ev) {
+  if (e->integrator == 1) {
+    enqueue_step_verlet(e, ev);
+    return;
+  }
   const int n = (int)e->n_phys;
   const int nl = (int)(e->n_phys - e->n_dead);
   State &X = e->S[0], &Y = e->S[1], &Z = e->S[2];
   cudaStream_t s = e->s;
   // NL on state n
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
-  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->press,
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev, Y,
+                 e->press,
                  e->dconst, e->nbits, s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
   // PI on state n, time step, predictor
   if (ev) cudaEventRecord(ev[0], s);
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
                   e->press, Y.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
-                  nullptr, 1, s);
+                  nullptr, 1, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
   if (ev) cudaEventRecord(ev[1], s);
   launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
   launch_predictor(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
                    e->keysC, s);
   // NL on state n+1/2 (id/cid/code of Z are those of Y)
   radix_sort(e->keysC, e->keysD, e->perm2, nl, e->nbits, e->sort_tmp, s);
-  launch_reorder(nl, e->perm2, e->keysD, Z.posc, Z.velrho, Y.id, Y.cid, Y.code, X, e->press,
+  launch_reorder(nl, e->perm2, e->keysD, Z.posc, Z.velrho, Y.id, Y.cid, Y.code, nullptr, X,
+                 e->press,
                  e->dconst, e->nbits, s);
   launch_cells(nl, e->keysD, e->cstart, e->cells_hw, e->nbits, e->nvalid + 1, e->cells_tmp, s);
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid + 1, e->keysD, X.posc, X.velrho,
                   e->press, X.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
-                  nullptr, 0, s);
+                  nullptr, 0, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
   if (ev) cudaEventRecord(ev[3], s);
   launch_corrector(nl, e->perm2, e->keysD, e->keysB, Y, X, e->ace, e->dconst, e->ddyn, e->nbits,
                    e->keysA, s);
@@ -436,7 +503,8 @@ void enqueue_nl(sph_engine e) {
   const int nl = (int)(e->n_phys - e->n_dead);
   State &X = e->S[0], &Y = e->S[1];
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, e->s);
-  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, Y, e->press,
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev, Y,
+                 e->press,
                  e->dconst, e->nbits, e->s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, e->s);
 }
@@ -518,7 +586,8 @@ int sph_step(sph_engine e, int64_t nsteps) {
   }
   int64_t k = 0;
   if (!timing && e->opt.use_graph && e->n_dead == 0) {
-    if (!e->gexec || e->graph_n != e->n_phys || e->graph_dead != e->cells_hw) {
+    if (!e->gexec || e->graph_n != e->n_phys || e->graph_dead != e->cells_hw ||
+        e->graph_ext != (int)e->ext + 2 * (int)e->sps) {
       if (e->gexec) cudaGraphExecDestroy(e->gexec);
       e->gexec = nullptr;
       cudaGraph_t g;
@@ -530,12 +599,19 @@ int sph_step(sph_engine e, int64_t nsteps) {
       if (err != cudaSuccess) return fail(SPH_ERR_CUDA, cudaGetErrorString(err));
       e->graph_n = e->n_phys;
       e->graph_dead = e->cells_hw;  // cells in use at capture
+      e->graph_ext = (int)e->ext + 2 * (int)e->sps;
     }
     for (; k < nsteps; k++) CUDA_TRY(cudaGraphLaunch(e->gexec, e->s));
   }
-  // per step: 2 sorts (3 kernels per 8-bit pass), 2 reorders, 2 cell tables
-  // (4 kernels), 2 interactions, dt, predictor, corrector, end of step
-  const int64_t per_step = 6 * std::max(1, (e->nbits + 7) / 8) + 2 + 8 + 2 + 4;
+  // per Symplectic step: 2 sorts (3 kernels per 8-bit pass), 2 reorders, 2
+  // cell tables (4 kernels), 2 interactions, dt, predictor, corrector, end of
+  // step; per Verlet step: one sort, reorder, cell table and interaction, dt,
+  // update, end of step
+  const int64_t passes = std::max(1, (e->nbits + 7) / 8);
+  const int64_t pis = e->integrator == 1 ? 1 : 2;
+  const int64_t per_step = (e->integrator == 1 ? 3 * passes + 1 + 4 + 1 + 3
+                                               : 6 * passes + 2 + 8 + 2 + 4) +
+                           (e->sps ? pis : 0);  // strain pass before each interaction
   e->kernel_launches += per_step * nsteps;
   for (; k < nsteps; k++) {
     enqueue_step(e, timing ? &e->evs[4 * k] : nullptr);
@@ -549,9 +625,10 @@ int sph_step(sph_engine e, int64_t nsteps) {
     for (int64_t j = 0; j < nsteps; j++) {
       float a = 0.f, b = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&a, e->evs[4 * j], e->evs[4 * j + 1]));
-      CUDA_TRY(cudaEventElapsedTime(&b, e->evs[4 * j + 2], e->evs[4 * j + 3]));
+      if (e->integrator != 1)
+        CUDA_TRY(cudaEventElapsedTime(&b, e->evs[4 * j + 2], e->evs[4 * j + 3]));
       e->pi_ms += a + b;
-      e->pi_launches += 2;
+      e->pi_launches += e->integrator == 1 ? 1 : 2;
     }
     float tot = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&tot, t0, t1));
@@ -656,7 +733,8 @@ int sph_get_raw(sph_engine e, int32_t icase, void *buf, size_t *bytes) {
   if (rc) return rc;
   if (!bytes) return fail(SPH_ERR_ARG, "null size pointer");
   const int64_t n = e->slots[icase].n;
-  const size_t need = sizeof(RawHeader) + (size_t)n * (4 + 4 + 16 + 16);
+  const bool verlet = e->integrator == 1;
+  const size_t need = sizeof(RawHeader) + (size_t)n * (4 + 4 + 16 + 16 + (verlet ? 16 : 0));
   if (!buf) {
     *bytes = need;
     return SPH_OK;
@@ -667,22 +745,26 @@ int sph_get_raw(sph_engine e, int32_t icase, void *buf, size_t *bytes) {
   const int64_t np = e->n_phys;
   std::vector<uint32_t> keys(np), ids(np);
   std::vector<uint16_t> cid(np);
-  std::vector<float4> pc(np), vr(np);
+  std::vector<float4> pc(np), vr(np), vp(verlet ? np : 0);
   CUDA_TRY(cudaMemcpyAsync(keys.data(), e->keysA, 4 * np, cudaMemcpyDeviceToHost, e->s));
   CUDA_TRY(cudaMemcpyAsync(ids.data(), e->S[0].id, 4 * np, cudaMemcpyDeviceToHost, e->s));
   CUDA_TRY(cudaMemcpyAsync(cid.data(), e->S[0].cid, 2 * np, cudaMemcpyDeviceToHost, e->s));
   CUDA_TRY(cudaMemcpyAsync(pc.data(), e->S[0].posc, 16 * np, cudaMemcpyDeviceToHost, e->s));
   CUDA_TRY(cudaMemcpyAsync(vr.data(), e->S[0].velrho, 16 * np, cudaMemcpyDeviceToHost, e->s));
+  if (verlet)
+    CUDA_TRY(cudaMemcpyAsync(vp.data(), e->S[0].vrprev, 16 * np, cudaMemcpyDeviceToHost, e->s));
   CaseDyn d;
   CUDA_TRY(cudaMemcpyAsync(&d, e->ddyn + icase, sizeof(d), cudaMemcpyDeviceToHost, e->s));
   CUDA_TRY(cudaStreamSynchronize(e->s));
-  RawHeader hd{kRawMagic, 1, n, d.t, d.dt, d.step, d.pairs, d.n_out, (int32_t)d.flags};
+  RawHeader hd{kRawMagic, verlet ? 2u : 1u, n, d.t, d.dt, d.step, d.pairs, d.n_out,
+               (int32_t)d.flags};
   char *o = (char *)buf;
   std::memcpy(o, &hd, sizeof(hd));
   uint32_t *oid = (uint32_t *)(o + sizeof(hd));
   int32_t *ocell = (int32_t *)(oid + n);
   float4 *opc = (float4 *)(ocell + n);
   float4 *ovr = opc + n;
+  float4 *ovp = ovr + n;  // version 2 only
   const uint32_t kdead = key_dead(e->nbits), kout = key_out(e->nbits);
   const uint32_t cb = e->slots[icase].cellbase;
   int64_t j = 0;
@@ -692,6 +774,7 @@ int sph_get_raw(sph_engine e, int32_t icase, void *buf, size_t *bytes) {
     ocell[j] = keys[i] >= kout ? -1 : (int32_t)(key_cell(keys[i], e->nbits) - cb);
     std::memcpy(opc + j, &pc[i], 16);
     std::memcpy(ovr + j, &vr[i], 16);
+    if (verlet) std::memcpy(ovp + j, &vp[i], 16);
     j++;
   }
   if (j != n) return fail(SPH_ERR_STATE, "raw export found the wrong particle count");
@@ -704,9 +787,13 @@ int sph_create_from_raw(const sph_case_params *params, const sph_particles *part
   if (!buf || bytes < sizeof(RawHeader)) return fail(SPH_ERR_ARG, "bad raw buffer");
   RawHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
-  if (hd.magic != kRawMagic || hd.version != 1) return fail(SPH_ERR_ARG, "not a raw snapshot");
+  if (hd.magic != kRawMagic || (hd.version != 1 && hd.version != 2))
+    return fail(SPH_ERR_ARG, "not a raw snapshot");
+  if (!params || (params->integrator == 1) != (hd.version == 2))
+    return fail(SPH_ERR_ARG, "snapshot and params disagree on the integrator");
   if (!parts || parts->n != hd.n) return fail(SPH_ERR_ARG, "particle count does not match snapshot");
-  if (bytes < sizeof(RawHeader) + (size_t)hd.n * 40) return fail(SPH_ERR_ARG, "truncated snapshot");
+  if (bytes < sizeof(RawHeader) + (size_t)hd.n * (hd.version == 2 ? 56 : 40))
+    return fail(SPH_ERR_ARG, "truncated snapshot");
   int rc = create_engine(params, parts, 1, stream, alloc, free_fn, alloc_ctx, out);
   if (rc) return rc;
   sph_engine e = *out;
@@ -747,6 +834,8 @@ int sph_create_from_raw(const sph_case_params *params, const sph_particles *part
                     e->S[0], e->keysA, 0, e->s);
   // ids: the import wrote 0..n-1; restore the snapshot ids
   CUDA_TRY(cudaMemcpyAsync(e->S[0].id, ids, 4 * n, cudaMemcpyHostToDevice, e->s));
+  if (hd.version == 2)  // v^{n-1}, rho^{n-1} of the Verlet scheme, same order
+    CUDA_TRY(cudaMemcpyAsync(e->S[0].vrprev, vr + n, 16 * n, cudaMemcpyHostToDevice, e->s));
   CaseDyn d;
   std::memset(&d, 0, sizeof(d));
   d.t = hd.t;
@@ -785,7 +874,7 @@ int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho, float 
   State &Y = e->S[1];
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
                   e->press, Y.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
-                  e->mu, 1, e->s);
+                  e->mu, 1, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, e->s);
   char *p = e->io;
   float *d_acc = (float *)p;
   p += align256(12 * n);
@@ -817,6 +906,26 @@ int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho, float 
     }
   }
   if (pairs) *pairs = (int64_t)d.pairs;
+  return SPH_OK;
+}
+
+int sph_eval_sps(sph_engine e, int32_t icase, float *tau6) {
+  int rc = valid_case(e, icase);
+  if (rc) return rc;
+  if (!tau6) return fail(SPH_ERR_ARG, "null output");
+  if (!e->tau4) return fail(SPH_ERR_STATE, "no case of this engine uses visc_mode 1");
+  const int64_t n = e->slots[icase].n;
+  enqueue_nl(e);
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &Y = e->S[1];
+  launch_strain(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, Y.cid, e->cstart,
+                e->cells_hw, e->nbits, e->dconst, e->tau4, e->tau2, e->s);
+  float *d_tau = (float *)e->io;  // 24 n bytes <= io_bytes (48 per particle)
+  CUDA_TRY(cudaMemsetAsync(d_tau, 0, 24 * n, e->s));
+  launch_scatter_tau(nl, Y.cid, Y.id, icase, e->nvalid, e->tau4, e->tau2, d_tau, e->s);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(tau6, d_tau, 24 * n, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
   return SPH_OK;
 }
 
@@ -914,6 +1023,11 @@ int sph_pool_admit(sph_engine e, const sph_case_params *params, const sph_partic
   if (rc) return rc;
   int used = 0;
   for (auto &s : e->slots) used += s.used;
+  if (params->integrator != 0)
+    return fail(SPH_ERR_ARG, "pools run the Symplectic scheme (integrator 0)");
+  // (the pool's tau buffers exist from creation; the flags only grow)
+  e->ext = e->ext || params->ddt_mode == 2 || params->visc_mode == 1;
+  e->sps = e->sps || params->visc_mode == 1;
   if (used == 0) e->margin = g.margin;
   if (g.margin != e->margin) return fail(SPH_ERR_ARG, "cell_mode differs from the pool's cases");
   int free_slot = -1;

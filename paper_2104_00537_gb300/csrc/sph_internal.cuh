@@ -36,8 +36,8 @@ struct CaseConst {
   float mot_axis[kMaxMotions][3];
   int32_t nx, ny, nz, margin;
   uint32_t cellbase;  // first global cell of this case
-  int32_t nmot, ddt, clamp;
-  int32_t max_out, active, n_fluid, pad_;
+  int32_t nmot, ddt, clamp, visc;  // visc: 0 artificial (Eq 21), 1 laminar + SPS (Eq 23-27)
+  int32_t max_out, active, n_fluid, verlet_steps;  // verlet_steps: N_S of Eq 31
   float h, csf, r2max, eta2;
   float m, rho0, inv_rho0, btait, gamma;
   float cw;     // -5 a_D / h^2: grad_a W_ab = cw (1 - q/2)^3 r_ab
@@ -47,7 +47,12 @@ struct CaseConst {
   float g[3];
   float cs0f;
   float inv_csf;  // 1 / cs
-  float pad3_;
+  float inv_gamma;
+  float khyd[3];  // -(rho0 / B) g: P^H_ab / B of Eq 20 is khyd . r_ab
+  float hyd_c[3]; // (k-1)/2, (k-2)/3, (k-3)/4 with k = 1/gamma (binomial series)
+  float nu0;      // Eq 23
+  float sps_cs2;  // (C_S Delta)^2 of Eq 25
+  float sps_cl2;  // C_l Delta^2 of Eq 25
 };
 
 // Mutable per-case values, updated on the device during a step.
@@ -92,6 +97,7 @@ struct State {
   uint32_t *id;
   uint16_t *cid;
   uint8_t *code;
+  float4 *vrprev;  // Verlet scheme only (else null): v^{n-1}, rho^{n-1} of Eq 30
 };
 
 // Sets the message returned by sph_last_error() (defined in sph_api.cu).

@@ -110,6 +110,7 @@ __global__ void k_upload(int n, const double *__restrict__ pos, const float *__r
     atomicAdd(&dyn[slot].n_out, 1);
   }
   st.velrho[d] = vr;
+  if (st.vrprev) st.vrprev[d] = vr;
   st.id[d] = id_base + (uint32_t)i;
   st.cid[d] = (uint16_t)slot;
   st.code[d] = code;
@@ -126,7 +127,8 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
                           const float4 *__restrict__ velrho_src,
                           const uint32_t *__restrict__ id_src,
                           const uint16_t *__restrict__ cid_src,
-                          const uint8_t *__restrict__ code_src, State dst,
+                          const uint8_t *__restrict__ code_src,
+                          const float4 *__restrict__ vrprev_src, State dst,
                           float *__restrict__ press, const CaseConst *__restrict__ cc,
                           int nbits) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,6 +148,7 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
   dst.id[i] = id_src[p];
   dst.cid[i] = cidx;
   dst.code[i] = code_src[p];
+  if (vrprev_src) dst.vrprev[i] = vrprev_src[p];
   press[i] = tait_pressure(C, vr.w) / vr.w;
 }
 
@@ -295,12 +298,44 @@ struct Acc {
   unsigned cnt, cntb;
 };
 
+// Hydrostatic density difference rho^H_ab of Eq 19: Eq 28 solved for the
+// density at the pressure P^H_ab = rho0 g z_ab of Eq 20, minus rho0, i.e.
+// rho0 ((1 + x)^k - 1) with x = P^H_ab / B and k = 1/gamma.  Within the
+// kernel support |x| is small (|x| <= 2h gamma |g| / cs0^2, about 1e-3 for
+// the usual cs0), where the binomial series to x^4 is used: its first
+// omitted term is below 2e-9 relative for |x| < 1e-2; otherwise log1p/expm1.
+__device__ __forceinline__ float rho_hydro(const CaseConst &C, float rx, float ry, float rz) {
+  const float x = fmaf(C.khyd[0], rx, fmaf(C.khyd[1], ry, C.khyd[2] * rz));  // P^H / B
+  if (fabsf(x) < 1e-2f) {
+    const float s = fmaf(C.hyd_c[0] * x, fmaf(C.hyd_c[1] * x, fmaf(C.hyd_c[2], x, 1.f), 1.f), 1.f);
+    return C.rho0 * C.inv_gamma * x * s;
+  }
+  return C.rho0 * expm1f(log1pf(x) * C.inv_gamma);
+}
+
+// Per-target data of the physics beyond the default model: Eq 19-20 density
+// diffusion (hyd) and laminar viscosity + SPS stress (sps, Eq 23-27).
+struct Ext {
+  const CaseConst *C;
+  bool hyd, sps;
+  float kl;      // -4 nu0 rho_a (Eq 23, in the units of the momentum sums)
+  float ta[6];   // rho_a (tau/rho)_a: xx, yy, zz, xy, xz, yz (Eq 25)
+  const float4 *__restrict__ tau4;  // (tau/rho)_b: xx, yy, zz, xy
+  const float2 *__restrict__ tau2;  // (tau/rho)_b: xz, yz
+};
+
 // Pair terms for a fluid particle a and a neighbour b (ddt: b in F).
 // grad_a W_ab = cw t^3 r_ab with t = 1 - r/(2h) (derivative of Eq 11).
-// Qb = P_b / rho_b, so (P_a + P_b) / rho_b = P_a / rho_b + Qb.
+// Qb = P_b / rho_b, so (P_a + P_b) / rho_b = P_a / rho_b + Qb.  All momentum
+// terms are summed in units of -rho_a / (m cw), like the pressure term.
+// EXT = 0 compiles the Eq 19 and Eq 23-27 branches out, 1 keeps Eq 19, 2
+// both; X describes target a and j is b's index (bfluid: b in F).
+template <int EXT = 0>
 __device__ __forceinline__ void pair_fluid(const float4 &va, float Pa, float kv, float hih,
                                            float eta2, float rx, float ry, float rz, float r2,
-                                           const float4 &vb, float Qb, bool ddt, Acc &A) {
+                                           const float4 &vb, float Qb, bool ddt, Acc &A,
+                                           const Ext *X = nullptr, int j = 0,
+                                           bool bfluid = true) {
   const float rr = r2 * rsqrtf(r2);
   const float t = fmaf(-hih, rr, 1.f);
   const float t3 = t * t * t;
@@ -309,7 +344,11 @@ __device__ __forceinline__ void pair_fluid(const float4 &va, float Pa, float kv,
   const float ib = __fdividef(1.f, vb.w);
   const float w = t3 * ib;
   A.s1 = fmaf(w, vr, A.s1);
-  if (ddt) A.s2 = fmaf(w, vb.w - va.w, A.s2);
+  if (ddt) {
+    float d = vb.w - va.w;
+    if (EXT >= 1 && X->hyd) d -= rho_hydro(*X->C, rx, ry, rz);
+    A.s2 = fmaf(w, d, A.s2);
+  }
   const float sab = va.w + vb.w;
   const float ie = __fdividef(1.f, (r2 + eta2) * sab);
   const float mu = vr * ie * sab;  // v_ab.r_ab / (r^2 + eta^2)
@@ -320,6 +359,23 @@ __device__ __forceinline__ void pair_fluid(const float4 &va, float Pa, float kv,
   A.ax = fmaf(s, rx, A.ax);
   A.ay = fmaf(s, ry, A.ay);
   A.az = fmaf(s, rz, A.az);
+  if (EXT == 2 && X->sps) {
+    // Eq 23: m 4 nu0 (r.gradW) v_ab / ((rho_a + rho_b)(r^2 + eta^2)), r.gradW = cw t^3 r^2
+    const float cl = X->kl * t3 * r2 * ie;
+    A.ax = fmaf(cl, vx, A.ax);
+    A.ay = fmaf(cl, vy, A.ay);
+    A.az = fmaf(cl, vz, A.az);
+    // Eq 26: m (tau_a + tau_b)^{ij} / (rho_a rho_b) grad^j W with tau = rho (tau/rho);
+    // boundary particles carry no SPS stress
+    const float4 b4 = bfluid ? X->tau4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 b2 = bfluid ? X->tau2[j] : make_float2(0.f, 0.f);
+    const float txx = fmaf(X->ta[0], ib, b4.x), tyy = fmaf(X->ta[1], ib, b4.y);
+    const float tzz = fmaf(X->ta[2], ib, b4.z), txy = fmaf(X->ta[3], ib, b4.w);
+    const float txz = fmaf(X->ta[4], ib, b2.x), tyz = fmaf(X->ta[5], ib, b2.y);
+    A.ax = fmaf(-t3, fmaf(txx, rx, fmaf(txy, ry, txz * rz)), A.ax);
+    A.ay = fmaf(-t3, fmaf(txy, rx, fmaf(tyy, ry, tyz * rz)), A.ay);
+    A.az = fmaf(-t3, fmaf(txz, rx, fmaf(tyz, ry, tzz * rz)), A.az);
+  }
 }
 
 // Boundary particle a: continuity over fluid neighbours only (Eq 36).
@@ -383,14 +439,18 @@ __device__ __forceinline__ void finish_target(const CaseConst &C, int i, int n, 
 //   candidate while another computes a pair.
 // VARIANT 1 (inline): test and pair terms in one loop (divergent).
 // (VARIANT 2, the queued pair loop, is k_interact_q below.)
-template <int M, int VARIANT>
-__global__ void __launch_bounds__(128)
+// EXT (VARIANT 0 only): 1 adds the Eq 19-20 density diffusion, 2 also the
+// laminar + SPS viscosity of Eq 23-27 (tau4/tau2 from k_strain), per case;
+// warps without such cases still take the default pair loop.
+template <int M, int VARIANT, int EXT = 0>
+__global__ void __launch_bounds__(128, EXT == 2 ? 6 : 0)
 k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
            const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
            const float *__restrict__ press, const uint16_t *__restrict__ cid,
            const uint32_t *__restrict__ cstart, uint32_t cap1, int nbits,
            const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
-           float4 *__restrict__ ace, float *__restrict__ mu_out, int want_dt) {
+           float4 *__restrict__ ace, float *__restrict__ mu_out, int want_dt,
+           const float4 *__restrict__ tau4 = nullptr, const float2 *__restrict__ tau2 = nullptr) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -410,6 +470,24 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   const float Pa = has ? press[i] * va.w : 0.f;  // press holds P / rho
   const float kv = C.kvisc * va.w;
   const bool ddt_on = C.ddt != 0;
+  Ext X;
+  X.C = &C;
+  X.hyd = EXT >= 1 && C.ddt == 2;
+  X.sps = EXT == 2 && C.visc == 1 && afluid;
+  X.kl = -4.f * C.nu0 * va.w;
+  X.tau4 = tau4;
+  X.tau2 = tau2;
+  {
+    const float4 t4 = X.sps ? tau4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 t2 = X.sps ? tau2[i] : make_float2(0.f, 0.f);
+    X.ta[0] = va.w * t4.x;
+    X.ta[1] = va.w * t4.y;
+    X.ta[2] = va.w * t4.z;
+    X.ta[3] = va.w * t4.w;
+    X.ta[4] = va.w * t2.x;
+    X.ta[5] = va.w * t2.y;
+  }
+  const bool warp_plain = __all_sync(full, (afluid || !has) && !X.hyd && !X.sps);
   Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
   constexpr int W = 2 * M + 1;
 
@@ -455,7 +533,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
             }
           }
           if (part) A.cntb += __popc(m); else A.cnt += __popc(m);
-          if (__all_sync(full, afluid || !has)) {  // fluid targets only
+          if (warp_plain) {  // fluid targets, Eq 18 or no diffusion
             while (__any_sync(full, m != 0u)) {
               if (m) {
                 const int k = 31 - __clz(m);
@@ -466,7 +544,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
                 const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
                 const float ry = sy - pb.y, rz = sz - pb.z;
                 const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt, A);
+                pair_fluid<false>(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt, A);
               }
             }
           } else {
@@ -481,7 +559,8 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
                 const float ry = sy - pb.y, rz = sz - pb.z;
                 const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
                 if (afluid)
-                  pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt, A);
+                  pair_fluid<EXT>(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt, A,
+                                  &X, j, part == 0);
                 else
                   pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
               }
@@ -658,6 +737,125 @@ k_interact_q(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict
   }
   while (__any_sync(full, cur != 0u || head != tail)) pair_step();
   finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
+}
+
+// First neighbour pass of the laminar + SPS model (Eq 24-25): for every
+// fluid particle a of a case with visc_mode 1, the SPH velocity gradient
+// G^{ij} = sum_{b in P} V_b (v_b - v_a)^i grad^j_a W_ab, its symmetric part
+// S, |S| = (2 S:S)^(1/2) / 2 and nu_SPS = (C_S Delta)^2 |S|, then
+//   tau/rho = 2 nu_SPS (S - tr(S)/3 I) - (2/3) C_l Delta^2 |S|^2 I,
+// written as tau4 = (xx, yy, zz, xy), tau2 = (xz, yz); zero for the others.
+// Same rows, pruning and 32-candidate test as the interaction kernel.
+template <int M>
+__global__ void __launch_bounds__(128, 6)
+k_strain(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
+         const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
+         const uint16_t *__restrict__ cid, const uint32_t *__restrict__ cstart, uint32_t cap1,
+         int nbits, const CaseConst *__restrict__ cc, float4 *__restrict__ tau4,
+         float2 *__restrict__ tau2) {
+  const unsigned full = 0xffffffffu;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvalid = *nvalid_p;
+  const bool has = i < nvalid;
+  const int cidx = i < n ? (int)cid[i] : 0;
+  const CaseConst &C = cc[cidx];
+  const uint32_t key = has ? keys[i] : 0u;
+  const bool act = has && !key_boundary(key, nbits) && C.visc == 1;
+  if (__all_sync(full, !act)) {
+    if (i < n) {
+      tau4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      tau2[i] = make_float2(0.f, 0.f);
+    }
+    return;
+  }
+  const int gc = (int)key_cell(key, nbits);
+  const int nx = C.nx, nxy = C.nx * C.ny;
+  const float cs = C.csf, ics = C.inv_csf, r2max = C.r2max, hih = C.half_inv_h;
+  const float r2prune = r2max * 1.0001f;
+  const unsigned r2max_u = __float_as_uint(r2max) - 1u;
+  const float4 pa = act ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 va = act ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+  float gxx = 0.f, gyy = 0.f, gzz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
+  constexpr int W = 2 * M + 1;
+#pragma unroll 1
+  for (int row = 0; row < W * W; row++) {
+    const int dy = row % W - M, dz = row / W - M;
+    const float gy = slab_gap(dy, pa.y, cs), gz = slab_gap(dz, pa.z, cs);
+    const float d2 = fmaf(gy, gy, gz * gz);
+    int loF = 0, hiF = 0, loB = 0, hiB = 0;
+    if (act && d2 < r2prune) {
+      const float L = sqrtf(r2prune - d2);
+      const int kx0 = max(-M, (int)floorf((pa.x - L) * ics));
+      const int kx1 = min(M, (int)floorf((pa.x + L) * ics));
+      const int c0 = gc + dz * nxy + dy * nx + kx0;
+      const int c1 = gc + dz * nxy + dy * nx + kx1 + 1;
+      loF = (int)cstart[c0];
+      hiF = (int)cstart[c1];
+      loB = (int)cstart[cap1 + c0];
+      hiB = (int)cstart[cap1 + c1];
+    }
+    const float sy = fmaf(-(float)dy, cs, pa.y), sz = fmaf(-(float)dz, cs, pa.z);
+#pragma unroll 1
+    for (int part = 0; part < 2; part++) {  // b in F, then b in B
+      const int lo = part ? loB : loF;
+      const int len = (part ? hiB : hiF) - lo;
+      const int maxlen = (int)__reduce_max_sync(full, (unsigned)max(len, 0));
+#pragma unroll 1
+      for (int base = 0; base < maxlen; base += 32) {
+        unsigned m = 0u;
+        const int nk = min(32, maxlen - base);
+#pragma unroll 8
+        for (int k = 0; k < nk; k++) {
+          if (base + k < len) {
+            const float4 pb = posc[lo + base + k];
+            const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+            const float ry = sy - pb.y, rz = sz - pb.z;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            if (__float_as_uint(r2) - 1u < r2max_u) m |= 1u << k;
+          }
+        }
+        while (__any_sync(full, m != 0u)) {
+          if (m) {
+            const int k = 31 - __clz(m);
+            m ^= 1u << k;
+            const int j = lo + base + k;
+            const float4 pb = posc[j];
+            const float4 vb = velrho[j];
+            const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+            const float ry = sy - pb.y, rz = sz - pb.z;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            const float t = fmaf(-hih, r2 * rsqrtf(r2), 1.f);
+            const float w = t * t * t * __fdividef(1.f, vb.w);  // V_b grad W / (m cw r_ab)
+            const float dvx = vb.x - va.x, dvy = vb.y - va.y, dvz = vb.z - va.z;
+            gxx = fmaf(w * dvx, rx, gxx);
+            gyy = fmaf(w * dvy, ry, gyy);
+            gzz = fmaf(w * dvz, rz, gzz);
+            gxy = fmaf(w, fmaf(dvx, ry, dvy * rx), gxy);
+            gxz = fmaf(w, fmaf(dvx, rz, dvz * rx), gxz);
+            gyz = fmaf(w, fmaf(dvy, rz, dvz * ry), gyz);
+          }
+        }
+      }
+    }
+  }
+  if (i >= n) return;
+  if (!act) {
+    tau4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    tau2[i] = make_float2(0.f, 0.f);
+    return;
+  }
+  const float k = C.m * C.cw;
+  const float sxx = k * gxx, syy = k * gyy, szz = k * gzz;
+  const float sxy = 0.5f * k * gxy, sxz = 0.5f * k * gxz, syz = 0.5f * k * gyz;
+  const float ss = fmaf(sxx, sxx, fmaf(syy, syy, szz * szz)) +
+                   2.f * fmaf(sxy, sxy, fmaf(sxz, sxz, syz * syz));
+  const float smag = 0.5f * sqrtf(2.f * ss);
+  const float nu2 = 2.f * C.sps_cs2 * smag;
+  const float tr3 = (sxx + syy + szz) * (1.f / 3.f);
+  const float iso = -(2.f / 3.f) * C.sps_cl2 * smag * smag;
+  tau4[i] = make_float4(fmaf(nu2, sxx - tr3, iso), fmaf(nu2, syy - tr3, iso),
+                        fmaf(nu2, szz - tr3, iso), nu2 * sxy);
+  tau2[i] = make_float2(nu2 * sxz, nu2 * syz);
 }
 
 // ---- time step and motion ----------------------------------------------------
@@ -860,6 +1058,82 @@ __global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
   keys_next[i] = kn;
 }
 
+// ---- Verlet scheme ---------------------------------------------------------------
+
+// One Verlet step (Eq 30, or Eq 31 when the case's count of completed steps
+// is a multiple of N_S) from the sorted state n (src, with v^{n-1}, rho^{n-1}
+// in src.vrprev) and F^n, R^n (ace) to state n+1 in dst, same order:
+//   r^{n+1} = r^n + dt v^n + dt^2 F^n / 2            (FP64 displacement)
+//   v^{n+1} = v^{n-1} + 2 dt F^n   |  v^n + dt F^n    (Eq 30 | Eq 31)
+//   rho^{n+1} = rho^{n-1} + 2 dt R^n | rho^n + dt R^n
+// and v^n, rho^n become dst.vrprev.  Boundary particles: density as above
+// (clamped >= rho0 when set), fixed ones keep r and v, moving ones follow
+// Eq 37 at t + dt.  Cases that take no step (dt = 0) are copied unchanged.
+__global__ void k_verlet(int n, const uint32_t *__restrict__ keys_in, State src,
+                         const float4 *__restrict__ ace, const CaseConst *__restrict__ cc,
+                         CaseDyn *__restrict__ dyn, int nbits, State dst,
+                         uint32_t *__restrict__ keys_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys_in[i];
+  const float4 p = src.posc[i];
+  const float4 v = src.velrho[i];
+  const float4 vp = src.vrprev[i];
+  const int cidx = src.cid[i];
+  const uint8_t code = src.code[i];
+  dst.id[i] = src.id[i];
+  dst.cid[i] = (uint16_t)cidx;
+  dst.code[i] = code;
+  const CaseConst &C = cc[cidx];
+  const CaseDyn &D = dyn[cidx];
+  const double dt = D.dt;
+  if (k >= key_out(nbits) || !(dt > 0.0)) {  // frozen, released or not stepping
+    dst.posc[i] = p;
+    dst.velrho[i] = v;
+    dst.vrprev[i] = vp;
+    keys_out[i] = k;
+    return;
+  }
+  const bool eq31 = (D.step % C.verlet_steps) == 0;
+  const float dtf = (float)dt;
+  const float4 a = ace[i];
+  const float4 base = eq31 ? v : vp;  // v, rho at n (Eq 31) or n-1 (Eq 30)
+  const float fdt = eq31 ? dtf : 2.f * dtf;
+  float rho = fmaf(fdt, a.w, base.w);
+  double disp[3];
+  float4 vnew;
+  if (code == 0) {
+    vnew = make_float4(fmaf(fdt, a.x, base.x), fmaf(fdt, a.y, base.y), fmaf(fdt, a.z, base.z), rho);
+    const double hdt2 = 0.5 * dt * dt;
+    disp[0] = fma(hdt2, (double)a.x, dt * (double)v.x);
+    disp[1] = fma(hdt2, (double)a.y, dt * (double)v.y);
+    disp[2] = fma(hdt2, (double)a.z, dt * (double)v.z);
+  } else {
+    if (C.clamp && rho < C.rho0) rho = C.rho0;
+    if (code >= 2) {
+      const int g = code - 2;
+      const double d = D.mot[g][2];
+      const float vm = (float)D.mot[g][3];
+      disp[0] = d * C.mot_axis[g][0];
+      disp[1] = d * C.mot_axis[g][1];
+      disp[2] = d * C.mot_axis[g][2];
+      vnew = make_float4(vm * C.mot_axis[g][0], vm * C.mot_axis[g][1], vm * C.mot_axis[g][2],
+                         rho);
+    } else {
+      disp[0] = disp[1] = disp[2] = 0.0;
+      vnew = make_float4(v.x, v.y, v.z, rho);
+    }
+  }
+  float4 pnew;
+  bool left;
+  const uint32_t kn = move_particle(k, p, disp, C, code != 0, nbits, pnew, left);
+  if (left) atomicAdd(&dyn[cidx].n_out, 1);  // frozen at state n+1
+  dst.posc[i] = pnew;
+  dst.velrho[i] = vnew;
+  dst.vrprev[i] = v;
+  keys_out[i] = kn;
+}
+
 // ---- read-out ------------------------------------------------------------------
 
 __device__ __forceinline__ void cell_position(uint32_t k, const float4 &p, const CaseConst &C,
@@ -920,6 +1194,7 @@ __global__ void k_import_raw(int n, const int32_t *__restrict__ cell,
                         : key_make(C.cellbase + (uint32_t)cell[i], code != 0, nbits);
   st.posc[d] = posc[i];
   st.velrho[d] = velrho[i];
+  if (st.vrprev) st.vrprev[d] = velrho[i];
   st.id[d] = id_base + (uint32_t)i;
   st.cid[d] = (uint16_t)slot;
   st.code[d] = code;
@@ -1071,11 +1346,11 @@ void launch_upload(int n, const double *pos, const float *vel, const float *rho,
 
 void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
                     const float4 *posc, const float4 *velrho, const uint32_t *id,
-                    const uint16_t *cid, const uint8_t *code, State dst, float *press,
-                    const CaseConst *cc, int nbits, cudaStream_t s) {
+                    const uint16_t *cid, const uint8_t *code, const float4 *vrprev, State dst,
+                    float *press, const CaseConst *cc, int nbits, cudaStream_t s) {
   if (n > 0)
     k_reorder<<<nblk(n, 256), 256, 0, s>>>(n, perm, keys_sorted, posc, velrho, id, cid, code,
-                                           dst, press, cc, nbits);
+                                           vrprev, dst, press, cc, nbits);
 }
 
 size_t cells_temp_words(int64_t cap_cells) {
@@ -1104,13 +1379,33 @@ void launch_interact(int margin, int variant, int n, const int *nvalid, const ui
                      const float4 *posc, const float4 *velrho, const float *press,
                      const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                      const CaseConst *cc, CaseDyn *dyn, float4 *ace, float *mu, int want_dt,
-                     cudaStream_t s) {
+                     bool ext, float4 *tau4, float2 *tau2, cudaStream_t s) {
   if (n <= 0) return;
   const int b = 128;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_PI_ARGS                                                                      \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, mu, want_dt
-  if (margin == 1) {
+  if (ext) {
+    // extended physics: strain pass (tau, when a laminar + SPS case is
+    // present: tau4 != null), then the compacted pair loop with the Eq 19
+    // and Eq 23-27 terms
+#define SPH_EXT(MM)                                                                            \
+  if (tau4)                                                                                    \
+    k_strain<MM><<<nblk(n, b), b, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,  \
+                                          nbits, cc, tau4, tau2);                           \
+  if (tau4)                                                                                    \
+    k_interact<MM, 0, 2><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS, tau4, tau2);                    \
+  else                                                                                         \
+    k_interact<MM, 0, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS, tau4, tau2);
+    if (margin == 1) {
+      SPH_EXT(1)
+    } else if (margin == 3) {
+      SPH_EXT(3)
+    } else {
+      SPH_EXT(2)
+    }
+#undef SPH_EXT
+  } else if (margin == 1) {
     if (variant == 2)
       k_interact_q<1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else if (variant == 1)
@@ -1160,6 +1455,13 @@ void launch_corrector(int n, const uint32_t *perm2, const uint32_t *keys_half,
                                              nbits, keys_next);
 }
 
+void launch_verlet(int n, const uint32_t *keys_in, State src, const float4 *ace,
+                   const CaseConst *cc, CaseDyn *dyn, int nbits, State dst, uint32_t *keys_out,
+                   cudaStream_t s) {
+  if (n > 0)
+    k_verlet<<<nblk(n, 256), 256, 0, s>>>(n, keys_in, src, ace, cc, dyn, nbits, dst, keys_out);
+}
+
 void launch_export(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
                    uint32_t id_base, int nbits, double *pos, float *vel, float *rho,
                    float *press, cudaStream_t s) {
@@ -1184,6 +1486,49 @@ void launch_scatter_forces(int n, const uint16_t *cid, const uint32_t *id, int s
   if (n > 0)
     k_scatter_forces<<<nblk(n, 256), 256, 0, s>>>(n, cid, id, slot, id_base, nvalid, ace, mu,
                                                   acc_out, drho_out, mu_out);
+}
+
+// tau/rho (sorted order, tau4/tau2) to the original order of one case: [6 n].
+__global__ void k_scatter_tau(int n, const uint16_t *__restrict__ cid,
+                              const uint32_t *__restrict__ id, int slot,
+                              const int *__restrict__ nvalid_p, const float4 *__restrict__ tau4,
+                              const float2 *__restrict__ tau2, float *__restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cid[i] != slot) return;
+  const bool valid = i < *nvalid_p;
+  const float4 a = valid ? tau4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float2 b = valid ? tau2[i] : make_float2(0.f, 0.f);
+  float *o = out + 6 * (size_t)id[i];
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = a.z;
+  o[3] = a.w;
+  o[4] = b.x;
+  o[5] = b.y;
+}
+
+void launch_strain(int margin, int n, const int *nvalid, const uint32_t *keys,
+                   const float4 *posc, const float4 *velrho, const uint16_t *cid,
+                   const uint32_t *cstart, int64_t cap_cells, int nbits, const CaseConst *cc,
+                   float4 *tau4, float2 *tau2, cudaStream_t s) {
+  if (n <= 0) return;
+  const uint32_t cap1 = (uint32_t)(cap_cells + 1);
+  if (margin == 1)
+    k_strain<1><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
+                                             nbits, cc, tau4, tau2);
+  else if (margin == 3)
+    k_strain<3><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
+                                             nbits, cc, tau4, tau2);
+  else
+    k_strain<2><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
+                                             nbits, cc, tau4, tau2);
+}
+
+void launch_scatter_tau(int n, const uint16_t *cid, const uint32_t *id, int slot,
+                        const int *nvalid, const float4 *tau4, const float2 *tau2, float *out,
+                        cudaStream_t s) {
+  if (n > 0)
+    k_scatter_tau<<<nblk(n, 256), 256, 0, s>>>(n, cid, id, slot, nvalid, tau4, tau2, out);
 }
 
 void launch_pair_stats(int n, const int *nvalid, const uint32_t *keys, State st,

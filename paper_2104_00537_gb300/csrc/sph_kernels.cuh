@@ -10,23 +10,35 @@ void launch_upload(int n, const double *pos, const float *vel, const float *rho,
                    int dst0, cudaStream_t s);
 void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
                     const float4 *posc, const float4 *velrho, const uint32_t *id,
-                    const uint16_t *cid, const uint8_t *code, State dst, float *press,
-                    const CaseConst *cc, int nbits, cudaStream_t s);
+                    const uint16_t *cid, const uint8_t *code, const float4 *vrprev, State dst,
+                    float *press, const CaseConst *cc, int nbits, cudaStream_t s);
 // Words of temporary storage launch_cells needs for cap_cells cells.
 size_t cells_temp_words(int64_t cap_cells);
 // Cell start table of the sorted keys (and nvalid); returns kernels launched.
 int launch_cells(int n, const uint32_t *keys, uint32_t *cstart, int64_t cap_cells, int nbits,
                  int *nvalid, uint32_t *tmp, cudaStream_t s);
+// Strain pass of the laminar + SPS model alone (tau/rho of Eq 25, sorted order).
+void launch_strain(int margin, int n, const int *nvalid, const uint32_t *keys,
+                   const float4 *posc, const float4 *velrho, const uint16_t *cid,
+                   const uint32_t *cstart, int64_t cap_cells, int nbits, const CaseConst *cc,
+                   float4 *tau4, float2 *tau2, cudaStream_t s);
+void launch_scatter_tau(int n, const uint16_t *cid, const uint32_t *id, int slot,
+                        const int *nvalid, const float4 *tau4, const float2 *tau2, float *out,
+                        cudaStream_t s);
 void launch_interact(int margin, int variant, int n, const int *nvalid, const uint32_t *keys,
                      const float4 *posc, const float4 *velrho, const float *press,
                      const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                      const CaseConst *cc, CaseDyn *dyn, float4 *ace, float *mu, int want_dt,
-                     cudaStream_t s);
+                     bool ext, float4 *tau4, float2 *tau2, cudaStream_t s);
 void launch_dt(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t s);
 void launch_end_step(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t s);
 void launch_predictor(int n, const uint32_t *keys_in, State src, const float4 *ace,
                       const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
                       float4 *velrho_out, uint32_t *keys_out, cudaStream_t s);
+// Verlet step (Eq 30-31) from the sorted state src to dst (same order).
+void launch_verlet(int n, const uint32_t *keys_in, State src, const float4 *ace,
+                   const CaseConst *cc, CaseDyn *dyn, int nbits, State dst, uint32_t *keys_out,
+                   cudaStream_t s);
 void launch_corrector(int n, const uint32_t *perm2, const uint32_t *keys_half,
                       const uint32_t *keys_n, State sn, State x, const float4 *ace,
                       const CaseConst *cc, CaseDyn *dyn, int nbits, uint32_t *keys_next,

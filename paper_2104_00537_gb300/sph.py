@@ -38,7 +38,9 @@ class CaseParams(C.Structure):
                 ("gravity", D3), ("domain_min", D3), ("domain_max", D3),
                 ("dt_fixed", C.c_double), ("dt_min", C.c_double),
                 ("cell_mode", C.c_int32), ("ddt_mode", C.c_int32),
-                ("clamp_boundary_rho", C.c_int32), ("max_out", C.c_int32)]
+                ("clamp_boundary_rho", C.c_int32), ("max_out", C.c_int32),
+                ("integrator", C.c_int32), ("verlet_steps", C.c_int32),
+                ("visc_mode", C.c_int32), ("pad_", C.c_int32), ("nu0", C.c_double)]
 
 
 class Motion(C.Structure):
@@ -102,6 +104,7 @@ def load(build_if_missing: bool = True):
                                           C.c_size_t, vp, ALLOC_FN, FREE_FN, vp,
                                           C.POINTER(vp)]),
         "sph_eval_forces": (C.c_int, [vp, i32, vp, vp, vp, dp, C.POINTER(i64)]),
+        "sph_eval_sps": (C.c_int, [vp, i32, vp]),
         "sph_get_order": (C.c_int, [vp, i32, vp, vp, C.POINTER(i64)]),
         "sph_pair_stats": (C.c_int, [vp, i32, vp, vp]),
         "sph_pool_create": (C.c_int, [i64, i64, i32, vp, ALLOC_FN, FREE_FN, vp, C.POINTER(vp)]),
@@ -144,6 +147,10 @@ def make_params(p: dict) -> CaseParams:
     c.ddt_mode = int(p.get("ddt_mode", 1))
     c.clamp_boundary_rho = int(p.get("clamp_boundary_rho", 1))
     c.max_out = int(p.get("max_out", -1))
+    c.integrator = int(p.get("integrator", 0))
+    c.verlet_steps = int(p.get("verlet_steps", 40))
+    c.visc_mode = int(p.get("visc_mode", 0))
+    c.nu0 = float(p.get("nu0", 1e-6))
     return c
 
 
@@ -326,6 +333,12 @@ class Engine:
         check(self.lib.sph_eval_forces(self.h, icase, acc.ctypes.data, drho.ctypes.data,
                                        mu.ctypes.data, C.byref(dt), C.byref(pairs)))
         return dict(acc=acc, drho=drho, mumax=mu, dt=dt.value, pairs=pairs.value)
+
+    def eval_sps(self, icase=0):
+        """tau / rho of Eq 25 per particle (original order): xx, yy, zz, xy, xz, yz."""
+        tau = np.zeros((self._n(icase), 6), np.float32)
+        check(self.lib.sph_eval_sps(self.h, icase, tau.ctypes.data))
+        return tau
 
     def order(self, icase=0):
         n = self._n(icase)

@@ -156,6 +156,40 @@ def test_one_evaluation_in_motion(c0, variant):
 
 
 @pytest.mark.parametrize("variant", [0, 2])
+def test_fourtakas_ddt_evaluation(variant):
+    """Eq 17 with Eq 19-20 (ddt_mode 2): one evaluation at rest (hydrostatic
+    start: the term nearly vanishes) and one after 60 steps of motion."""
+    case = cases.dam_break(0.02, ddt_mode=2)
+    eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=variant)
+    check_eval(case, eng)
+    eng.step(60)
+    check_eval(case, eng)
+    eng.destroy()
+
+
+@pytest.mark.parametrize("ddt_mode", [1, 2])
+def test_still_tank_hydrostatic_gpu(ddt_mode):
+    """Eq 28 + DBC on the GPU path: after 1 s at rest the pressure in
+    horizontal slabs is within 2 % of rho0 g (H - z)."""
+    c = cases.still_tank(0.01, size=(0.16, 0.16), depth=0.3, height=0.34, ddt_mode=ddt_mode)
+    eng = sph.Engine.create(c)
+    eng.set_options(use_graph=1)
+    while eng.stats()["t"] < 1.0:
+        eng.step(200)
+    st = eng.get_state()
+    f = c.ptype == 0
+    P, z = st["press"][f].astype(np.float64), st["pos"][f, 2]
+    H, h = c.meta["surface"], c.params["h"]
+    for z0 in np.arange(2 * h, H - 2 * h, 0.04):
+        sel = (z >= z0) & (z < z0 + 0.04)
+        expect = 1000.0 * 9.81 * (H - z[sel].mean())
+        assert P[sel].mean() == pytest.approx(expect, rel=0.02), z0
+    assert eng.stats()["flags"] == 0
+    eng.destroy()
+
+
+@pytest.mark.parametrize("variant", [0, 2])
 def test_one_evaluation_ragged_sizes(variant):
     """Random clouds of awkward sizes (not multiples of any tile)."""
     from tests.lattice import random_cloud
