@@ -27,7 +27,7 @@ class OrcParams(C.Structure):
                 ("dmax", C.c_double * 3), ("dt_fixed", C.c_double),
                 ("cell_mode", C.c_int32), ("ddt_mode", C.c_int32),
                 ("clamp_boundary_rho", C.c_int32), ("visc_mode", C.c_int32),
-                ("nu0", C.c_double)]
+                ("nu0", C.c_double), ("boundary_mode", C.c_int32), ("mdbc_slip", C.c_int32)]
 
 
 class OrcMotion(C.Structure):
@@ -79,12 +79,15 @@ def lib():
         L.orc_step.restype = C.c_int64
         L.orc_step.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _U8,
                                _I32, _U8, C.c_void_p, C.POINTER(C.c_double),
-                               C.POINTER(C.c_double), C.c_int64]
+                               C.POINTER(C.c_double), C.c_int64, _D]
+        L.orc_mdbc.restype = C.c_int
+        L.orc_mdbc.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _U8, _I32,
+                               C.c_void_p, _D, C.c_double, C.c_void_p]
         L.orc_step_verlet.restype = C.c_int64
         L.orc_step_verlet.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _D, _D,
                                       _U8, _I32, _U8, C.c_void_p, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32,
-                                      C.c_int64]
+                                      C.c_int64, _D]
         L.orc_diag.restype = C.c_int
         L.orc_diag.argtypes = [P, C.c_int64, _D, _D, _U8, C.c_void_p, _D]
         _lib = L
@@ -105,6 +108,8 @@ def make_params(p: dict) -> OrcParams:
     o.clamp_boundary_rho = int(p.get("clamp_boundary_rho", 1))
     o.visc_mode = int(p.get("visc_mode", 0))
     o.nu0 = float(p.get("nu0", 1e-6))
+    o.boundary_mode = int(p.get("boundary_mode", 0))
+    o.mdbc_slip = int(p.get("mdbc_slip", 0))
     return o
 
 
@@ -146,6 +151,32 @@ def sps_tau(params: dict, pos, vel, rho, ptype, out=None):
                          _ptr(out_), tau) != 0:
         raise ValueError("oracle sps_tau failed")
     return tau
+
+
+def mdbc(case, pos, vel, rho, t=0.0, out=None, with_dets=False):
+    """Eq 38-39 boundary values on the given state: returns (rho, vel) with
+    the boundary entries replaced (and the moment determinants if asked)."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    vel = np.array(vel, np.float64, order="C")
+    rho = np.array(rho, np.float64, order="C")
+    ptype = np.ascontiguousarray(case.ptype, np.uint8)
+    group = np.ascontiguousarray(case.group, np.int32)
+    ghost = ghost_of(case)
+    out_ = None if out is None else np.ascontiguousarray(out, np.uint8)
+    dets = np.zeros(len(ptype))
+    mot = make_motions(case.motions)
+    if lib().orc_mdbc(C.byref(make_params(case.params)), C.cast(mot, C.c_void_p),
+                      len(case.motions), len(ptype), pos, vel, rho, ptype, group, _ptr(out_),
+                      ghost, float(t), dets.ctypes.data_as(C.c_void_p)) != 0:
+        raise ValueError("oracle mdbc failed")
+    return (rho, vel, dets) if with_dets else (rho, vel)
+
+
+def ghost_of(case):
+    g = getattr(case, "ghost", None)
+    if g is None:
+        g = np.zeros((len(case.pos), 3))
+    return np.ascontiguousarray(g, np.float64)
 
 
 def rho_hydro(params: dict, rab):
@@ -269,6 +300,7 @@ class OracleState:
         self.vel_prev = self.vel.copy()
         self.rho_prev = self.rho.copy()
         self.step_count = C.c_int64(0)
+        self.ghost = ghost_of(case)
 
     def step(self, nsteps=1):
         L = lib()
@@ -281,7 +313,7 @@ class OracleState:
                                        self.vel_prev, self.rho_prev, self.ptype, self.group,
                                        self.out, self.order.ctypes.data_as(C.c_void_p),
                                        C.byref(self.t), C.byref(self.last_dt),
-                                       C.byref(self.step_count), ns, int(nsteps))
+                                       C.byref(self.step_count), ns, int(nsteps), self.ghost)
             if npairs < 0:
                 raise ValueError("oracle step failed")
             self.steps += nsteps
@@ -291,7 +323,7 @@ class OracleState:
                             len(self.motions), len(self.pos), self.pos, self.vel,
                             self.rho, self.ptype, self.group, self.out,
                             self.order.ctypes.data_as(C.c_void_p), C.byref(self.t),
-                            C.byref(self.last_dt), int(nsteps))
+                            C.byref(self.last_dt), int(nsteps), self.ghost)
         if npairs < 0:
             raise ValueError("oracle step failed")
         self.steps += nsteps

@@ -492,6 +492,8 @@ int64_t orc_interact_range(const orc_params *p, int64_t n, const double *pos,
       double ac[3] = {0.0, 0.0, 0.0}, dr = 0.0, mu = 0.0;
       int a_fluid = type[a] == 0;
       int active = !(out && out[a]) && (!use_cells || cl.cellof[a] >= 0);
+      /* mDBC: the density of B comes from Eq 38, not from Eq 36 */
+      if (p->boundary_mode == 1 && !a_fluid) active = 0;
       if (active) {
         const double *ra = pos + 3 * a;
         int64_t nc = candidates(use_cells, &cl, n, out, a, &buf, &cap);
@@ -565,7 +567,9 @@ static int inside_domain(const orc_params *p, const double *r) {
 int64_t orc_step(const orc_params *p, const orc_motion *motions, int32_t nmot,
                  int64_t n, double *pos, double *vel, double *rho,
                  const uint8_t *type, const int32_t *group, uint8_t *out,
-                 int64_t *order, double *t, double *last_dt, int64_t nsteps) {
+                 int64_t *order, double *t, double *last_dt, int64_t nsteps,
+                 const double *ghost) {
+  if (p->boundary_mode == 1 && !ghost) return -1;
   size_t N = (size_t)(n ? n : 1);
   double *acc = (double *)malloc(sizeof(double) * 3 * N);
   double *drho = (double *)malloc(sizeof(double) * N);
@@ -581,6 +585,8 @@ int64_t orc_step(const orc_params *p, const orc_motion *motions, int32_t nmot,
       orc_sort(p, n, pos, type, out, order, tmp);
       memcpy(order, tmp, sizeof(int64_t) * (size_t)n);
     }
+    if (p->boundary_mode == 1)
+      orc_mdbc(p, motions, nmot, n, pos, vel, rho, type, group, out, ghost, *t, NULL);
     int64_t np = orc_interact(p, n, pos, vel, rho, type, out, 1, acc, drho, mu);
     if (np < 0) { pairs = -1; break; }
     pairs += np;
@@ -625,6 +631,9 @@ int64_t orc_step(const orc_params *p, const orc_motion *motions, int32_t nmot,
       orc_sort(p, n, pos, type, out, order, tmp);
       memcpy(order, tmp, sizeof(int64_t) * (size_t)n);
     }
+    if (p->boundary_mode == 1)
+      orc_mdbc(p, motions, nmot, n, pos, vel, rho, type, group, out, ghost, t0 + 0.5 * dt,
+               NULL);
     np = orc_interact(p, n, pos, vel, rho, type, out, 1, acc, drho, mu);
     if (np < 0) { pairs = -1; break; }
     pairs += np;
@@ -669,14 +678,171 @@ int64_t orc_step(const orc_params *p, const orc_motion *motions, int32_t nmot,
   return pairs;
 }
 
+
+/* ---- modified dynamic boundary condition (Sect. 2.6.2) ------------------- */
+
+/* Solves the 4x4 system A x = b by Gaussian elimination with partial
+ * pivoting; returns det(A) (x untouched when det == 0). */
+static double solve4(double A[4][4], double b[4], double x[4]) {
+  double det = 1.0;
+  for (int c = 0; c < 4; c++) {
+    int piv = c;
+    for (int r = c + 1; r < 4; r++)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (A[piv][c] == 0.0) return 0.0;
+    if (piv != c) {
+      for (int k = 0; k < 4; k++) {
+        double tmp = A[c][k];
+        A[c][k] = A[piv][k];
+        A[piv][k] = tmp;
+      }
+      double tb = b[c];
+      b[c] = b[piv];
+      b[piv] = tb;
+      det = -det;
+    }
+    det *= A[c][c];
+    for (int r = c + 1; r < 4; r++) {
+      double f = A[r][c] / A[c][c];
+      for (int k = c; k < 4; k++) A[r][k] -= f * A[c][k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = 3; r >= 0; r--) {
+    double v = b[r];
+    for (int k = r + 1; k < 4; k++) v -= A[r][k] * x[k];
+    x[r] = v / A[r][r];
+  }
+  return det;
+}
+
+int orc_mdbc(const orc_params *p, const orc_motion *motions, int32_t nmot, int64_t n,
+             const double *pos, double *vel, double *rho, const uint8_t *type,
+             const int32_t *group, const uint8_t *out, const double *ghost, double t,
+             double *dets) {
+  if (!ghost) return -1;
+  double origin[3], cs;
+  int64_t nc[3];
+  int32_t margin;
+  if (orc_grid(p, origin, &cs, nc, &margin)) return -1;
+  cell_list cl;
+  if (cl_build(p, n, pos, type, out, &cl)) {
+    cl_free(&cl);
+    return -1;
+  }
+  const double m = p->rho0 * p->dp * p->dp * p->dp;
+  const double R2 = 4.0 * p->h * p->h;
+  /* new values go to scratch first: every ghost sees the fluid state only,
+   * and boundary values do not feed each other */
+  double *nrho = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double *nvel = (double *)malloc(sizeof(double) * 3 * (size_t)(n ? n : 1));
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t B = 0; B < n; B++) {
+    nrho[B] = rho[B];
+    for (int k = 0; k < 3; k++) nvel[3 * B + k] = vel[3 * B + k];
+    if (dets) dets[B] = 0.0;
+    if (type[B] == 0 || (out && out[B]) || cl.cellof[B] < 0) continue;
+    const double *g = ghost + 3 * B;
+    double rG[3] = {pos[3 * B] + g[0], pos[3 * B + 1] + g[1], pos[3 * B + 2] + g[2]};
+    /* imposed velocity of B at time t (Eq 37) */
+    double vw[3] = {0.0, 0.0, 0.0};
+    int gi = group ? group[B] : -1;
+    if (gi >= 0 && gi < nmot) {
+      const orc_motion *mo = motions + gi;
+      double v = motion_vel(mo, t);
+      for (int k = 0; k < 3; k++) vw[k] = v * mo->axis[k];
+    }
+    /* moment sums over fluid b in the ghost's support */
+    double A[4][4] = {{0}}, rhs[4] = {0}, sv[3] = {0, 0, 0}, sw = 0.0;
+    int64_t c[3];
+    for (int k = 0; k < 3; k++) c[k] = (int64_t)floor((rG[k] - origin[k]) / cs);
+    for (int64_t z = c[2] - margin; z <= c[2] + margin; z++)
+      for (int64_t y = c[1] - margin; y <= c[1] + margin; y++)
+        for (int64_t x = c[0] - margin; x <= c[0] + margin; x++) {
+          if (x < 0 || y < 0 || z < 0 || x >= nc[0] || y >= nc[1] || z >= nc[2]) continue;
+          int64_t cc = (z * cl.nc[1] + y) * cl.nc[0] + x;
+          for (int64_t q = cl.start[cc]; q < cl.start[cc + 1]; q++) {
+            int64_t b = cl.order[q];
+            if (type[b] != 0) continue;
+            double d[3] = {rG[0] - pos[3 * b], rG[1] - pos[3 * b + 1], rG[2] - pos[3 * b + 2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < R2)) continue;
+            double r = sqrt(r2);
+            double W = orc_wendland_w(r, p->h);
+            double F = orc_wendland_gradfac(r, p->h); /* grad_G W = F (r_G - r_b) */
+            double Vb = m / rho[b];
+            double e[3] = {-d[0], -d[1], -d[2]}; /* r_b - r_G */
+            A[0][0] += Vb * W;
+            for (int k = 0; k < 3; k++) {
+              A[0][k + 1] += Vb * e[k] * W;
+              A[k + 1][0] += Vb * F * d[k];
+              for (int l = 0; l < 3; l++) A[k + 1][l + 1] += Vb * F * d[k] * e[l];
+              sv[k] += Vb * vel[3 * b + k] * W;
+            }
+            rhs[0] += m * W;
+            for (int k = 0; k < 3; k++) rhs[k + 1] += m * F * d[k];
+            sw += Vb * W;
+          }
+        }
+    if (sw <= 0.0) { /* no fluid near the ghost */
+      nrho[B] = p->rho0;
+      if (p->mdbc_slip) for (int k = 0; k < 3; k++) nvel[3 * B + k] = vw[k];
+      continue;
+    }
+    double Ac[4][4], bc[4], x[4] = {0, 0, 0, 0};
+    for (int r = 0; r < 4; r++) {
+      bc[r] = rhs[r];
+      for (int k = 0; k < 4; k++) Ac[r][k] = A[r][k];
+    }
+    double det = solve4(Ac, bc, x);
+    if (dets) dets[B] = det;
+    double rhoG, grad[3] = {0.0, 0.0, 0.0};
+    if (fabs(det) >= ORC_MDBC_DET_MIN) {
+      rhoG = x[0];
+      for (int k = 0; k < 3; k++) grad[k] = x[k + 1];
+    } else {
+      rhoG = rhs[0] / sw; /* Shepard */
+    }
+    /* Eq 38: rho_B = rho_G + (r_B - r_G) . grad rho_G, r_B - r_G = -ghost */
+    double rB = rhoG - (g[0] * grad[0] + g[1] * grad[1] + g[2] * grad[2]);
+    nrho[B] = rB; /* used as is: the rho >= rho0 clamp is a device of Eq 36 */
+    /* Eq 39: v_G by the Shepard sum */
+    double vG[3] = {sv[0] / sw, sv[1] / sw, sv[2] / sw};
+    if (p->mdbc_slip == 1) {
+      for (int k = 0; k < 3; k++) nvel[3 * B + k] = 2.0 * vw[k] - vG[k];
+    } else if (p->mdbc_slip == 2) {
+      double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+      double nn[3] = {0.0, 0.0, 0.0};
+      if (gn > 0.0) for (int k = 0; k < 3; k++) nn[k] = g[k] / gn;
+      double vn = 0.0, wn = 0.0;
+      for (int k = 0; k < 3; k++) {
+        vn += vG[k] * nn[k];
+        wn += vw[k] * nn[k];
+      }
+      /* tangential part of v_G kept, normal part reversed about the wall's */
+      for (int k = 0; k < 3; k++) nvel[3 * B + k] = vG[k] + (2.0 * wn - 2.0 * vn) * nn[k];
+    }
+  }
+  for (int64_t B = 0; B < n; B++) {
+    rho[B] = nrho[B];
+    for (int k = 0; k < 3; k++) vel[3 * B + k] = nvel[3 * B + k];
+  }
+  free(nrho);
+  free(nvel);
+  cl_free(&cl);
+  return 0;
+}
+
 /* ---- Verlet scheme (Sect. 2.5.1) ---------------------------------------- */
 
 int64_t orc_step_verlet(const orc_params *p, const orc_motion *motions, int32_t nmot,
                         int64_t n, double *pos, double *vel, double *rho,
                         double *vel_prev, double *rho_prev, const uint8_t *type,
                         const int32_t *group, uint8_t *out, int64_t *order, double *t,
-                        double *last_dt, int64_t *step, int32_t ns, int64_t nsteps) {
+                        double *last_dt, int64_t *step, int32_t ns, int64_t nsteps,
+                        const double *ghost) {
   if (ns < 1) return -1;
+  if (p->boundary_mode == 1 && !ghost) return -1;
   size_t N = (size_t)(n ? n : 1);
   double *acc = (double *)malloc(sizeof(double) * 3 * N);
   double *drho = (double *)malloc(sizeof(double) * N);
@@ -689,6 +855,8 @@ int64_t orc_step_verlet(const orc_params *p, const orc_motion *motions, int32_t 
       orc_sort(p, n, pos, type, out, order, tmp);
       memcpy(order, tmp, sizeof(int64_t) * (size_t)n);
     }
+    if (p->boundary_mode == 1)
+      orc_mdbc(p, motions, nmot, n, pos, vel, rho, type, group, out, ghost, *t, NULL);
     int64_t np = orc_interact(p, n, pos, vel, rho, type, out, 1, acc, drho, mu);
     if (np < 0) { pairs = -1; break; }
     pairs += np;

@@ -36,7 +36,16 @@ typedef struct {
   int32_t visc_mode;          /* 0: artificial viscosity, Eq 21-22;
                                * 1: laminar viscosity + SPS, Eq 23-27      */
   double nu0;                 /* kinematic viscosity of Eq 23 (m^2/s)      */
+  int32_t boundary_mode;      /* 0: DBC, Eq 36; 1: mDBC, Eq 38-39          */
+  int32_t mdbc_slip;          /* mDBC velocity of B: 0 the imposed one (Eq 37);
+                               * 1 no-slip, 2 v_wall - v_G; 2 free-slip:
+                               * tangential part of v_G, normal part of
+                               * 2 v_wall - v_G (normal = ghost direction)  */
 } orc_params;
+
+/* mDBC: |det| of the corrected-SPH moment matrix below which the ghost node
+ * falls back to the Shepard value (Eq 39 form) with a zero gradient. */
+#define ORC_MDBC_DET_MIN 1e-3
 
 /* SPS constants of Eq 25: Smagorinsky C_S and C_l; Delta = dp. */
 #define ORC_SPS_CS 0.12
@@ -59,6 +68,21 @@ double orc_tait(const orc_params *p, double rho);
  * out = {xx, yy, zz, xy, xz, yz}.  Zero for boundary and frozen particles. */
 int orc_sps_tau(const orc_params *p, int64_t n, const double *pos, const double *vel,
                 const double *rho, const uint8_t *type, const uint8_t *out, double *tau6);
+
+/* mDBC (Sect. 2.6.2, Eq 38-39): for every in-domain boundary particle B,
+ * the ghost node r_G = r_B + ghost[B] (mirror image of B across the wall
+ * surface), the corrected SPH estimate (first-order consistent moment
+ * equations over b in F) of rho_G and grad rho_G, rho_B = rho_G +
+ * (r_B - r_G) . grad rho_G (Eq 38), and v_G by the Shepard sum of Eq 39.
+ * Writes rho[B] (not clamped: clamp_boundary_rho applies to Eq 36) and, with
+ * mdbc_slip 1 or 2, vel[B] from v_G and B's imposed velocity v_wall at time
+ * t (Eq 37; zero for fixed walls).  Without fluid in the ghost's support
+ * rho_B = rho0 and v_B = v_wall.  dets (optional, [n]) receives the moment
+ * matrix determinant of every boundary particle (0 for the others). */
+int orc_mdbc(const orc_params *p, const orc_motion *motions, int32_t nmot, int64_t n,
+             const double *pos, double *vel, double *rho, const uint8_t *type,
+             const int32_t *group, const uint8_t *out, const double *ghost, double t,
+             double *dets);
 
 /* Hydrostatic density difference of Eq 19: the density that Eq 28, solved
  * for rho, gives at the pressure P^H_ab = rho0 g z_ab of Eq 20, minus rho0.
@@ -115,7 +139,8 @@ double orc_dt(const orc_params *p, int64_t n, const double *acc,
 int64_t orc_step(const orc_params *p, const orc_motion *motions, int32_t nmot,
                  int64_t n, double *pos, double *vel, double *rho,
                  const uint8_t *type, const int32_t *group, uint8_t *out,
-                 int64_t *order, double *t, double *last_dt, int64_t nsteps);
+                 int64_t *order, double *t, double *last_dt, int64_t nsteps,
+                 const double *ghost);
 
 /* nsteps Verlet steps (Eq 30, with the Eq 31 step whenever the count of
  * completed steps *step is a multiple of ns; so the first step, which has
@@ -127,7 +152,8 @@ int64_t orc_step_verlet(const orc_params *p, const orc_motion *motions, int32_t 
                         int64_t n, double *pos, double *vel, double *rho,
                         double *vel_prev, double *rho_prev, const uint8_t *type,
                         const int32_t *group, uint8_t *out, int64_t *order, double *t,
-                        double *last_dt, int64_t *step, int32_t ns, int64_t nsteps);
+                        double *last_dt, int64_t *step, int32_t ns, int64_t nsteps,
+                        const double *ghost);
 
 /* Diagnostics: res = {total mass, fluid kinetic energy, fluid momentum x, y,
  * z, front (max x of in-domain fluid), number out of domain}. */

@@ -54,6 +54,7 @@ class Case:
     group: np.ndarray          # [n] int32: motion index, -1 = none
     motions: list = field(default_factory=list)
     meta: dict = field(default_factory=dict)
+    ghost: np.ndarray = None   # [n,3] r_G - r_B of boundary particles (mDBC), or None
 
     @property
     def n(self) -> int:
@@ -71,7 +72,7 @@ def default_params(dp: float, depth: float, domain_min, domain_max, **kw) -> dic
              gravity=(0.0, 0.0, -G), domain_min=tuple(float(x) for x in domain_min),
              domain_max=tuple(float(x) for x in domain_max), cell_mode=0, ddt_mode=1,
              clamp_boundary_rho=1, dt_fixed=0.0, dt_min=0.0, integrator=0, verlet_steps=40,
-             visc_mode=0, nu0=1e-6)
+             visc_mode=0, nu0=1e-6, boundary_mode=0, mdbc_slip=0)
     p.update(kw)
     return p
 
@@ -84,14 +85,44 @@ def _grid_points(ix, iy, iz) -> np.ndarray:
                      Z.transpose(2, 1, 0).ravel()], axis=1)
 
 
-def tank_walls(NX: int, NY: int, NZ: int, ix0: int = 0) -> np.ndarray:
-    """Two-layer open-top tank walls in lattice units: planes at i = ix0, NX;
-    j = 0, NY; k = 0, plus one layer outward."""
+def tank_walls(NX: int, NY: int, NZ: int, ix0: int = 0, layers: int = 2) -> np.ndarray:
+    """Open-top tank walls in lattice units: planes at i = ix0, NX; j = 0, NY;
+    k = 0, plus layers - 1 more layers outward (two by default; the mDBC
+    cases use enough layers to fill the kernel support, ceil(2h/dp))."""
     r = lambda a, b: np.arange(a, b + 1)
-    bottom = _grid_points(r(ix0 - 1, NX + 1), r(-1, NY + 1), [-1, 0])
-    xw = _grid_points([ix0 - 1, ix0, NX, NX + 1], r(-1, NY + 1), r(1, NZ))
-    yw = _grid_points(r(ix0 + 1, NX - 1), [-1, 0, NY, NY + 1], r(1, NZ))
+    L = layers - 1
+    bottom = _grid_points(r(ix0 - L, NX + L), r(-L, NY + L), r(-L, 0))
+    xw = _grid_points(list(range(ix0 - L, ix0 + 1)) + list(range(NX, NX + L + 1)),
+                      r(-L, NY + L), r(1, NZ))
+    yw = _grid_points(r(ix0 + 1, NX - 1), list(range(-L, 1)) + list(range(NY, NY + L + 1)),
+                      r(1, NZ))
     return np.concatenate([bottom, xw, yw], axis=0)
+
+
+def wall_layers(dp: float, kw: dict) -> int:
+    """Wall layers of a case: 2 for the dynamic boundary condition (Eq 36);
+    for mDBC (Eq 38-39) enough to fill the support 2h behind the wall."""
+    if kw.get("boundary_mode", 0) == 1:
+        h = kw.get("h", math.sqrt(3.0) * dp)
+        return int(math.ceil(2.0 * h / dp - 1e-9))
+    return 2
+
+
+def wall_ghosts(bound_lat, lo, hi) -> np.ndarray:
+    """Ghost-node offsets r_G - r_B (lattice units) of boundary points for the
+    modified dynamic boundary condition: the mirror image of each point in
+    every wall plane it lies behind.  The fluid side is the box lo..hi of
+    lattice indices (hi[k] None: open); a wall plane lies half a spacing
+    outside it, between the inner wall layer and the first fluid layer."""
+    b = np.asarray(bound_lat, np.float64)
+    g = np.zeros_like(b)
+    for k in range(3):
+        below = b[:, k] < lo[k]
+        g[below, k] = 2.0 * (lo[k] - 0.5 - b[below, k])
+        if hi[k] is not None:
+            above = b[:, k] > hi[k]
+            g[above, k] = 2.0 * (hi[k] + 0.5 - b[above, k])
+    return g
 
 
 def hydrostatic_rho(depth_below_surface, rho0, cs0, gamma):
@@ -102,7 +133,8 @@ def hydrostatic_rho(depth_below_surface, rho0, cs0, gamma):
 
 
 def _assemble(name, params, fluid_lat, bound_lat, dp, seed, surface_z, footprint=None,
-              bound_group=None, motions=(), origin=(0.0, 0.0, 0.0), meta=None):
+              bound_group=None, motions=(), origin=(0.0, 0.0, 0.0), meta=None,
+              bound_ghost=None):
     nf, nb = len(fluid_lat), len(bound_lat)
     pos = np.concatenate([fluid_lat, bound_lat], axis=0).astype(np.float64) * dp
     pos += np.asarray(origin, np.float64)
@@ -128,7 +160,11 @@ def _assemble(name, params, fluid_lat, bound_lat, dp, seed, surface_z, footprint
             sel = group == gi
             vel[sel] = np.asarray(m["axis"], np.float64) * v0
     vel = vel.astype(np.float32).astype(np.float64)
-    return Case(name, params, pos, vel, rho, ptype, group, list(motions), dict(meta or {}))
+    ghost = np.zeros((nf + nb, 3))
+    if bound_ghost is not None:
+        ghost[nf:] = np.asarray(bound_ghost, np.float64) * dp
+    return Case(name, params, pos, vel, rho, ptype, group, list(motions), dict(meta or {}),
+                ghost)
 
 
 def dam_break(dp: float = 0.02, seed: int = 0, column=(0.4, 0.4, 0.4),
@@ -141,15 +177,17 @@ def dam_break(dp: float = 0.02, seed: int = 0, column=(0.4, 0.4, 0.4),
     nfx, nfy, nfz = (int(round(L / dp)) for L in column)
     r = lambda a, b: np.arange(a, b + 1)
     fluid = _grid_points(r(1, nfx), r(1, nfy), r(1, nfz))
-    walls = tank_walls(NX, NY, NZ)
+    nl = wall_layers(dp, kw)
+    walls = tank_walls(NX, NY, NZ, layers=nl)
     surface = (nfz + 0.5) * dp
     depth = nfz * dp
-    dmin = (-2 * dp, -2 * dp, -2 * dp)
-    dmax = ((NX + 2) * dp, (NY + 2) * dp, 1.5 * NZ * dp)
+    dmin = (-nl * dp, -nl * dp, -nl * dp)
+    dmax = ((NX + nl) * dp, (NY + nl) * dp, 1.5 * NZ * dp)
     params = default_params(dp, depth, dmin, dmax, **kw)
     return _assemble("dam_break", params, fluid, walls, dp, seed, surface,
                      footprint=((0.0, (nfx + 1) * dp), (0.0, (nfy + 1) * dp)),
-                     meta=dict(column=column, tank=(NX * dp, NY * dp, NZ * dp), seed=seed))
+                     meta=dict(column=column, tank=(NX * dp, NY * dp, NZ * dp), seed=seed),
+                     bound_ghost=wall_ghosts(walls, (1, 1, 1), (NX - 1, NY - 1, None)))
 
 
 def still_tank(dp: float = 0.02, seed: int = 0, size=(0.2, 0.2), depth: float = 0.3,
@@ -160,13 +198,15 @@ def still_tank(dp: float = 0.02, seed: int = 0, size=(0.2, 0.2), depth: float = 
     nfz = int(round(depth / dp))
     r = lambda a, b: np.arange(a, b + 1)
     fluid = _grid_points(r(1, NX - 1), r(1, NY - 1), r(1, nfz))
-    walls = tank_walls(NX, NY, NZ)
+    nl = wall_layers(dp, kw)
+    walls = tank_walls(NX, NY, NZ, layers=nl)
     surface = (nfz + 0.5) * dp
-    dmin = (-2 * dp, -2 * dp, -2 * dp)
-    dmax = ((NX + 2) * dp, (NY + 2) * dp, (NZ + 2) * dp)
+    dmin = (-nl * dp, -nl * dp, -nl * dp)
+    dmax = ((NX + nl) * dp, (NY + nl) * dp, (NZ + 2) * dp)
     params = default_params(dp, nfz * dp, dmin, dmax, **kw)
     return _assemble("still_tank", params, fluid, walls, dp, seed, surface,
-                     meta=dict(surface=surface, seed=seed))
+                     meta=dict(surface=surface, seed=seed),
+                     bound_ghost=wall_ghosts(walls, (1, 1, 1), (NX - 1, NY - 1, None)))
 
 
 def wave_flume(dp: float = 0.008, seed: int = 0, length=25.0, width=1.0, height=1.2,
@@ -178,22 +218,26 @@ def wave_flume(dp: float = 0.008, seed: int = 0, length=25.0, width=1.0, height=
     back = int(math.ceil((0.5 * stroke + 4 * dp) / dp))  # walls extend behind the piston
     r = lambda a, b: np.arange(a, b + 1)
     fluid = _grid_points(r(1, NX - 1), r(1, NY - 1), r(1, nfz))
-    walls = tank_walls(NX, NY, NZ, ix0=-back)
+    nl = wall_layers(dp, kw)
+    walls = tank_walls(NX, NY, NZ, ix0=-back, layers=nl)
     # the back wall of tank_walls sits at -back; drop it and add the piston
-    keep = ~np.isin(walls[:, 0], [-back - 1, -back]) | (walls[:, 2] <= 0)
+    keep = ~np.isin(walls[:, 0], np.arange(-back - nl + 1, -back + 1)) | (walls[:, 2] <= 0)
     walls = walls[keep]
-    piston = _grid_points([-1, 0], r(1, NY - 1), r(1, NZ))
+    piston = _grid_points(np.arange(-nl + 1, 1), r(1, NY - 1), r(1, NZ))
     bound = np.concatenate([walls, piston], axis=0)
     bgroup = np.concatenate([np.full(len(walls), -1, np.int32), np.zeros(len(piston), np.int32)])
     surface = (nfz + 0.5) * dp
-    dmin = (-(back + 2) * dp, -2 * dp, -2 * dp)
-    dmax = ((NX + 2) * dp, (NY + 2) * dp, (NZ + 2) * dp)
+    dmin = (-(back + nl) * dp, -nl * dp, -nl * dp)
+    dmax = ((NX + nl) * dp, (NY + nl) * dp, (NZ + 2) * dp)
     params = default_params(dp, nfz * dp, dmin, dmax, **kw)
     motions = [dict(axis=(1.0, 0.0, 0.0), amp=0.5 * stroke, omega=2 * math.pi / period,
                     phase=0.0)]
+    ghost = np.concatenate([wall_ghosts(walls, (-back + 1, 1, 1), (NX - 1, NY - 1, None)),
+                            wall_ghosts(piston, (1, 1, 1), (NX - 1, NY - 1, None))], axis=0)
     return _assemble("wave_flume", params, fluid, bound, dp, seed, surface,
                      bound_group=bgroup, motions=motions,
-                     meta=dict(length=length, width=width, depth=depth, seed=seed))
+                     meta=dict(length=length, width=width, depth=depth, seed=seed),
+                     bound_ghost=ghost)
 
 
 def sloshing_tank(n_target: int, depth: float, amp: float, freq: float, seed: int = 0,
@@ -205,17 +249,19 @@ def sloshing_tank(n_target: int, depth: float, amp: float, freq: float, seed: in
     nfz = max(1, int(round(depth / dp)))
     r = lambda a, b: np.arange(a, b + 1)
     fluid = _grid_points(r(1, NX - 1), r(1, NY - 1), r(1, nfz))
-    walls = tank_walls(NX, NY, NZ)
+    nl = wall_layers(dp, kw)
+    walls = tank_walls(NX, NY, NZ, layers=nl)
     surface = (nfz + 0.5) * dp
-    pad = amp / dp + 3
-    dmin = (-pad * dp, -2 * dp, -2 * dp)
-    dmax = ((NX + pad) * dp, (NY + 2) * dp, (NZ + 2) * dp)
+    pad = amp / dp + nl + 1
+    dmin = (-pad * dp, -nl * dp, -nl * dp)
+    dmax = ((NX + pad) * dp, (NY + nl) * dp, (NZ + 2) * dp)
     params = default_params(dp, nfz * dp, dmin, dmax, **kw)
     motions = [dict(axis=(1.0, 0.0, 0.0), amp=amp, omega=2 * math.pi * freq, phase=0.0)]
     bgroup = np.zeros(len(walls), np.int32)
     return _assemble("sloshing_tank", params, fluid, walls, dp, seed, surface,
                      bound_group=bgroup, motions=motions,
-                     meta=dict(depth=depth, amp=amp, freq=freq, seed=seed))
+                     meta=dict(depth=depth, amp=amp, freq=freq, seed=seed),
+                     bound_ghost=wall_ghosts(walls, (1, 1, 1), (NX - 1, NY - 1, None)))
 
 
 def batch_dam_breaks(n_cases: int = 256, seed: int = 0, n_min: int = 5000,

@@ -350,6 +350,93 @@ def test_fourtakas_ddt_without_gravity_is_eq18():
     assert np.array_equal(out[0], out[1])
 
 
+# ---- Eq 38-39: modified dynamic boundary condition ---------------------------
+
+def mdbc_tank(**kw):
+    return cases.still_tank(0.02, size=(0.16, 0.16), depth=0.2, height=0.3,
+                            boundary_mode=1, **kw)
+
+
+def test_mdbc_reproduces_a_linear_density_field():
+    """The corrected SPH moments at the ghost node are first-order consistent:
+    for rho linear in space, rho_G and grad rho_G are exact, so Eq 38 puts
+    the same linear field on the boundary particles (where the moment matrix
+    is regular; elsewhere the Shepard value is checked by the next pin)."""
+    c = mdbc_tank()
+    f, b = c.ptype == 0, c.ptype == 1
+    grad = np.array([30.0, -20.0, 50.0])
+    lin = lambda r: 1000.0 + r @ grad
+    rho = c.rho.copy()
+    rho[f] = lin(c.pos[f])
+    rho_b, _, dets = oracle.mdbc(c, c.pos, c.vel, rho, with_dets=True)
+    reg = b & (np.abs(dets) >= 1e-3)
+    assert reg.sum() > 0.5 * b.sum()
+    np.testing.assert_allclose(rho_b[reg], lin(c.pos[reg]), rtol=1e-10)
+    np.testing.assert_array_equal(rho_b[f], rho[f])  # fluid untouched
+
+
+def test_mdbc_reproduces_a_constant_field_everywhere():
+    """Constant density and velocity: corrected and Shepard branches both
+    return the constant; no-slip mirrors the velocity about a fixed wall."""
+    c = mdbc_tank(mdbc_slip=1)
+    f, b = c.ptype == 0, c.ptype == 1
+    rho = np.full(c.n, 1003.0)
+    vel = np.zeros((c.n, 3))
+    vel[f] = [0.2, -0.1, 0.05]
+    rho_b, vel_b = oracle.mdbc(c, c.pos, vel, rho)
+    g = c.pos + c.ghost
+    has_fluid = np.array([np.any(np.sum((c.pos[f] - g[i]) ** 2, 1) < 4 * c.params["h"] ** 2)
+                          for i in range(c.n)])
+    sel = b & has_fluid
+    np.testing.assert_allclose(rho_b[sel], 1003.0, rtol=1e-12)
+    np.testing.assert_allclose(vel_b[sel], np.tile([-0.2, 0.1, -0.05], (sel.sum(), 1)),
+                               rtol=1e-12)
+    assert np.all(rho_b[b & ~has_fluid] == c.params["rho0"])
+
+
+def test_mdbc_free_slip_keeps_the_tangential_velocity():
+    """mdbc_slip 2 at the bottom wall (ghost straight up): the tangential part
+    of v_G is kept, the normal part reversed."""
+    c = mdbc_tank(mdbc_slip=2)
+    f = c.ptype == 0
+    vel = np.zeros((c.n, 3))
+    vel[f] = [0.2, -0.1, 0.05]
+    _, vel_b = oracle.mdbc(c, c.pos, vel, c.rho)
+    gh = c.ghost
+    bottom = (c.ptype == 1) & (gh[:, 0] == 0) & (gh[:, 1] == 0) & (gh[:, 2] > 0)
+    assert bottom.sum() > 10
+    np.testing.assert_allclose(vel_b[bottom], np.tile([0.2, -0.1, -0.05], (bottom.sum(), 1)),
+                               rtol=1e-12)
+
+
+def test_mdbc_moving_wall_no_slip():
+    """A translating tank (Eq 37) with fluid at rest: v_B = 2 v_wall - 0."""
+    c = cases.sloshing_tank(1500, 0.2, 0.03, 1.0, boundary_mode=1, mdbc_slip=1)
+    b = c.ptype == 1
+    m = c.motions[0]
+    t = 0.13
+    vel = np.zeros((c.n, 3))
+    _, vel_b = oracle.mdbc(c, c.pos, vel, c.rho, t=t)
+    vw = m["amp"] * m["omega"] * np.cos(m["omega"] * t)
+    g = c.pos + c.ghost
+    near = np.array([np.any(np.sum((c.pos[~b] - g[i]) ** 2, 1) < 4 * c.params["h"] ** 2)
+                     for i in range(c.n)])
+    sel = b & near
+    np.testing.assert_allclose(vel_b[sel, 0], 2 * vw, rtol=1e-12)
+    np.testing.assert_allclose(vel_b[sel, 1:], 0.0, atol=1e-15)
+
+
+def test_mdbc_boundary_density_not_from_eq36():
+    """With mDBC the boundary density comes from Eq 38: no Eq 36 term."""
+    c = mdbc_tank()
+    c.vel[c.ptype == 0] = [0.1, 0.0, -0.2]
+    _, drho, _, npairs = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)
+    assert np.all(drho[c.ptype == 1] == 0.0)
+    c.params["boundary_mode"] = 0
+    _, drho0, _, npairs0 = oracle.interact(c.params, c.pos, c.vel, c.rho, c.ptype)
+    assert np.abs(drho0[c.ptype == 1]).max() > 0 and npairs0 > npairs
+
+
 def test_boundary_particles_dbc():
     """Eq 36: boundary particles get no acceleration, and their density only
     changes through fluid neighbours; fluid-boundary pairs push the fluid."""
@@ -471,10 +558,13 @@ def test_dam_break_steps_conserve_mass_and_stay_finite():
 
 
 @pytest.mark.slow
-def test_still_tank_is_hydrostatic():
-    """Eq 28 + DBC: after 1 s at rest, pressure in horizontal slabs is within
-    2 % of rho0 g (H - z) (slabs at least 2h from the bottom and surface)."""
-    c = cases.still_tank(0.02, size=(0.16, 0.16), depth=0.3, height=0.34)
+@pytest.mark.parametrize("boundary_mode", [0, 1])
+def test_still_tank_is_hydrostatic(boundary_mode):
+    """Eq 28 + DBC (Eq 36) or mDBC (Eq 38-39): after 1 s at rest, pressure in
+    horizontal slabs is within 2 % of rho0 g (H - z) (slabs at least 2h from
+    the bottom and surface)."""
+    c = cases.still_tank(0.02, size=(0.16, 0.16), depth=0.3, height=0.34,
+                         boundary_mode=boundary_mode)
     s = oracle.OracleState(c)
     while s.t.value < 1.0:
         s.step(50)
@@ -490,3 +580,5 @@ def test_still_tank_is_hydrostatic():
             continue
         expect = 1000.0 * 9.81 * (H - z[sel].mean())
         assert P[sel].mean() == pytest.approx(expect, rel=0.02), z0
+    # no particle crosses the wall surface (half a spacing above the wall layer)
+    assert z.min() > 0.5 * c.params["dp"]
