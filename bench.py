@@ -65,16 +65,16 @@ def measured_traffic(cell_mode, workload_name):
     return d["dram_bytes_read"] + d["dram_bytes_write"]
 
 
-def workload(name, rank=0):
+def workload(name, rank=0, **kw):
     from paper_2104_00537_gb300 import cases
     if name == "dam_break":
-        return [cases.dam_break(0.004, seed=rank)], "3-D dam break dp=0.004 (1.48M particles)"
+        return [cases.dam_break(0.004, seed=rank, **kw)], "3-D dam break dp=0.004 (1.48M particles)"
     if name == "dam_break_small":
-        return [cases.dam_break(0.02, seed=rank)], "3-D dam break dp=0.02 (28k particles)"
+        return [cases.dam_break(0.02, seed=rank, **kw)], "3-D dam break dp=0.02 (28k particles)"
     if name == "wave_flume":
-        return [cases.wave_flume(0.008, seed=rank)], "wave flume 25x1x1.2 m dp=0.008 (32M particles)"
+        return [cases.wave_flume(0.008, seed=rank, **kw)], "wave flume 25x1x1.2 m dp=0.008 (32M particles)"
     if name == "batched":
-        return cases.batch_dam_breaks(256, seed=rank), "256 dam breaks, 5k-200k fluid each"
+        return cases.batch_dam_breaks(256, seed=rank, **kw), "256 dam breaks, 5k-200k fluid each"
     raise ValueError(name)
 
 
@@ -343,6 +343,8 @@ def main():
     ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "verlet"])
     ap.add_argument("--visc-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--nu0", type=float, default=1e-6)
+    ap.add_argument("--boundary-mode", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--mdbc-slip", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-block", type=int, default=20000)
@@ -368,13 +370,15 @@ def main():
     from paper_2104_00537_gb300 import sph
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    cs, desc = workload(args.workload, rank)
+    cs, desc = workload(args.workload, rank, boundary_mode=args.boundary_mode)
     for c in cs:
         c.params["cell_mode"] = args.cell_mode
         c.params["ddt_mode"] = args.ddt_mode
         c.params["integrator"] = 1 if args.integrator == "verlet" else 0
         c.params["visc_mode"] = args.visc_mode
         c.params["nu0"] = args.nu0
+        c.params["boundary_mode"] = args.boundary_mode
+        c.params["mdbc_slip"] = args.mdbc_slip
     with torch.cuda.stream(stream):
         eng = sph.Engine.batch(cs, stream=stream) if len(cs) > 1 else \
             sph.Engine.create(cs[0], stream=stream)
@@ -430,8 +434,8 @@ def main():
     roofline = {"bound": "alu", "kernel": "k_interact", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": measured_traffic(args.cell_mode, args.workload)
-                if (args.ddt_mode, args.pi_variant, args.integrator, args.visc_mode) ==
-                (1, 0, "symplectic", 0)
+                if (args.ddt_mode, args.pi_variant, args.integrator, args.visc_mode,
+                    args.boundary_mode) == (1, 0, "symplectic", 0, 0)
                 else None,
                 "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
                 "pi_ms_per_launch": 1000 * pi_avg_s,
@@ -446,6 +450,9 @@ def main():
                       "density_diffusion": ["none", "Eq 18", "Eq 19-20"][args.ddt_mode],
                       "viscosity": ["artificial, Eq 21", "laminar + SPS, Eq 23-27 (nu0 %g)"
                                     % args.nu0][args.visc_mode],
+                      "boundary": ["DBC, Eq 36 (2 wall layers)",
+                                   "mDBC, Eq 38-39 (wall layers filling 2h, slip mode %d)"
+                                   % args.mdbc_slip][args.boundary_mode],
                       "integrator": {"symplectic": "Symplectic, Eq 33-34 (2 PI per step)",
                                      "verlet": "Verlet, Eq 30-31, N_S = 40 (1 PI per step)"}[
                           args.integrator],

@@ -73,8 +73,16 @@ typedef struct {
                                * turbulence (Eq 24-27, C_S = 0.12, C_l =
                                * 0.0066, Delta = dp); needs one more
                                * neighbour pass per interaction             */
-  int32_t pad_;
+  int32_t boundary_mode;      /* 0: dynamic boundary condition, Eq 36;
+                               * 1: modified DBC, Eq 38-39 (needs ghost
+                               * offsets, sph_particles.ghost)             */
   double nu0;                 /* kinematic viscosity of Eq 23 (m^2/s)       */
+  int32_t mdbc_slip;          /* mDBC boundary velocity: 0 the imposed one
+                               * (Eq 37); 1 no-slip, 2 v_wall - v_G; 2 free
+                               * slip: tangential part of v_G with the
+                               * normal part of 2 v_wall - v_G (normal along
+                               * the ghost offset)                          */
+  int32_t pad2_;
 } sph_case_params;
 
 /* Imposed translation of a group of boundary particles (Eq 37):
@@ -95,6 +103,10 @@ typedef struct {
   const int32_t *motion_group;  /* [n] index into motions, -1 fixed; or NULL   */
   const sph_motion *motions;    /* [n_motions] (at most 8 per case)            */
   int32_t n_motions;
+  const float *ghost;           /* [3n] mDBC ghost offset r_G - r_B of each
+                                 * boundary particle (the mirror image across
+                                 * the wall surface, Sect. 2.6.2); required
+                                 * when boundary_mode = 1, else ignored     */
 } sph_particles;
 
 /* Counters and diagnostics of one case (FP64 reductions on the device). */
@@ -198,6 +210,14 @@ int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho,
  * with visc_mode 0.  SPH_ERR_STATE if no case of the engine uses
  * visc_mode 1. */
 int sph_eval_sps(sph_engine e, int32_t icase, float *tau6);
+
+/* sph_eval_boundary: the values that the modified dynamic boundary condition
+ * (Sect. 2.6.2) gives the boundary particles of case icase on its current
+ * state, without advancing it: rho [n] (Eq 38) and vel [3n] (Eq 39 with the
+ * case's mdbc_slip), original particle order; fluid and frozen particles
+ * report their state values.  Host buffers, caller-owned, either may be
+ * NULL.  SPH_ERR_STATE if no case of the engine uses boundary_mode 1. */
+int sph_eval_boundary(sph_engine e, int32_t icase, float *vel, float *rho);
 /* sph_get_order: rebuild the neighbour list and return, for case icase, the
  * original ids in device (cell-sorted) order and their cell ids (-1 out). */
 int sph_get_order(sph_engine e, int32_t icase, int64_t *ids, int64_t *cells,

@@ -805,6 +805,7 @@ int orc_mdbc(const orc_params *p, const orc_motion *motions, int32_t nmot, int64
     }
     /* Eq 38: rho_B = rho_G + (r_B - r_G) . grad rho_G, r_B - r_G = -ghost */
     double rB = rhoG - (g[0] * grad[0] + g[1] * grad[1] + g[2] * grad[2]);
+    if (!(rB > 0.0 && rB < 1e30)) rB = rhs[0] / sw; /* not a usable density: Shepard */
     nrho[B] = rB; /* used as is: the rho >= rho0 clamp is a device of Eq 36 */
     /* Eq 39: v_G by the Shepard sum */
     double vG[3] = {sv[0] / sw, sv[1] / sw, sv[2] / sw};

@@ -57,6 +57,9 @@ int make_grid(const sph_case_params &p, Grid &g) {
   if (p.visc_mode < 0 || p.visc_mode > 1)
     return fail(SPH_ERR_ARG, "visc_mode must be 0 (artificial) or 1 (laminar + SPS)");
   if (!(p.nu0 >= 0)) return fail(SPH_ERR_ARG, "nu0 must be >= 0");
+  if (p.boundary_mode < 0 || p.boundary_mode > 1)
+    return fail(SPH_ERR_ARG, "boundary_mode must be 0 (DBC) or 1 (mDBC)");
+  if (p.mdbc_slip < 0 || p.mdbc_slip > 2) return fail(SPH_ERR_ARG, "mdbc_slip must be 0, 1 or 2");
   const double dmin[3] = {p.domain_min.x, p.domain_min.y, p.domain_min.z};
   const double dmax[3] = {p.domain_max.x, p.domain_max.y, p.domain_max.z};
   // cells of 2h, h or 2h/3: the 2h support spans margin = 1, 2 or 3 cells
@@ -122,6 +125,7 @@ void fill_const(const sph_case_params &p, const sph_particles &parts, const Grid
   const double kPi = 3.14159265358979323846;
   const double aD = 21.0 / (16.0 * kPi * p.h * p.h * p.h);  // Eq 11, 3-D
   C.cw = (float)(-5.0 * aD / (p.h * p.h));
+  C.wk = (float)aD;
   C.half_inv_h = (float)(0.5 / p.h);
   // artificial viscosity only in visc_mode 0; laminar + SPS constants otherwise
   C.kvisc = p.visc_mode == 0 ? (float)(-2.0 * p.alpha * p.cs0 * p.h) : 0.f;
@@ -129,6 +133,8 @@ void fill_const(const sph_case_params &p, const sph_particles &parts, const Grid
   C.nu0 = (float)p.nu0;
   C.sps_cs2 = (float)(0.12 * p.dp * 0.12 * p.dp);
   C.sps_cl2 = (float)(0.0066 * p.dp * p.dp);
+  C.bmode = p.boundary_mode;
+  C.mdbc_slip = p.mdbc_slip;
   C.kddt = p.ddt_mode != 0 ? (float)(2.0 * p.delta * p.h * p.cs0) : 0.f;
   C.g[0] = (float)p.gravity.x;
   C.g[1] = (float)p.gravity.y;
@@ -175,6 +181,7 @@ struct sph_engine_t {
   int integrator = 0;  // 0 Symplectic (Eq 33-34), 1 Verlet (Eq 30-31), all cases
   bool ext = false;    // a case uses Eq 19-20 diffusion or laminar + SPS viscosity
   bool sps = false;    // a case uses laminar + SPS viscosity (tau buffers below)
+  bool mdbc = false;   // a case uses the modified dynamic boundary condition
   float4 *tau4 = nullptr;  // (tau/rho) of Eq 25 in sorted order: xx, yy, zz, xy
   float2 *tau2 = nullptr;  //   xz, yz
   bool pool = false;
@@ -203,7 +210,7 @@ struct sph_engine_t {
   sph_options opt{};
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_n = -1, graph_dead = -1;  // n_phys and cells_hw of the captured graph
-  int graph_ext = 0;                       // ext + 2 sps of the captured graph
+  int graph_ext = 0;                       // ext + 2 sps + 4 mdbc of the captured graph
   std::vector<cudaEvent_t> evs;
   double pi_ms = 0, step_ms = 0;
   int64_t pi_launches = 0, kernel_launches = 0;
@@ -260,6 +267,7 @@ int allocate(sph_engine e) {
     e->S[b].cid = (uint16_t *)A(2 * N);
     e->S[b].code = (uint8_t *)A(N);
     e->S[b].vrprev = e->integrator == 1 && b < 2 ? (float4 *)A(16 * N) : nullptr;
+    e->S[b].ghost = e->mdbc || e->pool ? (float4 *)A(16 * N) : nullptr;
   }
   e->keysA = (uint32_t *)A(4 * N);
   e->keysB = (uint32_t *)A(4 * N);
@@ -279,7 +287,7 @@ int allocate(sph_engine e) {
   e->nvalid = (int *)A(16);
   e->sort_tmp = A(radix_sort_temp_bytes(N));
   e->diag = (double *)A(sizeof(double) * (8 * 1024 + 8));
-  e->io_bytes = align256(48 * (size_t)N) + 4096;
+  e->io_bytes = align256(64 * (size_t)N) + 4096;
   e->io = (char *)A(e->io_bytes);
   if (!ok) return fail(SPH_ERR_OOM, "device allocation failed");
   for (int b = 0; b < 3; b++) {  // defined contents for the padding
@@ -318,6 +326,9 @@ int check_particles(const sph_case_params *p, const sph_particles *parts) {
       if (parts->motion_group[i] >= parts->n_motions)
         return fail(SPH_ERR_ARG, "motion_group index out of range");
   if (!(p->cfl > 0) && !(p->dt_fixed > 0)) return fail(SPH_ERR_ARG, "cfl or dt_fixed must be > 0");
+  if (p->boundary_mode == 1 && !parts->ghost)
+    for (int64_t i = 0; i < parts->n; i++)
+      if (parts->type[i] != 0) return fail(SPH_ERR_ARG, "mDBC needs the ghost offsets");
   return SPH_OK;
 }
 
@@ -335,7 +346,11 @@ int upload_case(sph_engine e, int slot, const sph_particles *parts, int64_t dst0
   uint8_t *d_type = (uint8_t *)p;
   p += align256(n);
   int32_t *d_group = (int32_t *)p;
+  p += align256(4 * n);
+  float *d_ghost = (float *)p;
   CUDA_TRY(cudaMemcpyAsync(d_pos, parts->pos, 24 * n, cudaMemcpyHostToDevice, e->s));
+  if (parts->ghost)
+    CUDA_TRY(cudaMemcpyAsync(d_ghost, parts->ghost, 12 * n, cudaMemcpyHostToDevice, e->s));
   if (parts->vel) CUDA_TRY(cudaMemcpyAsync(d_vel, parts->vel, 12 * n, cudaMemcpyHostToDevice, e->s));
   CUDA_TRY(cudaMemcpyAsync(d_rho, parts->rho, 4 * n, cudaMemcpyHostToDevice, e->s));
   CUDA_TRY(cudaMemcpyAsync(d_type, parts->type, n, cudaMemcpyHostToDevice, e->s));
@@ -343,7 +358,7 @@ int upload_case(sph_engine e, int slot, const sph_particles *parts, int64_t dst0
     CUDA_TRY(cudaMemcpyAsync(d_group, parts->motion_group, 4 * n, cudaMemcpyHostToDevice, e->s));
   launch_upload((int)n, d_pos, parts->vel ? d_vel : nullptr, d_rho, d_type,
                 parts->motion_group ? d_group : nullptr, slot, 0, e->dconst, e->ddyn, e->nbits,
-                e->S[0], e->keysA, (int)dst0, e->s);
+                e->S[0], e->keysA, (int)dst0, parts->ghost ? d_ghost : nullptr, e->s);
   CUDA_TRY(cudaGetLastError());
   // the io buffer is reused by the next call: wait for the copies
   CUDA_TRY(cudaStreamSynchronize(e->s));
@@ -415,6 +430,7 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
   for (int c = 0; c < ncases; c++) {
     e->ext = e->ext || params[c].ddt_mode == 2 || params[c].visc_mode == 1;
     e->sps = e->sps || params[c].visc_mode == 1;
+    e->mdbc = e->mdbc || params[c].boundary_mode == 1;
   }
   rc = allocate(e);
   int64_t cell0 = 0, p0 = 0;
@@ -443,9 +459,13 @@ void enqueue_step_verlet(sph_engine e, cudaEvent_t *ev) {
   State &X = e->S[0], &Y = e->S[1];
   cudaStream_t s = e->s;
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
-  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev, Y,
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
+                 X.ghost, Y,
                  e->press, e->dconst, e->nbits, s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
+  if (e->mdbc)
+    launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
+                e->ddyn, 0, s);
   if (ev) cudaEventRecord(ev[0], s);
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
                   e->press, Y.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
@@ -468,10 +488,14 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
   cudaStream_t s = e->s;
   // NL on state n
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
-  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev, Y,
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
+                 X.ghost, Y,
                  e->press,
                  e->dconst, e->nbits, s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
+  if (e->mdbc)  // boundary values of Eq 38-39 on state n
+    launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
+                e->ddyn, 0, s);
   // PI on state n, time step, predictor
   if (ev) cudaEventRecord(ev[0], s);
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
@@ -483,10 +507,14 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
                    e->keysC, s);
   // NL on state n+1/2 (id/cid/code of Z are those of Y)
   radix_sort(e->keysC, e->keysD, e->perm2, nl, e->nbits, e->sort_tmp, s);
-  launch_reorder(nl, e->perm2, e->keysD, Z.posc, Z.velrho, Y.id, Y.cid, Y.code, nullptr, X,
+  launch_reorder(nl, e->perm2, e->keysD, Z.posc, Z.velrho, Y.id, Y.cid, Y.code, nullptr,
+                 Y.ghost, X,
                  e->press,
                  e->dconst, e->nbits, s);
   launch_cells(nl, e->keysD, e->cstart, e->cells_hw, e->nbits, e->nvalid + 1, e->cells_tmp, s);
+  if (e->mdbc)  // boundary values of Eq 38-39 on state n+1/2
+    launch_mdbc(e->margin, nl, e->nvalid + 1, e->keysD, X, e->press, e->cstart, e->nbits,
+                e->dconst, e->ddyn, 1, s);
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid + 1, e->keysD, X.posc, X.velrho,
                   e->press, X.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
@@ -503,7 +531,8 @@ void enqueue_nl(sph_engine e) {
   const int nl = (int)(e->n_phys - e->n_dead);
   State &X = e->S[0], &Y = e->S[1];
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, e->s);
-  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev, Y,
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
+                 X.ghost, Y,
                  e->press,
                  e->dconst, e->nbits, e->s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, e->s);
@@ -587,7 +616,7 @@ int sph_step(sph_engine e, int64_t nsteps) {
   int64_t k = 0;
   if (!timing && e->opt.use_graph && e->n_dead == 0) {
     if (!e->gexec || e->graph_n != e->n_phys || e->graph_dead != e->cells_hw ||
-        e->graph_ext != (int)e->ext + 2 * (int)e->sps) {
+        e->graph_ext != (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc) {
       if (e->gexec) cudaGraphExecDestroy(e->gexec);
       e->gexec = nullptr;
       cudaGraph_t g;
@@ -599,7 +628,7 @@ int sph_step(sph_engine e, int64_t nsteps) {
       if (err != cudaSuccess) return fail(SPH_ERR_CUDA, cudaGetErrorString(err));
       e->graph_n = e->n_phys;
       e->graph_dead = e->cells_hw;  // cells in use at capture
-      e->graph_ext = (int)e->ext + 2 * (int)e->sps;
+      e->graph_ext = (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc;
     }
     for (; k < nsteps; k++) CUDA_TRY(cudaGraphLaunch(e->gexec, e->s));
   }
@@ -611,7 +640,8 @@ int sph_step(sph_engine e, int64_t nsteps) {
   const int64_t pis = e->integrator == 1 ? 1 : 2;
   const int64_t per_step = (e->integrator == 1 ? 3 * passes + 1 + 4 + 1 + 3
                                                : 6 * passes + 2 + 8 + 2 + 4) +
-                           (e->sps ? pis : 0);  // strain pass before each interaction
+                           (e->sps ? pis : 0) +  // strain pass before each interaction
+                           (e->mdbc ? pis : 0);  // ghost-node pass before each interaction
   e->kernel_launches += per_step * nsteps;
   for (; k < nsteps; k++) {
     enqueue_step(e, timing ? &e->evs[4 * k] : nullptr);
@@ -806,6 +836,7 @@ int sph_create_from_raw(const sph_case_params *params, const sph_particles *part
   // reorder type/group into snapshot order on the host, then import
   std::vector<uint8_t> type(n);
   std::vector<int32_t> group(n, -1);
+  std::vector<float> ghost(parts->ghost ? 3 * n : 0);
   for (int64_t j = 0; j < n; j++) {
     if (ids[j] >= (uint32_t)n) {
       sph_destroy(e);
@@ -814,6 +845,8 @@ int sph_create_from_raw(const sph_case_params *params, const sph_particles *part
     }
     type[j] = parts->type[ids[j]];
     if (parts->motion_group) group[j] = parts->motion_group[ids[j]];
+    if (parts->ghost)
+      for (int k = 0; k < 3; k++) ghost[3 * j + k] = parts->ghost[3 * ids[j] + k];
   }
   char *p = e->io;
   int32_t *d_cell = (int32_t *)p;
@@ -825,13 +858,17 @@ int sph_create_from_raw(const sph_case_params *params, const sph_particles *part
   uint8_t *d_type = (uint8_t *)p;
   p += align256(n);
   int32_t *d_group = (int32_t *)p;
+  p += align256(4 * n);
+  float *d_ghost = (float *)p;
+  if (parts->ghost)
+    CUDA_TRY(cudaMemcpyAsync(d_ghost, ghost.data(), 12 * n, cudaMemcpyHostToDevice, e->s));
   CUDA_TRY(cudaMemcpyAsync(d_cell, cell, 4 * n, cudaMemcpyHostToDevice, e->s));
   CUDA_TRY(cudaMemcpyAsync(d_pc, pc, 16 * n, cudaMemcpyHostToDevice, e->s));
   CUDA_TRY(cudaMemcpyAsync(d_vr, vr, 16 * n, cudaMemcpyHostToDevice, e->s));
   CUDA_TRY(cudaMemcpyAsync(d_type, type.data(), n, cudaMemcpyHostToDevice, e->s));
   CUDA_TRY(cudaMemcpyAsync(d_group, group.data(), 4 * n, cudaMemcpyHostToDevice, e->s));
   launch_import_raw((int)n, d_cell, d_pc, d_vr, d_type, d_group, 0, 0, e->dconst, e->nbits,
-                    e->S[0], e->keysA, 0, e->s);
+                    e->S[0], e->keysA, 0, parts->ghost ? d_ghost : nullptr, e->s);
   // ids: the import wrote 0..n-1; restore the snapshot ids
   CUDA_TRY(cudaMemcpyAsync(e->S[0].id, ids, 4 * n, cudaMemcpyHostToDevice, e->s));
   if (hd.version == 2)  // v^{n-1}, rho^{n-1} of the Verlet scheme, same order
@@ -872,6 +909,9 @@ int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho, float 
   enqueue_nl(e);
   const int nl = (int)(e->n_phys - e->n_dead);
   State &Y = e->S[1];
+  if (e->mdbc)
+    launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
+                e->ddyn, 0, e->s);
   launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
                   e->press, Y.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
                   e->mu, 1, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, e->s);
@@ -925,6 +965,29 @@ int sph_eval_sps(sph_engine e, int32_t icase, float *tau6) {
   launch_scatter_tau(nl, Y.cid, Y.id, icase, e->nvalid, e->tau4, e->tau2, d_tau, e->s);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(tau6, d_tau, 24 * n, cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  return SPH_OK;
+}
+
+int sph_eval_boundary(sph_engine e, int32_t icase, float *vel, float *rho) {
+  int rc = valid_case(e, icase);
+  if (rc) return rc;
+  if (!e->mdbc) return fail(SPH_ERR_STATE, "no case of this engine uses boundary_mode 1");
+  const int64_t n = e->slots[icase].n;
+  enqueue_nl(e);
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &Y = e->S[1];
+  launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
+              e->ddyn, 0, e->s);
+  char *p = e->io;
+  float *d_vel = (float *)p;
+  p += align256(12 * n);
+  float *d_rho = (float *)p;
+  launch_export(nl, e->keysB, Y, e->dconst, icase, 0, e->nbits, nullptr, vel ? d_vel : nullptr,
+                rho ? d_rho : nullptr, nullptr, e->s);
+  CUDA_TRY(cudaGetLastError());
+  if (vel) CUDA_TRY(cudaMemcpyAsync(vel, d_vel, 12 * n, cudaMemcpyDeviceToHost, e->s));
+  if (rho) CUDA_TRY(cudaMemcpyAsync(rho, d_rho, 4 * n, cudaMemcpyDeviceToHost, e->s));
   CUDA_TRY(cudaStreamSynchronize(e->s));
   return SPH_OK;
 }
@@ -1028,6 +1091,7 @@ int sph_pool_admit(sph_engine e, const sph_case_params *params, const sph_partic
   // (the pool's tau buffers exist from creation; the flags only grow)
   e->ext = e->ext || params->ddt_mode == 2 || params->visc_mode == 1;
   e->sps = e->sps || params->visc_mode == 1;
+  e->mdbc = e->mdbc || params->boundary_mode == 1;
   if (used == 0) e->margin = g.margin;
   if (g.margin != e->margin) return fail(SPH_ERR_ARG, "cell_mode differs from the pool's cases");
   int free_slot = -1;

@@ -37,6 +37,7 @@ struct CaseConst {
   int32_t nx, ny, nz, margin;
   uint32_t cellbase;  // first global cell of this case
   int32_t nmot, ddt, clamp, visc;  // visc: 0 artificial (Eq 21), 1 laminar + SPS (Eq 23-27)
+  int32_t bmode, mdbc_slip;        // bmode: 0 DBC (Eq 36), 1 mDBC (Eq 38-39)
   int32_t max_out, active, n_fluid, verlet_steps;  // verlet_steps: N_S of Eq 31
   float h, csf, r2max, eta2;
   float m, rho0, inv_rho0, btait, gamma;
@@ -53,6 +54,8 @@ struct CaseConst {
   float nu0;      // Eq 23
   float sps_cs2;  // (C_S Delta)^2 of Eq 25
   float sps_cl2;  // C_l Delta^2 of Eq 25
+  float wk;       // a_D of Eq 11: W = a_D t^4 (5 - 4t), t = 1 - r/(2h)
+  float pad4_;
 };
 
 // Mutable per-case values, updated on the device during a step.
@@ -98,6 +101,7 @@ struct State {
   uint16_t *cid;
   uint8_t *code;
   float4 *vrprev;  // Verlet scheme only (else null): v^{n-1}, rho^{n-1} of Eq 30
+  float4 *ghost;   // mDBC only (else null): ghost offset r_G - r_B (xyz) of Eq 38
 };
 
 // Sets the message returned by sph_last_error() (defined in sph_api.cu).

@@ -73,10 +73,14 @@ __global__ void k_upload(int n, const double *__restrict__ pos, const float *__r
                          const float *__restrict__ rho, const uint8_t *__restrict__ type,
                          const int32_t *__restrict__ group, int slot, uint32_t id_base,
                          const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
-                         int nbits, State st, uint32_t *__restrict__ keys, int dst0) {
+                         int nbits, State st, uint32_t *__restrict__ keys, int dst0,
+                         const float *__restrict__ ghost) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const CaseConst &C = cc[slot];
+  if (st.ghost)
+    st.ghost[dst0 + i] = ghost ? make_float4(ghost[3 * i], ghost[3 * i + 1], ghost[3 * i + 2], 0.f)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
   int c[3];
   float off[3];
   bool inside = true;
@@ -128,7 +132,8 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
                           const uint32_t *__restrict__ id_src,
                           const uint16_t *__restrict__ cid_src,
                           const uint8_t *__restrict__ code_src,
-                          const float4 *__restrict__ vrprev_src, State dst,
+                          const float4 *__restrict__ vrprev_src,
+                          const float4 *__restrict__ ghost_src, State dst,
                           float *__restrict__ press, const CaseConst *__restrict__ cc,
                           int nbits) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -149,6 +154,7 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
   dst.cid[i] = cidx;
   dst.code[i] = code_src[p];
   if (vrprev_src) dst.vrprev[i] = vrprev_src[p];
+  if (ghost_src) dst.ghost[i] = ghost_src[p];
   press[i] = tait_pressure(C, vr.w) / vr.w;
 }
 
@@ -470,6 +476,8 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   const float Pa = has ? press[i] * va.w : 0.f;  // press holds P / rho
   const float kv = C.kvisc * va.w;
   const bool ddt_on = C.ddt != 0;
+  // boundary targets of an mDBC case take their density from Eq 38, not Eq 36
+  const bool work = has && (afluid || C.bmode == 0);
   Ext X;
   X.C = &C;
   X.hyd = EXT >= 1 && C.ddt == 2;
@@ -497,7 +505,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
     const float gy = slab_gap(dy, pa.y, cs), gz = slab_gap(dz, pa.z, cs);
     const float d2 = fmaf(gy, gy, gz * gz);
     int loF = 0, hiF = 0, loB = 0, hiB = 0;
-    if (has && d2 < r2prune) {
+    if (work && d2 < r2prune) {
       const float L = sqrtf(r2prune - d2);
       const int kx0 = max(-M, (int)floorf((pa.x - L) * ics));
       const int kx1 = min(M, (int)floorf((pa.x + L) * ics));
@@ -636,6 +644,7 @@ k_interact_q(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict
   const float Pa = has ? press[i] * va.w : 0.f;
   const float kv = C.kvisc * va.w;
   const bool ddt_on = C.ddt != 0;
+  const bool work = has && (afluid || C.bmode == 0);
   const bool warp_fluid = __all_sync(full, afluid || !has);
   const unsigned active = __ballot_sync(full, has);
   Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
@@ -683,7 +692,7 @@ k_interact_q(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict
     const float gy = slab_gap(dy, pa.y, cs), gz = slab_gap(dz, pa.z, cs);
     const float d2 = fmaf(gy, gy, gz * gz);
     int loF = 0, hiF = 0, loB = 0, hiB = 0;
-    if (has && d2 < r2prune) {
+    if (work && d2 < r2prune) {
       const float L = sqrtf(r2prune - d2);
       const int kx0 = max(-M, (int)floorf((pa.x - L) * ics));
       const int kx1 = min(M, (int)floorf((pa.x + L) * ics));
@@ -856,6 +865,221 @@ k_strain(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ k
   tau4[i] = make_float4(fmaf(nu2, sxx - tr3, iso), fmaf(nu2, syy - tr3, iso),
                         fmaf(nu2, szz - tr3, iso), nu2 * sxy);
   tau2[i] = make_float2(nu2 * sxz, nu2 * syz);
+}
+
+// ---- modified dynamic boundary condition (Eq 38-39) ------------------------------
+
+// Solves A x = b (4x4, FP64) by Gaussian elimination with partial pivoting;
+// returns det(A); x is left unset when det == 0.
+__device__ double solve4(double A[4][4], double b[4], double x[4]) {
+  double det = 1.0;
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    int piv = c;
+#pragma unroll
+    for (int r = c + 1; r < 4; r++)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (A[piv][c] == 0.0) return 0.0;
+    if (piv != c) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const double t = A[c][k];
+        A[c][k] = A[piv][k];
+        A[piv][k] = t;
+      }
+      const double t = b[c];
+      b[c] = b[piv];
+      b[piv] = t;
+      det = -det;
+    }
+    det *= A[c][c];
+#pragma unroll
+    for (int r = c + 1; r < 4; r++) {
+      const double f = A[r][c] / A[c][c];
+#pragma unroll
+      for (int k = c; k < 4; k++) A[r][k] -= f * A[c][k];
+      b[r] -= f * b[c];
+    }
+  }
+#pragma unroll
+  for (int r = 3; r >= 0; r--) {
+    double v = b[r];
+#pragma unroll
+    for (int k = r + 1; k < 4; k++) v -= A[r][k] * x[k];
+    x[r] = v / A[r][r];
+  }
+  return det;
+}
+
+constexpr double kMdbcDetMin = 1e-3;  // |det| below: Shepard value, zero gradient
+
+// One thread per particle (sorted order); boundary particles of mDBC cases
+// get their density from the ghost node r_G = r_B + ghost (Eq 38) and, with
+// mdbc_slip, their velocity from the Shepard sum of Eq 39.  The moment sums
+// run over fluid particles within 2h of r_G, found from the ghost's own cell
+// (rows clamped to the grid).  stage selects the time of the imposed wall
+// velocity: t (0) or t + dt/2 (1).  Also refreshes P/rho of the particle.
+template <int M>
+__global__ void __launch_bounds__(128)
+k_mdbc(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys, State st,
+       float *__restrict__ press, const uint32_t *__restrict__ cstart, int nbits,
+       const CaseConst *__restrict__ cc, const CaseDyn *__restrict__ dyn, int stage) {
+  const unsigned full = 0xffffffffu;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvalid = *nvalid_p;
+  const bool has = i < nvalid;
+  const int cidx = i < n ? (int)st.cid[i] : 0;
+  const CaseConst &C = cc[cidx];
+  const uint32_t key = has ? keys[i] : 0u;
+  const bool act = has && key_boundary(key, nbits) && C.bmode == 1;
+  if (__all_sync(full, !act)) return;
+  const float cs = C.csf, ics = C.inv_csf, r2max = C.r2max, hih = C.half_inv_h;
+  const float r2prune = r2max * 1.0001f;
+  // ghost position: cell of B shifted by the whole cells of (offset + ghost)
+  int cx = 0, cy = 0, cz = 0;
+  float4 pb = make_float4(0.f, 0.f, 0.f, 0.f), g = pb;
+  if (act) {
+    decode_cell(key_cell(key, nbits) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+    pb = st.posc[i];
+    g = st.ghost[i];
+  }
+  const float qx0 = pb.x + g.x, qy0 = pb.y + g.y, qz0 = pb.z + g.z;
+  const int sx = (int)floorf(qx0 * ics), sy = (int)floorf(qy0 * ics), sz = (int)floorf(qz0 * ics);
+  const int gx = cx + sx, gy = cy + sy, gz = cz + sz;                       // ghost cell
+  const float ox = fmaf(-(float)sx, cs, qx0), oy = fmaf(-(float)sy, cs, qy0),
+              oz = fmaf(-(float)sz, cs, qz0);                               // offset in it
+  const int nx = C.nx, ny = C.ny, nz = C.nz, nxy = nx * ny;
+  const int base0 = (int)C.cellbase;
+  // moment sums (per unit particle mass): A00 = sum W / rho_b, A0k = sum e_k W / rho_b,
+  // Ak0 = sum F d_k / rho_b, Akl = sum F d_k e_l / rho_b (e = -d = r_b - r_G),
+  // vs = sum v W / rho_b, and the right-hand side for (rho_G - rho0, grad rho_G):
+  // r0 = sum W (rho_b - rho0) / rho_b, rk = sum F d_k (rho_b - rho0) / rho_b.  The
+  // same system as for rho_G itself (A (rho0, 0) is rho0 times A's first column),
+  // but its right-hand side has no FP32 cancellation of rho0-sized terms.
+  float a00 = 0.f, a01 = 0.f, a02 = 0.f, a03 = 0.f, a10 = 0.f, a20 = 0.f, a30 = 0.f;
+  float dxx = 0.f, dyy = 0.f, dzz = 0.f, dxy = 0.f, dxz = 0.f, dyz = 0.f;
+  float r0 = 0.f, r1 = 0.f, r2s = 0.f, r3 = 0.f, vsx = 0.f, vsy = 0.f, vsz = 0.f;
+  constexpr int W = 2 * M + 1;
+#pragma unroll 1
+  for (int row = 0; row < W * W; row++) {
+    const int dy = row % W - M, dz = row / W - M;
+    const int yy = gy + dy, zz = gz + dz;
+    int lo = 0, hi = 0;
+    const float sgy = slab_gap(dy, oy, cs), sgz = slab_gap(dz, oz, cs);
+    const float d2 = fmaf(sgy, sgy, sgz * sgz);
+    if (act && d2 < r2prune && yy >= 0 && yy < ny && zz >= 0 && zz < nz) {
+      const float L = sqrtf(r2prune - d2);
+      const int x0 = max(0, gx + max(-M, (int)floorf((ox - L) * ics)));
+      const int x1 = min(nx - 1, gx + min(M, (int)floorf((ox + L) * ics)));
+      if (x1 >= x0) {
+        const int c0 = base0 + zz * nxy + yy * nx;
+        lo = (int)cstart[c0 + x0];  // fluid segment only (b in F)
+        hi = (int)cstart[c0 + x1 + 1];
+      }
+    }
+    const float ry0 = fmaf((float)(gy - yy), cs, oy), rz0 = fmaf((float)(gz - zz), cs, oz);
+    const int len = hi - lo;
+    const int maxlen = (int)__reduce_max_sync(full, (unsigned)max(len, 0));
+#pragma unroll 1
+    for (int k = 0; k < maxlen; k++) {
+      if (k < len) {
+        const int j = lo + k;
+        const float4 pf = st.posc[j];
+        const float ddx = fmaf((float)gx - pf.w, cs, ox - pf.x);  // d = r_G - r_b
+        const float ddy = ry0 - pf.y, ddz = rz0 - pf.z;
+        const float rr2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+        if (rr2 < r2max) {
+          const float4 vb = st.velrho[j];
+          const float ib = __fdividef(1.f, vb.w);
+          const float t = fmaf(-hih, rr2 * rsqrtf(rr2 + 1e-30f), 1.f);
+          const float t3 = t * t * t;
+          const float w = C.wk * t3 * t * fmaf(-4.f, t, 5.f);  // W (Eq 11)
+          const float f = C.cw * t3;                            // grad_G W = f d
+          const float wv = w * ib, fv = f * ib;
+          const float dr = (vb.w - C.rho0) * ib;  // (rho_b - rho0) / rho_b
+          a00 += wv;
+          a01 = fmaf(-wv, ddx, a01);
+          a02 = fmaf(-wv, ddy, a02);
+          a03 = fmaf(-wv, ddz, a03);
+          a10 = fmaf(fv, ddx, a10);
+          a20 = fmaf(fv, ddy, a20);
+          a30 = fmaf(fv, ddz, a30);
+          dxx = fmaf(fv * ddx, ddx, dxx);
+          dyy = fmaf(fv * ddy, ddy, dyy);
+          dzz = fmaf(fv * ddz, ddz, dzz);
+          dxy = fmaf(fv * ddx, ddy, dxy);
+          dxz = fmaf(fv * ddx, ddz, dxz);
+          dyz = fmaf(fv * ddy, ddz, dyz);
+          r0 = fmaf(w, dr, r0);
+          r1 = fmaf(f * dr, ddx, r1);
+          r2s = fmaf(f * dr, ddy, r2s);
+          r3 = fmaf(f * dr, ddz, r3);
+          vsx = fmaf(wv, vb.x, vsx);
+          vsy = fmaf(wv, vb.y, vsy);
+          vsz = fmaf(wv, vb.z, vsz);
+        }
+      }
+    }
+  }
+  if (!act) return;
+  // imposed velocity of B at the evaluation time (Eq 37)
+  float vw[3] = {0.f, 0.f, 0.f};
+  const uint8_t code = st.code[i];
+  if (code >= 2) {
+    const int gi = code - 2;
+    const CaseDyn &D = dyn[cidx];
+    const double te = D.t + (stage ? 0.5 * D.dt : 0.0);
+    const float v = (float)(C.mot_amp[gi] * C.mot_omega[gi] *
+                            cos(C.mot_omega[gi] * te + C.mot_phase[gi]));
+    vw[0] = v * C.mot_axis[gi][0];
+    vw[1] = v * C.mot_axis[gi][1];
+    vw[2] = v * C.mot_axis[gi][2];
+  }
+  float4 out = st.velrho[i];
+  if (!(a00 > 0.f)) {  // no fluid near the ghost
+    out.w = C.rho0;
+    if (C.mdbc_slip) {
+      out.x = vw[0];
+      out.y = vw[1];
+      out.z = vw[2];
+    }
+  } else {
+    double A[4][4] = {{a00, a01, a02, a03},
+                      {a10, -dxx, -dxy, -dxz},
+                      {a20, -dxy, -dyy, -dyz},
+                      {a30, -dxz, -dyz, -dzz}};
+    double b[4] = {r0, r1, r2s, r3}, x[4] = {0.0, 0.0, 0.0, 0.0};
+    // the sums are per unit particle mass: the determinant of the moment
+    // matrix with volumes V_b = m / rho_b is m^4 times this one
+    const double m2 = C.m_d * C.m_d;
+    const double det = solve4(A, b, x) * (m2 * m2);
+    const double shep = (double)C.rho0 + (double)r0 / (double)a00;  // Shepard value
+    double rhoB = shep;
+    if (fabs(det) >= kMdbcDetMin) {
+      // Eq 38 with r_B - r_G = -ghost
+      rhoB = (double)C.rho0 + x[0] - ((double)g.x * x[1] + (double)g.y * x[2] + (double)g.z * x[3]);
+      if (!(rhoB > 0.0 && rhoB < 1e30)) rhoB = shep;  // not a usable density
+    }
+    out.w = (float)rhoB;
+    const float vgx = vsx / a00, vgy = vsy / a00, vgz = vsz / a00;  // Eq 39
+    if (C.mdbc_slip == 1) {
+      out.x = 2.f * vw[0] - vgx;
+      out.y = 2.f * vw[1] - vgy;
+      out.z = 2.f * vw[2] - vgz;
+    } else if (C.mdbc_slip == 2) {
+      const float gn = sqrtf(g.x * g.x + g.y * g.y + g.z * g.z);
+      const float inv = gn > 0.f ? 1.f / gn : 0.f;
+      const float nx_ = g.x * inv, ny_ = g.y * inv, nz_ = g.z * inv;
+      const float vn = vgx * nx_ + vgy * ny_ + vgz * nz_;
+      const float wn = vw[0] * nx_ + vw[1] * ny_ + vw[2] * nz_;
+      const float k2 = 2.f * (wn - vn);
+      out.x = fmaf(k2, nx_, vgx);
+      out.y = fmaf(k2, ny_, vgy);
+      out.z = fmaf(k2, nz_, vgz);
+    }
+  }
+  st.velrho[i] = out;
+  press[i] = tait_pressure(C, out.w) / out.w;
 }
 
 // ---- time step and motion ----------------------------------------------------
@@ -1084,6 +1308,7 @@ __global__ void k_verlet(int n, const uint32_t *__restrict__ keys_in, State src,
   dst.id[i] = src.id[i];
   dst.cid[i] = (uint16_t)cidx;
   dst.code[i] = code;
+  if (src.ghost) dst.ghost[i] = src.ghost[i];
   const CaseConst &C = cc[cidx];
   const CaseDyn &D = dyn[cidx];
   const double dt = D.dt;
@@ -1184,9 +1409,13 @@ __global__ void k_import_raw(int n, const int32_t *__restrict__ cell,
                              const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
                              const uint8_t *__restrict__ type, const int32_t *__restrict__ group,
                              int slot, uint32_t id_base, const CaseConst *__restrict__ cc,
-                             int nbits, State st, uint32_t *__restrict__ keys, int dst0) {
+                             int nbits, State st, uint32_t *__restrict__ keys, int dst0,
+                             const float *__restrict__ ghost) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (st.ghost)
+    st.ghost[dst0 + i] = ghost ? make_float4(ghost[3 * i], ghost[3 * i + 1], ghost[3 * i + 2], 0.f)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
   const CaseConst &C = cc[slot];
   uint8_t code = type[i] == 0 ? 0 : (group && group[i] >= 0 ? (uint8_t)(2 + group[i]) : 1);
   int d = dst0 + i;
@@ -1338,19 +1567,20 @@ static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 void launch_upload(int n, const double *pos, const float *vel, const float *rho,
                    const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
                    const CaseConst *cc, CaseDyn *dyn, int nbits, State st, uint32_t *keys,
-                   int dst0, cudaStream_t s) {
+                   int dst0, const float *ghost, cudaStream_t s) {
   if (n > 0)
     k_upload<<<nblk(n, 256), 256, 0, s>>>(n, pos, vel, rho, type, group, slot, id_base, cc,
-                                          dyn, nbits, st, keys, dst0);
+                                          dyn, nbits, st, keys, dst0, ghost);
 }
 
 void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
                     const float4 *posc, const float4 *velrho, const uint32_t *id,
-                    const uint16_t *cid, const uint8_t *code, const float4 *vrprev, State dst,
-                    float *press, const CaseConst *cc, int nbits, cudaStream_t s) {
+                    const uint16_t *cid, const uint8_t *code, const float4 *vrprev,
+                    const float4 *ghost, State dst, float *press, const CaseConst *cc, int nbits,
+                    cudaStream_t s) {
   if (n > 0)
     k_reorder<<<nblk(n, 256), 256, 0, s>>>(n, perm, keys_sorted, posc, velrho, id, cid, code,
-                                           vrprev, dst, press, cc, nbits);
+                                           vrprev, ghost, dst, press, cc, nbits);
 }
 
 size_t cells_temp_words(int64_t cap_cells) {
@@ -1455,6 +1685,21 @@ void launch_corrector(int n, const uint32_t *perm2, const uint32_t *keys_half,
                                              nbits, keys_next);
 }
 
+void launch_mdbc(int margin, int n, const int *nvalid, const uint32_t *keys, State st,
+                 float *press, const uint32_t *cstart, int nbits, const CaseConst *cc,
+                 const CaseDyn *dyn, int stage, cudaStream_t s) {
+  if (n <= 0) return;
+  if (margin == 1)
+    k_mdbc<1><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, press, cstart, nbits, cc, dyn,
+                                           stage);
+  else if (margin == 3)
+    k_mdbc<3><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, press, cstart, nbits, cc, dyn,
+                                           stage);
+  else
+    k_mdbc<2><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, press, cstart, nbits, cc, dyn,
+                                           stage);
+}
+
 void launch_verlet(int n, const uint32_t *keys_in, State src, const float4 *ace,
                    const CaseConst *cc, CaseDyn *dyn, int nbits, State dst, uint32_t *keys_out,
                    cudaStream_t s) {
@@ -1473,10 +1718,10 @@ void launch_export(int n, const uint32_t *keys, State st, const CaseConst *cc, i
 void launch_import_raw(int n, const int32_t *cell, const float4 *posc, const float4 *velrho,
                        const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
                        const CaseConst *cc, int nbits, State st, uint32_t *keys, int dst0,
-                       cudaStream_t s) {
+                       const float *ghost, cudaStream_t s) {
   if (n > 0)
     k_import_raw<<<nblk(n, 256), 256, 0, s>>>(n, cell, posc, velrho, type, group, slot, id_base,
-                                              cc, nbits, st, keys, dst0);
+                                              cc, nbits, st, keys, dst0, ghost);
 }
 
 void launch_scatter_forces(int n, const uint16_t *cid, const uint32_t *id, int slot,

@@ -7,11 +7,12 @@ namespace sph {
 void launch_upload(int n, const double *pos, const float *vel, const float *rho,
                    const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
                    const CaseConst *cc, CaseDyn *dyn, int nbits, State st, uint32_t *keys,
-                   int dst0, cudaStream_t s);
+                   int dst0, const float *ghost, cudaStream_t s);
 void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
                     const float4 *posc, const float4 *velrho, const uint32_t *id,
-                    const uint16_t *cid, const uint8_t *code, const float4 *vrprev, State dst,
-                    float *press, const CaseConst *cc, int nbits, cudaStream_t s);
+                    const uint16_t *cid, const uint8_t *code, const float4 *vrprev,
+                    const float4 *ghost, State dst, float *press, const CaseConst *cc, int nbits,
+                    cudaStream_t s);
 // Words of temporary storage launch_cells needs for cap_cells cells.
 size_t cells_temp_words(int64_t cap_cells);
 // Cell start table of the sorted keys (and nvalid); returns kernels launched.
@@ -35,6 +36,11 @@ void launch_end_step(int ncases, const CaseConst *cc, CaseDyn *dyn, cudaStream_t
 void launch_predictor(int n, const uint32_t *keys_in, State src, const float4 *ace,
                       const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
                       float4 *velrho_out, uint32_t *keys_out, cudaStream_t s);
+// mDBC boundary values (Eq 38-39) on the sorted state st, before an
+// interaction; stage 0: wall velocity at t, 1: at t + dt/2.
+void launch_mdbc(int margin, int n, const int *nvalid, const uint32_t *keys, State st,
+                 float *press, const uint32_t *cstart, int nbits, const CaseConst *cc,
+                 const CaseDyn *dyn, int stage, cudaStream_t s);
 // Verlet step (Eq 30-31) from the sorted state src to dst (same order).
 void launch_verlet(int n, const uint32_t *keys_in, State src, const float4 *ace,
                    const CaseConst *cc, CaseDyn *dyn, int nbits, State dst, uint32_t *keys_out,
@@ -49,7 +55,7 @@ void launch_export(int n, const uint32_t *keys, State st, const CaseConst *cc, i
 void launch_import_raw(int n, const int32_t *cell, const float4 *posc, const float4 *velrho,
                        const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
                        const CaseConst *cc, int nbits, State st, uint32_t *keys, int dst0,
-                       cudaStream_t s);
+                       const float *ghost, cudaStream_t s);
 void launch_scatter_forces(int n, const uint16_t *cid, const uint32_t *id, int slot,
                            uint32_t id_base, const int *nvalid, const float4 *ace,
                            const float *mu, float *acc_out, float *drho_out, float *mu_out,

@@ -40,7 +40,8 @@ class CaseParams(C.Structure):
                 ("cell_mode", C.c_int32), ("ddt_mode", C.c_int32),
                 ("clamp_boundary_rho", C.c_int32), ("max_out", C.c_int32),
                 ("integrator", C.c_int32), ("verlet_steps", C.c_int32),
-                ("visc_mode", C.c_int32), ("pad_", C.c_int32), ("nu0", C.c_double)]
+                ("visc_mode", C.c_int32), ("boundary_mode", C.c_int32), ("nu0", C.c_double),
+                ("mdbc_slip", C.c_int32), ("pad2_", C.c_int32)]
 
 
 class Motion(C.Structure):
@@ -51,7 +52,7 @@ class Motion(C.Structure):
 class Particles(C.Structure):
     _fields_ = [("n", C.c_int64), ("pos", C.c_void_p), ("vel", C.c_void_p),
                 ("rho", C.c_void_p), ("type", C.c_void_p), ("motion_group", C.c_void_p),
-                ("motions", C.c_void_p), ("n_motions", C.c_int32)]
+                ("motions", C.c_void_p), ("n_motions", C.c_int32), ("ghost", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -105,6 +106,7 @@ def load(build_if_missing: bool = True):
                                           C.POINTER(vp)]),
         "sph_eval_forces": (C.c_int, [vp, i32, vp, vp, vp, dp, C.POINTER(i64)]),
         "sph_eval_sps": (C.c_int, [vp, i32, vp]),
+        "sph_eval_boundary": (C.c_int, [vp, i32, vp, vp]),
         "sph_get_order": (C.c_int, [vp, i32, vp, vp, C.POINTER(i64)]),
         "sph_pair_stats": (C.c_int, [vp, i32, vp, vp]),
         "sph_pool_create": (C.c_int, [i64, i64, i32, vp, ALLOC_FN, FREE_FN, vp, C.POINTER(vp)]),
@@ -151,6 +153,8 @@ def make_params(p: dict) -> CaseParams:
     c.verlet_steps = int(p.get("verlet_steps", 40))
     c.visc_mode = int(p.get("visc_mode", 0))
     c.nu0 = float(p.get("nu0", 1e-6))
+    c.boundary_mode = int(p.get("boundary_mode", 0))
+    c.mdbc_slip = int(p.get("mdbc_slip", 0))
     return c
 
 
@@ -164,6 +168,8 @@ class HostParticles:
         self.rho = np.ascontiguousarray(case.rho, np.float32).reshape(n)
         self.type = np.ascontiguousarray(case.ptype, np.uint8).reshape(n)
         self.group = np.ascontiguousarray(case.group, np.int32).reshape(n)
+        g = getattr(case, "ghost", None)
+        self.ghost = None if g is None else np.ascontiguousarray(g, np.float32).reshape(n, 3)
         self.motions = (Motion * max(1, len(case.motions)))()
         for i, m in enumerate(case.motions):
             self.motions[i].axis = D3(*map(float, m["axis"]))
@@ -175,12 +181,14 @@ class HostParticles:
         self.struct = Particles(n, self.pos.ctypes.data, self.vel.ctypes.data,
                                 self.rho.ctypes.data, self.type.ctypes.data,
                                 self.group.ctypes.data, C.addressof(self.motions),
-                                len(case.motions))
+                                len(case.motions),
+                                None if self.ghost is None else self.ghost.ctypes.data)
 
     def _pin(self):
         import torch
         self._pinned = []
-        for name in ("pos", "vel", "rho", "type", "group"):
+        for name in ("pos", "vel", "rho", "type", "group") + (("ghost",) if self.ghost is not None
+                                                               else ()):
             a = getattr(self, name)
             t = torch.from_numpy(a).pin_memory()
             self._pinned.append(t)
@@ -339,6 +347,14 @@ class Engine:
         tau = np.zeros((self._n(icase), 6), np.float32)
         check(self.lib.sph_eval_sps(self.h, icase, tau.ctypes.data))
         return tau
+
+    def eval_boundary(self, icase=0):
+        """mDBC boundary values (Eq 38-39) on the current state: (vel [n,3], rho [n])."""
+        n = self._n(icase)
+        vel = np.zeros((n, 3), np.float32)
+        rho = np.zeros(n, np.float32)
+        check(self.lib.sph_eval_boundary(self.h, icase, vel.ctypes.data, rho.ctypes.data))
+        return vel, rho
 
     def order(self, icase=0):
         n = self._n(icase)
