@@ -42,6 +42,17 @@ F_PAIR_FF_HYD = F_PAIR_FF + 11
 # the stored tau (33) and the strain pass of Eq 24-25 (33); Eq 21 drops (4)
 F_PAIR_VISC = 9 + 33 + 33 - 4
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# Algorithmic HBM bytes per particle of one Symplectic step: two sorts of
+# three 8-bit passes (20 each), two reorders (90), two cell tables (~7),
+# predictor (91), corrector (115), two interactions (52)
+STEP_BYTES_PER_PARTICLE = 2 * 3 * 20 + 2 * 90 + 2 * 7 + 91 + 115 + 2 * 52
+
+
+def hbm_peak_gbs():
+    try:
+        return float(json.load(open(MEASURED_PEAKS))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0  # fallback figure for a GB300 copy
 
 
 def fp32_peak_tflops(mhz=SM_MAX_MHZ):
@@ -441,6 +452,15 @@ def main():
                 "pi_ms_per_launch": 1000 * pi_avg_s,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal max clock)"}
 
+    # whole-step bound T = interaction FLOPs / FP32 peak + step bytes / HBM peak
+    # (default Symplectic step: two interactions); reported against ms_per_step
+    step_bound = None
+    if args.integrator == "symplectic" and args.boundary_mode == 0 and args.visc_mode == 0:
+        t_alu = flops / args.steps / (peak * 1e12)
+        t_hbm = STEP_BYTES_PER_PARTICLE * n_particles / (hbm_peak_gbs() * 1e9)
+        step_bound = {"ms": 1000 * (t_alu + t_hbm), "alu_ms": 1000 * t_alu,
+                      "hbm_ms": 1000 * t_hbm,
+                      "frac": 1000 * (t_alu + t_hbm) / (ms_max / args.steps)}
     out = {"metric": "particle_interactions_per_s", "value": value, "unit": "interactions/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -461,7 +481,8 @@ def main():
                             (n_particles * 177 / 1e6),
                       "parallelism": "replicas" if world > 1 else "single"},
            "steps_per_s": steps_per_s, "interactions_per_step": pairs / args.steps,
-           "gpu_launches": tm["kernel_launches"], "roofline": roofline, "clocks": clk}
+           "gpu_launches": tm["kernel_launches"], "roofline": roofline, "clocks": clk,
+           "step_bound": step_bound}
 
     if rank == 0 and not args.no_e2e:
         # end to end through the public API from pinned host memory: create
