@@ -461,7 +461,7 @@ void enqueue_step_verlet(sph_engine e, cudaEvent_t *ev) {
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
   launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
                  X.ghost, Y,
-                 e->press, e->dconst, e->nbits, s);
+                 e->press, e->dconst, e->ddyn, e->nbits, s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
   if (e->mdbc)
     launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
@@ -490,8 +490,7 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
   launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
                  X.ghost, Y,
-                 e->press,
-                 e->dconst, e->nbits, s);
+                 e->press, e->dconst, e->ddyn, e->nbits, s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
   if (e->mdbc)  // boundary values of Eq 38-39 on state n
     launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
@@ -509,8 +508,7 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
   radix_sort(e->keysC, e->keysD, e->perm2, nl, e->nbits, e->sort_tmp, s);
   launch_reorder(nl, e->perm2, e->keysD, Z.posc, Z.velrho, Y.id, Y.cid, Y.code, nullptr,
                  Y.ghost, X,
-                 e->press,
-                 e->dconst, e->nbits, s);
+                 e->press, e->dconst, e->ddyn, e->nbits, s);
   launch_cells(nl, e->keysD, e->cstart, e->cells_hw, e->nbits, e->nvalid + 1, e->cells_tmp, s);
   if (e->mdbc)  // boundary values of Eq 38-39 on state n+1/2
     launch_mdbc(e->margin, nl, e->nvalid + 1, e->keysD, X, e->press, e->cstart, e->nbits,
@@ -534,7 +532,7 @@ void enqueue_nl(sph_engine e) {
   launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
                  X.ghost, Y,
                  e->press,
-                 e->dconst, e->nbits, e->s);
+                 e->dconst, e->ddyn, e->nbits, e->s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, e->s);
 }
 

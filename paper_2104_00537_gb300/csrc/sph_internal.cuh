@@ -68,11 +68,16 @@ struct CaseDyn {
   unsigned int dtmin_bits;  // float bits of min_a min(dt_f, dt_cv) (positive floats order as ints)
   unsigned int flags;       // kFlag*
   int n_out;
-  int pad_;
+  unsigned int v2max_bits;  // float bits of max |v|^2 over in-domain particles at the last reorder
   double mot[kMaxMotions][4];  // displacement and velocity at t+dt/2 and t+dt
 };
 
 constexpr unsigned kFlagNaN = 1u, kFlagDtMin = 2u, kFlagQuota = 4u;
+// neighbour-list path: a target had more than kListCap list entries; a
+// half-step displacement exceeded half the list's skin
+constexpr unsigned kFlagListFull = 8u, kFlagSkin = 16u;
+constexpr int kListCap = 384;          // list entries per target
+constexpr int kListMaxParticles = 1 << 25;  // entry = index (25 bits) | row (6 bits)
 // Readable entries of posc/velrho/press past the last particle, so that a
 // warp may test 32 candidates at a time without per-candidate bounds checks.
 constexpr int64_t kReadPad = 1024;

@@ -135,27 +135,41 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
                           const float4 *__restrict__ vrprev_src,
                           const float4 *__restrict__ ghost_src, State dst,
                           float *__restrict__ press, const CaseConst *__restrict__ cc,
-                          int nbits) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t p = perm[i];
-  float4 pc = posc_src[p];
-  float4 vr = velrho_src[p];
-  uint16_t cidx = cid_src[p];
-  const CaseConst &C = cc[cidx];
-  const uint32_t k = keys_sorted[i];
-  if (k < key_out(nbits)) {
-    const uint32_t lin = key_cell(k, nbits) - C.cellbase;
-    pc.w = (float)(lin % (uint32_t)C.nx);
+                          CaseDyn *__restrict__ dyn, int nbits) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int cidx = -1;
+  unsigned v2 = 0u;
+  if (i < n) {
+    uint32_t p = perm[i];
+    float4 pc = posc_src[p];
+    float4 vr = velrho_src[p];
+    cidx = cid_src[p];
+    const CaseConst &C = cc[cidx];
+    const uint32_t k = keys_sorted[i];
+    if (k < key_out(nbits)) {
+      const uint32_t lin = key_cell(k, nbits) - C.cellbase;
+      pc.w = (float)(lin % (uint32_t)C.nx);
+      v2 = __float_as_uint(fmaf(vr.x, vr.x, fmaf(vr.y, vr.y, vr.z * vr.z)));
+    }
+    dst.posc[i] = pc;
+    dst.velrho[i] = vr;
+    dst.id[i] = id_src[p];
+    dst.cid[i] = (uint16_t)cidx;
+    dst.code[i] = code_src[p];
+    if (vrprev_src) dst.vrprev[i] = vrprev_src[p];
+    if (ghost_src) dst.ghost[i] = ghost_src[p];
+    press[i] = tait_pressure(C, vr.w) / vr.w;
   }
-  dst.posc[i] = pc;
-  dst.velrho[i] = vr;
-  dst.id[i] = id_src[p];
-  dst.cid[i] = cidx;
-  dst.code[i] = code_src[p];
-  if (vrprev_src) dst.vrprev[i] = vrprev_src[p];
-  if (ghost_src) dst.ghost[i] = ghost_src[p];
-  press[i] = tait_pressure(C, vr.w) / vr.w;
+  // max |v|^2 per case (for the neighbour list's skin): one atomic per warp
+  // when the warp holds one case
+  const unsigned full = 0xffffffffu;
+  const int c0 = __shfl_sync(full, cidx, 0);
+  if (__all_sync(full, cidx == c0)) {
+    const unsigned m = __reduce_max_sync(full, v2);
+    if ((threadIdx.x & 31) == 0 && c0 >= 0 && m) atomicMax(&dyn[c0].v2max_bits, m);
+  } else if (cidx >= 0 && v2) {
+    atomicMax(&dyn[cidx].v2max_bits, v2);
+  }
 }
 
 // ---- cell start table --------------------------------------------------------
@@ -1128,6 +1142,7 @@ __global__ void k_end_step(int ncases, const CaseConst *__restrict__ cc,
     D.t += D.dt;
     D.step += 1;
   }
+  D.v2max_bits = 0u;
 }
 
 // ---- Symplectic predictor / corrector ------------------------------------------
@@ -1576,11 +1591,11 @@ void launch_upload(int n, const double *pos, const float *vel, const float *rho,
 void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
                     const float4 *posc, const float4 *velrho, const uint32_t *id,
                     const uint16_t *cid, const uint8_t *code, const float4 *vrprev,
-                    const float4 *ghost, State dst, float *press, const CaseConst *cc, int nbits,
-                    cudaStream_t s) {
+                    const float4 *ghost, State dst, float *press, const CaseConst *cc,
+                    CaseDyn *dyn, int nbits, cudaStream_t s) {
   if (n > 0)
     k_reorder<<<nblk(n, 256), 256, 0, s>>>(n, perm, keys_sorted, posc, velrho, id, cid, code,
-                                           vrprev, ghost, dst, press, cc, nbits);
+                                           vrprev, ghost, dst, press, cc, dyn, nbits);
 }
 
 size_t cells_temp_words(int64_t cap_cells) {

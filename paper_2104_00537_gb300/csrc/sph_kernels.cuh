@@ -11,8 +11,8 @@ void launch_upload(int n, const double *pos, const float *vel, const float *rho,
 void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
                     const float4 *posc, const float4 *velrho, const uint32_t *id,
                     const uint16_t *cid, const uint8_t *code, const float4 *vrprev,
-                    const float4 *ghost, State dst, float *press, const CaseConst *cc, int nbits,
-                    cudaStream_t s);
+                    const float4 *ghost, State dst, float *press, const CaseConst *cc,
+                    CaseDyn *dyn, int nbits, cudaStream_t s);
 // Words of temporary storage launch_cells needs for cap_cells cells.
 size_t cells_temp_words(int64_t cap_cells);
 // Cell start table of the sorted keys (and nvalid); returns kernels launched.
