@@ -59,13 +59,13 @@ def fp32_peak_tflops(mhz=SM_MAX_MHZ):
     return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
-def measured_traffic(cell_mode, workload_name):
-    """DRAM bytes per interaction launch from the committed ncu capture, or None
-    when the capture does not match (other workload / cell size, or the kernel
-    source changed since the counters were taken)."""
+def measured_traffic(cell_mode, workload_name, kernel="k_interact"):
+    """DRAM bytes per interaction launch from the committed ncu capture of
+    `kernel`, or None when the capture does not match (other workload / cell
+    size, or the kernel source changed since the counters were taken)."""
     import hashlib
     try:
-        d = json.load(open(os.path.join(ROOT, "profiles", "k_interact_traffic.json")))
+        d = json.load(open(os.path.join(ROOT, "profiles", kernel + "_traffic.json")))
         src = open(os.path.join(ROOT, d["source"]), "rb").read()
     except (OSError, ValueError, KeyError):
         return None
@@ -350,7 +350,7 @@ def main():
     ap.add_argument("--workload", default="dam_break")
     ap.add_argument("--cell-mode", type=int, default=1)
     ap.add_argument("--ddt-mode", type=int, default=1, choices=[0, 1, 2])
-    ap.add_argument("--pi-variant", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--pi-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3])
     ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "verlet"])
     ap.add_argument("--visc-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--nu0", type=float, default=1e-6)
@@ -395,6 +395,13 @@ def main():
             sph.Engine.create(cs[0], stream=stream)
     eng.set_options(pi_variant=args.pi_variant)
     n_particles = sum(c.n for c in cs)
+    # the engine runs the per-step list (3) where it supports it, unless told otherwise
+    list_ok = (args.integrator == "symplectic" and args.ddt_mode <= 1 and args.visc_mode == 0
+               and args.boundary_mode == 0 and n_particles < (1 << 25))
+    eff_var = args.pi_variant if args.pi_variant in (0, 1, 2) else (3 if list_ok else 0)
+    if eff_var == 3 and not list_ok:
+        eff_var = 0
+    kernel = "k_interact_list" if eff_var == 3 else "k_interact"
 
     # warm-up
     eng.step(args.warmup)
@@ -442,12 +449,11 @@ def main():
     pi_avg_s = tm["pi_ms"] / 1000.0 / launches
     achieved = flops / launches / pi_avg_s / 1e12
     peak = fp32_peak_tflops()
-    roofline = {"bound": "alu", "kernel": "k_interact", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": measured_traffic(args.cell_mode, args.workload)
-                if (args.ddt_mode, args.pi_variant, args.integrator, args.visc_mode,
-                    args.boundary_mode) == (1, 0, "symplectic", 0, 0)
-                else None,
+                "traffic": measured_traffic(args.cell_mode, args.workload, kernel)
+                if (args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) ==
+                (1, "symplectic", 0, 0) and eff_var in (0, 3) else None,
                 "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
                 "pi_ms_per_launch": 1000 * pi_avg_s,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal max clock)"}
@@ -476,7 +482,7 @@ def main():
                       "integrator": {"symplectic": "Symplectic, Eq 33-34 (2 PI per step)",
                                      "verlet": "Verlet, Eq 30-31, N_S = 40 (1 PI per step)"}[
                           args.integrator],
-                      "pi_variant": args.pi_variant,
+                      "pi_variant": eff_var,
                       "l2": "state (%.0f MB) larger than L2 (129 MB), no flush" %
                             (n_particles * 177 / 1e6),
                       "parallelism": "replicas" if world > 1 else "single"},

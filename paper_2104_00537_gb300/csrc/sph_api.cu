@@ -182,6 +182,12 @@ struct sph_engine_t {
   bool ext = false;    // a case uses Eq 19-20 diffusion or laminar + SPS viscosity
   bool sps = false;    // a case uses laminar + SPS viscosity (tau buffers below)
   bool mdbc = false;   // a case uses the modified dynamic boundary condition
+  // per-step neighbour list (pi_variant 3): list_cap chunk records per target
+  bool list_ok = false;
+  int list_cap = 0;
+  int64_t list_ld = 0;
+  uint2 *nlist = nullptr;
+  uint16_t *ncount = nullptr;
   float4 *tau4 = nullptr;  // (tau/rho) of Eq 25 in sorted order: xx, yy, zz, xy
   float2 *tau2 = nullptr;  //   xz, yz
   bool pool = false;
@@ -280,6 +286,11 @@ int allocate(sph_engine e) {
   e->cstart = (uint32_t *)A(4 * (2 * e->cap_cells + 2));
   e->cells_tmp = (uint32_t *)A(4 * cells_temp_words(e->cap_cells));
   e->press = (float *)A(4 * NP);
+  if (e->list_ok) {
+    e->list_ld = N;
+    e->nlist = (uint2 *)A(sizeof(uint2) * (size_t)e->list_cap * (size_t)N);
+    e->ncount = (uint16_t *)A(2 * N);
+  }
   if (e->sps || e->pool) {
     e->tau4 = (float4 *)A(16 * N);
     e->tau2 = (float2 *)A(8 * N);
@@ -432,6 +443,21 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     e->sps = e->sps || params[c].visc_mode == 1;
     e->mdbc = e->mdbc || params[c].boundary_mode == 1;
   }
+  // the per-step list serves the Symplectic scheme with the default physics
+  e->list_ok = e->integrator == 0 && !e->ext && !e->mdbc && np < kListMaxParticles;
+  if (e->list_ok) {
+    // chunk records per target: two parts of (2M+1)^2 rows, each row's pruned
+    // range (2M+1 cells of ~1.3 x (cs/dp)^3 particles) in chunks of 32
+    double cap = 32.0;
+    for (int c = 0; c < ncases; c++) {
+      const int M = params[c].cell_mode + 1;
+      const double ppc = 1.3 * std::pow(2.0 * params[c].h / M / params[c].dp, 3.0);
+      const double chunks = std::ceil((2 * M + 1) * ppc / 32.0);
+      cap = std::max(cap, 2.0 * (2 * M + 1) * (2 * M + 1) * chunks);
+    }
+    e->list_cap = std::min(4096, ((int)std::ceil(cap) + 31) / 32 * 32);
+    e->opt.pi_variant = 3;
+  }
   rc = allocate(e);
   int64_t cell0 = 0, p0 = 0;
   for (int c = 0; c < ncases && rc == SPH_OK; c++) {
@@ -476,10 +502,44 @@ void enqueue_step_verlet(sph_engine e, cudaEvent_t *ev) {
   launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
 }
 
+// One Symplectic step with the per-step neighbour list: NL on state n (Y),
+// PI that also writes the list, Δt, half step in Y's order and cells (Z),
+// PI over the list, full step into X.  ev: 4 events around the two PI launches.
+void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
+  const int n = (int)e->n_phys;
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &X = e->S[0], &Y = e->S[1], &Z = e->S[2];
+  cudaStream_t s = e->s;
+  radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
+                 X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, s);
+  launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
+  if (ev) cudaEventRecord(ev[0], s);
+  launch_interact_build(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
+                        e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
+                        e->list_cap, e->ncount, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
+  launch_predictor_list(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
+                        e->keysC, e->press, s);
+  if (ev) cudaEventRecord(ev[2], s);
+  launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
+                       e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
+                       e->list_cap, e->ncount, s);
+  if (ev) cudaEventRecord(ev[3], s);
+  launch_corrector_list(nl, e->keysB, e->keysC, Y, Z.velrho, e->ace, e->dconst, e->ddyn,
+                        e->nbits, X, e->keysA, s);
+  launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
+}
+
 // One Symplectic step (all cases).  ev: 4 events around the two PI launches.
 void enqueue_step(sph_engine e, cudaEvent_t *ev) {
   if (e->integrator == 1) {
     enqueue_step_verlet(e, ev);
+    return;
+  }
+  if (e->opt.pi_variant == 3 && e->list_ok) {
+    enqueue_step_list(e, ev);
     return;
   }
   const int n = (int)e->n_phys;
@@ -547,6 +607,13 @@ int check_flags(sph_engine e) {
       return fail(SPH_ERR_UNSTABLE, "case " + std::to_string(c) + ": NaN/Inf in the interaction");
     if (d[c].flags & kFlagDtMin)
       return fail(SPH_ERR_UNSTABLE, "case " + std::to_string(c) + ": dt below dt_min");
+    if (d[c].flags & kFlagListFull)
+      return fail(SPH_ERR_STATE, "case " + std::to_string(c) +
+                                     ": a particle has more neighbour-list candidates than the "
+                                     "list holds; use pi_variant 0");
+    if (d[c].flags & kFlagSkin)
+      return fail(SPH_ERR_UNSTABLE, "case " + std::to_string(c) +
+                                        ": a half-step displacement exceeded the list's skin");
     int mo = e->hconst[c].max_out;
     if (mo >= 0 && d[c].n_out > mo)
       return fail(SPH_ERR_DOMAIN, "case " + std::to_string(c) + ": " +
@@ -585,9 +652,15 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
   if (!e || !opt) return fail(SPH_ERR_ARG, "null argument");
   if (opt->pi_block != 0 && opt->pi_block != 128)
     return fail(SPH_ERR_ARG, "pi_block must be 0 (default) or 128");
-  if (opt->pi_variant < 0 || opt->pi_variant > 2)
-    return fail(SPH_ERR_ARG, "pi_variant must be 0 (compacted), 1 (inline) or 2 (queued)");
+  if (opt->pi_variant < -1 || opt->pi_variant > 3)
+    return fail(SPH_ERR_ARG,
+                "pi_variant must be -1 (engine default), 0 (compacted), 1 (inline), 2 (queued) "
+                "or 3 (per-step neighbour list)");
   e->opt = *opt;
+  // -1: the per-step list where the engine supports it, else the compacted loop;
+  // 3 without list support falls back to the compacted loop too
+  if (e->opt.pi_variant == -1 || (e->opt.pi_variant == 3 && !e->list_ok))
+    e->opt.pi_variant = e->list_ok ? 3 : 0;
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
   e->gexec = nullptr;
   return SPH_OK;
@@ -632,11 +705,14 @@ int sph_step(sph_engine e, int64_t nsteps) {
   }
   // per Symplectic step: 2 sorts (3 kernels per 8-bit pass), 2 reorders, 2
   // cell tables (4 kernels), 2 interactions, dt, predictor, corrector, end of
-  // step; per Verlet step: one sort, reorder, cell table and interaction, dt,
-  // update, end of step
+  // step; with the per-step list: one sort, reorder, cell table, the list, 2
+  // interactions, dt, predictor, corrector, end; per Verlet step: one sort,
+  // reorder, cell table and interaction, dt, update, end of step
   const int64_t passes = std::max(1, (e->nbits + 7) / 8);
   const int64_t pis = e->integrator == 1 ? 1 : 2;
+  const bool listed = e->integrator == 0 && e->opt.pi_variant == 3 && e->list_ok;
   const int64_t per_step = (e->integrator == 1 ? 3 * passes + 1 + 4 + 1 + 3
+                            : listed           ? 3 * passes + 1 + 4 + 2 + 4
                                                : 6 * passes + 2 + 8 + 2 + 4) +
                            (e->sps ? pis : 0) +  // strain pass before each interaction
                            (e->mdbc ? pis : 0);  // ghost-node pass before each interaction

@@ -447,6 +447,17 @@ __device__ __forceinline__ void finish_target(const CaseConst &C, int i, int n, 
   reduce_case(i < n ? cidx : -1, has, npairs, nfb, nbf, dtbits, bad, dyn);
 }
 
+// Skin of the list built on state n: dt |v|max x 1.25, with dt bounded by
+// Eq 35 (dt <= C_CFL h / cs0 since dt_cv <= h / cs0) or the fixed step, plus
+// 1e-3 h; the 25 % covers the change of a wall's imposed speed over dt / 2.
+__device__ __forceinline__ float list_skin(const CaseConst &C, const CaseDyn &D) {
+  const double dtb = C.dt_fixed > 0.0 ? C.dt_fixed : C.cfl * C.h_d / C.cs0_d;
+  const double vmax = sqrt((double)__uint_as_float(D.v2max_bits));
+  return (float)(1.25 * dtb * vmax + 1e-3 * C.h_d);
+}
+
+constexpr uint32_t kListIndexMask = (1u << 25) - 1u;
+
 // One thread per particle a in sorted order (all fluid targets first, then
 // boundary targets, so warps rarely mix the two).  The (2M+1)^2 rows of
 // neighbour cells (fixed dy, dz) are visited in lock-step by the warp; in a
@@ -462,7 +473,11 @@ __device__ __forceinline__ void finish_target(const CaseConst &C, int i, int n, 
 // EXT (VARIANT 0 only): 1 adds the Eq 19-20 density diffusion, 2 also the
 // laminar + SPS viscosity of Eq 23-27 (tau4/tau2 from k_strain), per case;
 // warps without such cases still take the default pair loop.
-template <int M, int VARIANT, int EXT = 0>
+//
+// LIST (VARIANT 0, EXT 0): also writes the target's per-step neighbour list:
+// for every tested chunk with a candidate within 2h + skin, one record
+// (first index | row offset, mask of those candidates) to list[i cap + c].
+template <int M, int VARIANT, int EXT = 0, bool LIST = false>
 __global__ void __launch_bounds__(128, EXT == 2 ? 6 : 0)
 k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
            const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
@@ -470,7 +485,9 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
            const uint32_t *__restrict__ cstart, uint32_t cap1, int nbits,
            const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
            float4 *__restrict__ ace, float *__restrict__ mu_out, int want_dt,
-           const float4 *__restrict__ tau4 = nullptr, const float2 *__restrict__ tau2 = nullptr) {
+           const float4 *__restrict__ tau4 = nullptr, const float2 *__restrict__ tau2 = nullptr,
+           uint2 *__restrict__ list = nullptr, int cap = 0,
+           uint16_t *__restrict__ count = nullptr) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -482,9 +499,16 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   const int gc = (int)key_cell(key, nbits);
   const int nx = C.nx, nxy = C.nx * C.ny;
   const float cs = C.csf, ics = C.inv_csf, r2max = C.r2max, eta2 = C.eta2, hih = C.half_inv_h;
-  const float r2prune = r2max * 1.0001f;  // conservative: pruning never drops a pair
   // 0 < r2 < r2max as one unsigned compare (r2 >= 0; +0 wraps to UINT_MAX)
   const unsigned r2max_u = __float_as_uint(r2max) - 1u;
+  float r2l = r2max;  // list radius^2: (2h + skin)^2 with LIST
+  if (LIST) {
+    const float R = sqrtf(r2max) + list_skin(C, dyn[cidx]);
+    r2l = R * R;
+  }
+  const unsigned r2l_u = __float_as_uint(r2l) - 1u;
+  const float r2prune = r2l * 1.0001f;  // conservative: pruning never drops a pair
+  int lcnt = 0;                          // LIST: records written
   const float4 pa = has ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float4 va = has ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
   const float Pa = has ? press[i] * va.w : 0.f;  // press holds P / rho
@@ -533,6 +557,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
       }
     }
     const float sy = fmaf(-(float)dy, cs, pa.y), sz = fmaf(-(float)dz, cs, pa.z);
+    const uint32_t rowbits = ((uint32_t)(dy + 3) << 25) | ((uint32_t)(dz + 3) << 28);
 #pragma unroll 1
     for (int part = 0; part < 2; part++) {  // fluid neighbours, then boundary neighbours
       const int lo = part ? loB : loF;
@@ -542,7 +567,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
 #pragma unroll 1
       for (int base = 0; base < maxlen; base += 32) {
         if (VARIANT == 0) {
-          unsigned m = 0u;
+          unsigned m = 0u, ml = 0u;
           const int nk = min(32, maxlen - base);
 #pragma unroll 8
           for (int k = 0; k < nk; k++) {
@@ -552,7 +577,12 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
               const float ry = sy - pb.y, rz = sz - pb.z;
               const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
               if (__float_as_uint(r2) - 1u < r2max_u) m |= 1u << k;
+              if (LIST && __float_as_uint(r2) - 1u < r2l_u) ml |= 1u << k;
             }
+          }
+          if (LIST && ml) {
+            if (lcnt < cap) list[(int64_t)i * cap + lcnt] = make_uint2((uint32_t)(lo + base) | rowbits, ml);
+            lcnt++;
           }
           if (part) A.cntb += __popc(m); else A.cnt += __popc(m);
           if (warp_plain) {  // fluid targets, Eq 18 or no diffusion
@@ -615,6 +645,10 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
     }
   }
 
+  if (LIST && i < n) {
+    count[i] = (uint16_t)min(lcnt, cap);
+    if (has && lcnt > cap) atomicOr(&dyn[cidx].flags, kFlagListFull);
+  }
   finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
 }
 
@@ -1171,30 +1205,14 @@ __device__ __forceinline__ uint32_t move_particle(uint32_t k, const float4 &p, c
   return key_make(C.cellbase + lin, boundary, nbits);
 }
 
-__global__ void k_predictor(int n, const uint32_t *__restrict__ keys_in, State src,
-                            const float4 *__restrict__ ace, const CaseConst *__restrict__ cc,
-                            CaseDyn *__restrict__ dyn, int nbits, float4 *__restrict__ posc_out,
-                            float4 *__restrict__ velrho_out, uint32_t *__restrict__ keys_out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t k = keys_in[i];
-  const float4 p = src.posc[i];
-  const float4 v = src.velrho[i];
-  if (k >= key_out(nbits)) {  // frozen or released: unchanged
-    posc_out[i] = p;
-    velrho_out[i] = v;
-    keys_out[i] = k;
-    return;
-  }
-  const int cidx = src.cid[i];
-  const uint8_t code = src.code[i];
-  const CaseConst &C = cc[cidx];
-  const CaseDyn &D = dyn[cidx];
+// Eq 33-34 half step of one particle: displacement dt/2 v^n (FP64) and
+// v, rho at n+1/2; boundary particles: density only (clamped), moving ones
+// displaced by Eq 37 at t + dt/2.
+__device__ __forceinline__ void predictor_core(const CaseConst &C, const CaseDyn &D,
+                                               uint8_t code, const float4 &v, const float4 &a,
+                                               double disp[3], float4 &vn) {
   const double hdt = 0.5 * D.dt;
   const float hdtf = (float)hdt;
-  const float4 a = ace[i];
-  double disp[3];
-  float4 vn;
   if (code == 0) {
     disp[0] = hdt * (double)v.x;
     disp[1] = hdt * (double)v.y;
@@ -1217,6 +1235,30 @@ __global__ void k_predictor(int n, const uint32_t *__restrict__ keys_in, State s
       vn = make_float4(v.x, v.y, v.z, rho);
     }
   }
+}
+
+__global__ void k_predictor(int n, const uint32_t *__restrict__ keys_in, State src,
+                            const float4 *__restrict__ ace, const CaseConst *__restrict__ cc,
+                            CaseDyn *__restrict__ dyn, int nbits, float4 *__restrict__ posc_out,
+                            float4 *__restrict__ velrho_out, uint32_t *__restrict__ keys_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys_in[i];
+  const float4 p = src.posc[i];
+  const float4 v = src.velrho[i];
+  if (k >= key_out(nbits)) {  // frozen or released: unchanged
+    posc_out[i] = p;
+    velrho_out[i] = v;
+    keys_out[i] = k;
+    return;
+  }
+  const int cidx = src.cid[i];
+  const uint8_t code = src.code[i];
+  const CaseConst &C = cc[cidx];
+  const CaseDyn &D = dyn[cidx];
+  double disp[3];
+  float4 vn;
+  predictor_core(C, D, code, v, ace[i], disp, vn);
   float4 pn;
   bool left;
   uint32_t kn = move_particle(k, p, disp, C, code != 0, nbits, pn, left);
@@ -1234,36 +1276,20 @@ __global__ void k_predictor(int n, const uint32_t *__restrict__ keys_in, State s
   keys_out[i] = kn;
 }
 
-__global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
-                            const uint32_t *__restrict__ keys_half,
-                            const uint32_t *__restrict__ keys_n, State sn, State x,
-                            const float4 *__restrict__ ace, const CaseConst *__restrict__ cc,
-                            CaseDyn *__restrict__ dyn, int nbits,
-                            uint32_t *__restrict__ keys_next) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t p = perm2[i];
-  const uint32_t kh = keys_half[i];
-  if (kh >= key_out(nbits)) {  // frozen (already in x) or released
-    keys_next[i] = kh;
-    return;
-  }
-  const float4 pn = sn.posc[p];
-  const float4 vn = sn.velrho[p];
-  const uint32_t k = keys_n[p];
-  const int cidx = x.cid[i];
-  const uint8_t code = x.code[i];
-  const CaseConst &C = cc[cidx];
-  const CaseDyn &D = dyn[cidx];
+// Eq 33-34 full step of one particle from state n (key k, pn, vn), the
+// half-step density rhoh and F, R at n+1/2 (a): the new position (cell +
+// offset, FP64 displacement), velocity and density; returns the new key.
+__device__ __forceinline__ uint32_t corrector_core(const CaseConst &C, const CaseDyn &D,
+                                                   uint8_t code, uint32_t k, const float4 &pn,
+                                                   const float4 &vn, float rhoh, const float4 &a,
+                                                   int nbits, int cidx, CaseDyn *dyn,
+                                                   float4 &pnew, float4 &vnew) {
   const double dt = D.dt;
   const float dtf = (float)dt;
-  const float4 a = ace[i];
-  const float rhoh = x.velrho[i].w;
   // Eq 34: rho^{n+1} = rho^n (2 - eps) / (2 + eps), eps = -(R / rho^{n+1/2}) dt
   const float eps = -(a.w / rhoh) * dtf;
   float rho = vn.w * (2.f - eps) / (2.f + eps);
   double disp[3];
-  float4 vnew;
   if (code == 0) {
     vnew = make_float4(fmaf(dtf, a.x, vn.x), fmaf(dtf, a.y, vn.y), fmaf(dtf, a.z, vn.z), rho);
     // r^{n+1} = r^n + dt (v^{n+1} + v^n) / 2: the FP32 sum of two FP32
@@ -1288,13 +1314,211 @@ __global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
       vnew = make_float4(vn.x, vn.y, vn.z, rho);
     }
   }
-  float4 pnew;
   bool left;
-  uint32_t kn = move_particle(k, pn, disp, C, code != 0, nbits, pnew, left);
+  const uint32_t kn = move_particle(k, pn, disp, C, code != 0, nbits, pnew, left);
   if (left) atomicAdd(&dyn[cidx].n_out, 1);  // frozen at state n+1
+  return kn;
+}
+
+__global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
+                            const uint32_t *__restrict__ keys_half,
+                            const uint32_t *__restrict__ keys_n, State sn, State x,
+                            const float4 *__restrict__ ace, const CaseConst *__restrict__ cc,
+                            CaseDyn *__restrict__ dyn, int nbits,
+                            uint32_t *__restrict__ keys_next) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t p = perm2[i];
+  const uint32_t kh = keys_half[i];
+  if (kh >= key_out(nbits)) {  // frozen (already in x) or released
+    keys_next[i] = kh;
+    return;
+  }
+  const float4 pn = sn.posc[p];
+  const float4 vn = sn.velrho[p];
+  const uint32_t k = keys_n[p];
+  const int cidx = x.cid[i];
+  const uint8_t code = x.code[i];
+  const CaseConst &C = cc[cidx];
+  const CaseDyn &D = dyn[cidx];
+  float4 pnew, vnew;
+  const uint32_t kn = corrector_core(C, D, code, k, pn, vn, x.velrho[i].w, ace[i], nbits, cidx,
+                                     dyn, pnew, vnew);
   x.posc[i] = pnew;
   x.velrho[i] = vnew;
   keys_next[i] = kn;
+}
+
+// ---- per-step neighbour list (pi_variant 3) ---------------------------------------
+//
+// The Symplectic step evaluates the interaction on state n and on state n+1/2.
+// Instead of sorting again for n+1/2, the candidate test runs once per step,
+// on state n, with radius 2h + skin, and writes every candidate that passes
+// into a per-target list (entry = index | row offset); both evaluations then
+// walk the list and keep the pairs with 0 < r^2 < (2h)^2 at their own state.
+// The half-step state keeps the cells of state n (offsets may leave [0, cs)
+// by a half-step displacement), so relative positions stay cell + offset in
+// FP32.  The skin covers twice the largest half-step displacement, which the
+// predictor checks (kFlagSkin).  The pair set of each evaluation is the same
+// as with a fresh neighbour list; only the order of the sums differs.
+
+
+// The interaction over a target's list (state n or n+1/2, same order and
+// cells): the pair terms of k_interact for the entries inside 2h.
+__global__ void __launch_bounds__(128)
+k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
+                const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
+                const float *__restrict__ press, const uint16_t *__restrict__ cid,
+                const uint32_t *__restrict__ cstart, uint32_t cap1, int nbits,
+                const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
+                float4 *__restrict__ ace, int want_dt, const uint2 *__restrict__ list,
+                int cap, const uint16_t *__restrict__ count) {
+  const unsigned full = 0xffffffffu;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvalid = *nvalid_p;
+  const uint32_t key = i < nvalid ? keys[i] : key_out(nbits);
+  const bool has = key < key_out(nbits);  // not frozen at this state
+  const int cidx = i < n ? (int)cid[i] : 0;
+  const CaseConst &C = cc[cidx];
+  const bool afluid = has && !key_boundary(key, nbits);
+  const float cs = C.csf, eta2 = C.eta2, hih = C.half_inv_h;
+  const unsigned r2max_u = __float_as_uint(C.r2max) - 1u;
+  const float4 pa = has ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 va = has ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+  const float Pa = has ? press[i] * va.w : 0.f;
+  const float kv = C.kvisc * va.w;
+  const bool ddt_on = C.ddt != 0;
+  const int jb = (int)cstart[cap1 - 1];  // first boundary particle of the key order
+  const int nrec = has ? (int)count[i] : 0;
+  const bool warp_fluid = __all_sync(full, afluid || !has);
+  Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
+  const uint2 *__restrict__ mine = list + (int64_t)i * cap;
+  // one candidate per lane per iteration, records taken in order: the warp
+  // waits only for its lane with the most candidates in total
+  int r = 0;
+  unsigned cm = 0u;
+  int cbase = 0;
+  float sy = 0.f, sz = 0.f;
+#pragma unroll 1
+  for (;;) {
+    if (cm == 0u && r < nrec) {
+      const uint2 rec = mine[r++];
+      cbase = (int)(rec.x & kListIndexMask);
+      cm = rec.y;
+      sy = fmaf(-(float)((int)((rec.x >> 25) & 7u) - 3), cs, pa.y);
+      sz = fmaf(-(float)((int)(rec.x >> 28) - 3), cs, pa.z);
+    }
+    if (!__any_sync(full, cm != 0u)) break;
+    if (cm) {
+      const int k = 31 - __clz(cm);
+      cm ^= 1u << k;
+      const int j = cbase + k;
+      const float4 pb = posc[j];
+      const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+      const float ry = sy - pb.y, rz = sz - pb.z;
+      const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      if (__float_as_uint(r2) - 1u < r2max_u) {
+        const float4 vb = velrho[j];
+        const bool bfluid = j < jb;
+        if (warp_fluid || afluid) {
+          pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt_on && bfluid, A);
+          if (bfluid) A.cnt++; else A.cntb++;
+        } else {
+          pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
+          A.cnt++;
+        }
+      }
+    }
+  }
+  finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, nullptr, dyn);
+}
+
+// Half step for the list path: state n+1/2 in the same order and the same
+// cells as state n (Eq 33-34 as k_predictor); a particle that leaves the
+// domain is frozen at state n and moved out of every list's reach.
+__global__ void k_predictor_list(int n, const uint32_t *__restrict__ keys_in, State src,
+                                 const float4 *__restrict__ ace,
+                                 const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
+                                 int nbits, float4 *__restrict__ posc_out,
+                                 float4 *__restrict__ velrho_out, uint32_t *__restrict__ keys_out,
+                                 float *__restrict__ press) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys_in[i];
+  const float4 p = src.posc[i];
+  const float4 v = src.velrho[i];
+  const int cidx = src.cid[i];
+  const CaseConst &C = cc[cidx];
+  if (k >= key_out(nbits)) {
+    posc_out[i] = p;
+    velrho_out[i] = v;
+    keys_out[i] = k;
+    return;
+  }
+  const uint8_t code = src.code[i];
+  const CaseDyn &D = dyn[cidx];
+  double disp[3];
+  float4 vn;
+  predictor_core(C, D, code, v, ace[i], disp, vn);
+  const double hs = 0.5 * (double)list_skin(C, D);
+  if (disp[0] * disp[0] + disp[1] * disp[1] + disp[2] * disp[2] > hs * hs)
+    atomicOr(&dyn[cidx].flags, kFlagSkin);
+  float4 ptmp;
+  bool left;
+  (void)move_particle(k, p, disp, C, code != 0, nbits, ptmp, left);
+  if (left) {
+    posc_out[i] = make_float4(1e30f, 1e30f, 1e30f, p.w);
+    velrho_out[i] = v;
+    keys_out[i] = key_out(nbits);
+    atomicAdd(&dyn[cidx].n_out, 1);
+    return;
+  }
+  posc_out[i] = make_float4((float)((double)p.x + disp[0]), (float)((double)p.y + disp[1]),
+                            (float)((double)p.z + disp[2]), p.w);
+  velrho_out[i] = vn;
+  keys_out[i] = k;
+  press[i] = tait_pressure(C, vn.w) / vn.w;  // P/rho of Eq 28 at n+1/2
+}
+
+// Full step for the list path, in the order of state n (sn): writes state n+1
+// to x (id, case and code copied) and its keys.
+__global__ void k_corrector_list(int n, const uint32_t *__restrict__ keys_n,
+                                 const uint32_t *__restrict__ keys_half, State sn,
+                                 const float4 *__restrict__ velrho_half,
+                                 const float4 *__restrict__ ace, const CaseConst *__restrict__ cc,
+                                 CaseDyn *__restrict__ dyn, int nbits, State x,
+                                 uint32_t *__restrict__ keys_next) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys_n[i];
+  const float4 pn = sn.posc[i];
+  const float4 vn = sn.velrho[i];
+  const int cidx = sn.cid[i];
+  const uint8_t code = sn.code[i];
+  x.id[i] = sn.id[i];
+  x.cid[i] = (uint16_t)cidx;
+  x.code[i] = code;
+  const CaseConst &C = cc[cidx];
+  if (k >= key_out(nbits)) {  // frozen before this step, or released
+    x.posc[i] = pn;
+    x.velrho[i] = vn;
+    keys_next[i] = k;
+    return;
+  }
+  if (keys_half[i] >= key_out(nbits)) {  // left at the half step: frozen at state n
+    int cx, cy, cz;
+    decode_cell(key_cell(k, nbits) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+    x.posc[i] = make_float4((float)(cx * C.cs + pn.x), (float)(cy * C.cs + pn.y),
+                            (float)(cz * C.cs + pn.z), 0.f);
+    x.velrho[i] = vn;
+    keys_next[i] = key_out(nbits);
+    return;
+  }
+  float4 pnew, vnew;
+  keys_next[i] = corrector_core(C, dyn[cidx], code, k, pn, vn, velrho_half[i].w, ace[i], nbits,
+                                cidx, dyn, pnew, vnew);
+  x.posc[i] = pnew;
+  x.velrho[i] = vnew;
 }
 
 // ---- Verlet scheme ---------------------------------------------------------------
@@ -1713,6 +1937,54 @@ void launch_mdbc(int margin, int n, const int *nvalid, const uint32_t *keys, Sta
   else
     k_mdbc<2><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, press, cstart, nbits, cc, dyn,
                                            stage);
+}
+
+void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
+                          const float4 *velrho, const float *press, const uint16_t *cid,
+                          const uint32_t *cstart, int64_t cap_cells, int nbits,
+                          const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
+                          const uint2 *list, int cap, const uint16_t *count,
+                          cudaStream_t s) {
+  if (n <= 0) return;
+  k_interact_list<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, press, cid, cstart,
+                                               (uint32_t)(cap_cells + 1), nbits, cc, dyn, ace,
+                                               want_dt, list, cap, count);
+}
+
+void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t *keys,
+                           const float4 *posc, const float4 *velrho, const float *press,
+                           const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
+                           int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
+                           uint2 *list, int cap, uint16_t *count, cudaStream_t s) {
+  if (n <= 0) return;
+  const uint32_t cap1 = (uint32_t)(cap_cells + 1);
+#define SPH_IB_ARGS                                                                        \
+  n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 1, \
+      nullptr, nullptr, list, cap, count
+  if (margin == 1)
+    k_interact<1, 0, 0, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+  else if (margin == 3)
+    k_interact<3, 0, 0, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+  else
+    k_interact<2, 0, 0, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+#undef SPH_IB_ARGS
+}
+
+void launch_predictor_list(int n, const uint32_t *keys_in, State src, const float4 *ace,
+                           const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
+                           float4 *velrho_out, uint32_t *keys_out, float *press, cudaStream_t s) {
+  if (n > 0)
+    k_predictor_list<<<nblk(n, 256), 256, 0, s>>>(n, keys_in, src, ace, cc, dyn, nbits, posc_out,
+                                                  velrho_out, keys_out, press);
+}
+
+void launch_corrector_list(int n, const uint32_t *keys_n, const uint32_t *keys_half, State sn,
+                           const float4 *velrho_half, const float4 *ace, const CaseConst *cc,
+                           CaseDyn *dyn, int nbits, State x, uint32_t *keys_next,
+                           cudaStream_t s) {
+  if (n > 0)
+    k_corrector_list<<<nblk(n, 256), 256, 0, s>>>(n, keys_n, keys_half, sn, velrho_half, ace, cc,
+                                                  dyn, nbits, x, keys_next);
 }
 
 void launch_verlet(int n, const uint32_t *keys_in, State src, const float4 *ace,

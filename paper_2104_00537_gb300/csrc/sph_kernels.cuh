@@ -41,6 +41,29 @@ void launch_predictor(int n, const uint32_t *keys_in, State src, const float4 *a
 void launch_mdbc(int margin, int n, const int *nvalid, const uint32_t *keys, State st,
                  float *press, const uint32_t *cstart, int nbits, const CaseConst *cc,
                  const CaseDyn *dyn, int stage, cudaStream_t s);
+// Per-step neighbour list (Symplectic, default physics): build on state n
+// with radius 2h + skin; interaction over the list; predictor and corrector
+// that keep the order and the cells of state n for the half step.
+// First evaluation of the list step: the compacted pair loop on state n that
+// also writes every target's list (chunk records, radius 2h + skin) and count.
+void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t *keys,
+                           const float4 *posc, const float4 *velrho, const float *press,
+                           const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
+                           int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
+                           uint2 *list, int cap, uint16_t *count, cudaStream_t s);
+void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
+                          const float4 *velrho, const float *press, const uint16_t *cid,
+                          const uint32_t *cstart, int64_t cap_cells, int nbits,
+                          const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
+                          const uint2 *list, int cap, const uint16_t *count,
+                          cudaStream_t s);
+void launch_predictor_list(int n, const uint32_t *keys_in, State src, const float4 *ace,
+                           const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
+                           float4 *velrho_out, uint32_t *keys_out, float *press, cudaStream_t s);
+void launch_corrector_list(int n, const uint32_t *keys_n, const uint32_t *keys_half, State sn,
+                           const float4 *velrho_half, const float4 *ace, const CaseConst *cc,
+                           CaseDyn *dyn, int nbits, State x, uint32_t *keys_next,
+                           cudaStream_t s);
 // Verlet step (Eq 30-31) from the sorted state src to dst (same order).
 void launch_verlet(int n, const uint32_t *keys_in, State src, const float4 *ace,
                    const CaseConst *cc, CaseDyn *dyn, int nbits, State dst, uint32_t *keys_out,

@@ -297,7 +297,9 @@ class Engine:
     def step(self, nsteps=1):
         check(self.lib.sph_step(self.h, int(nsteps)))
 
-    def set_options(self, pi_block=0, pi_variant=0, use_graph=0, timing=0):
+    def set_options(self, pi_block=0, pi_variant=-1, use_graph=0, timing=0):
+        """pi_variant -1 keeps the engine default (the per-step neighbour list,
+        3, where the engine supports it, else the compacted loop, 0)."""
         o = Options(pi_block, pi_variant, use_graph, timing)
         check(self.lib.sph_set_options(self.h, C.byref(o)))
 

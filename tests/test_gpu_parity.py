@@ -220,10 +220,14 @@ def c0_100(c0):
     return o
 
 
+@pytest.mark.parametrize("variant", [3, 0])
 @pytest.mark.parametrize("use_graph", [0, 1])
-def test_dam_break_100_steps(c0, c0_100, use_graph):
+def test_dam_break_100_steps(c0, c0_100, use_graph, variant):
+    """Variant 3 (the default here): one neighbour list per step on state n
+    with a skin, no re-sort for the half step; variant 0: a fresh neighbour
+    list for each of the two evaluations.  Both against the oracle."""
     eng = sph.Engine.create(c0)
-    eng.set_options(use_graph=use_graph)
+    eng.set_options(use_graph=use_graph, pi_variant=variant)
     m0 = eng.stats()["mass"]
     eng.step(100)
     s = eng.stats()
@@ -304,7 +308,8 @@ def test_moving_boundary_and_sloshing_parity():
     eng.destroy()
 
 
-def test_out_of_domain_particle_is_frozen():
+@pytest.mark.parametrize("variant", [3, 0])
+def test_out_of_domain_particle_is_frozen(variant):
     """A particle shot out of the domain is frozen, keeps its mass, and the
     quota error fires when max_out is exceeded."""
     c = cases.dam_break(0.04)
@@ -314,6 +319,7 @@ def test_out_of_domain_particle_is_frozen():
     c.pos[f] = (0.8, 0.3, ztop - 0.004)               # alone, just below it
     c.vel[f] = (0.0, 0.0, 5.0)
     eng = sph.Engine.create(c)
+    eng.set_options(pi_variant=variant)
     eng.step(3)
     s = eng.stats()
     o = oracle.OracleState(c)
@@ -322,6 +328,7 @@ def test_out_of_domain_particle_is_frozen():
     assert s["mass"] == o.diag()["mass"]
     c.params["max_out"] = 0
     eng2 = sph.Engine.create(c)
+    eng2.set_options(pi_variant=variant)
     with pytest.raises(sph.SphError) as ei:
         eng2.step(3)
     assert ei.value.code == -5
@@ -383,9 +390,12 @@ def test_pool_mix_equals_alone():
     pool.pool_step(7)
     pool.release(sa)                  # a leaves; b keeps running
     pool.pool_step(3)
+    # pools run the compacted pair loop (variant 0); so do the single engines here
     ea = sph.Engine.create(ca)
+    ea.set_options(pi_variant=0)
     ea.step(12)
     eb = sph.Engine.create(cb)
+    eb.set_options(pi_variant=0)
     eb.step(10)
     st = pool.get_state(sb)
     ref = eb.get_state()
