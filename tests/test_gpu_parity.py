@@ -426,3 +426,50 @@ def test_wave_flume_fiftieth_scale():
     s = eng.stats()
     assert s["mass"] == o.diag()["mass"] and s["n_out"] == 0
     eng.destroy()
+
+
+# ---- degenerate inputs ------------------------------------------------------------
+
+def _subset(case, keep):
+    keep = np.asarray(keep)
+    g = None if case.ghost is None else case.ghost[keep]
+    return cases.Case(case.name, dict(case.params), case.pos[keep], case.vel[keep],
+                      case.rho[keep], case.ptype[keep], case.group[keep], list(case.motions),
+                      dict(case.meta), g)
+
+
+@pytest.mark.parametrize("variant", [3, 0])
+def test_boundary_only_case(variant):
+    """No fluid: no pairs (Eq 36 needs b in F), nothing moves, and the step is
+    C_CFL h / cs0 (no fluid for Eq 35)."""
+    c = _subset(cases.still_tank(0.02), cases.still_tank(0.02).ptype == 1)
+    eng = sph.Engine.create(c)
+    eng.set_options(pi_variant=variant)
+    st0 = eng.get_state()
+    eng.step(3)
+    s, st = eng.stats(), eng.get_state()
+    p = c.params
+    assert s["interactions"] == 0 and s["flags"] == 0
+    assert s["last_dt"] == pytest.approx(p["cfl"] * p["h"] / p["cs0"], rel=1e-12)
+    assert np.array_equal(st["pos"], st0["pos"])
+    eng.destroy()
+
+
+def test_empty_case_and_empty_batch_member():
+    """A case without particles: creation, steps and stats are no-ops; as a
+    member of a batch it does not disturb the others."""
+    full = cases.dam_break(0.04, seed=7)
+    empty = _subset(full, np.zeros(full.n, bool))
+    e = sph.Engine.create(empty)
+    e.step(2)
+    assert e.stats()["n"] == 0 and e.stats()["step"] == 0
+    e.destroy()
+    bat = sph.Engine.batch([full, empty])
+    bat.step(4)
+    alone = sph.Engine.create(full)
+    alone.step(4)
+    a, b = alone.get_state(), bat.get_state(0)
+    for k in ("pos", "vel", "rho"):
+        assert np.array_equal(a[k], b[k]), k
+    bat.destroy()
+    alone.destroy()
