@@ -126,6 +126,7 @@ void fill_const(const sph_case_params &p, const sph_particles &parts, const Grid
   const double aD = 21.0 / (16.0 * kPi * p.h * p.h * p.h);  // Eq 11, 3-D
   C.cw = (float)(-5.0 * aD / (p.h * p.h));
   C.wk = (float)aD;
+  C.list_k = (float)(1.25 * (p.dt_fixed > 0 ? p.dt_fixed : p.cfl * p.h / p.cs0));
   C.half_inv_h = (float)(0.5 / p.h);
   // artificial viscosity only in visc_mode 0; laminar + SPS constants otherwise
   C.kvisc = p.visc_mode == 0 ? (float)(-2.0 * p.alpha * p.cs0 * p.h) : 0.f;

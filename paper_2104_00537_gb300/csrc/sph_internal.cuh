@@ -55,7 +55,7 @@ struct CaseConst {
   float sps_cs2;  // (C_S Delta)^2 of Eq 25
   float sps_cl2;  // C_l Delta^2 of Eq 25
   float wk;       // a_D of Eq 11: W = a_D t^4 (5 - 4t), t = 1 - r/(2h)
-  float pad4_;
+  float list_k;   // 1.25 x the Eq 35 bound on dt (or the fixed dt): skin = list_k |v|max + 1e-3 h
 };
 
 // Mutable per-case values, updated on the device during a step.

@@ -451,9 +451,7 @@ __device__ __forceinline__ void finish_target(const CaseConst &C, int i, int n, 
 // Eq 35 (dt <= C_CFL h / cs0 since dt_cv <= h / cs0) or the fixed step, plus
 // 1e-3 h; the 25 % covers the change of a wall's imposed speed over dt / 2.
 __device__ __forceinline__ float list_skin(const CaseConst &C, const CaseDyn &D) {
-  const double dtb = C.dt_fixed > 0.0 ? C.dt_fixed : C.cfl * C.h_d / C.cs0_d;
-  const double vmax = sqrt((double)__uint_as_float(D.v2max_bits));
-  return (float)(1.25 * dtb * vmax + 1e-3 * C.h_d);
+  return fmaf(C.list_k, sqrtf(__uint_as_float(D.v2max_bits)), 1e-3f * C.h);
 }
 
 constexpr uint32_t kListIndexMask = (1u << 25) - 1u;
@@ -1460,9 +1458,9 @@ __global__ void k_predictor_list(int n, const uint32_t *__restrict__ keys_in, St
   double disp[3];
   float4 vn;
   predictor_core(C, D, code, v, ace[i], disp, vn);
-  const double hs = 0.5 * (double)list_skin(C, D);
-  if (disp[0] * disp[0] + disp[1] * disp[1] + disp[2] * disp[2] > hs * hs)
-    atomicOr(&dyn[cidx].flags, kFlagSkin);
+  const float hs = 0.5f * list_skin(C, D);
+  const float dx = (float)disp[0], dy = (float)disp[1], dz = (float)disp[2];
+  if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > hs * hs) atomicOr(&dyn[cidx].flags, kFlagSkin);
   float4 ptmp;
   bool left;
   (void)move_particle(k, p, disp, C, code != 0, nbits, ptmp, left);
