@@ -1362,7 +1362,9 @@ __global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
 
 
 // The interaction over a target's list (state n or n+1/2, same order and
-// cells): the pair terms of k_interact for the entries inside 2h.
+// cells): the pair terms of k_interact for the entries inside 2h.  EXT 1
+// adds the Eq 19-20 density diffusion for the cases that use it.
+template <int EXT>
 __global__ void __launch_bounds__(128)
 k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
                 const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
@@ -1386,6 +1388,10 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
   const float Pa = has ? press[i] * va.w : 0.f;
   const float kv = C.kvisc * va.w;
   const bool ddt_on = C.ddt != 0;
+  Ext X;
+  X.C = &C;
+  X.hyd = EXT >= 1 && C.ddt == 2;
+  X.sps = false;
   const int jb = (int)cstart[cap1 - 1];  // first boundary particle of the key order
   const int nrec = has ? (int)count[i] : 0;
   const bool warp_fluid = __all_sync(full, afluid || !has);
@@ -1419,7 +1425,8 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
         const float4 vb = velrho[j];
         const bool bfluid = j < jb;
         if (warp_fluid || afluid) {
-          pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j], ddt_on && bfluid, A);
+          pair_fluid<EXT>(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j],
+                          ddt_on && bfluid, A, &X, j, bfluid);
           if (bfluid) A.cnt++; else A.cntb++;
         } else {
           pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
@@ -1941,30 +1948,43 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const float4 *velrho, const float *press, const uint16_t *cid,
                           const uint32_t *cstart, int64_t cap_cells, int nbits,
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
-                          const uint2 *list, int cap, const uint16_t *count,
+                          const uint2 *list, int cap, const uint16_t *count, bool ext,
                           cudaStream_t s) {
   if (n <= 0) return;
-  k_interact_list<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, press, cid, cstart,
-                                               (uint32_t)(cap_cells + 1), nbits, cc, dyn, ace,
-                                               want_dt, list, cap, count);
+#define SPH_IL_ARGS                                                                      \
+  n, nvalid, keys, posc, velrho, press, cid, cstart, (uint32_t)(cap_cells + 1), nbits, cc, \
+      dyn, ace, want_dt, list, cap, count
+  if (ext)
+    k_interact_list<1><<<nblk(n, 128), 128, 0, s>>>(SPH_IL_ARGS);
+  else
+    k_interact_list<0><<<nblk(n, 128), 128, 0, s>>>(SPH_IL_ARGS);
+#undef SPH_IL_ARGS
 }
 
 void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t *keys,
                            const float4 *posc, const float4 *velrho, const float *press,
                            const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
                            int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
-                           uint2 *list, int cap, uint16_t *count, cudaStream_t s) {
+                           uint2 *list, int cap, uint16_t *count, bool ext, cudaStream_t s) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_IB_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 1, \
       nullptr, nullptr, list, cap, count
-  if (margin == 1)
+  if (ext) {
+    if (margin == 1)
+      k_interact<1, 0, 1, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+    else if (margin == 3)
+      k_interact<3, 0, 1, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+    else
+      k_interact<2, 0, 1, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+  } else if (margin == 1) {
     k_interact<1, 0, 0, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
-  else if (margin == 3)
+  } else if (margin == 3) {
     k_interact<3, 0, 0, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
-  else
+  } else {
     k_interact<2, 0, 0, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+  }
 #undef SPH_IB_ARGS
 }
 

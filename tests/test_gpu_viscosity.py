@@ -95,3 +95,24 @@ def test_pool_sps_case_equals_alone():
         assert np.array_equal(a[k], b[k]), k
     e.destroy()
     pool.destroy()
+
+
+@pytest.mark.parametrize("variant", [3, 0])
+def test_fourtakas_dam_break_steps(variant):
+    """Eq 19-20 over whole steps, with the per-step list (3) and with two
+    neighbour lists per step (0), against the oracle."""
+    c = cases.dam_break(0.02, ddt_mode=2)
+    eng = sph.Engine.create(c)
+    eng.set_options(pi_variant=variant)
+    eng.step(60)
+    s, st = eng.stats(), eng.get_state()
+    o = oracle.OracleState(c)
+    o.step(60)
+    od = o.diag()
+    dp = c.params["dp"]
+    assert abs(s["t"] - o.t.value) < 1e-3 * o.t.value
+    assert abs(s["ke"] - od["ke"]) < 0.01 * od["ke"]
+    assert np.abs(st["pos"] - o.pos).max() < 0.5 * dp
+    assert np.abs(st["rho"] - o.rho).max() < 1.0
+    assert s["flags"] == 0
+    eng.destroy()
