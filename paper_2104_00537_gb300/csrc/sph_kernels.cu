@@ -1397,8 +1397,9 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
   const bool warp_fluid = __all_sync(full, afluid || !has);
   Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
   const uint2 *__restrict__ mine = list + (int64_t)i * cap;
-  // one candidate per lane per iteration, records taken in order: the warp
-  // waits only for its lane with the most candidates in total
+  // two candidates per lane per iteration (their loads issued together),
+  // records taken in order: the warp waits only for its lane with the most
+  // candidates in total
   int r = 0;
   unsigned cm = 0u;
   int cbase = 0;
@@ -1414,23 +1415,35 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
     }
     if (!__any_sync(full, cm != 0u)) break;
     if (cm) {
-      const int k = 31 - __clz(cm);
-      cm ^= 1u << k;
-      const int j = cbase + k;
-      const float4 pb = posc[j];
-      const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
-      const float ry = sy - pb.y, rz = sz - pb.z;
-      const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-      if (__float_as_uint(r2) - 1u < r2max_u) {
-        const float4 vb = velrho[j];
-        const bool bfluid = j < jb;
-        if (warp_fluid || afluid) {
-          pair_fluid<EXT>(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, press[j],
-                          ddt_on && bfluid, A, &X, j, bfluid);
-          if (bfluid) A.cnt++; else A.cntb++;
-        } else {
-          pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
-          A.cnt++;
+      const int k1 = 31 - __clz(cm);
+      cm ^= 1u << k1;
+      const bool h2 = cm != 0u;
+      const int k2 = h2 ? 31 - __clz(cm) : k1;
+      if (h2) cm ^= 1u << k2;
+      const int j1 = cbase + k1, j2 = cbase + k2;
+      const float4 pb1 = posc[j1];
+      const float4 pb2 = posc[j2];
+      const float4 vb1 = velrho[j1];
+      const float4 vb2 = velrho[j2];
+      const float q1 = press[j1], q2 = press[j2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const float4 pb = u ? pb2 : pb1;
+        const float4 vb = u ? vb2 : vb1;
+        const int j = u ? j2 : j1;
+        const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+        const float ry = sy - pb.y, rz = sz - pb.z;
+        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        if ((u == 0 || h2) && __float_as_uint(r2) - 1u < r2max_u) {
+          const bool bfluid = j < jb;
+          if (warp_fluid || afluid) {
+            pair_fluid<EXT>(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, u ? q2 : q1,
+                            ddt_on && bfluid, A, &X, j, bfluid);
+            if (bfluid) A.cnt++; else A.cntb++;
+          } else {
+            pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
+            A.cnt++;
+          }
         }
       }
     }
