@@ -396,8 +396,8 @@ def main():
     eng.set_options(pi_variant=args.pi_variant)
     n_particles = sum(c.n for c in cs)
     # the engine runs the per-step list (3) where it supports it, unless told otherwise
-    list_ok = (args.integrator == "symplectic" and args.visc_mode == 0
-               and args.boundary_mode == 0 and n_particles < (1 << 25))
+    list_ok = (args.integrator == "symplectic" and args.boundary_mode == 0
+               and n_particles < (1 << 25))
     eff_var = args.pi_variant if args.pi_variant in (0, 1, 2) else (3 if list_ok else 0)
     if eff_var == 3 and not list_ok:
         eff_var = 0

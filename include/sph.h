@@ -145,8 +145,8 @@ typedef struct {
                        * Symplectic step on state n with a skin, both
                        * evaluations over the list, no re-sort for the half
                        * step (single and batched engines with the
-                       * Symplectic scheme, visc_mode 0, boundary_mode 0;
-                       * else it falls back to 0)                        */
+                       * Symplectic scheme and boundary_mode 0; else it
+                       * falls back to 0)                                */
   int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
   int32_t timing;     /* 1: time every PI launch with CUDA events              */
 } sph_options;

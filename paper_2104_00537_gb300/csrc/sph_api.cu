@@ -446,7 +446,7 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
   }
   // the per-step list serves the Symplectic scheme with DBC and artificial
   // viscosity (either density diffusion term)
-  e->list_ok = e->integrator == 0 && !e->sps && !e->mdbc && np < kListMaxParticles;
+  e->list_ok = e->integrator == 0 && !e->mdbc && np < kListMaxParticles;
   if (e->list_ok) {
     // chunk records per target: two parts of (2M+1)^2 rows, each row's pruned
     // range (2M+1 cells of ~1.3 x (cs/dp)^3 particles) in chunks of 32
@@ -519,7 +519,7 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[0], s);
   launch_interact_build(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                         e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                        e->list_cap, e->ncount, e->ext, s);
+                        e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
   if (ev) cudaEventRecord(ev[1], s);
   launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
   launch_predictor_list(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
@@ -527,7 +527,7 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
-                       e->list_cap, e->ncount, e->ext, s);
+                       e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
   if (ev) cudaEventRecord(ev[3], s);
   launch_corrector_list(nl, e->keysB, e->keysC, Y, Z.velrho, e->ace, e->dconst, e->ddyn,
                         e->nbits, X, e->keysA, s);

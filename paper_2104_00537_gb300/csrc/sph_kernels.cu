@@ -794,6 +794,25 @@ k_interact_q(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict
   finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
 }
 
+// tau/rho of Eq 25 from the sums g of V_b-weighted velocity differences
+// (units of 1/(m cw)): S, |S| = (2 S:S)^(1/2) / 2, nu_SPS = (C_S Delta)^2 |S|.
+__device__ __forceinline__ void sps_tau_from_gradient(const CaseConst &C, float gxx, float gyy,
+                                                      float gzz, float gxy, float gxz,
+                                                      float gyz, float4 &t4, float2 &t2) {
+  const float k = C.m * C.cw;
+  const float sxx = k * gxx, syy = k * gyy, szz = k * gzz;
+  const float sxy = 0.5f * k * gxy, sxz = 0.5f * k * gxz, syz = 0.5f * k * gyz;
+  const float ss = fmaf(sxx, sxx, fmaf(syy, syy, szz * szz)) +
+                   2.f * fmaf(sxy, sxy, fmaf(sxz, sxz, syz * syz));
+  const float smag = 0.5f * sqrtf(2.f * ss);
+  const float nu2 = 2.f * C.sps_cs2 * smag;
+  const float tr3 = (sxx + syy + szz) * (1.f / 3.f);
+  const float iso = -(2.f / 3.f) * C.sps_cl2 * smag * smag;
+  t4 = make_float4(fmaf(nu2, sxx - tr3, iso), fmaf(nu2, syy - tr3, iso),
+                   fmaf(nu2, szz - tr3, iso), nu2 * sxy);
+  t2 = make_float2(nu2 * sxz, nu2 * syz);
+}
+
 // First neighbour pass of the laminar + SPS model (Eq 24-25): for every
 // fluid particle a of a case with visc_mode 1, the SPH velocity gradient
 // G^{ij} = sum_{b in P} V_b (v_b - v_a)^i grad^j_a W_ab, its symmetric part
@@ -899,18 +918,7 @@ k_strain(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ k
     tau2[i] = make_float2(0.f, 0.f);
     return;
   }
-  const float k = C.m * C.cw;
-  const float sxx = k * gxx, syy = k * gyy, szz = k * gzz;
-  const float sxy = 0.5f * k * gxy, sxz = 0.5f * k * gxz, syz = 0.5f * k * gyz;
-  const float ss = fmaf(sxx, sxx, fmaf(syy, syy, szz * szz)) +
-                   2.f * fmaf(sxy, sxy, fmaf(sxz, sxz, syz * syz));
-  const float smag = 0.5f * sqrtf(2.f * ss);
-  const float nu2 = 2.f * C.sps_cs2 * smag;
-  const float tr3 = (sxx + syy + szz) * (1.f / 3.f);
-  const float iso = -(2.f / 3.f) * C.sps_cl2 * smag * smag;
-  tau4[i] = make_float4(fmaf(nu2, sxx - tr3, iso), fmaf(nu2, syy - tr3, iso),
-                        fmaf(nu2, szz - tr3, iso), nu2 * sxy);
-  tau2[i] = make_float2(nu2 * sxz, nu2 * syz);
+  sps_tau_from_gradient(C, gxx, gyy, gzz, gxy, gxz, gyz, tau4[i], tau2[i]);
 }
 
 // ---- modified dynamic boundary condition (Eq 38-39) ------------------------------
@@ -1363,16 +1371,19 @@ __global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
 
 // The interaction over a target's list (state n or n+1/2, same order and
 // cells): the pair terms of k_interact for the entries inside 2h.  EXT 1
-// adds the Eq 19-20 density diffusion for the cases that use it.
+// adds the Eq 19-20 density diffusion, EXT 2 also laminar + SPS (tau4/tau2
+// from k_strain_list), for the cases that use them.
 template <int EXT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, EXT == 2 ? 6 : 0)
 k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
                 const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
                 const float *__restrict__ press, const uint16_t *__restrict__ cid,
                 const uint32_t *__restrict__ cstart, uint32_t cap1, int nbits,
                 const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
                 float4 *__restrict__ ace, int want_dt, const uint2 *__restrict__ list,
-                int cap, const uint16_t *__restrict__ count) {
+                int cap, const uint16_t *__restrict__ count,
+                const float4 *__restrict__ tau4 = nullptr,
+                const float2 *__restrict__ tau2 = nullptr) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -1391,7 +1402,20 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
   Ext X;
   X.C = &C;
   X.hyd = EXT >= 1 && C.ddt == 2;
-  X.sps = false;
+  X.sps = EXT == 2 && C.visc == 1 && afluid;
+  X.kl = -4.f * C.nu0 * va.w;
+  X.tau4 = tau4;
+  X.tau2 = tau2;
+  {
+    const float4 t4 = X.sps ? tau4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 t2 = X.sps ? tau2[i] : make_float2(0.f, 0.f);
+    X.ta[0] = va.w * t4.x;
+    X.ta[1] = va.w * t4.y;
+    X.ta[2] = va.w * t4.z;
+    X.ta[3] = va.w * t4.w;
+    X.ta[4] = va.w * t2.x;
+    X.ta[5] = va.w * t2.y;
+  }
   const int jb = (int)cstart[cap1 - 1];  // first boundary particle of the key order
   const int nrec = has ? (int)count[i] : 0;
   const bool warp_fluid = __all_sync(full, afluid || !has);
@@ -1449,6 +1473,81 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
     }
   }
   finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, nullptr, dyn);
+}
+
+
+// The strain pass of the laminar + SPS model (as k_strain) over the target's
+// list records, for the half-step state kept in the order and cells of state n.
+__global__ void __launch_bounds__(128)
+k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
+              const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
+              const uint16_t *__restrict__ cid, int nbits, const CaseConst *__restrict__ cc,
+              const uint2 *__restrict__ list, int cap, const uint16_t *__restrict__ count,
+              float4 *__restrict__ tau4, float2 *__restrict__ tau2) {
+  const unsigned full = 0xffffffffu;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvalid = *nvalid_p;
+  const uint32_t key = i < nvalid ? keys[i] : key_out(nbits);
+  const int cidx = i < n ? (int)cid[i] : 0;
+  const CaseConst &C = cc[cidx];
+  const bool act = key < key_out(nbits) && !key_boundary(key, nbits) && C.visc == 1;
+  if (__all_sync(full, !act)) {
+    if (i < n) {
+      tau4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      tau2[i] = make_float2(0.f, 0.f);
+    }
+    return;
+  }
+  const float cs = C.csf, hih = C.half_inv_h;
+  const unsigned r2max_u = __float_as_uint(C.r2max) - 1u;
+  const float4 pa = act ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 va = act ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+  const int nrec = act ? (int)count[i] : 0;
+  const uint2 *__restrict__ mine = list + (int64_t)i * cap;
+  float gxx = 0.f, gyy = 0.f, gzz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
+  int r = 0;
+  unsigned cm = 0u;
+  int cbase = 0;
+  float sy = 0.f, sz = 0.f;
+#pragma unroll 1
+  for (;;) {
+    if (cm == 0u && r < nrec) {
+      const uint2 rec = mine[r++];
+      cbase = (int)(rec.x & kListIndexMask);
+      cm = rec.y;
+      sy = fmaf(-(float)((int)((rec.x >> 25) & 7u) - 3), cs, pa.y);
+      sz = fmaf(-(float)((int)(rec.x >> 28) - 3), cs, pa.z);
+    }
+    if (!__any_sync(full, cm != 0u)) break;
+    if (cm) {
+      const int k = 31 - __clz(cm);
+      cm ^= 1u << k;
+      const int j = cbase + k;
+      const float4 pb = posc[j];
+      const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+      const float ry = sy - pb.y, rz = sz - pb.z;
+      const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      if (__float_as_uint(r2) - 1u < r2max_u) {
+        const float4 vb = velrho[j];
+        const float t = fmaf(-hih, r2 * rsqrtf(r2), 1.f);
+        const float w = t * t * t * __fdividef(1.f, vb.w);
+        const float dvx = vb.x - va.x, dvy = vb.y - va.y, dvz = vb.z - va.z;
+        gxx = fmaf(w * dvx, rx, gxx);
+        gyy = fmaf(w * dvy, ry, gyy);
+        gzz = fmaf(w * dvz, rz, gzz);
+        gxy = fmaf(w, fmaf(dvx, ry, dvy * rx), gxy);
+        gxz = fmaf(w, fmaf(dvx, rz, dvz * rx), gxz);
+        gyz = fmaf(w, fmaf(dvy, rz, dvz * ry), gyz);
+      }
+    }
+  }
+  if (i >= n) return;
+  if (!act) {
+    tau4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    tau2[i] = make_float2(0.f, 0.f);
+    return;
+  }
+  sps_tau_from_gradient(C, gxx, gyy, gzz, gxy, gxz, gyz, tau4[i], tau2[i]);
 }
 
 // Half step for the list path: state n+1/2 in the same order and the same
@@ -1962,15 +2061,20 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const uint32_t *cstart, int64_t cap_cells, int nbits,
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
                           const uint2 *list, int cap, const uint16_t *count, bool ext,
-                          cudaStream_t s) {
+                          float4 *tau4, float2 *tau2, cudaStream_t s) {
   if (n <= 0) return;
 #define SPH_IL_ARGS                                                                      \
   n, nvalid, keys, posc, velrho, press, cid, cstart, (uint32_t)(cap_cells + 1), nbits, cc, \
-      dyn, ace, want_dt, list, cap, count
-  if (ext)
+      dyn, ace, want_dt, list, cap, count, tau4, tau2
+  if (tau4) {  // laminar + SPS cases present: strain pass over the list first
+    k_strain_list<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, nbits, cc,
+                                               list, cap, count, tau4, tau2);
+    k_interact_list<2><<<nblk(n, 128), 128, 0, s>>>(SPH_IL_ARGS);
+  } else if (ext) {
     k_interact_list<1><<<nblk(n, 128), 128, 0, s>>>(SPH_IL_ARGS);
-  else
+  } else {
     k_interact_list<0><<<nblk(n, 128), 128, 0, s>>>(SPH_IL_ARGS);
+  }
 #undef SPH_IL_ARGS
 }
 
@@ -1978,13 +2082,28 @@ void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t 
                            const float4 *posc, const float4 *velrho, const float *press,
                            const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
                            int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
-                           uint2 *list, int cap, uint16_t *count, bool ext, cudaStream_t s) {
+                           uint2 *list, int cap, uint16_t *count, bool ext, float4 *tau4,
+                           float2 *tau2, cudaStream_t s) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_IB_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 1, \
-      nullptr, nullptr, list, cap, count
-  if (ext) {
+      tau4, tau2, list, cap, count
+  if (tau4) {  // laminar + SPS cases: strain pass on state n, then EXT 2
+    if (margin == 1) {
+      k_strain<1><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
+                                               nbits, cc, tau4, tau2);
+      k_interact<1, 0, 2, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+    } else if (margin == 3) {
+      k_strain<3><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
+                                               nbits, cc, tau4, tau2);
+      k_interact<3, 0, 2, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+    } else {
+      k_strain<2><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
+                                               nbits, cc, tau4, tau2);
+      k_interact<2, 0, 2, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+    }
+  } else if (ext) {
     if (margin == 1)
       k_interact<1, 0, 1, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
     else if (margin == 3)

@@ -50,13 +50,14 @@ void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t 
                            const float4 *posc, const float4 *velrho, const float *press,
                            const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
                            int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
-                           uint2 *list, int cap, uint16_t *count, bool ext, cudaStream_t s);
+                           uint2 *list, int cap, uint16_t *count, bool ext, float4 *tau4,
+                           float2 *tau2, cudaStream_t s);
 void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
                           const float4 *velrho, const float *press, const uint16_t *cid,
                           const uint32_t *cstart, int64_t cap_cells, int nbits,
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
                           const uint2 *list, int cap, const uint16_t *count, bool ext,
-                          cudaStream_t s);
+                          float4 *tau4, float2 *tau2, cudaStream_t s);
 void launch_predictor_list(int n, const uint32_t *keys_in, State src, const float4 *ace,
                            const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
                            float4 *velrho_out, uint32_t *keys_out, float *press, cudaStream_t s);

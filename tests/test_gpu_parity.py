@@ -473,3 +473,22 @@ def test_empty_case_and_empty_batch_member():
         assert np.array_equal(a[k], b[k]), k
     bat.destroy()
     alone.destroy()
+
+
+def test_list_overflow_is_reported():
+    """Particles packed at dp/2 (eight times the density the list capacity is
+    sized for) overflow the per-step list: the step reports it instead of
+    dropping pairs, and the two-list path (variant 0) steps the same case."""
+    from tests.lattice import lattice_case
+    c = lattice_case(n=28, dp=0.02)
+    c.pos = c.pos * 0.5                      # spacing dp/2, h still sqrt(3) dp
+    eng = sph.Engine.create(c)
+    with pytest.raises(sph.SphError) as ei:
+        eng.step(1)
+    assert ei.value.code == -8 and "pi_variant 0" in str(ei.value)
+    eng.destroy()
+    e0 = sph.Engine.create(c)
+    e0.set_options(pi_variant=0)
+    e0.step(1)
+    assert e0.stats()["interactions"] > 0
+    e0.destroy()

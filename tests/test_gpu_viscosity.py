@@ -49,10 +49,13 @@ def test_sps_one_evaluation(steps):
     eng.destroy()
 
 
-def test_sps_dam_break_100_steps():
+@pytest.mark.parametrize("variant", [3, 0])
+def test_sps_dam_break_100_steps(variant):
+    """Per-step list (3: strain pass and interaction over the list at the half
+    step) and two neighbour lists per step (0)."""
     c = sps_case()
     eng = sph.Engine.create(c)
-    eng.set_options(use_graph=1)
+    eng.set_options(use_graph=1, pi_variant=variant)
     eng.step(100)
     s = eng.stats()
     st = eng.get_state()
@@ -89,6 +92,7 @@ def test_pool_sps_case_equals_alone():
     s = pool.admit(c, t_end=1.0)
     pool.pool_step(8)
     e = sph.Engine.create(c)
+    e.set_options(pi_variant=0)  # pools run two neighbour lists per step
     e.step(8)
     a, b = pool.get_state(s), e.get_state()
     for k in ("pos", "vel", "rho"):
