@@ -350,7 +350,7 @@ def main():
     ap.add_argument("--workload", default="dam_break")
     ap.add_argument("--cell-mode", type=int, default=1)
     ap.add_argument("--ddt-mode", type=int, default=1, choices=[0, 1, 2])
-    ap.add_argument("--pi-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3])
+    ap.add_argument("--pi-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4])
     ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "verlet"])
     ap.add_argument("--visc-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--nu0", type=float, default=1e-6)
@@ -398,10 +398,10 @@ def main():
     # the engine runs the per-step list (3) where it supports it, unless told otherwise
     list_ok = (args.integrator == "symplectic" and args.boundary_mode == 0
                and n_particles < (1 << 25))
-    eff_var = args.pi_variant if args.pi_variant in (0, 1, 2) else (3 if list_ok else 0)
-    if eff_var == 3 and not list_ok:
+    eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4) else (4 if list_ok else 0)
+    if eff_var in (3, 4) and not list_ok:
         eff_var = 0
-    kernel = "k_interact_list" if eff_var == 3 else "k_interact"
+    kernel = {3: "k_interact_list", 4: "k_interact_list"}.get(eff_var, "k_interact")
 
     # warm-up
     eng.step(args.warmup)
@@ -453,7 +453,7 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": measured_traffic(args.cell_mode, args.workload, kernel)
                 if (args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) ==
-                (1, "symplectic", 0, 0) and eff_var in (0, 3) else None,
+                (1, "symplectic", 0, 0) and eff_var in (0, 4) else None,
                 "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
                 "pi_ms_per_launch": 1000 * pi_avg_s,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal max clock)"}

@@ -137,16 +137,17 @@ typedef void (*sph_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 /* Engine-wide launch options (the autotuner's knobs). */
 typedef struct {
   int32_t pi_block;   /* threads per block of the interaction kernel (0: default) */
-  int32_t pi_variant; /* interaction pair loop: -1 the engine default (3 where
+  int32_t pi_variant; /* interaction pair loop: -1 the engine default (4 where
                        * supported, else 0); 0 compacted hit masks; 1 test
                        * and evaluate inline; 2 hit masks queued per lane
-                       * across rows (same sums as 0, bit for bit); 3 a
-                       * per-step neighbour list: one candidate test per
-                       * Symplectic step on state n with a skin, both
-                       * evaluations over the list, no re-sort for the half
-                       * step (single and batched engines with the
-                       * Symplectic scheme and boundary_mode 0; else it
-                       * falls back to 0)                                */
+                       * across rows (same sums as 0, bit for bit); 3 and 4
+                       * a per-step neighbour list: one candidate test per
+                       * Symplectic step on state n with a skin, no re-sort
+                       * for the half step; 3 writes the list during the
+                       * first evaluation, 4 builds it alone and evaluates
+                       * both states over it (single and batched engines
+                       * with the Symplectic scheme and boundary_mode 0;
+                       * else they fall back to 0)                       */
   int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
   int32_t timing;     /* 1: time every PI launch with CUDA events              */
 } sph_options;

@@ -458,7 +458,7 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
       cap = std::max(cap, 2.0 * (2 * M + 1) * (2 * M + 1) * chunks);
     }
     e->list_cap = std::min(4096, ((int)std::ceil(cap) + 31) / 32 * 32);
-    e->opt.pi_variant = 3;
+    e->opt.pi_variant = 4;
   }
   rc = allocate(e);
   int64_t cell0 = 0, p0 = 0;
@@ -505,8 +505,9 @@ void enqueue_step_verlet(sph_engine e, cudaEvent_t *ev) {
 }
 
 // One Symplectic step with the per-step neighbour list: NL on state n (Y),
-// PI that also writes the list, Δt, half step in Y's order and cells (Z),
-// PI over the list, full step into X.  ev: 4 events around the two PI launches.
+// the list (written by the first PI, variant 3, or built alone and then
+// evaluated, variant 4), Δt, half step in Y's order and cells (Z), PI over the
+// list, full step into X.  ev: 4 events around the two evaluations.
 void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   const int n = (int)e->n_phys;
   const int nl = (int)(e->n_phys - e->n_dead);
@@ -516,10 +517,21 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
                  X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
-  if (ev) cudaEventRecord(ev[0], s);
-  launch_interact_build(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
-                        e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                        e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
+  if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
+    if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
+    launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
+                      e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
+                      e->list_cap, e->ncount, s);
+    launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
+                         e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
+                         e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
+  } else {
+    if (ev) cudaEventRecord(ev[0], s);
+    launch_interact_build(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
+                          e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
+                          e->nlist, e->list_cap, e->ncount, e->ext,
+                          e->sps ? e->tau4 : nullptr, e->tau2, s);
+  }
   if (ev) cudaEventRecord(ev[1], s);
   launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
   launch_predictor_list(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
@@ -540,7 +552,7 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
     enqueue_step_verlet(e, ev);
     return;
   }
-  if (e->opt.pi_variant == 3 && e->list_ok) {
+  if ((e->opt.pi_variant == 3 || e->opt.pi_variant == 4) && e->list_ok) {
     enqueue_step_list(e, ev);
     return;
   }
@@ -654,15 +666,16 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
   if (!e || !opt) return fail(SPH_ERR_ARG, "null argument");
   if (opt->pi_block != 0 && opt->pi_block != 128)
     return fail(SPH_ERR_ARG, "pi_block must be 0 (default) or 128");
-  if (opt->pi_variant < -1 || opt->pi_variant > 3)
+  if (opt->pi_variant < -1 || opt->pi_variant > 4)
     return fail(SPH_ERR_ARG,
-                "pi_variant must be -1 (engine default), 0 (compacted), 1 (inline), 2 (queued) "
-                "or 3 (per-step neighbour list)");
+                "pi_variant must be -1 (engine default), 0 (compacted), 1 (inline), 2 (queued), "
+                "3 (per-step list written by the first evaluation) or 4 (per-step list built "
+                "alone)");
   e->opt = *opt;
-  // -1: the per-step list where the engine supports it, else the compacted loop;
-  // 3 without list support falls back to the compacted loop too
-  if (e->opt.pi_variant == -1 || (e->opt.pi_variant == 3 && !e->list_ok))
-    e->opt.pi_variant = e->list_ok ? 3 : 0;
+  // -1: the per-step list (built alone, 4) where the engine supports it, else
+  // the compacted loop; 3 and 4 without list support fall back to it too
+  if (e->opt.pi_variant == -1 || (e->opt.pi_variant >= 3 && !e->list_ok))
+    e->opt.pi_variant = e->list_ok ? 4 : 0;
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
   e->gexec = nullptr;
   return SPH_OK;
@@ -712,9 +725,10 @@ int sph_step(sph_engine e, int64_t nsteps) {
   // reorder, cell table and interaction, dt, update, end of step
   const int64_t passes = std::max(1, (e->nbits + 7) / 8);
   const int64_t pis = e->integrator == 1 ? 1 : 2;
-  const bool listed = e->integrator == 0 && e->opt.pi_variant == 3 && e->list_ok;
+  const bool listed = e->integrator == 0 && e->opt.pi_variant >= 3 && e->list_ok;
   const int64_t per_step = (e->integrator == 1 ? 3 * passes + 1 + 4 + 1 + 3
-                            : listed           ? 3 * passes + 1 + 4 + 2 + 4
+                            : listed           ? 3 * passes + 1 + 4 + 2 + 4 +
+                                                     (e->opt.pi_variant == 4 ? 1 : 0)
                                                : 6 * passes + 2 + 8 + 2 + 4) +
                            (e->sps ? pis : 0) +  // strain pass before each interaction
                            (e->mdbc ? pis : 0);  // ghost-node pass before each interaction

@@ -472,10 +472,11 @@ constexpr uint32_t kListIndexMask = (1u << 25) - 1u;
 // laminar + SPS viscosity of Eq 23-27 (tau4/tau2 from k_strain), per case;
 // warps without such cases still take the default pair loop.
 //
-// LIST (VARIANT 0, EXT 0): also writes the target's per-step neighbour list:
+// LIST (VARIANT 0): 1 also writes the target's per-step neighbour list, 2
+// writes only the list (no pair terms, no outputs besides the list):
 // for every tested chunk with a candidate within 2h + skin, one record
 // (first index | row offset, mask of those candidates) to list[i cap + c].
-template <int M, int VARIANT, int EXT = 0, bool LIST = false>
+template <int M, int VARIANT, int EXT = 0, int LIST = 0>
 __global__ void __launch_bounds__(128, EXT == 2 ? 6 : 0)
 k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
            const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
@@ -582,6 +583,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
             if (lcnt < cap) list[(int64_t)i * cap + lcnt] = make_uint2((uint32_t)(lo + base) | rowbits, ml);
             lcnt++;
           }
+          if (LIST != 2) {
           if (part) A.cntb += __popc(m); else A.cnt += __popc(m);
           if (warp_plain) {  // fluid targets, Eq 18 or no diffusion
             while (__any_sync(full, m != 0u)) {
@@ -616,6 +618,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
               }
             }
           }
+          }
         } else {
           const int nk = min(32, maxlen - base);
 #pragma unroll 1
@@ -647,6 +650,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
     count[i] = (uint16_t)min(lcnt, cap);
     if (has && lcnt > cap) atomicOr(&dyn[cidx].flags, kFlagListFull);
   }
+  if (LIST == 2) return;
   finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
 }
 
@@ -2078,6 +2082,25 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
 #undef SPH_IL_ARGS
 }
 
+void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *keys,
+                       const float4 *posc, const float4 *velrho, const float *press,
+                       const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
+                       const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
+                       uint16_t *count, cudaStream_t s) {
+  if (n <= 0) return;
+  const uint32_t cap1 = (uint32_t)(cap_cells + 1);
+#define SPH_BL_ARGS                                                                        \
+  n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 0, \
+      nullptr, nullptr, list, cap, count
+  if (margin == 1)
+    k_interact<1, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
+  else if (margin == 3)
+    k_interact<3, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
+  else
+    k_interact<2, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
+#undef SPH_BL_ARGS
+}
+
 void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t *keys,
                            const float4 *posc, const float4 *velrho, const float *press,
                            const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
@@ -2093,29 +2116,29 @@ void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t 
     if (margin == 1) {
       k_strain<1><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
                                                nbits, cc, tau4, tau2);
-      k_interact<1, 0, 2, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+      k_interact<1, 0, 2, 1><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
     } else if (margin == 3) {
       k_strain<3><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
                                                nbits, cc, tau4, tau2);
-      k_interact<3, 0, 2, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+      k_interact<3, 0, 2, 1><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
     } else {
       k_strain<2><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
                                                nbits, cc, tau4, tau2);
-      k_interact<2, 0, 2, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+      k_interact<2, 0, 2, 1><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
     }
   } else if (ext) {
     if (margin == 1)
-      k_interact<1, 0, 1, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+      k_interact<1, 0, 1, 1><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
     else if (margin == 3)
-      k_interact<3, 0, 1, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+      k_interact<3, 0, 1, 1><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
     else
-      k_interact<2, 0, 1, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+      k_interact<2, 0, 1, 1><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
   } else if (margin == 1) {
-    k_interact<1, 0, 0, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+    k_interact<1, 0, 0, 1><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
   } else if (margin == 3) {
-    k_interact<3, 0, 0, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+    k_interact<3, 0, 0, 1><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
   } else {
-    k_interact<2, 0, 0, true><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
+    k_interact<2, 0, 0, 1><<<nblk(n, 128), 128, 0, s>>>(SPH_IB_ARGS);
   }
 #undef SPH_IB_ARGS
 }

@@ -44,6 +44,12 @@ void launch_mdbc(int margin, int n, const int *nvalid, const uint32_t *keys, Sta
 // Per-step neighbour list (Symplectic, default physics): build on state n
 // with radius 2h + skin; interaction over the list; predictor and corrector
 // that keep the order and the cells of state n for the half step.
+// The list alone (the candidate test of the compacted loop, no pair terms).
+void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *keys,
+                       const float4 *posc, const float4 *velrho, const float *press,
+                       const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
+                       const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
+                       uint16_t *count, cudaStream_t s);
 // First evaluation of the list step: the compacted pair loop on state n that
 // also writes every target's list (chunk records, radius 2h + skin) and count.
 void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t *keys,

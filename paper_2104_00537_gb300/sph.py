@@ -299,7 +299,7 @@ class Engine:
 
     def set_options(self, pi_block=0, pi_variant=-1, use_graph=0, timing=0):
         """pi_variant -1 keeps the engine default (the per-step neighbour list,
-        3, where the engine supports it, else the compacted loop, 0)."""
+        4, where the engine supports it, else the compacted loop, 0)."""
         o = Options(pi_block, pi_variant, use_graph, timing)
         check(self.lib.sph_set_options(self.h, C.byref(o)))
 

@@ -220,12 +220,13 @@ def c0_100(c0):
     return o
 
 
-@pytest.mark.parametrize("variant", [3, 0])
+@pytest.mark.parametrize("variant", [4, 3, 0])
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_dam_break_100_steps(c0, c0_100, use_graph, variant):
-    """Variant 3 (the default here): one neighbour list per step on state n
-    with a skin, no re-sort for the half step; variant 0: a fresh neighbour
-    list for each of the two evaluations.  Both against the oracle."""
+    """Variants 4 (the default here) and 3: one neighbour list per step on
+    state n with a skin, no re-sort for the half step (4 builds it alone, 3
+    writes it during the first evaluation); variant 0: a fresh neighbour list
+    for each of the two evaluations.  All against the oracle."""
     eng = sph.Engine.create(c0)
     eng.set_options(use_graph=use_graph, pi_variant=variant)
     m0 = eng.stats()["mass"]
@@ -308,7 +309,7 @@ def test_moving_boundary_and_sloshing_parity():
     eng.destroy()
 
 
-@pytest.mark.parametrize("variant", [3, 0])
+@pytest.mark.parametrize("variant", [4, 3, 0])
 def test_out_of_domain_particle_is_frozen(variant):
     """A particle shot out of the domain is frozen, keeps its mass, and the
     quota error fires when max_out is exceeded."""
@@ -438,7 +439,7 @@ def _subset(case, keep):
                       dict(case.meta), g)
 
 
-@pytest.mark.parametrize("variant", [3, 0])
+@pytest.mark.parametrize("variant", [4, 3, 0])
 def test_boundary_only_case(variant):
     """No fluid: no pairs (Eq 36 needs b in F), nothing moves, and the step is
     C_CFL h / cs0 (no fluid for Eq 35)."""

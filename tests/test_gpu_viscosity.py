@@ -49,7 +49,7 @@ def test_sps_one_evaluation(steps):
     eng.destroy()
 
 
-@pytest.mark.parametrize("variant", [3, 0])
+@pytest.mark.parametrize("variant", [4, 3, 0])
 def test_sps_dam_break_100_steps(variant):
     """Per-step list (3: strain pass and interaction over the list at the half
     step) and two neighbour lists per step (0)."""
@@ -101,7 +101,7 @@ def test_pool_sps_case_equals_alone():
     pool.destroy()
 
 
-@pytest.mark.parametrize("variant", [3, 0])
+@pytest.mark.parametrize("variant", [4, 3, 0])
 def test_fourtakas_dam_break_steps(variant):
     """Eq 19-20 over whole steps, with the per-step list (3) and with two
     neighbour lists per step (0), against the oracle."""
