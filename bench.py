@@ -310,7 +310,8 @@ def run_served(args):
     for _, c, _ in trace:
         c.params["cell_mode"] = args.cell_mode
     free, _ = torch.cuda.mem_get_info()
-    max_p = int(min(free * 0.3 / 200, 64_000_000))   # about 200 B per particle slot
+    # about 200 B of state and 1.5 KB of per-step list per particle slot
+    max_p = int(min(free * 0.3 / 1800, 16_000_000))
     max_cells = int(min(free * 0.05 / 8, 200_000_000))
     results = {}
     for name, slots in (("served", 64), ("plain", 1)):

@@ -217,7 +217,7 @@ struct sph_engine_t {
   sph_options opt{};
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_n = -1, graph_dead = -1;  // n_phys and cells_hw of the captured graph
-  int graph_ext = 0;                       // ext + 2 sps + 4 mdbc of the captured graph
+  int graph_ext = 0;  // ext + 2 sps + 4 mdbc + 8 list of the captured graph
   std::vector<cudaEvent_t> evs;
   double pi_ms = 0, step_ms = 0;
   int64_t pi_launches = 0, kernel_launches = 0;
@@ -254,6 +254,24 @@ struct sph_engine_t {
 namespace {
 
 int bits_for(int64_t cap_cells) { return key_bits(cap_cells); }
+
+// Chunk records per target for the per-step list: two parts of (2M+1)^2 rows,
+// each row's pruned range (2M+1 cells of ~1.3 x (cs/dp)^3 particles) in
+// chunks of 32; rounded up to a multiple of 32.
+int list_records_needed(int cell_mode, double h, double dp) {
+  const int M = cell_mode + 1;
+  const double ppc = 1.3 * std::pow(2.0 * h / M / dp, 3.0);
+  const double chunks = std::ceil((2 * M + 1) * ppc / 32.0);
+  const double cap = 2.0 * (2 * M + 1) * (2 * M + 1) * chunks;
+  return std::min(4096, ((int)std::ceil(cap) + 31) / 32 * 32);
+}
+
+// The per-step list applies to this step: Symplectic scheme, no mDBC case, a
+// list variant chosen and the list allocated.
+bool use_list(sph_engine e) {
+  return e->integrator == 0 && e->list_ok && !e->mdbc &&
+         (e->opt.pi_variant == 3 || e->opt.pi_variant == 4);
+}
 
 int allocate(sph_engine e) {
   const int64_t N = e->cap_p > 0 ? e->cap_p : 1;
@@ -444,20 +462,14 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     e->sps = e->sps || params[c].visc_mode == 1;
     e->mdbc = e->mdbc || params[c].boundary_mode == 1;
   }
-  // the per-step list serves the Symplectic scheme with DBC and artificial
-  // viscosity (either density diffusion term)
+  // the per-step list serves the Symplectic scheme with DBC (any density
+  // diffusion and viscosity)
   e->list_ok = e->integrator == 0 && !e->mdbc && np < kListMaxParticles;
   if (e->list_ok) {
-    // chunk records per target: two parts of (2M+1)^2 rows, each row's pruned
-    // range (2M+1 cells of ~1.3 x (cs/dp)^3 particles) in chunks of 32
-    double cap = 32.0;
-    for (int c = 0; c < ncases; c++) {
-      const int M = params[c].cell_mode + 1;
-      const double ppc = 1.3 * std::pow(2.0 * params[c].h / M / params[c].dp, 3.0);
-      const double chunks = std::ceil((2 * M + 1) * ppc / 32.0);
-      cap = std::max(cap, 2.0 * (2 * M + 1) * (2 * M + 1) * chunks);
-    }
-    e->list_cap = std::min(4096, ((int)std::ceil(cap) + 31) / 32 * 32);
+    int cap = 32;
+    for (int c = 0; c < ncases; c++)
+      cap = std::max(cap, list_records_needed(params[c].cell_mode, params[c].h, params[c].dp));
+    e->list_cap = cap;
     e->opt.pi_variant = 4;
   }
   rc = allocate(e);
@@ -552,7 +564,7 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
     enqueue_step_verlet(e, ev);
     return;
   }
-  if ((e->opt.pi_variant == 3 || e->opt.pi_variant == 4) && e->list_ok) {
+  if (use_list(e)) {
     enqueue_step_list(e, ev);
     return;
   }
@@ -702,7 +714,7 @@ int sph_step(sph_engine e, int64_t nsteps) {
   int64_t k = 0;
   if (!timing && e->opt.use_graph && e->n_dead == 0) {
     if (!e->gexec || e->graph_n != e->n_phys || e->graph_dead != e->cells_hw ||
-        e->graph_ext != (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc) {
+        e->graph_ext != (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc + 8 * (int)use_list(e)) {
       if (e->gexec) cudaGraphExecDestroy(e->gexec);
       e->gexec = nullptr;
       cudaGraph_t g;
@@ -714,7 +726,7 @@ int sph_step(sph_engine e, int64_t nsteps) {
       if (err != cudaSuccess) return fail(SPH_ERR_CUDA, cudaGetErrorString(err));
       e->graph_n = e->n_phys;
       e->graph_dead = e->cells_hw;  // cells in use at capture
-      e->graph_ext = (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc;
+      e->graph_ext = (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc + 8 * (int)use_list(e);
     }
     for (; k < nsteps; k++) CUDA_TRY(cudaGraphLaunch(e->gexec, e->s));
   }
@@ -725,7 +737,7 @@ int sph_step(sph_engine e, int64_t nsteps) {
   // reorder, cell table and interaction, dt, update, end of step
   const int64_t passes = std::max(1, (e->nbits + 7) / 8);
   const int64_t pis = e->integrator == 1 ? 1 : 2;
-  const bool listed = e->integrator == 0 && e->opt.pi_variant >= 3 && e->list_ok;
+  const bool listed = use_list(e);
   const int64_t per_step = (e->integrator == 1 ? 3 * passes + 1 + 4 + 1 + 3
                             : listed           ? 3 * passes + 1 + 4 + 2 + 4 +
                                                      (e->opt.pi_variant == 4 ? 1 : 0)
@@ -1151,6 +1163,14 @@ int sph_pool_create(int64_t max_particles, int64_t max_cells, int32_t max_cases,
   e->slots.resize(max_cases);
   e->hconst.resize(max_cases);
   e->free_cells.push_back({0, max_cells});
+  // per-step list for the pool's cases, sized for h up to 1.2 sqrt(3) dp and any
+  // cell size; a case needing more records turns the list off (admission)
+  e->list_ok = max_particles < kListMaxParticles;
+  if (e->list_ok) {
+    const double hq = 1.2 * std::sqrt(3.0);
+    for (int cm = 0; cm < 3; cm++) e->list_cap = std::max(e->list_cap, list_records_needed(cm, hq, 1.0));
+    e->opt.pi_variant = 4;
+  }
   rc = allocate(e);
   if (rc == SPH_OK) {
     cudaError_t err = cudaStreamSynchronize(e->s);
@@ -1182,6 +1202,8 @@ int sph_pool_admit(sph_engine e, const sph_case_params *params, const sph_partic
   e->ext = e->ext || params->ddt_mode == 2 || params->visc_mode == 1;
   e->sps = e->sps || params->visc_mode == 1;
   e->mdbc = e->mdbc || params->boundary_mode == 1;
+  if (e->list_ok && list_records_needed(params->cell_mode, params->h, params->dp) > e->list_cap)
+    e->list_ok = false;  // from now on the pool runs two neighbour lists per step
   if (used == 0) e->margin = g.margin;
   if (g.margin != e->margin) return fail(SPH_ERR_ARG, "cell_mode differs from the pool's cases");
   int free_slot = -1;

@@ -391,12 +391,9 @@ def test_pool_mix_equals_alone():
     pool.pool_step(7)
     pool.release(sa)                  # a leaves; b keeps running
     pool.pool_step(3)
-    # pools run the compacted pair loop (variant 0); so do the single engines here
     ea = sph.Engine.create(ca)
-    ea.set_options(pi_variant=0)
     ea.step(12)
     eb = sph.Engine.create(cb)
-    eb.set_options(pi_variant=0)
     eb.step(10)
     st = pool.get_state(sb)
     ref = eb.get_state()

@@ -92,7 +92,6 @@ def test_pool_sps_case_equals_alone():
     s = pool.admit(c, t_end=1.0)
     pool.pool_step(8)
     e = sph.Engine.create(c)
-    e.set_options(pi_variant=0)  # pools run two neighbour lists per step
     e.step(8)
     a, b = pool.get_state(s), e.get_state()
     for k in ("pos", "vel", "rho"):
