@@ -267,6 +267,34 @@ def test_queued_pair_loop_is_bit_identical(cell_mode):
     assert res[0][3]["interactions"] == res[1][3]["interactions"]
 
 
+@pytest.fixture(scope="module")
+def c0_2000(c0):
+    o = oracle.OracleState(c0)
+    o.step(2000)
+    return o
+
+
+@pytest.mark.parametrize("variant", [4, 0])
+def test_dam_break_2000_steps(c0, c0_2000, variant):
+    """The longer comparison (2,000 steps, t ~ 0.46 s: the column has
+    collapsed and the front has run 0.9 m along the tank): front within
+    0.5 dp, kinetic energy within 1 %, 99 % of the particles within 0.5 dp of
+    the oracle's (measured on GB300: 0.04 dp, 7e-5, 0.04 dp)."""
+    eng = sph.Engine.create(c0)
+    eng.set_options(use_graph=1, pi_variant=variant)
+    eng.step(2000)
+    s, st = eng.stats(), eng.get_state()
+    o = c0_2000
+    od = o.diag()
+    dp = c0.params["dp"]
+    assert abs(s["t"] - o.t.value) < 1e-3 * o.t.value
+    assert abs(s["front"] - od["front"]) < 0.5 * dp
+    assert abs(s["ke"] - od["ke"]) < 0.01 * od["ke"]
+    assert np.percentile(np.linalg.norm(st["pos"] - o.pos, axis=1), 99) < 0.5 * dp
+    assert s["mass"] == od["mass"] and s["flags"] == 0
+    eng.destroy()
+
+
 def test_determinism(c0):
     a = sph.Engine.create(c0)
     b = sph.Engine.create(c0)
