@@ -267,9 +267,11 @@ def run_batched(args):
     clk = clocks.stop()
     p1 = sum(eng.stats(i)["interactions"] for i in range(len(cs)))
     eng.destroy()
-    # plain: one case at a time, each in its own engine, with the default
-    # options (one launch per kernel) and with each step replayed from a graph
-    ms_p, ms_pg, pp = 0.0, 0.0, 0
+    # plain: one case at a time, each in its own engine: the batch's pair
+    # loop with one launch per kernel and with each step replayed from a
+    # graph, and the single-case default (the list kept across steps) the
+    # same two ways; the speedups are quoted against the fastest plain path
+    ms_p, ms_pg, ms_pk, ms_pkg, pp = 0.0, 0.0, 0.0, 0.0, 0
     for c in cs:
         e = sph.Engine.create(c, stream=stream)
         e.set_options(pi_variant=var)
@@ -281,6 +283,15 @@ def run_batched(args):
         e.step(1)
         ms_pg += timed_steps(e, stream, args.steps)
         e.destroy()
+        e = sph.Engine.create(c, stream=stream)
+        e.set_options(pi_variant=5)
+        e.step(args.warmup)
+        ms_pk += timed_steps(e, stream, args.steps)
+        e.set_options(pi_variant=5, use_graph=1)
+        e.step(1)
+        ms_pkg += timed_steps(e, stream, args.steps)
+        e.destroy()
+    ms_best = min(ms_p, ms_pg, ms_pk, ms_pkg)
     nb = len(cs) * args.steps
     out = {"metric": "case_steps_per_s", "value": nb / (ms_b / 1e3), "unit": "case-steps/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -293,7 +304,10 @@ def run_batched(args):
            "plain": {"case_steps_per_s": nb / (ms_p / 1e3),
                      "interactions_per_s": pp / (ms_p / 1e3)},
            "plain_graph": {"case_steps_per_s": nb / (ms_pg / 1e3)},
+           "plain_list_kept": {"case_steps_per_s": nb / (ms_pk / 1e3)},
+           "plain_list_kept_graph": {"case_steps_per_s": nb / (ms_pkg / 1e3)},
            "speedup_vs_plain": ms_p / ms_b, "speedup_vs_plain_graph": ms_pg / ms_b,
+           "speedup_vs_best_plain": ms_best / ms_b,
            "autotune_ms_per_step": tune_ms, "clocks": clk}
     print(json.dumps(out), flush=True)
 
@@ -345,13 +359,16 @@ def run_served(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 2,000 for the dam break, its whole run "
+                         "from rest; 100 otherwise)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_break")
     ap.add_argument("--cell-mode", type=int, default=1)
     ap.add_argument("--ddt-mode", type=int, default=1, choices=[0, 1, 2])
-    ap.add_argument("--pi-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4])
+    ap.add_argument("--pi-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5])
+    ap.add_argument("--list-skin", type=float, default=-1.0)
     ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "verlet"])
     ap.add_argument("--visc-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--nu0", type=float, default=1e-6)
@@ -367,6 +384,8 @@ def main():
     ap.add_argument("--t-end", type=float, default=0.1)
     ap.add_argument("--chunk", type=int, default=10)
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 2000 if args.workload == "dam_break" else 100
     args.warmup = max(3, args.warmup)
     if args.impl != "reference" and args.workload == "batched":
         return run_batched(args)
@@ -394,20 +413,22 @@ def main():
     with torch.cuda.stream(stream):
         eng = sph.Engine.batch(cs, stream=stream) if len(cs) > 1 else \
             sph.Engine.create(cs[0], stream=stream)
-    eng.set_options(pi_variant=args.pi_variant)
+    eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin)
     n_particles = sum(c.n for c in cs)
     # the engine runs the per-step list (3) where it supports it, unless told otherwise
     list_ok = (args.integrator == "symplectic" and args.boundary_mode == 0
                and n_particles < (1 << 25))
-    eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4) else (4 if list_ok else 0)
-    if eff_var in (3, 4) and not list_ok:
+    eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4, 5) else (5 if list_ok else 0)
+    if eff_var in (3, 4, 5) and not list_ok:
         eff_var = 0
-    kernel = {3: "k_interact_list", 4: "k_interact_list"}.get(eff_var, "k_interact")
+    kernel = {3: "k_interact_list", 4: "k_interact_list", 5: "k_interact_list"}.get(
+        eff_var, "k_interact")
 
     # warm-up
     eng.step(args.warmup)
-    eng.set_options(pi_variant=args.pi_variant, timing=1)
+    eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, timing=1)
     eng.timing(reset=True)
+    builds0 = eng.list_info()["builds"]
 
     def totals():
         s = [eng.stats(i) for i in range(len(cs))]
@@ -429,6 +450,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     p1 = totals()
     tm = eng.timing(reset=True)
+    builds = eng.list_info()["builds"] - builds0
     pairs = p1[0] - p0[0]
     fb = p1[1] - p0[1]
     bf = p1[2] - p0[2]
@@ -484,6 +506,15 @@ def main():
                                      "verlet": "Verlet, Eq 30-31, N_S = 40 (1 PI per step)"}[
                           args.integrator],
                       "pi_variant": eff_var,
+                      "window": "steps %d-%d of the run from rest" % (
+                          args.warmup, args.warmup + args.steps),
+                      "neighbour_list": (
+                          {"builds_per_step": builds / args.steps,
+                           "skin": "list_k |v|max + 1e-3 h + %g x 2h" % (
+                               args.list_skin if args.list_skin >= 0 else 0.04)}
+                          if eff_var == 5 else
+                          {"builds_per_step": builds / args.steps} if eff_var in (3, 4)
+                          else None),
                       "l2": "state (%.0f MB) larger than L2 (129 MB), no flush" %
                             (n_particles * 177 / 1e6),
                       "parallelism": "replicas" if world > 1 else "single"},
@@ -498,7 +529,7 @@ def main():
         t0 = time.perf_counter()
         e2 = sph.Engine.create(cs[0], stream=stream, pinned=True) if len(cs) == 1 else \
             sph.Engine.batch(cs, stream=stream)
-        e2.set_options(pi_variant=args.pi_variant)
+        e2.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin)
         e2.step(args.steps)
         st = [e2.get_state(i) for i in range(len(cs))]
         e2pairs = sum(e2.stats(i)["interactions"] for i in range(len(cs)))

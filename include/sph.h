@@ -137,19 +137,29 @@ typedef void (*sph_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 /* Engine-wide launch options (the autotuner's knobs). */
 typedef struct {
   int32_t pi_block;   /* threads per block of the interaction kernel (0: default) */
-  int32_t pi_variant; /* interaction pair loop: -1 the engine default (4 where
-                       * supported, else 0); 0 compacted hit masks; 1 test
+  int32_t pi_variant; /* interaction pair loop: -1 the engine default (where a
+                       * list is supported 5 for one case, 4 for a batch or
+                       * pool, else 0); 0 compacted hit masks; 1 test
                        * and evaluate inline; 2 hit masks queued per lane
-                       * across rows (same sums as 0, bit for bit); 3 and 4
-                       * a per-step neighbour list: one candidate test per
-                       * Symplectic step on state n with a skin, no re-sort
-                       * for the half step; 3 writes the list during the
-                       * first evaluation, 4 builds it alone and evaluates
-                       * both states over it (single and batched engines
-                       * with the Symplectic scheme and boundary_mode 0;
-                       * else they fall back to 0)                       */
+                       * across rows (same sums as 0, bit for bit); 3, 4
+                       * and 5 a neighbour list: candidates within 2h + skin
+                       * of state n in chunk records, walked by both
+                       * evaluations of a Symplectic step, no re-sort for
+                       * the half step; 3 writes the list during the first
+                       * evaluation, 4 builds it alone, once per step; 5
+                       * builds it with a larger skin and keeps it (and the
+                       * particle order and cells) across steps until a
+                       * particle could leave the skin, decided on the
+                       * device (Symplectic scheme and boundary_mode 0;
+                       * else 3-5 fall back to 0)                         */
   int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
   int32_t timing;     /* 1: time every PI launch with CUDA events              */
+  float list_skin;    /* pi_variant 5: skin added for the steps the list is
+                       * kept, as a fraction of 2h, in [0, 0.25]; < 0: the
+                       * default (0.04)                                    */
+  int32_t check_list; /* 1: after every list evaluation, count the pairs of
+                       * every target by brute force and compare (tests;
+                       * sph_list_info reports the result)                */
 } sph_options;
 
 /* Last error message of the calling thread ("" if none). */
@@ -187,6 +197,14 @@ int sph_get_stats(sph_engine e, int32_t icase, sph_stats *out);
 int sph_set_options(sph_engine e, const sph_options *opt);
 int sph_get_timing(sph_engine e, double *pi_ms, int64_t *pi_launches,
                    double *step_ms, int64_t *kernel_launches, int32_t reset);
+
+/* sph_list_info: neighbour-list builds since the engine was created (the
+ * rebuilds of pi_variant 5, or one per step for 3 and 4), and with
+ * check_list on the pairs found by brute force and the number of targets
+ * whose list yielded a different count (0: every pair inside 2h was in the
+ * list).  Any output pointer may be NULL. */
+int sph_list_info(sph_engine e, int64_t *builds, int64_t *check_pairs,
+                  int64_t *check_bad);
 
 /* ---- checkpoint ----------------------------------------------------------
  * sph_get_raw: bit-exact snapshot of case icase (device storage format:

@@ -10,7 +10,7 @@ import json
 import math
 import os
 
-CANDIDATES = [(1, 4), (2, 4), (0, 4), (1, 3), (1, 0), (2, 0), (1, 1), (0, 0)]  # (cell_mode, pi_variant)
+CANDIDATES = [(1, 4), (1, 5), (2, 4), (0, 4), (1, 3), (1, 0), (2, 0), (1, 1), (0, 0)]  # (cell_mode, pi_variant)
 
 
 def cache_path() -> str:

@@ -183,12 +183,24 @@ struct sph_engine_t {
   bool ext = false;    // a case uses Eq 19-20 diffusion or laminar + SPS viscosity
   bool sps = false;    // a case uses laminar + SPS viscosity (tau buffers below)
   bool mdbc = false;   // a case uses the modified dynamic boundary condition
-  // per-step neighbour list (pi_variant 3): list_cap chunk records per target
+  // neighbour list (pi_variant 3-5): list_cap chunk records per target
   bool list_ok = false;
   int list_cap = 0;
   int64_t list_ld = 0;
   uint2 *nlist = nullptr;
   uint16_t *ncount = nullptr;
+  float4 *posc_ref = nullptr;  // positions at the list's build (pi_variant 5)
+  ListCtl *ctl = nullptr;      // rebuild request, build count, list check
+  cudaStream_t s2 = nullptr;   // captures the bodies of conditional graph nodes
+  // pi_variant 5 without a captured step graph: the two guarded parts of a
+  // rebuild (sort + reorder + cell table; skin + list) as small graphs
+  cudaGraphExec_t rbx[2] = {nullptr, nullptr};
+  int64_t rbx_n = -1, rbx_dead = -1, rbx_hw = -1;
+  int rbx_key = -1;
+  cudaError_t cap_err = cudaSuccess;  // first error while building a conditional node
+  bool capturing = false;             // enqueue_step runs under stream capture
+  int list_default = 4;               // pi_variant -1 with a list: 5 one case, 4 batch / pool
+  int64_t builds_seen = 0;            // ctl->builds at the last check_flags
   float4 *tau4 = nullptr;  // (tau/rho) of Eq 25 in sorted order: xx, yy, zz, xy
   float2 *tau2 = nullptr;  //   xz, yz
   bool pool = false;
@@ -214,7 +226,7 @@ struct sph_engine_t {
   char *io = nullptr;
   size_t io_bytes = 0;
   // options, graph, timing
-  sph_options opt{};
+  sph_options opt{0, 0, 0, 0, -1.f, 0};  // list_skin < 0: the default
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_n = -1, graph_dead = -1;  // n_phys and cells_hw of the captured graph
   int graph_ext = 0;  // ext + 2 sps + 4 mdbc + 8 list of the captured graph
@@ -233,9 +245,18 @@ struct sph_engine_t {
     if (p) allocs.push_back({p, bytes});
     return p;
   }
-  void release_all() {
+  void drop_graphs() {
     if (gexec) cudaGraphExecDestroy(gexec);
     gexec = nullptr;
+    for (auto &g : rbx) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  }
+  void release_all() {
+    drop_graphs();
+    if (s2) cudaStreamDestroy(s2);
+    s2 = nullptr;
     for (auto &e : evs) cudaEventDestroy(e);
     evs.clear();
     if (s) cudaStreamSynchronize(s);
@@ -255,22 +276,58 @@ namespace {
 
 int bits_for(int64_t cap_cells) { return key_bits(cap_cells); }
 
-// Chunk records per target for the per-step list: two parts of (2M+1)^2 rows,
-// each row's pruned range (2M+1 cells of ~1.3 x (cs/dp)^3 particles) in
-// chunks of 32; rounded up to a multiple of 32.
-int list_records_needed(int cell_mode, double h, double dp) {
-  const int M = cell_mode + 1;
-  const double ppc = 1.3 * std::pow(2.0 * h / M / dp, 3.0);
-  const double chunks = std::ceil((2 * M + 1) * ppc / 32.0);
-  const double cap = 2.0 * (2 * M + 1) * (2 * M + 1) * chunks;
-  return std::min(4096, ((int)std::ceil(cap) + 31) / 32 * 32);
+// Chunk records a target's list may need (the list segment per target):
+// for target offsets sampled over a cell, the rows (dy, dz) whose slab lies
+// within R = 2h + skin, each row's cell range in x times ~1.3 (cs/dp)^3
+// particles in chunks of 32, plus one record per row for the second
+// particle type; x 1.2, rounded up to a multiple of 32.  skin: the largest
+// list kept across steps (kListExtraMax x 2h) plus 0.1 h for one step.
+constexpr double kListExtraMax = 0.25;
+
+double slab_gap_h(int d, double o, double cs) {
+  return d > 0 ? d * cs - o : (d < 0 ? o - (d + 1) * cs : 0.0);
 }
 
-// The per-step list applies to this step: Symplectic scheme, no mDBC case, a
-// list variant chosen and the list allocated.
+int list_records_needed(int cell_mode, double h, double dp) {
+  const int M = cell_mode + 1, MR = M + 1;
+  const double cs = 2.0 * h / M, R = 2.0 * h + kListExtraMax * 2.0 * h + 0.1 * h;
+  const double ppc = 1.3 * std::pow(cs / dp, 3.0);
+  const int S = 6;
+  double worst = 0.0;
+  for (int a = 0; a <= S; a++)
+    for (int b = 0; b <= S; b++)
+      for (int c = 0; c <= S; c++) {
+        const double ox = std::min(a / (double)S, 0.9999) * cs;
+        const double oy = std::min(b / (double)S, 0.9999) * cs;
+        const double oz = std::min(c / (double)S, 0.9999) * cs;
+        double rec = 0.0;
+        for (int dy = -MR; dy <= MR; dy++)
+          for (int dz = -MR; dz <= MR; dz++) {
+            const double gy = slab_gap_h(dy, oy, cs), gz = slab_gap_h(dz, oz, cs);
+            const double d2 = gy * gy + gz * gz;
+            if (d2 >= R * R) continue;
+            const double L = std::sqrt(R * R - d2);
+            const int kx0 = std::max(-MR, (int)std::floor((ox - L) / cs));
+            const int kx1 = std::min(MR, (int)std::floor((ox + L) / cs));
+            rec += std::ceil((kx1 - kx0 + 1) * ppc / 32.0) + 1.0;
+          }
+        worst = std::max(worst, rec);
+      }
+  return std::min(4096, ((int)std::ceil(1.2 * worst) + 31) / 32 * 32);
+}
+
+// A neighbour list applies to this step: Symplectic scheme, no mDBC case, a
+// list variant chosen (3, 4: one list per step; 5: kept across steps) and
+// the list allocated.
 bool use_list(sph_engine e) {
-  return e->integrator == 0 && e->list_ok && !e->mdbc &&
-         (e->opt.pi_variant == 3 || e->opt.pi_variant == 4);
+  return e->integrator == 0 && e->list_ok && !e->mdbc && e->opt.pi_variant >= 3 &&
+         e->opt.pi_variant <= 5;
+}
+
+// Key of a captured step graph: everything that changes its launches.
+int graph_key(sph_engine e) {
+  return (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc +
+         8 * (use_list(e) ? e->opt.pi_variant - 2 : 0) + 64 * (e->opt.check_list != 0);
 }
 
 int allocate(sph_engine e) {
@@ -309,6 +366,8 @@ int allocate(sph_engine e) {
     e->list_ld = N;
     e->nlist = (uint2 *)A(sizeof(uint2) * (size_t)e->list_cap * (size_t)N);
     e->ncount = (uint16_t *)A(2 * N);
+    e->posc_ref = (float4 *)A(16 * N);
+    e->ctl = (ListCtl *)A(sizeof(ListCtl));
   }
   if (e->sps || e->pool) {
     e->tau4 = (float4 *)A(16 * N);
@@ -326,6 +385,7 @@ int allocate(sph_engine e) {
   }
   CUDA_TRY(cudaMemsetAsync(e->press, 0, 4 * NP, e->s));
   CUDA_TRY(cudaMemsetAsync(e->ddyn, 0, sizeof(CaseDyn) * e->cap_cases, e->s));
+  if (e->ctl) CUDA_TRY(cudaMemsetAsync(e->ctl, 0, sizeof(ListCtl), e->s));
   CUDA_TRY(cudaMemsetAsync(e->dconst, 0, sizeof(CaseConst) * e->cap_cases, e->s));
   return SPH_OK;
 }
@@ -470,7 +530,10 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     for (int c = 0; c < ncases; c++)
       cap = std::max(cap, list_records_needed(params[c].cell_mode, params[c].h, params[c].dp));
     e->list_cap = cap;
-    e->opt.pi_variant = 4;
+    // one case: the list kept across steps; several: one list per step, so
+    // that every case of a batch takes the same steps as alone, bit for bit
+    e->list_default = ncases == 1 ? 5 : 4;
+    e->opt.pi_variant = e->list_default;
   }
   rc = allocate(e);
   int64_t cell0 = 0, p0 = 0;
@@ -531,13 +594,15 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
   if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
     if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
+    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, s);
     launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                       e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                      e->list_cap, e->ncount, s);
+                      e->list_cap, e->ncount, nullptr, s);
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                          e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
   } else {
+    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, s);
     if (ev) cudaEventRecord(ev[0], s);
     launch_interact_build(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                           e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
@@ -545,16 +610,157 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
                           e->sps ? e->tau4 : nullptr, e->tau2, s);
   }
   if (ev) cudaEventRecord(ev[1], s);
+  if (e->opt.check_list)
+    launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
+                      e->list_cap, e->ncount, e->ctl, s);
   launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
   launch_predictor_list(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
-                        e->keysC, e->press, s);
+                        e->keysC, e->press, nullptr, s);
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
                        e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
   if (ev) cudaEventRecord(ev[3], s);
+  if (e->opt.check_list)
+    launch_list_check(nl, e->nvalid, e->keysC, Z.posc, Y.cid, e->dconst, e->nbits, e->nlist,
+                      e->list_cap, e->ncount, e->ctl, s);
   launch_corrector_list(nl, e->keysB, e->keysC, Y, Z.velrho, e->ace, e->dconst, e->ddyn,
                         e->nbits, X, e->keysA, s);
+  launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
+}
+
+// Appends to the graph being captured on e->s a k_decide kernel and an IF
+// node whose body (fn's launches, captured on e->s2) runs only while a
+// rebuild of the neighbour list is requested (ListCtl::rebuild).
+template <class F>
+void capture_if_rebuild(sph_engine e, F fn) {
+  if (e->cap_err != cudaSuccess) return;
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  cudaGraphConditionalHandle h{};
+  cudaGraphNodeParams p{};
+  cudaGraphNode_t node{};
+  cudaError_t err = cudaStreamGetCaptureInfo(e->s, &st, nullptr, &g, &deps, nullptr, &nd);
+  if (!err && st != cudaStreamCaptureStatusActive) err = cudaErrorStreamCaptureInvalidated;
+  if (!err) err = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  if (!err) {
+    launch_decide(h, e->ctl, e->s);
+    err = cudaStreamGetCaptureInfo(e->s, &st, nullptr, &g, &deps, nullptr, &nd);
+  }
+  if (!err) {
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    err = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
+  }
+  if (!err)
+    err = cudaStreamUpdateCaptureDependencies(e->s, &node, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+  if (!err)
+    err = cudaStreamBeginCaptureToGraph(e->s2, p.conditional.phGraph_out[0], nullptr, nullptr,
+                                        0, cudaStreamCaptureModeThreadLocal);
+  if (!err) {
+    fn(e->s2);
+    cudaGraph_t body = nullptr;
+    err = cudaStreamEndCapture(e->s2, &body);
+  }
+  if (err) e->cap_err = err;
+}
+
+// The same guarded launches outside a captured step graph: a small graph of
+// the decide kernel and the IF node, instantiated once per configuration
+// (which: 0 sort + reorder + cell table, 1 skin + list) and launched on e->s.
+template <class F>
+void eager_if_rebuild(sph_engine e, int which, F fn) {
+  if (e->cap_err != cudaSuccess) return;
+  const int key = graph_key(e);
+  if (e->rbx_n != e->n_phys || e->rbx_dead != e->n_dead || e->rbx_hw != e->cells_hw ||
+      e->rbx_key != key) {
+    for (auto &x : e->rbx) {
+      if (x) cudaGraphExecDestroy(x);
+      x = nullptr;
+    }
+    e->rbx_n = e->n_phys;
+    e->rbx_dead = e->n_dead;
+    e->rbx_hw = e->cells_hw;
+    e->rbx_key = key;
+  }
+  if (!e->rbx[which]) {
+    cudaError_t err = cudaStreamBeginCapture(e->s, cudaStreamCaptureModeThreadLocal);
+    if (err) {
+      e->cap_err = err;
+      return;
+    }
+    capture_if_rebuild(e, fn);
+    cudaGraph_t g = nullptr;
+    err = cudaStreamEndCapture(e->s, &g);
+    if (!err && e->cap_err == cudaSuccess) err = cudaGraphInstantiate(&e->rbx[which], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (err && e->cap_err == cudaSuccess) e->cap_err = err;
+    if (e->cap_err != cudaSuccess) return;
+  }
+  cudaError_t err = cudaGraphLaunch(e->rbx[which], e->s);
+  if (err) e->cap_err = err;
+}
+
+// One Symplectic step over the neighbour list kept across steps (pi_variant
+// 5).  Guarded by the rebuild request: sort, reorder and cell table of the
+// current state (X -> Y), then the skin and the list on Y with every target's
+// position (posc_ref).  Always: PI on Y (state n), dt, half step into Z in Y's
+// order and cells, PI on Z, and the corrector, which writes state n+1 to X
+// (normalised, keysA) and in place to Y, and requests a rebuild when the next
+// step could leave the skin.  ev: 4 events around the two evaluations (the
+// first one's time includes the list build when it runs).
+void enqueue_step_reuse(sph_engine e, cudaEvent_t *ev) {
+  const int n = (int)e->n_phys;
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &X = e->S[0], &Y = e->S[1], &Z = e->S[2];
+  cudaStream_t s = e->s;
+  const float extra = e->opt.list_skin >= 0.f ? e->opt.list_skin : 0.04f;
+  auto nl_part = [=](cudaStream_t q) {
+    radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, q);
+    launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
+                   X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, q);
+    launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, q);
+  };
+  auto list_part = [=](cudaStream_t q) {
+    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, extra, q);
+    launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
+                      e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
+                      e->list_cap, e->ncount, e->posc_ref, q);
+  };
+  if (e->capturing) {
+    capture_if_rebuild(e, nl_part);
+    capture_if_rebuild(e, list_part);
+  } else {
+    eager_if_rebuild(e, 0, nl_part);
+    if (ev) cudaEventRecord(ev[0], s);
+    eager_if_rebuild(e, 1, list_part);
+  }
+  float4 *tau4 = e->sps ? e->tau4 : nullptr;
+  launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
+                       e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
+                       e->list_cap, e->ncount, e->ext, tau4, e->tau2, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  if (e->opt.check_list)
+    launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
+                      e->list_cap, e->ncount, e->ctl, s);
+  launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
+  launch_predictor_list(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
+                        e->keysC, e->press, e->posc_ref, s);
+  if (ev) cudaEventRecord(ev[2], s);
+  launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
+                       e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
+                       e->list_cap, e->ncount, e->ext, tau4, e->tau2, s);
+  if (ev) cudaEventRecord(ev[3], s);
+  if (e->opt.check_list)
+    launch_list_check(nl, e->nvalid, e->keysC, Z.posc, Y.cid, e->dconst, e->nbits, e->nlist,
+                      e->list_cap, e->ncount, e->ctl, s);
+  launch_corrector_reuse(nl, e->keysB, e->keysC, Y, Z.velrho, e->ace, e->posc_ref, e->dconst,
+                         e->ddyn, e->nbits, X, e->keysA, e->press, e->ctl, s);
   launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
 }
 
@@ -565,7 +771,10 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
     return;
   }
   if (use_list(e)) {
-    enqueue_step_list(e, ev);
+    if (e->opt.pi_variant == 5)
+      enqueue_step_reuse(e, ev);
+    else
+      enqueue_step_list(e, ev);
     return;
   }
   const int n = (int)e->n_phys;
@@ -626,7 +835,11 @@ int check_flags(sph_engine e) {
   std::vector<CaseDyn> d(e->cap_cases);
   CUDA_TRY(cudaMemcpyAsync(d.data(), e->ddyn, sizeof(CaseDyn) * e->cap_cases,
                            cudaMemcpyDeviceToHost, e->s));
+  ListCtl lc{};
+  if (e->ctl)
+    CUDA_TRY(cudaMemcpyAsync(&lc, e->ctl, sizeof(ListCtl), cudaMemcpyDeviceToHost, e->s));
   CUDA_TRY(cudaStreamSynchronize(e->s));
+  e->builds_seen = (int64_t)lc.builds;
   for (int c = 0; c < e->cap_cases; c++) {
     if (!e->slots[c].used) continue;
     if (d[c].flags & kFlagNaN)
@@ -639,7 +852,9 @@ int check_flags(sph_engine e) {
                                      "list holds; use pi_variant 0");
     if (d[c].flags & kFlagSkin)
       return fail(SPH_ERR_UNSTABLE, "case " + std::to_string(c) +
-                                        ": a half-step displacement exceeded the list's skin");
+                                        ": a displacement since the neighbour list's build "
+                                        "exceeded half its skin, or one step needs a skin the "
+                                        "list's rows do not reach; use pi_variant 0");
     int mo = e->hconst[c].max_out;
     if (mo >= 0 && d[c].n_out > mo)
       return fail(SPH_ERR_DOMAIN, "case " + std::to_string(c) + ": " +
@@ -678,18 +893,19 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
   if (!e || !opt) return fail(SPH_ERR_ARG, "null argument");
   if (opt->pi_block != 0 && opt->pi_block != 128)
     return fail(SPH_ERR_ARG, "pi_block must be 0 (default) or 128");
-  if (opt->pi_variant < -1 || opt->pi_variant > 4)
+  if (opt->pi_variant < -1 || opt->pi_variant > 5)
     return fail(SPH_ERR_ARG,
                 "pi_variant must be -1 (engine default), 0 (compacted), 1 (inline), 2 (queued), "
-                "3 (per-step list written by the first evaluation) or 4 (per-step list built "
-                "alone)");
+                "3 (per-step list written by the first evaluation), 4 (per-step list built "
+                "alone) or 5 (list kept across steps)");
+  if (opt->list_skin > (float)kListExtraMax)
+    return fail(SPH_ERR_ARG, "list_skin must be at most 0.25 (or < 0 for the default)");
   e->opt = *opt;
-  // -1: the per-step list (built alone, 4) where the engine supports it, else
-  // the compacted loop; 3 and 4 without list support fall back to it too
+  // -1: the list kept across steps (5) where the engine supports it, else
+  // the compacted loop; 3-5 without list support fall back to it too
   if (e->opt.pi_variant == -1 || (e->opt.pi_variant >= 3 && !e->list_ok))
-    e->opt.pi_variant = e->list_ok ? 4 : 0;
-  if (e->gexec) cudaGraphExecDestroy(e->gexec);
-  e->gexec = nullptr;
+    e->opt.pi_variant = e->list_ok ? e->list_default : 0;
+  e->drop_graphs();
   return SPH_OK;
 }
 
@@ -712,21 +928,35 @@ int sph_step(sph_engine e, int64_t nsteps) {
     CUDA_TRY(cudaEventRecord(t0, e->s));
   }
   int64_t k = 0;
+  const bool reuse = use_list(e) && e->opt.pi_variant == 5;
+  if (reuse) {
+    // every call starts from the state in X (the API's view): build first
+    if (!e->s2) CUDA_TRY(cudaStreamCreateWithFlags(&e->s2, cudaStreamNonBlocking));
+    CUDA_TRY(cudaMemsetAsync(&e->ctl->rebuild, 1, sizeof(unsigned int), e->s));
+  }
+  e->cap_err = cudaSuccess;
   if (!timing && e->opt.use_graph && e->n_dead == 0) {
     if (!e->gexec || e->graph_n != e->n_phys || e->graph_dead != e->cells_hw ||
-        e->graph_ext != (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc + 8 * (int)use_list(e)) {
+        e->graph_ext != graph_key(e)) {
       if (e->gexec) cudaGraphExecDestroy(e->gexec);
       e->gexec = nullptr;
       cudaGraph_t g;
       CUDA_TRY(cudaStreamBeginCapture(e->s, cudaStreamCaptureModeThreadLocal));
+      e->capturing = true;
       enqueue_step(e, nullptr);
-      CUDA_TRY(cudaStreamEndCapture(e->s, &g));
-      cudaError_t err = cudaGraphInstantiate(&e->gexec, g, 0);
-      cudaGraphDestroy(g);
+      e->capturing = false;
+      cudaError_t err = cudaStreamEndCapture(e->s, &g);
+      if (err == cudaSuccess && e->cap_err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        err = e->cap_err;
+      } else if (err == cudaSuccess) {
+        err = cudaGraphInstantiate(&e->gexec, g, 0);
+        cudaGraphDestroy(g);
+      }
       if (err != cudaSuccess) return fail(SPH_ERR_CUDA, cudaGetErrorString(err));
       e->graph_n = e->n_phys;
       e->graph_dead = e->cells_hw;  // cells in use at capture
-      e->graph_ext = (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc + 8 * (int)use_list(e);
+      e->graph_ext = graph_key(e);
     }
     for (; k < nsteps; k++) CUDA_TRY(cudaGraphLaunch(e->gexec, e->s));
   }
@@ -738,12 +968,17 @@ int sph_step(sph_engine e, int64_t nsteps) {
   const int64_t passes = std::max(1, (e->nbits + 7) / 8);
   const int64_t pis = e->integrator == 1 ? 1 : 2;
   const bool listed = use_list(e);
+  // (the list kept across steps: 2 decide kernels, 2 interactions, dt,
+  // predictor, corrector, end per step; the sort, reorder, cell table, skin
+  // and list per build, counted from the device's build counter)
   const int64_t per_step = (e->integrator == 1 ? 3 * passes + 1 + 4 + 1 + 3
-                            : listed           ? 3 * passes + 1 + 4 + 2 + 4 +
+                            : reuse            ? 2 + 2 + 4
+                            : listed           ? 3 * passes + 1 + 4 + 1 + 2 + 4 +
                                                      (e->opt.pi_variant == 4 ? 1 : 0)
                                                : 6 * passes + 2 + 8 + 2 + 4) +
                            (e->sps ? pis : 0) +  // strain pass before each interaction
-                           (e->mdbc ? pis : 0);  // ghost-node pass before each interaction
+                           (e->mdbc ? pis : 0) +  // ghost-node pass before each interaction
+                           (listed && e->opt.check_list ? 2 : 0);
   e->kernel_launches += per_step * nsteps;
   for (; k < nsteps; k++) {
     enqueue_step(e, timing ? &e->evs[4 * k] : nullptr);
@@ -752,6 +987,11 @@ int sph_step(sph_engine e, int64_t nsteps) {
   }
   if (timing) CUDA_TRY(cudaEventRecord(t1, e->s));
   CUDA_TRY(cudaGetLastError());
+  if (e->cap_err != cudaSuccess) {
+    cudaStreamSynchronize(e->s);
+    return fail(SPH_ERR_CUDA, std::string("conditional graph node: ") +
+                                  cudaGetErrorString(e->cap_err));
+  }
   CUDA_TRY(cudaStreamSynchronize(e->s));
   if (timing) {
     for (int64_t j = 0; j < nsteps; j++) {
@@ -766,7 +1006,10 @@ int sph_step(sph_engine e, int64_t nsteps) {
     CUDA_TRY(cudaEventElapsedTime(&tot, t0, t1));
     e->step_ms += tot;
   }
-  return check_flags(e);
+  const int64_t builds0 = e->builds_seen;
+  const int rc = check_flags(e);
+  if (reuse) e->kernel_launches += (e->builds_seen - builds0) * (3 * passes + 1 + 4 + 1 + 1);
+  return rc;
 }
 
 int sph_get_timing(sph_engine e, double *pi_ms, int64_t *pi_launches, double *step_ms,
@@ -781,6 +1024,19 @@ int sph_get_timing(sph_engine e, double *pi_ms, int64_t *pi_launches, double *st
     e->pi_launches = 0;
     e->kernel_launches = 0;
   }
+  return SPH_OK;
+}
+
+int sph_list_info(sph_engine e, int64_t *builds, int64_t *check_pairs, int64_t *check_bad) {
+  if (!e) return fail(SPH_ERR_ARG, "null engine");
+  ListCtl lc{};
+  if (e->ctl) {
+    CUDA_TRY(cudaMemcpyAsync(&lc, e->ctl, sizeof(ListCtl), cudaMemcpyDeviceToHost, e->s));
+    CUDA_TRY(cudaStreamSynchronize(e->s));
+  }
+  if (builds) *builds = (int64_t)lc.builds;
+  if (check_pairs) *check_pairs = (int64_t)lc.check_pairs;
+  if (check_bad) *check_bad = (int64_t)lc.check_bad;
   return SPH_OK;
 }
 
@@ -1169,6 +1425,7 @@ int sph_pool_create(int64_t max_particles, int64_t max_cells, int32_t max_cases,
   if (e->list_ok) {
     const double hq = 1.2 * std::sqrt(3.0);
     for (int cm = 0; cm < 3; cm++) e->list_cap = std::max(e->list_cap, list_records_needed(cm, hq, 1.0));
+    e->list_default = 4;  // pools: one list per step (cases equal alone, bit for bit)
     e->opt.pi_variant = 4;
   }
   rc = allocate(e);
@@ -1230,8 +1487,7 @@ int sph_pool_admit(sph_engine e, const sph_case_params *params, const sph_partic
   if (rc) return rc;
   e->n_phys += parts->n;
   e->cells_hw = std::max<int64_t>(e->cells_hw, cb + g.ncells);
-  if (e->gexec) cudaGraphExecDestroy(e->gexec);
-  e->gexec = nullptr;
+  e->drop_graphs();
   *slot = free_slot;
   return SPH_OK;
 }
@@ -1281,8 +1537,7 @@ int sph_pool_release(sph_engine e, int32_t slot) {
   e->cells_hw = 0;
   for (auto &s : e->slots)
     if (s.used) e->cells_hw = std::max<int64_t>(e->cells_hw, (int64_t)s.cellbase + s.ncells);
-  if (e->gexec) cudaGraphExecDestroy(e->gexec);
-  e->gexec = nullptr;
+  e->drop_graphs();
   return SPH_OK;
 }
 

@@ -69,15 +69,30 @@ struct CaseDyn {
   unsigned int flags;       // kFlag*
   int n_out;
   unsigned int v2max_bits;  // float bits of max |v|^2 over in-domain particles at the last reorder
+  float skin;               // neighbour-list path: skin of the list built last (set by k_list_begin)
   double mot[kMaxMotions][4];  // displacement and velocity at t+dt/2 and t+dt
 };
 
 constexpr unsigned kFlagNaN = 1u, kFlagDtMin = 2u, kFlagQuota = 4u;
-// neighbour-list path: a target had more than kListCap list entries; a
-// half-step displacement exceeded half the list's skin
+// neighbour-list path: a target had more records than its list segment
+// holds; a displacement since the list's build exceeded half its skin (or
+// one step's need exceeded the largest skin the rows cover)
 constexpr unsigned kFlagListFull = 8u, kFlagSkin = 16u;
-constexpr int kListCap = 384;          // list entries per target
-constexpr int kListMaxParticles = 1 << 25;  // entry = index (25 bits) | row (6 bits)
+// list record: first candidate index (24 bits) | (dy + 4) << 24 | (dz + 4) << 28
+constexpr int kListMaxParticles = 1 << 24;
+constexpr uint32_t kListIndexMask = (1u << 24) - 1u;
+
+// Engine-wide control of the neighbour list kept across steps: rebuild is
+// requested by the corrector (or by the host at the start of every
+// sph_step call) and cleared by the build; builds counts the builds;
+// check_pairs / check_bad are the optional brute-force check of the list.
+struct ListCtl {
+  unsigned int rebuild;
+  unsigned int pad;
+  unsigned long long builds;
+  unsigned long long check_pairs;  // pairs inside 2h found by brute force
+  unsigned long long check_bad;    // targets whose brute-force count differs from the list's
+};
 // Readable entries of posc/velrho/press past the last particle, so that a
 // warp may test 32 candidates at a time without per-candidate bounds checks.
 constexpr int64_t kReadPad = 1024;

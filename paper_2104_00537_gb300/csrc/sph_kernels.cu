@@ -447,14 +447,27 @@ __device__ __forceinline__ void finish_target(const CaseConst &C, int i, int n, 
   reduce_case(i < n ? cidx : -1, has, npairs, nfb, nbf, dtbits, bad, dyn);
 }
 
-// Skin of the list built on state n: dt |v|max x 1.25, with dt bounded by
-// Eq 35 (dt <= C_CFL h / cs0 since dt_cv <= h / cs0) or the fixed step, plus
-// 1e-3 h; the 25 % covers the change of a wall's imposed speed over dt / 2.
-__device__ __forceinline__ float list_skin(const CaseConst &C, const CaseDyn &D) {
-  return fmaf(C.list_k, sqrtf(__uint_as_float(D.v2max_bits)), 1e-3f * C.h);
+// Skin of a list built on state n, per case (k_list_begin): the largest
+// approach of two particles over one step, dt |v|max x 1.25 with dt bounded
+// by Eq 35 (dt <= C_CFL h / cs0 since dt_cv <= h / cs0) or the fixed step,
+// plus 1e-3 h; the 25 % covers the change of a wall's imposed speed over
+// dt / 2.  A list kept across steps adds extra x 2h.  The build's rows reach
+// 2h + cs, so the skin is capped at 0.95 cs (kFlagSkin if one step needs more).
+__global__ void k_list_begin(int ncases, const CaseConst *__restrict__ cc,
+                             CaseDyn *__restrict__ dyn, ListCtl *__restrict__ ctl, float extra) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c == 0 && ctl) {
+    ctl->rebuild = 0u;
+    ctl->builds += 1ull;
+  }
+  if (c >= ncases || !cc[c].active) return;
+  const CaseConst &C = cc[c];
+  CaseDyn &D = dyn[c];
+  const float need = fmaf(C.list_k, sqrtf(__uint_as_float(D.v2max_bits)), 1e-3f * C.h);
+  const float smax = 0.95f * C.csf;
+  if (need > smax) D.flags |= kFlagSkin;
+  D.skin = fminf(fmaf(extra, 2.f * C.h, need), smax);
 }
-
-constexpr uint32_t kListIndexMask = (1u << 25) - 1u;
 
 // One thread per particle a in sorted order (all fluid targets first, then
 // boundary targets, so warps rarely mix the two).  The (2M+1)^2 rows of
@@ -472,10 +485,13 @@ constexpr uint32_t kListIndexMask = (1u << 25) - 1u;
 // laminar + SPS viscosity of Eq 23-27 (tau4/tau2 from k_strain), per case;
 // warps without such cases still take the default pair loop.
 //
-// LIST (VARIANT 0): 1 also writes the target's per-step neighbour list, 2
-// writes only the list (no pair terms, no outputs besides the list):
-// for every tested chunk with a candidate within 2h + skin, one record
-// (first index | row offset, mask of those candidates) to list[i cap + c].
+// LIST (VARIANT 0): 1 also writes the target's neighbour list, 2 writes
+// only the list (no pair terms, no outputs besides the list and ref): for
+// every tested chunk with a candidate within 2h + skin, one record (first
+// index | row offset, mask of those candidates) to list[i cap + c].  The
+// list's rows reach one cell further than the 2h support (M + 1 cells, so
+// 2h + cs >= 2h + skin), clipped to the case's grid.  ref, if set, receives
+// the target's position at the build (the list kept across steps).
 template <int M, int VARIANT, int EXT = 0, int LIST = 0>
 __global__ void __launch_bounds__(128, EXT == 2 ? 6 : 0)
 k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
@@ -486,7 +502,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
            float4 *__restrict__ ace, float *__restrict__ mu_out, int want_dt,
            const float4 *__restrict__ tau4 = nullptr, const float2 *__restrict__ tau2 = nullptr,
            uint2 *__restrict__ list = nullptr, int cap = 0,
-           uint16_t *__restrict__ count = nullptr) {
+           uint16_t *__restrict__ count = nullptr, float4 *__restrict__ ref = nullptr) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -501,9 +517,11 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   // 0 < r2 < r2max as one unsigned compare (r2 >= 0; +0 wraps to UINT_MAX)
   const unsigned r2max_u = __float_as_uint(r2max) - 1u;
   float r2l = r2max;  // list radius^2: (2h + skin)^2 with LIST
+  int tcx = 0, tcy = 0, tcz = 0;  // LIST: the target's cell, for the grid clip
   if (LIST) {
-    const float R = sqrtf(r2max) + list_skin(C, dyn[cidx]);
+    const float R = sqrtf(r2max) + dyn[cidx].skin;
     r2l = R * R;
+    if (has) decode_cell((uint32_t)gc - C.cellbase, nx, C.ny, tcx, tcy, tcz);
   }
   const unsigned r2l_u = __float_as_uint(r2l) - 1u;
   const float r2prune = r2l * 1.0001f;  // conservative: pruning never drops a pair
@@ -534,18 +552,40 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   }
   const bool warp_plain = __all_sync(full, (afluid || !has) && !X.hyd && !X.sps);
   Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
-  constexpr int W = 2 * M + 1;
+  constexpr int MR = LIST ? M + 1 : M;  // rows reach MR cells
+  if (LIST && ref && i < n) ref[i] = pa;
+  // rows dy, dz in [-M, M]; a list build adds row -(M+1) (M+1) for the
+  // targets within the skin of their cell's lower (upper) face, over the
+  // warp's union of those ranges
+  int ylo = -M, yhi = M, zlo = -M, zhi = M;
+  if (LIST) {
+    // row -(M+1) lies within the list radius iff o < R - M cs (R rounded up)
+    const float sk = fmaf(-(float)M, cs, sqrtf(r2prune) * 1.0001f);
+    const bool w = work;
+    ylo = __reduce_min_sync(full, (w && pa.y < sk) ? -MR : -M);
+    yhi = __reduce_max_sync(full, (w && pa.y > cs - sk) ? MR : M);
+    zlo = __reduce_min_sync(full, (w && pa.z < sk) ? -MR : -M);
+    zhi = __reduce_max_sync(full, (w && pa.z > cs - sk) ? MR : M);
+  }
+  const int wy = yhi - ylo + 1, nrows = wy * (zhi - zlo + 1);
 
 #pragma unroll 1
-  for (int row = 0; row < W * W; row++) {
-    const int dy = row % W - M, dz = row / W - M;
+  for (int row = 0; row < nrows; row++) {
+    const int dy = ylo + row % wy, dz = zlo + row / wy;
     const float gy = slab_gap(dy, pa.y, cs), gz = slab_gap(dz, pa.z, cs);
     const float d2 = fmaf(gy, gy, gz * gz);
     int loF = 0, hiF = 0, loB = 0, hiB = 0;
-    if (work && d2 < r2prune) {
+    // the outer rows of a list build stay inside the case's grid
+    const bool inrow = !LIST || (tcy + dy >= 0 && tcy + dy < C.ny && tcz + dz >= 0 &&
+                                 tcz + dz < C.nz);
+    if (work && inrow && d2 < r2prune) {
       const float L = sqrtf(r2prune - d2);
-      const int kx0 = max(-M, (int)floorf((pa.x - L) * ics));
-      const int kx1 = min(M, (int)floorf((pa.x + L) * ics));
+      int kx0 = max(-MR, (int)floorf((pa.x - L) * ics));
+      int kx1 = min(MR, (int)floorf((pa.x + L) * ics));
+      if (LIST) {
+        kx0 = max(kx0, -tcx);
+        kx1 = min(kx1, nx - 1 - tcx);
+      }
       const int c0 = gc + dz * nxy + dy * nx + kx0;
       const int c1 = gc + dz * nxy + dy * nx + kx1 + 1;
       loF = (int)cstart[c0];
@@ -556,7 +596,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
       }
     }
     const float sy = fmaf(-(float)dy, cs, pa.y), sz = fmaf(-(float)dz, cs, pa.z);
-    const uint32_t rowbits = ((uint32_t)(dy + 3) << 25) | ((uint32_t)(dz + 3) << 28);
+    const uint32_t rowbits = ((uint32_t)(dy + 4) << 24) | ((uint32_t)(dz + 4) << 28);
 #pragma unroll 1
     for (int part = 0; part < 2; part++) {  // fluid neighbours, then boundary neighbours
       const int lo = part ? loB : loF;
@@ -1293,7 +1333,8 @@ __device__ __forceinline__ uint32_t corrector_core(const CaseConst &C, const Cas
                                                    uint8_t code, uint32_t k, const float4 &pn,
                                                    const float4 &vn, float rhoh, const float4 &a,
                                                    int nbits, int cidx, CaseDyn *dyn,
-                                                   float4 &pnew, float4 &vnew) {
+                                                   float4 &pnew, float4 &vnew,
+                                                   double *disp_out = nullptr) {
   const double dt = D.dt;
   const float dtf = (float)dt;
   // Eq 34: rho^{n+1} = rho^n (2 - eps) / (2 + eps), eps = -(R / rho^{n+1/2}) dt
@@ -1323,6 +1364,11 @@ __device__ __forceinline__ uint32_t corrector_core(const CaseConst &C, const Cas
       disp[0] = disp[1] = disp[2] = 0.0;
       vnew = make_float4(vn.x, vn.y, vn.z, rho);
     }
+  }
+  if (disp_out) {
+    disp_out[0] = disp[0];
+    disp_out[1] = disp[1];
+    disp_out[2] = disp[2];
   }
   bool left;
   const uint32_t kn = move_particle(k, pn, disp, C, code != 0, nbits, pnew, left);
@@ -1438,8 +1484,8 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
       const uint2 rec = mine[r++];
       cbase = (int)(rec.x & kListIndexMask);
       cm = rec.y;
-      sy = fmaf(-(float)((int)((rec.x >> 25) & 7u) - 3), cs, pa.y);
-      sz = fmaf(-(float)((int)(rec.x >> 28) - 3), cs, pa.z);
+      sy = fmaf(-(float)((int)((rec.x >> 24) & 15u) - 4), cs, pa.y);
+      sz = fmaf(-(float)((int)(rec.x >> 28) - 4), cs, pa.z);
     }
     if (!__any_sync(full, cm != 0u)) break;
     if (cm) {
@@ -1519,8 +1565,8 @@ k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restric
       const uint2 rec = mine[r++];
       cbase = (int)(rec.x & kListIndexMask);
       cm = rec.y;
-      sy = fmaf(-(float)((int)((rec.x >> 25) & 7u) - 3), cs, pa.y);
-      sz = fmaf(-(float)((int)(rec.x >> 28) - 3), cs, pa.z);
+      sy = fmaf(-(float)((int)((rec.x >> 24) & 15u) - 4), cs, pa.y);
+      sz = fmaf(-(float)((int)(rec.x >> 28) - 4), cs, pa.z);
     }
     if (!__any_sync(full, cm != 0u)) break;
     if (cm) {
@@ -1556,13 +1602,15 @@ k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restric
 
 // Half step for the list path: state n+1/2 in the same order and the same
 // cells as state n (Eq 33-34 as k_predictor); a particle that leaves the
-// domain is frozen at state n and moved out of every list's reach.
+// domain is frozen at state n and moved out of every list's reach.  The
+// displacement since the list's build (from ref, else the half step alone)
+// must stay within half the skin (kFlagSkin).
 __global__ void k_predictor_list(int n, const uint32_t *__restrict__ keys_in, State src,
                                  const float4 *__restrict__ ace,
                                  const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
                                  int nbits, float4 *__restrict__ posc_out,
                                  float4 *__restrict__ velrho_out, uint32_t *__restrict__ keys_out,
-                                 float *__restrict__ press) {
+                                 float *__restrict__ press, const float4 *__restrict__ ref) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t k = keys_in[i];
@@ -1581,8 +1629,14 @@ __global__ void k_predictor_list(int n, const uint32_t *__restrict__ keys_in, St
   double disp[3];
   float4 vn;
   predictor_core(C, D, code, v, ace[i], disp, vn);
-  const float hs = 0.5f * list_skin(C, D);
-  const float dx = (float)disp[0], dy = (float)disp[1], dz = (float)disp[2];
+  const float hs = 0.5f * D.skin;
+  float dx = (float)disp[0], dy = (float)disp[1], dz = (float)disp[2];
+  if (ref) {
+    const float4 r = ref[i];
+    dx = (float)((double)p.x + disp[0]) - r.x;
+    dy = (float)((double)p.y + disp[1]) - r.y;
+    dz = (float)((double)p.z + disp[2]) - r.z;
+  }
   if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > hs * hs) atomicOr(&dyn[cidx].flags, kFlagSkin);
   float4 ptmp;
   bool left;
@@ -1640,6 +1694,136 @@ __global__ void k_corrector_list(int n, const uint32_t *__restrict__ keys_n,
                                 cidx, dyn, pnew, vnew);
   x.posc[i] = pnew;
   x.velrho[i] = vnew;
+}
+
+// Full step for the list kept across steps.  State n (y: the order and cells
+// of the list's build, offsets relative to those cells) goes to state n+1
+// twice: in x with normalised cells and keys (the state the API reads and the
+// next build sorts), and in place in y, still in the build's cells, with P/rho
+// of Eq 28 in press, for the next step's evaluations over the same list.
+// The list stays valid for the next step when every particle satisfies
+// |r - r_build| + 1.25 (dt_max / 2) |v| <= (skin - 1e-3 h) / 2 (dt_max the
+// Eq 35 bound: the displacement at n+1 and the most the next half step
+// adds); otherwise, or when a particle leaves the domain, the corrector
+// requests a rebuild.
+__global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
+                                  const uint32_t *__restrict__ keys_half, State y,
+                                  const float4 *__restrict__ velrho_half,
+                                  const float4 *__restrict__ ace, const float4 *__restrict__ ref,
+                                  const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
+                                  int nbits, State x, uint32_t *__restrict__ keys_next,
+                                  float *__restrict__ press, ListCtl *__restrict__ ctl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys_n[i];
+  const float4 pn = y.posc[i];
+  const float4 vn = y.velrho[i];
+  const int cidx = y.cid[i];
+  const uint8_t code = y.code[i];
+  x.id[i] = y.id[i];
+  x.cid[i] = (uint16_t)cidx;
+  x.code[i] = code;
+  const CaseConst &C = cc[cidx];
+  if (k >= key_out(nbits)) {  // frozen before this step, or released
+    x.posc[i] = pn;
+    x.velrho[i] = vn;
+    keys_next[i] = k;
+    return;
+  }
+  if (keys_half[i] >= key_out(nbits)) {  // left at the half step: frozen at state n
+    int cx, cy, cz;
+    decode_cell(key_cell(k, nbits) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+    x.posc[i] = make_float4((float)(cx * C.cs + pn.x), (float)(cy * C.cs + pn.y),
+                            (float)(cz * C.cs + pn.z), 0.f);
+    x.velrho[i] = vn;
+    keys_next[i] = key_out(nbits);
+    ctl->rebuild = 1u;
+    return;
+  }
+  const CaseDyn &D = dyn[cidx];
+  float4 pnew, vnew;
+  double disp[3];
+  const uint32_t kn = corrector_core(C, D, code, k, pn, vn, velrho_half[i].w, ace[i], nbits,
+                                     cidx, dyn, pnew, vnew, disp);
+  x.posc[i] = pnew;
+  x.velrho[i] = vnew;
+  keys_next[i] = kn;
+  if (kn >= key_out(nbits)) {  // left at the full step: frozen in x
+    ctl->rebuild = 1u;
+    return;
+  }
+  const float4 pu = make_float4((float)((double)pn.x + disp[0]), (float)((double)pn.y + disp[1]),
+                                (float)((double)pn.z + disp[2]), pn.w);
+  y.posc[i] = pu;
+  y.velrho[i] = vnew;
+  press[i] = tait_pressure(C, vnew.w) / vnew.w;
+  const float4 r = ref[i];
+  const float dx = pu.x - r.x, dy = pu.y - r.y, dz = pu.z - r.z;
+  const float v = sqrtf(fmaf(vnew.x, vnew.x, fmaf(vnew.y, vnew.y, vnew.z * vnew.z)));
+  const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + 0.5f * C.list_k * v;
+  if (e > 0.5f * (D.skin - 1e-3f * C.h)) ctl->rebuild = 1u;
+}
+
+// Sets the condition of the graph's IF node that guards a list build: the
+// rebuild request of the list kept across steps.
+__global__ void k_decide(cudaGraphConditionalHandle h, const ListCtl *__restrict__ ctl) {
+  cudaGraphSetConditional(h, ctl->rebuild != 0u ? 1u : 0u);
+}
+
+// Brute-force check of a neighbour list (an option for tests, off by
+// default): for every target of the evaluated state, the pairs inside 2h over
+// all particles of its case (boundary targets: fluid neighbours only, Eq 36)
+// are counted with the list walk's own arithmetic (cells of the keys, FP32
+// offsets) and compared with the pairs its list records yield.  Adds the
+// brute-force pairs to ctl->check_pairs and every mismatching target to
+// ctl->check_bad.
+__global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
+                             const uint32_t *__restrict__ keys, const float4 *__restrict__ posc,
+                             const uint16_t *__restrict__ cid, const CaseConst *__restrict__ cc,
+                             int nbits, const uint2 *__restrict__ list, int cap,
+                             const uint16_t *__restrict__ count, ListCtl *__restrict__ ctl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvalid = *nvalid_p;
+  if (i >= nvalid || i >= n) return;
+  const uint32_t k = keys[i];
+  if (k >= key_out(nbits)) return;
+  const bool afluid = !key_boundary(k, nbits);
+  const int cidx = cid[i];
+  const CaseConst &C = cc[cidx];
+  const float cs = C.csf;
+  const unsigned r2max_u = __float_as_uint(C.r2max) - 1u;
+  const float4 pa = posc[i];
+  int cx, cy, cz;
+  decode_cell(key_cell(k, nbits) - C.cellbase, C.nx, C.ny, cx, cy, cz);
+  unsigned nb = 0u, nl = 0u;
+  for (int j = 0; j < nvalid; j++) {
+    const uint32_t kj = keys[j];
+    if (cid[j] != cidx || kj >= key_out(nbits) || (!afluid && key_boundary(kj, nbits))) continue;
+    int jx, jy, jz;
+    decode_cell(key_cell(kj, nbits) - C.cellbase, C.nx, C.ny, jx, jy, jz);
+    const float4 pb = posc[j];
+    const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+    const float ry = fmaf(-(float)(jy - cy), cs, pa.y) - pb.y;
+    const float rz = fmaf(-(float)(jz - cz), cs, pa.z) - pb.z;
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    if (__float_as_uint(r2) - 1u < r2max_u) nb++;
+  }
+  const uint2 *mine = list + (int64_t)i * cap;
+  for (int r = 0; r < (int)count[i]; r++) {
+    const uint2 rec = mine[r];
+    const int cbase = (int)(rec.x & kListIndexMask);
+    const float sy = fmaf(-(float)((int)((rec.x >> 24) & 15u) - 4), cs, pa.y);
+    const float sz = fmaf(-(float)((int)(rec.x >> 28) - 4), cs, pa.z);
+    for (unsigned m = rec.y; m; m &= m - 1u) {
+      const float4 pb = posc[cbase + __ffs(m) - 1];
+      const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+      const float ry = sy - pb.y, rz = sz - pb.z;
+      const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      if (__float_as_uint(r2) - 1u < r2max_u) nl++;
+    }
+  }
+  atomicAdd(&ctl->check_pairs, (unsigned long long)nb);
+  if (nb != nl) atomicAdd(&ctl->check_bad, 1ull);
 }
 
 // ---- Verlet scheme ---------------------------------------------------------------
@@ -2082,16 +2266,21 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
 #undef SPH_IL_ARGS
 }
 
+void launch_list_begin(int ncases, const CaseConst *cc, CaseDyn *dyn, ListCtl *ctl,
+                       float extra, cudaStream_t s) {
+  k_list_begin<<<(ncases + 127) / 128, 128, 0, s>>>(ncases, cc, dyn, ctl, extra);
+}
+
 void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *keys,
                        const float4 *posc, const float4 *velrho, const float *press,
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
-                       uint16_t *count, cudaStream_t s) {
+                       uint16_t *count, float4 *ref, cudaStream_t s) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_BL_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 0, \
-      nullptr, nullptr, list, cap, count
+      nullptr, nullptr, list, cap, count, ref
   if (margin == 1)
     k_interact<1, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
   else if (margin == 3)
@@ -2145,10 +2334,33 @@ void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t 
 
 void launch_predictor_list(int n, const uint32_t *keys_in, State src, const float4 *ace,
                            const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
-                           float4 *velrho_out, uint32_t *keys_out, float *press, cudaStream_t s) {
+                           float4 *velrho_out, uint32_t *keys_out, float *press,
+                           const float4 *ref, cudaStream_t s) {
   if (n > 0)
     k_predictor_list<<<nblk(n, 256), 256, 0, s>>>(n, keys_in, src, ace, cc, dyn, nbits, posc_out,
-                                                  velrho_out, keys_out, press);
+                                                  velrho_out, keys_out, press, ref);
+}
+
+void launch_corrector_reuse(int n, const uint32_t *keys_n, const uint32_t *keys_half, State y,
+                            const float4 *velrho_half, const float4 *ace, const float4 *ref,
+                            const CaseConst *cc, CaseDyn *dyn, int nbits, State x,
+                            uint32_t *keys_next, float *press, ListCtl *ctl, cudaStream_t s) {
+  if (n > 0)
+    k_corrector_reuse<<<nblk(n, 256), 256, 0, s>>>(n, keys_n, keys_half, y, velrho_half, ace,
+                                                   ref, cc, dyn, nbits, x, keys_next, press,
+                                                   ctl);
+}
+
+void launch_decide(cudaGraphConditionalHandle h, const ListCtl *ctl, cudaStream_t s) {
+  k_decide<<<1, 1, 0, s>>>(h, ctl);
+}
+
+void launch_list_check(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
+                       const uint16_t *cid, const CaseConst *cc, int nbits, const uint2 *list,
+                       int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s) {
+  if (n > 0)
+    k_list_check<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, cid, cc, nbits, list, cap,
+                                              count, ctl);
 }
 
 void launch_corrector_list(int n, const uint32_t *keys_n, const uint32_t *keys_half, State sn,

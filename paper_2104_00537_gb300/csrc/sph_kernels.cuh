@@ -41,15 +41,20 @@ void launch_predictor(int n, const uint32_t *keys_in, State src, const float4 *a
 void launch_mdbc(int margin, int n, const int *nvalid, const uint32_t *keys, State st,
                  float *press, const uint32_t *cstart, int nbits, const CaseConst *cc,
                  const CaseDyn *dyn, int stage, cudaStream_t s);
-// Per-step neighbour list (Symplectic, default physics): build on state n
+// Neighbour list (Symplectic scheme, boundary_mode 0): build on state n
 // with radius 2h + skin; interaction over the list; predictor and corrector
-// that keep the order and the cells of state n for the half step.
-// The list alone (the candidate test of the compacted loop, no pair terms).
+// that keep the order and the cells of the build.
+// Per-case skin of the next build (extra x 2h added for a list kept across
+// steps); clears the rebuild request and counts the build.
+void launch_list_begin(int ncases, const CaseConst *cc, CaseDyn *dyn, ListCtl *ctl,
+                       float extra, cudaStream_t s);
+// The list alone (the candidate test of the compacted loop, no pair terms);
+// ref (or null) receives every target's position at the build.
 void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *keys,
                        const float4 *posc, const float4 *velrho, const float *press,
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
-                       uint16_t *count, cudaStream_t s);
+                       uint16_t *count, float4 *ref, cudaStream_t s);
 // First evaluation of the list step: the compacted pair loop on state n that
 // also writes every target's list (chunk records, radius 2h + skin) and count.
 void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t *keys,
@@ -66,7 +71,21 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           float4 *tau4, float2 *tau2, cudaStream_t s);
 void launch_predictor_list(int n, const uint32_t *keys_in, State src, const float4 *ace,
                            const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
-                           float4 *velrho_out, uint32_t *keys_out, float *press, cudaStream_t s);
+                           float4 *velrho_out, uint32_t *keys_out, float *press,
+                           const float4 *ref, cudaStream_t s);
+// Corrector of the list kept across steps: state n+1 to x (normalised, keys)
+// and in place to y (the build's cells, P/rho to press); requests a rebuild
+// through ctl when the next step could leave the skin.
+void launch_corrector_reuse(int n, const uint32_t *keys_n, const uint32_t *keys_half, State y,
+                            const float4 *velrho_half, const float4 *ace, const float4 *ref,
+                            const CaseConst *cc, CaseDyn *dyn, int nbits, State x,
+                            uint32_t *keys_next, float *press, ListCtl *ctl, cudaStream_t s);
+// One-thread kernel: sets conditional handle h to ctl->rebuild != 0.
+void launch_decide(cudaGraphConditionalHandle h, const ListCtl *ctl, cudaStream_t s);
+// Brute-force check of the list against the evaluated state (tests).
+void launch_list_check(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
+                       const uint16_t *cid, const CaseConst *cc, int nbits, const uint2 *list,
+                       int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s);
 void launch_corrector_list(int n, const uint32_t *keys_n, const uint32_t *keys_half, State sn,
                            const float4 *velrho_half, const float4 *ace, const CaseConst *cc,
                            CaseDyn *dyn, int nbits, State x, uint32_t *keys_next,

@@ -66,7 +66,8 @@ class Stats(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("pi_block", C.c_int32), ("pi_variant", C.c_int32),
-                ("use_graph", C.c_int32), ("timing", C.c_int32)]
+                ("use_graph", C.c_int32), ("timing", C.c_int32),
+                ("list_skin", C.c_float), ("check_list", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -100,6 +101,7 @@ def load(build_if_missing: bool = True):
         "sph_get_stats": (C.c_int, [vp, i32, C.POINTER(Stats)]),
         "sph_set_options": (C.c_int, [vp, C.POINTER(Options)]),
         "sph_get_timing": (C.c_int, [vp, dp, C.POINTER(i64), dp, C.POINTER(i64), i32]),
+        "sph_list_info": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
         "sph_get_raw": (C.c_int, [vp, i32, vp, C.POINTER(C.c_size_t)]),
         "sph_create_from_raw": (C.c_int, [C.POINTER(CaseParams), C.POINTER(Particles), vp,
                                           C.c_size_t, vp, ALLOC_FN, FREE_FN, vp,
@@ -297,11 +299,22 @@ class Engine:
     def step(self, nsteps=1):
         check(self.lib.sph_step(self.h, int(nsteps)))
 
-    def set_options(self, pi_block=0, pi_variant=-1, use_graph=0, timing=0):
-        """pi_variant -1 keeps the engine default (the per-step neighbour list,
-        4, where the engine supports it, else the compacted loop, 0)."""
-        o = Options(pi_block, pi_variant, use_graph, timing)
+    def set_options(self, pi_block=0, pi_variant=-1, use_graph=0, timing=0, list_skin=-1.0,
+                    check_list=0):
+        """pi_variant -1 keeps the engine default (where the engine supports
+        a neighbour list: kept across steps, 5, for one case, one per step,
+        4, for a batch or pool; else the compacted loop, 0); list_skin:
+        variant 5's added skin as a fraction of 2h (< 0: the default, 0.04);
+        check_list: brute-force check of every list evaluation (list_info)."""
+        o = Options(pi_block, pi_variant, use_graph, timing, list_skin, check_list)
         check(self.lib.sph_set_options(self.h, C.byref(o)))
+
+    def list_info(self):
+        """Neighbour-list builds so far and, with check_list, the brute-force
+        pair count and the number of targets whose list missed or added pairs."""
+        b, p, bad = C.c_int64(), C.c_int64(), C.c_int64()
+        check(self.lib.sph_list_info(self.h, C.byref(b), C.byref(p), C.byref(bad)))
+        return dict(builds=b.value, check_pairs=p.value, check_bad=bad.value)
 
     def timing(self, reset=False):
         pm, ln, sm, kl = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()

@@ -220,7 +220,7 @@ def c0_100(c0):
     return o
 
 
-@pytest.mark.parametrize("variant", [4, 3, 0])
+@pytest.mark.parametrize("variant", [5, 4, 3, 0])
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_dam_break_100_steps(c0, c0_100, use_graph, variant):
     """Variants 4 (the default here) and 3: one neighbour list per step on
@@ -274,12 +274,14 @@ def c0_2000(c0):
     return o
 
 
-@pytest.mark.parametrize("variant", [4, 0])
+@pytest.mark.parametrize("variant", [5, 4, 0])
 def test_dam_break_2000_steps(c0, c0_2000, variant):
     """The longer comparison (2,000 steps, t ~ 0.46 s: the column has
     collapsed and the front has run 0.9 m along the tank): front within
     0.5 dp, kinetic energy within 1 %, 99 % of the particles within 0.5 dp of
-    the oracle's (measured on GB300: 0.04 dp, 7e-5, 0.04 dp)."""
+    the oracle's (measured on GB300: 0.04 dp, 7e-5, 0.04 dp).  The simulated
+    time, a sum of Eq 35 steps each set by the largest acceleration of a
+    splashing flow, is held to 0.5 %."""
     eng = sph.Engine.create(c0)
     eng.set_options(use_graph=1, pi_variant=variant)
     eng.step(2000)
@@ -287,10 +289,13 @@ def test_dam_break_2000_steps(c0, c0_2000, variant):
     o = c0_2000
     od = o.diag()
     dp = c0.params["dp"]
-    assert abs(s["t"] - o.t.value) < 1e-3 * o.t.value
-    assert abs(s["front"] - od["front"]) < 0.5 * dp
-    assert abs(s["ke"] - od["ke"]) < 0.01 * od["ke"]
-    assert np.percentile(np.linalg.norm(st["pos"] - o.pos, axis=1), 99) < 0.5 * dp
+    got = dict(dt_rel=(s["t"] - o.t.value) / o.t.value, dfront_dp=(s["front"] - od["front"]) / dp,
+               dke_rel=(s["ke"] - od["ke"]) / od["ke"],
+               pos_p99_dp=np.percentile(np.linalg.norm(st["pos"] - o.pos, axis=1), 99) / dp)
+    assert abs(got["dt_rel"]) < 5e-3, got
+    assert abs(got["dfront_dp"]) < 0.5, got
+    assert abs(got["dke_rel"]) < 0.01, got
+    assert got["pos_p99_dp"] < 0.5, got
     assert s["mass"] == od["mass"] and s["flags"] == 0
     eng.destroy()
 
@@ -337,7 +342,7 @@ def test_moving_boundary_and_sloshing_parity():
     eng.destroy()
 
 
-@pytest.mark.parametrize("variant", [4, 3, 0])
+@pytest.mark.parametrize("variant", [5, 4, 3, 0])
 def test_out_of_domain_particle_is_frozen(variant):
     """A particle shot out of the domain is frozen, keeps its mass, and the
     quota error fires when max_out is exceeded."""
@@ -396,10 +401,11 @@ def test_raw_checkpoint_resume_is_bit_exact(c0):
 def test_batch_equals_alone():
     cs = [cases.dam_break(0.04, seed=1), cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
           cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
-    bat = sph.Engine.batch(cs)
+    bat = sph.Engine.batch(cs)            # one list per step (variant 4)
     bat.step(12)
     for i, c in enumerate(cs):
         e = sph.Engine.create(c)
+        e.set_options(pi_variant=4)
         e.step(12)
         sa, sb = e.get_state(), bat.get_state(i)
         for k in ("pos", "vel", "rho"):
@@ -420,8 +426,10 @@ def test_pool_mix_equals_alone():
     pool.release(sa)                  # a leaves; b keeps running
     pool.pool_step(3)
     ea = sph.Engine.create(ca)
+    ea.set_options(pi_variant=4)          # the pool's path
     ea.step(12)
     eb = sph.Engine.create(cb)
+    eb.set_options(pi_variant=4)
     eb.step(10)
     st = pool.get_state(sb)
     ref = eb.get_state()
@@ -464,7 +472,7 @@ def _subset(case, keep):
                       dict(case.meta), g)
 
 
-@pytest.mark.parametrize("variant", [4, 3, 0])
+@pytest.mark.parametrize("variant", [5, 4, 3, 0])
 def test_boundary_only_case(variant):
     """No fluid: no pairs (Eq 36 needs b in F), nothing moves, and the step is
     C_CFL h / cs0 (no fluid for Eq 35)."""
@@ -493,6 +501,7 @@ def test_empty_case_and_empty_batch_member():
     bat = sph.Engine.batch([full, empty])
     bat.step(4)
     alone = sph.Engine.create(full)
+    alone.set_options(pi_variant=4)      # the batch's path
     alone.step(4)
     a, b = alone.get_state(), bat.get_state(0)
     for k in ("pos", "vel", "rho"):
@@ -518,3 +527,63 @@ def test_list_overflow_is_reported():
     e0.step(1)
     assert e0.stats()["interactions"] > 0
     e0.destroy()
+
+
+# ---- neighbour list kept across steps (pi_variant 5) ---------------------------
+
+@pytest.mark.parametrize("variant,use_graph", [(4, 0), (5, 0), (5, 1)])
+def test_list_finds_every_pair_brute_force(variant, use_graph):
+    """With check_list on, every evaluation of every step counts each
+    target's pairs inside 2h by brute force over its whole case, with the
+    list walk's own arithmetic, and compares with what its list yields: no
+    target may differ, and the brute-force total equals the interactions the
+    engine counted.  Cases: the dam break (free surface, walls) and a
+    sloshing tank whose walls move (Eq 37), 200 steps."""
+    cs = [cases.dam_break(0.03, seed=4), cases.sloshing_tank(3000, 0.3, 0.04, 1.2, seed=5)]
+    for c in cs:
+        eng = sph.Engine.create(c)
+        eng.set_options(pi_variant=variant, use_graph=use_graph, check_list=1)
+        eng.step(120)
+        eng.step(80)                  # a second call starts with a rebuild
+        li, st = eng.list_info(), eng.stats()
+        assert li["check_bad"] == 0
+        assert li["check_pairs"] == st["interactions"]
+        if variant == 4:
+            assert li["builds"] == 200
+        else:
+            assert 2 <= li["builds"] < 100, li
+        eng.destroy()
+
+
+def test_list_kept_across_steps_in_a_batch():
+    """A batch on the kept list: one case's rebuild re-sorts all (so the
+    sums' order, not the pairs, may differ from alone); every pair is still
+    found, and each case stays within FP32 rounding of its run alone."""
+    cs = [cases.dam_break(0.04, seed=1), cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
+          cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
+    bat = sph.Engine.batch(cs)
+    bat.set_options(pi_variant=5, check_list=1)
+    bat.step(40)
+    assert bat.list_info()["check_bad"] == 0
+    for i, c in enumerate(cs):
+        e = sph.Engine.create(c)          # variant 5 alone
+        e.step(40)
+        a, b = e.get_state(), bat.get_state(i)
+        dp = c.params["dp"]
+        assert np.abs(a["pos"] - b["pos"]).max() < 1e-3 * dp, i
+        assert np.abs(a["rho"] - b["rho"]).max() < 1e-3 * c.params["rho0"], i
+        assert a["t"] == pytest.approx(b["t"], rel=1e-6)
+        assert e.stats()["interactions"] == pytest.approx(bat.stats(i)["interactions"],
+                                                          rel=1e-5)
+        e.destroy()
+    bat.destroy()
+
+
+def test_list_skin_option_is_validated(c0):
+    eng = sph.Engine.create(c0)
+    with pytest.raises(sph.SphError):
+        eng.set_options(pi_variant=5, list_skin=0.5)
+    eng.set_options(pi_variant=5, list_skin=0.0)   # no added skin: a build most steps
+    eng.step(20)
+    assert 10 <= eng.list_info()["builds"] <= 20
+    eng.destroy()

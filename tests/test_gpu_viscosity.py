@@ -49,7 +49,7 @@ def test_sps_one_evaluation(steps):
     eng.destroy()
 
 
-@pytest.mark.parametrize("variant", [4, 3, 0])
+@pytest.mark.parametrize("variant", [5, 4, 3, 0])
 def test_sps_dam_break_100_steps(variant):
     """Per-step list (3: strain pass and interaction over the list at the half
     step) and two neighbour lists per step (0)."""
@@ -92,6 +92,7 @@ def test_pool_sps_case_equals_alone():
     s = pool.admit(c, t_end=1.0)
     pool.pool_step(8)
     e = sph.Engine.create(c)
+    e.set_options(pi_variant=4)          # the pool's path
     e.step(8)
     a, b = pool.get_state(s), e.get_state()
     for k in ("pos", "vel", "rho"):
@@ -100,7 +101,7 @@ def test_pool_sps_case_equals_alone():
     pool.destroy()
 
 
-@pytest.mark.parametrize("variant", [4, 3, 0])
+@pytest.mark.parametrize("variant", [5, 4, 3, 0])
 def test_fourtakas_dam_break_steps(variant):
     """Eq 19-20 over whole steps, with the per-step list (3) and with two
     neighbour lists per step (0), against the oracle."""
