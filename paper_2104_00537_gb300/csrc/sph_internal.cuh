@@ -78,9 +78,19 @@ constexpr unsigned kFlagNaN = 1u, kFlagDtMin = 2u, kFlagQuota = 4u;
 // holds; a displacement since the list's build exceeded half its skin (or
 // one step's need exceeded the largest skin the rows cover)
 constexpr unsigned kFlagListFull = 8u, kFlagSkin = 16u;
-// list record: first candidate index (24 bits) | (dy + 4) << 24 | (dz + 4) << 28
-constexpr int kListMaxParticles = 1 << 24;
-constexpr uint32_t kListIndexMask = (1u << 24) - 1u;
+// list record: first candidate index (25 bits) | row code << 25, with the
+// row code (dz + 4) * 9 + (dy + 4) for row offsets dy, dz in [-4, 4]
+constexpr int kListMaxParticles = 1 << 25;
+constexpr uint32_t kListIndexMask = (1u << 25) - 1u;
+__host__ __device__ inline uint32_t list_row_code(int dy, int dz) {
+  return (uint32_t)((dz + 4) * 9 + (dy + 4)) << 25;
+}
+__host__ __device__ inline void list_row_decode(uint32_t x, int &dy, int &dz) {
+  const int r = (int)(x >> 25);
+  const int q = r / 9;
+  dz = q - 4;
+  dy = r - 9 * q - 4;
+}
 
 // Engine-wide control of the neighbour list kept across steps: rebuild is
 // requested by the corrector (or by the host at the start of every

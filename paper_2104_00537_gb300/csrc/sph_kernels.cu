@@ -596,7 +596,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
       }
     }
     const float sy = fmaf(-(float)dy, cs, pa.y), sz = fmaf(-(float)dz, cs, pa.z);
-    const uint32_t rowbits = ((uint32_t)(dy + 4) << 24) | ((uint32_t)(dz + 4) << 28);
+    const uint32_t rowbits = list_row_code(dy, dz);
 #pragma unroll 1
     for (int part = 0; part < 2; part++) {  // fluid neighbours, then boundary neighbours
       const int lo = part ? loB : loF;
@@ -1484,8 +1484,10 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
       const uint2 rec = mine[r++];
       cbase = (int)(rec.x & kListIndexMask);
       cm = rec.y;
-      sy = fmaf(-(float)((int)((rec.x >> 24) & 15u) - 4), cs, pa.y);
-      sz = fmaf(-(float)((int)(rec.x >> 28) - 4), cs, pa.z);
+      int rdy, rdz;
+      list_row_decode(rec.x, rdy, rdz);
+      sy = fmaf(-(float)rdy, cs, pa.y);
+      sz = fmaf(-(float)rdz, cs, pa.z);
     }
     if (!__any_sync(full, cm != 0u)) break;
     if (cm) {
@@ -1565,8 +1567,10 @@ k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restric
       const uint2 rec = mine[r++];
       cbase = (int)(rec.x & kListIndexMask);
       cm = rec.y;
-      sy = fmaf(-(float)((int)((rec.x >> 24) & 15u) - 4), cs, pa.y);
-      sz = fmaf(-(float)((int)(rec.x >> 28) - 4), cs, pa.z);
+      int rdy, rdz;
+      list_row_decode(rec.x, rdy, rdz);
+      sy = fmaf(-(float)rdy, cs, pa.y);
+      sz = fmaf(-(float)rdz, cs, pa.z);
     }
     if (!__any_sync(full, cm != 0u)) break;
     if (cm) {
@@ -1605,6 +1609,7 @@ k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restric
 // domain is frozen at state n and moved out of every list's reach.  The
 // displacement since the list's build (from ref, else the half step alone)
 // must stay within half the skin (kFlagSkin).
+template <bool REF>
 __global__ void k_predictor_list(int n, const uint32_t *__restrict__ keys_in, State src,
                                  const float4 *__restrict__ ace,
                                  const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
@@ -1631,7 +1636,7 @@ __global__ void k_predictor_list(int n, const uint32_t *__restrict__ keys_in, St
   predictor_core(C, D, code, v, ace[i], disp, vn);
   const float hs = 0.5f * D.skin;
   float dx = (float)disp[0], dy = (float)disp[1], dz = (float)disp[2];
-  if (ref) {
+  if (REF) {
     const float4 r = ref[i];
     dx = (float)((double)p.x + disp[0]) - r.x;
     dy = (float)((double)p.y + disp[1]) - r.y;
@@ -1812,8 +1817,10 @@ __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
   for (int r = 0; r < (int)count[i]; r++) {
     const uint2 rec = mine[r];
     const int cbase = (int)(rec.x & kListIndexMask);
-    const float sy = fmaf(-(float)((int)((rec.x >> 24) & 15u) - 4), cs, pa.y);
-    const float sz = fmaf(-(float)((int)(rec.x >> 28) - 4), cs, pa.z);
+    int rdy, rdz;
+    list_row_decode(rec.x, rdy, rdz);
+    const float sy = fmaf(-(float)rdy, cs, pa.y);
+    const float sz = fmaf(-(float)rdz, cs, pa.z);
     for (unsigned m = rec.y; m; m &= m - 1u) {
       const float4 pb = posc[cbase + __ffs(m) - 1];
       const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
@@ -2336,9 +2343,14 @@ void launch_predictor_list(int n, const uint32_t *keys_in, State src, const floa
                            const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
                            float4 *velrho_out, uint32_t *keys_out, float *press,
                            const float4 *ref, cudaStream_t s) {
-  if (n > 0)
-    k_predictor_list<<<nblk(n, 256), 256, 0, s>>>(n, keys_in, src, ace, cc, dyn, nbits, posc_out,
-                                                  velrho_out, keys_out, press, ref);
+  if (n <= 0) return;
+  if (ref)
+    k_predictor_list<true><<<nblk(n, 256), 256, 0, s>>>(n, keys_in, src, ace, cc, dyn, nbits,
+                                                        posc_out, velrho_out, keys_out, press, ref);
+  else
+    k_predictor_list<false><<<nblk(n, 256), 256, 0, s>>>(n, keys_in, src, ace, cc, dyn, nbits,
+                                                         posc_out, velrho_out, keys_out, press,
+                                                         ref);
 }
 
 void launch_corrector_reuse(int n, const uint32_t *keys_n, const uint32_t *keys_half, State y,
