@@ -415,11 +415,14 @@ def main():
             sph.Engine.create(cs[0], stream=stream)
     eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin)
     n_particles = sum(c.n for c in cs)
-    # the engine runs the per-step list (3) where it supports it, unless told otherwise
-    list_ok = (args.integrator == "symplectic" and args.boundary_mode == 0
-               and n_particles < (1 << 25))
-    eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4, 5) else (5 if list_ok else 0)
+    # the pi_variant the engine runs (its default: 5 for one case, 4 for a Symplectic batch)
+    list_ok = args.boundary_mode == 0 and n_particles < (1 << 25)
+    default_var = 5 if len(cs) == 1 else (4 if args.integrator == "symplectic" else 0)
+    eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4, 5) else (
+        default_var if list_ok else 0)
     if eff_var in (3, 4, 5) and not list_ok:
+        eff_var = 0
+    if args.integrator == "verlet" and eff_var in (3, 4):
         eff_var = 0
     kernel = {3: "k_interact_list", 4: "k_interact_list", 5: "k_interact_list"}.get(
         eff_var, "k_interact")

@@ -320,8 +320,18 @@ int list_records_needed(int cell_mode, double h, double dp) {
 // list variant chosen (3, 4: one list per step; 5: kept across steps) and
 // the list allocated.
 bool use_list(sph_engine e) {
-  return e->integrator == 0 && e->list_ok && !e->mdbc && e->opt.pi_variant >= 3 &&
-         e->opt.pi_variant <= 5;
+  if (!e->list_ok || e->mdbc) return false;
+  if (e->integrator == 1) return e->opt.pi_variant == 5;  // Verlet: one PI per step
+  return e->opt.pi_variant >= 3 && e->opt.pi_variant <= 5;
+}
+
+// pi_variant as the engine runs it: -1 takes the engine's default; list
+// variants fall back to the compacted loop (0) where no list applies (no
+// list allocated, or 3 and 4 with the Verlet scheme).
+int resolve_variant(sph_engine e, int v) {
+  if (v == -1) v = e->list_ok ? e->list_default : 0;
+  if (v >= 3 && (!e->list_ok || (e->integrator == 1 && v != 5))) v = 0;
+  return v;
 }
 
 // Key of a captured step graph: everything that changes its launches.
@@ -522,9 +532,9 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     e->sps = e->sps || params[c].visc_mode == 1;
     e->mdbc = e->mdbc || params[c].boundary_mode == 1;
   }
-  // the per-step list serves the Symplectic scheme with DBC (any density
-  // diffusion and viscosity)
-  e->list_ok = e->integrator == 0 && !e->mdbc && np < kListMaxParticles;
+  // the neighbour list serves DBC cases (any density diffusion and
+  // viscosity; the Verlet scheme only with the list kept across steps)
+  e->list_ok = !e->mdbc && np < kListMaxParticles;
   if (e->list_ok) {
     int cap = 32;
     for (int c = 0; c < ncases; c++)
@@ -533,8 +543,8 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     // one case: the list kept across steps; several: one list per step, so
     // that every case of a batch takes the same steps as alone, bit for bit
     e->list_default = ncases == 1 ? 5 : 4;
-    e->opt.pi_variant = e->list_default;
   }
+  e->opt.pi_variant = resolve_variant(e, -1);
   rc = allocate(e);
   int64_t cell0 = 0, p0 = 0;
   for (int c = 0; c < ncases && rc == SPH_OK; c++) {
@@ -764,10 +774,57 @@ void enqueue_step_reuse(sph_engine e, cudaEvent_t *ev) {
   launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
 }
 
+// One Verlet step over the list kept across steps: the guarded sort +
+// reorder + cell table and skin + list (as enqueue_step_reuse), the PI on Y,
+// dt, and the update, which writes state n+1 to X (normalised) and in place to
+// Y and requests a rebuild when a particle is farther than (skin - 1e-3 h)/2
+// from its build position.  ev: 2 events around the PI (the build included).
+void enqueue_step_verlet_reuse(sph_engine e, cudaEvent_t *ev) {
+  const int n = (int)e->n_phys;
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &X = e->S[0], &Y = e->S[1];
+  cudaStream_t s = e->s;
+  const float extra = e->opt.list_skin >= 0.f ? e->opt.list_skin : 0.04f;
+  auto nl_part = [=](cudaStream_t q) {
+    radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, q);
+    launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
+                   X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, q);
+    launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, q);
+  };
+  auto list_part = [=](cudaStream_t q) {
+    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, extra, q);
+    launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
+                      e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
+                      e->list_cap, e->ncount, e->posc_ref, q);
+  };
+  if (e->capturing) {
+    capture_if_rebuild(e, nl_part);
+    capture_if_rebuild(e, list_part);
+  } else {
+    eager_if_rebuild(e, 0, nl_part);
+    if (ev) cudaEventRecord(ev[0], s);
+    eager_if_rebuild(e, 1, list_part);
+  }
+  launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
+                       e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
+                       e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  if (e->opt.check_list)
+    launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
+                      e->list_cap, e->ncount, e->ctl, s);
+  launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
+  launch_verlet_reuse(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, X, e->keysA,
+                      e->posc_ref, e->press, e->ctl, s);
+  launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
+}
+
 // One Symplectic step (all cases).  ev: 4 events around the two PI launches.
 void enqueue_step(sph_engine e, cudaEvent_t *ev) {
   if (e->integrator == 1) {
-    enqueue_step_verlet(e, ev);
+    if (use_list(e))
+      enqueue_step_verlet_reuse(e, ev);
+    else
+      enqueue_step_verlet(e, ev);
     return;
   }
   if (use_list(e)) {
@@ -901,10 +958,7 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
   if (opt->list_skin > (float)kListExtraMax)
     return fail(SPH_ERR_ARG, "list_skin must be at most 0.25 (or < 0 for the default)");
   e->opt = *opt;
-  // -1: the list kept across steps (5) where the engine supports it, else
-  // the compacted loop; 3-5 without list support fall back to it too
-  if (e->opt.pi_variant == -1 || (e->opt.pi_variant >= 3 && !e->list_ok))
-    e->opt.pi_variant = e->list_ok ? e->list_default : 0;
+  e->opt.pi_variant = resolve_variant(e, opt->pi_variant);
   e->drop_graphs();
   return SPH_OK;
 }
@@ -971,14 +1025,14 @@ int sph_step(sph_engine e, int64_t nsteps) {
   // (the list kept across steps: 2 decide kernels, 2 interactions, dt,
   // predictor, corrector, end per step; the sort, reorder, cell table, skin
   // and list per build, counted from the device's build counter)
-  const int64_t per_step = (e->integrator == 1 ? 3 * passes + 1 + 4 + 1 + 3
+  const int64_t per_step = (e->integrator == 1 ? (reuse ? 2 + 1 + 3 : 3 * passes + 1 + 4 + 1 + 3)
                             : reuse            ? 2 + 2 + 4
                             : listed           ? 3 * passes + 1 + 4 + 1 + 2 + 4 +
                                                      (e->opt.pi_variant == 4 ? 1 : 0)
                                                : 6 * passes + 2 + 8 + 2 + 4) +
                            (e->sps ? pis : 0) +  // strain pass before each interaction
                            (e->mdbc ? pis : 0) +  // ghost-node pass before each interaction
-                           (listed && e->opt.check_list ? 2 : 0);
+                           (listed && e->opt.check_list ? pis : 0);
   e->kernel_launches += per_step * nsteps;
   for (; k < nsteps; k++) {
     enqueue_step(e, timing ? &e->evs[4 * k] : nullptr);

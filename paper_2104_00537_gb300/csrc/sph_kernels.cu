@@ -1844,10 +1844,16 @@ __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
 // and v^n, rho^n become dst.vrprev.  Boundary particles: density as above
 // (clamped >= rho0 when set), fixed ones keep r and v, moving ones follow
 // Eq 37 at t + dt.  Cases that take no step (dt = 0) are copied unchanged.
+// REUSE (the list kept across steps): src is the state in the list build's
+// order and cells; state n+1 also goes into src in place (those cells, P/rho
+// to press), and the step requests a rebuild (ctl) when a particle is farther
+// than (skin - 1e-3 h) / 2 from its build position (ref) or leaves the domain.
+template <bool REUSE>
 __global__ void k_verlet(int n, const uint32_t *__restrict__ keys_in, State src,
                          const float4 *__restrict__ ace, const CaseConst *__restrict__ cc,
                          CaseDyn *__restrict__ dyn, int nbits, State dst,
-                         uint32_t *__restrict__ keys_out) {
+                         uint32_t *__restrict__ keys_out, const float4 *__restrict__ ref = nullptr,
+                         float *__restrict__ press = nullptr, ListCtl *__restrict__ ctl = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t k = keys_in[i];
@@ -1908,6 +1914,22 @@ __global__ void k_verlet(int n, const uint32_t *__restrict__ keys_in, State src,
   dst.velrho[i] = vnew;
   dst.vrprev[i] = v;
   keys_out[i] = kn;
+  if (REUSE) {
+    if (left) {
+      ctl->rebuild = 1u;
+      return;
+    }
+    const float4 pu = make_float4((float)((double)p.x + disp[0]), (float)((double)p.y + disp[1]),
+                                  (float)((double)p.z + disp[2]), p.w);
+    src.posc[i] = pu;
+    src.velrho[i] = vnew;
+    src.vrprev[i] = v;
+    press[i] = tait_pressure(C, vnew.w) / vnew.w;
+    const float4 r = ref[i];
+    const float dx = pu.x - r.x, dy = pu.y - r.y, dz = pu.z - r.z;
+    if (sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) > 0.5f * (D.skin - 1e-3f * C.h))
+      ctl->rebuild = 1u;
+  }
 }
 
 // ---- read-out ------------------------------------------------------------------
@@ -2388,7 +2410,17 @@ void launch_verlet(int n, const uint32_t *keys_in, State src, const float4 *ace,
                    const CaseConst *cc, CaseDyn *dyn, int nbits, State dst, uint32_t *keys_out,
                    cudaStream_t s) {
   if (n > 0)
-    k_verlet<<<nblk(n, 256), 256, 0, s>>>(n, keys_in, src, ace, cc, dyn, nbits, dst, keys_out);
+    k_verlet<false><<<nblk(n, 256), 256, 0, s>>>(n, keys_in, src, ace, cc, dyn, nbits, dst,
+                                                 keys_out);
+}
+
+void launch_verlet_reuse(int n, const uint32_t *keys_in, State y, const float4 *ace,
+                         const CaseConst *cc, CaseDyn *dyn, int nbits, State x,
+                         uint32_t *keys_out, const float4 *ref, float *press, ListCtl *ctl,
+                         cudaStream_t s) {
+  if (n > 0)
+    k_verlet<true><<<nblk(n, 256), 256, 0, s>>>(n, keys_in, y, ace, cc, dyn, nbits, x, keys_out,
+                                                ref, press, ctl);
 }
 
 void launch_export(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,

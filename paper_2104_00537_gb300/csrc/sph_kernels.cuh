@@ -94,6 +94,12 @@ void launch_corrector_list(int n, const uint32_t *keys_n, const uint32_t *keys_h
 void launch_verlet(int n, const uint32_t *keys_in, State src, const float4 *ace,
                    const CaseConst *cc, CaseDyn *dyn, int nbits, State dst, uint32_t *keys_out,
                    cudaStream_t s);
+// The same with the list kept across steps: state n+1 also in place into y
+// (the build's cells, P/rho to press); rebuild requested through ctl.
+void launch_verlet_reuse(int n, const uint32_t *keys_in, State y, const float4 *ace,
+                         const CaseConst *cc, CaseDyn *dyn, int nbits, State x,
+                         uint32_t *keys_out, const float4 *ref, float *press, ListCtl *ctl,
+                         cudaStream_t s);
 void launch_corrector(int n, const uint32_t *perm2, const uint32_t *keys_half,
                       const uint32_t *keys_n, State sn, State x, const float4 *ace,
                       const CaseConst *cc, CaseDyn *dyn, int nbits, uint32_t *keys_next,

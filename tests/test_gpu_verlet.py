@@ -33,11 +33,12 @@ def test_verlet_free_fall_gpu(ns):
     eng.destroy()
 
 
+@pytest.mark.parametrize("variant", [5, 0])
 @pytest.mark.parametrize("use_graph", [0, 1])
-def test_verlet_dam_break_100_steps(use_graph):
+def test_verlet_dam_break_100_steps(use_graph, variant):
     c = verlet(cases.dam_break, 0.02, ns=40)
     eng = sph.Engine.create(c)
-    eng.set_options(use_graph=use_graph)
+    eng.set_options(use_graph=use_graph, pi_variant=variant)
     m0 = eng.stats()["mass"]
     eng.step(100)
     s = eng.stats()
@@ -101,10 +102,11 @@ def test_verlet_raw_resume_is_bit_exact():
 def test_verlet_batch_equals_alone():
     cs = [verlet(cases.dam_break, 0.04, seed=1, ns=5),
           verlet(cases.sloshing_tank, 2000, 0.25, 0.02, 1.0, seed=2, ns=7)]
-    bat = sph.Engine.batch(cs)
+    bat = sph.Engine.batch(cs)            # Verlet batches: the compacted loop
     bat.step(12)
     for i, c in enumerate(cs):
         e = sph.Engine.create(c)
+        e.set_options(pi_variant=0)
         e.step(12)
         sa, sb = e.get_state(), bat.get_state(i)
         for k in ("pos", "vel", "rho"):
@@ -120,3 +122,34 @@ def test_verlet_rejected_where_unsupported():
     with pytest.raises(sph.SphError):  # pools run the Symplectic scheme
         pool.admit(verlet(cases.dam_break, 0.04), t_end=1.0)
     pool.destroy()
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_verlet_kept_list_finds_every_pair(use_graph):
+    """The Verlet scheme on the list kept across steps (one PI per step):
+    brute-force check of every evaluation, dam break and moving tank."""
+    for c in (verlet(cases.dam_break, 0.03, seed=4),
+              verlet(cases.sloshing_tank, 3000, 0.3, 0.04, 1.2, seed=5, ns=4)):
+        eng = sph.Engine.create(c)
+        eng.set_options(pi_variant=5, use_graph=use_graph, check_list=1)
+        eng.step(150)
+        li, st = eng.list_info(), eng.stats()
+        assert li["check_bad"] == 0
+        assert li["check_pairs"] == st["interactions"]
+        assert 2 <= li["builds"] < 75, li
+        eng.destroy()
+
+
+def test_verlet_batch_variants_fall_back():
+    """Per-step lists (3, 4) do not apply to the one-PI Verlet step: the
+    engine runs the compacted loop and gives the same state as variant 0."""
+    c = verlet(cases.dam_break, 0.04, seed=2)
+    a, b = sph.Engine.create(c), sph.Engine.create(c)
+    a.set_options(pi_variant=4)
+    b.set_options(pi_variant=0)
+    a.step(10)
+    b.step(10)
+    for k in ("pos", "vel", "rho"):
+        assert np.array_equal(a.get_state()[k], b.get_state()[k]), k
+    a.destroy()
+    b.destroy()
