@@ -59,21 +59,27 @@ def fp32_peak_tflops(mhz=SM_MAX_MHZ):
     return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
-def measured_traffic(cell_mode, workload_name, kernel="k_interact"):
-    """DRAM bytes per interaction launch from the committed ncu capture of
-    `kernel`, or None when the capture does not match (other workload / cell
-    size, or the kernel source changed since the counters were taken)."""
+def measured_traffic(cell_mode, workload_name, variant, builds_per_step=1.0):
+    """DRAM bytes per interaction launch, as bench.py times it, from the
+    committed ncu capture of the list kernels (profiles/k_interact_list_traffic.json),
+    or None when the capture does not match (other workload / cell size /
+    variant, or the kernel source changed since the counters were taken).
+    Variant 4: (build + two evaluations) / 2; variant 5: one evaluation plus
+    half the build times the builds per step."""
     import hashlib
     try:
-        d = json.load(open(os.path.join(ROOT, "profiles", kernel + "_traffic.json")))
+        d = json.load(open(os.path.join(ROOT, "profiles", "k_interact_list_traffic.json")))
         src = open(os.path.join(ROOT, d["source"]), "rb").read()
+        v = d["variants"][str(variant)]
     except (OSError, ValueError, KeyError):
         return None
     if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
         return None
     if workload_name != "dam_break" or cell_mode != 1:
         return None
-    return d["dram_bytes_read"] + d["dram_bytes_write"]
+    if variant == 4:
+        return (v["build_bytes"] + 2 * v["eval_bytes"]) / 2
+    return v["eval_bytes"] + builds_per_step * v["build_bytes"] / 2
 
 
 def workload(name, rank=0, **kw):
@@ -361,7 +367,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
                     help="timed steps (default: 2,000 for the dam break, its whole run "
-                         "from rest; 100 otherwise)")
+                         "from rest; 100 otherwise and for the reference arm)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_break")
@@ -384,8 +390,8 @@ def main():
     ap.add_argument("--t-end", type=float, default=0.1)
     ap.add_argument("--chunk", type=int, default=10)
     args = ap.parse_args()
-    if args.steps is None:
-        args.steps = 2000 if args.workload == "dam_break" else 100
+    if args.steps is None:  # the reference arm's steps are bounded samples: 100 by default
+        args.steps = 2000 if args.workload == "dam_break" and args.impl == "gb300" else 100
     args.warmup = max(3, args.warmup)
     if args.impl != "reference" and args.workload == "batched":
         return run_batched(args)
@@ -477,9 +483,10 @@ def main():
     peak = fp32_peak_tflops()
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": measured_traffic(args.cell_mode, args.workload, kernel)
+                "traffic": measured_traffic(args.cell_mode, args.workload, eff_var,
+                                            builds / args.steps)
                 if (args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) ==
-                (1, "symplectic", 0, 0) and eff_var in (0, 4) else None,
+                (1, "symplectic", 0, 0) and eff_var in (4, 5) else None,
                 "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
                 "pi_ms_per_launch": 1000 * pi_avg_s,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal max clock)"}
