@@ -422,7 +422,7 @@ def main():
     eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin)
     n_particles = sum(c.n for c in cs)
     # the pi_variant the engine runs (its default: 5 for one case, 4 for a Symplectic batch)
-    list_ok = args.boundary_mode == 0 and n_particles < (1 << 25)
+    list_ok = n_particles < (1 << 25)
     default_var = 5 if len(cs) == 1 else (4 if args.integrator == "symplectic" else 0)
     eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4, 5) else (
         default_var if list_ok else 0)

@@ -320,7 +320,7 @@ int list_records_needed(int cell_mode, double h, double dp) {
 // list variant chosen (3, 4: one list per step; 5: kept across steps) and
 // the list allocated.
 bool use_list(sph_engine e) {
-  if (!e->list_ok || e->mdbc) return false;
+  if (!e->list_ok) return false;
   if (e->integrator == 1) return e->opt.pi_variant == 5;  // Verlet: one PI per step
   return e->opt.pi_variant >= 3 && e->opt.pi_variant <= 5;
 }
@@ -332,6 +332,15 @@ int resolve_variant(sph_engine e, int v) {
   if (v == -1) v = e->list_ok ? e->list_default : 0;
   if (v >= 3 && (!e->list_ok || (e->integrator == 1 && v != 5))) v = 0;
   return v;
+}
+
+// The half-step state of the list path: positions and velocity-density of
+// z, everything else (case, code, ghost offsets) of y, same order.
+State half_state(const State &y, const State &z) {
+  State h = y;
+  h.posc = z.posc;
+  h.velrho = z.velrho;
+  return h;
 }
 
 // Key of a captured step graph: everything that changes its launches.
@@ -532,9 +541,9 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     e->sps = e->sps || params[c].visc_mode == 1;
     e->mdbc = e->mdbc || params[c].boundary_mode == 1;
   }
-  // the neighbour list serves DBC cases (any density diffusion and
-  // viscosity; the Verlet scheme only with the list kept across steps)
-  e->list_ok = !e->mdbc && np < kListMaxParticles;
+  // the neighbour list serves every physics option (the Verlet scheme only
+  // with the list kept across steps)
+  e->list_ok = np < kListMaxParticles;
   if (e->list_ok) {
     int cap = 32;
     for (int c = 0; c < ncases; c++)
@@ -602,6 +611,9 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
                  X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, s);
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, s);
+  if (e->mdbc)  // boundary values of Eq 38-39 on state n
+    launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
+                e->ddyn, 0, s);
   if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
     if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, s);
@@ -626,6 +638,9 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
   launch_predictor_list(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
                         e->keysC, e->press, nullptr, s);
+  if (e->mdbc)  // boundary values of Eq 38-39 on state n+1/2 (Y's cells)
+    launch_mdbc(e->margin, nl, e->nvalid, e->keysC, half_state(Y, Z), e->press, e->cstart,
+                e->nbits, e->dconst, e->ddyn, 1, s, true);
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
@@ -751,6 +766,9 @@ void enqueue_step_reuse(sph_engine e, cudaEvent_t *ev) {
     eager_if_rebuild(e, 1, list_part);
   }
   float4 *tau4 = e->sps ? e->tau4 : nullptr;
+  if (e->mdbc)  // boundary values of Eq 38-39 on state n (the build's cells)
+    launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
+                e->ddyn, 0, s, true);
   launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                        e->list_cap, e->ncount, e->ext, tau4, e->tau2, s);
@@ -761,6 +779,9 @@ void enqueue_step_reuse(sph_engine e, cudaEvent_t *ev) {
   launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
   launch_predictor_list(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
                         e->keysC, e->press, e->posc_ref, s);
+  if (e->mdbc)  // boundary values of Eq 38-39 on state n+1/2
+    launch_mdbc(e->margin, nl, e->nvalid, e->keysC, half_state(Y, Z), e->press, e->cstart,
+                e->nbits, e->dconst, e->ddyn, 1, s, true);
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
@@ -805,6 +826,9 @@ void enqueue_step_verlet_reuse(sph_engine e, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[0], s);
     eager_if_rebuild(e, 1, list_part);
   }
+  if (e->mdbc)  // boundary values of Eq 38-39 on state n (the build's cells)
+    launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
+                e->ddyn, 0, s, true);
   launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                        e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
@@ -1515,6 +1539,7 @@ int sph_pool_admit(sph_engine e, const sph_case_params *params, const sph_partic
   e->mdbc = e->mdbc || params->boundary_mode == 1;
   if (e->list_ok && list_records_needed(params->cell_mode, params->h, params->dp) > e->list_cap)
     e->list_ok = false;  // from now on the pool runs two neighbour lists per step
+  e->opt.pi_variant = resolve_variant(e, e->opt.pi_variant);
   if (used == 0) e->margin = g.margin;
   if (g.margin != e->margin) return fail(SPH_ERR_ARG, "cell_mode differs from the pool's cases");
   int free_slot = -1;

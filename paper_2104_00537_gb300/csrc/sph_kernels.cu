@@ -1017,7 +1017,10 @@ constexpr double kMdbcDetMin = 1e-3;  // |det| below: Shepard value, zero gradie
 // run over fluid particles within 2h of r_G, found from the ghost's own cell
 // (rows clamped to the grid).  stage selects the time of the imposed wall
 // velocity: t (0) or t + dt/2 (1).  Also refreshes P/rho of the particle.
-template <int M>
+// LIST: the state is in the cells of a neighbour list's build, particles up
+// to half the skin outside them, so the rows reach M + 1 cells and prune at
+// 2h + skin/2.
+template <int M, bool LIST>
 __global__ void __launch_bounds__(128)
 k_mdbc(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys, State st,
        float *__restrict__ press, const uint32_t *__restrict__ cstart, int nbits,
@@ -1032,7 +1035,12 @@ k_mdbc(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ key
   const bool act = has && key_boundary(key, nbits) && C.bmode == 1;
   if (__all_sync(full, !act)) return;
   const float cs = C.csf, ics = C.inv_csf, r2max = C.r2max, hih = C.half_inv_h;
-  const float r2prune = r2max * 1.0001f;
+  float r2prune = r2max * 1.0001f;
+  if (LIST) {
+    const float R = sqrtf(r2max) + 0.5f * dyn[cidx].skin;
+    r2prune = R * R * 1.0001f;
+  }
+  constexpr int MR = LIST ? M + 1 : M;
   // ghost position: cell of B shifted by the whole cells of (offset + ghost)
   int cx = 0, cy = 0, cz = 0;
   float4 pb = make_float4(0.f, 0.f, 0.f, 0.f), g = pb;
@@ -1057,18 +1065,18 @@ k_mdbc(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ key
   float a00 = 0.f, a01 = 0.f, a02 = 0.f, a03 = 0.f, a10 = 0.f, a20 = 0.f, a30 = 0.f;
   float dxx = 0.f, dyy = 0.f, dzz = 0.f, dxy = 0.f, dxz = 0.f, dyz = 0.f;
   float r0 = 0.f, r1 = 0.f, r2s = 0.f, r3 = 0.f, vsx = 0.f, vsy = 0.f, vsz = 0.f;
-  constexpr int W = 2 * M + 1;
+  constexpr int W = 2 * MR + 1;
 #pragma unroll 1
   for (int row = 0; row < W * W; row++) {
-    const int dy = row % W - M, dz = row / W - M;
+    const int dy = row % W - MR, dz = row / W - MR;
     const int yy = gy + dy, zz = gz + dz;
     int lo = 0, hi = 0;
     const float sgy = slab_gap(dy, oy, cs), sgz = slab_gap(dz, oz, cs);
     const float d2 = fmaf(sgy, sgy, sgz * sgz);
     if (act && d2 < r2prune && yy >= 0 && yy < ny && zz >= 0 && zz < nz) {
       const float L = sqrtf(r2prune - d2);
-      const int x0 = max(0, gx + max(-M, (int)floorf((ox - L) * ics)));
-      const int x1 = min(nx - 1, gx + min(M, (int)floorf((ox + L) * ics)));
+      const int x0 = max(0, gx + max(-MR, (int)floorf((ox - L) * ics)));
+      const int x1 = min(nx - 1, gx + min(MR, (int)floorf((ox + L) * ics)));
       if (x1 >= x0) {
         const int c0 = base0 + zz * nxy + yy * nx;
         lo = (int)cstart[c0 + x0];  // fluid segment only (b in F)
@@ -1678,6 +1686,7 @@ __global__ void k_corrector_list(int n, const uint32_t *__restrict__ keys_n,
   x.id[i] = sn.id[i];
   x.cid[i] = (uint16_t)cidx;
   x.code[i] = code;
+  if (x.ghost) x.ghost[i] = sn.ghost[i];  // mDBC ghost offsets follow the order
   const CaseConst &C = cc[cidx];
   if (k >= key_out(nbits)) {  // frozen before this step, or released
     x.posc[i] = pn;
@@ -1728,6 +1737,7 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
   x.id[i] = y.id[i];
   x.cid[i] = (uint16_t)cidx;
   x.code[i] = code;
+  if (x.ghost) x.ghost[i] = y.ghost[i];  // mDBC ghost offsets follow the order
   const CaseConst &C = cc[cidx];
   if (k >= key_out(nbits)) {  // frozen before this step, or released
     x.posc[i] = pn;
@@ -1795,6 +1805,7 @@ __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
   const bool afluid = !key_boundary(k, nbits);
   const int cidx = cid[i];
   const CaseConst &C = cc[cidx];
+  if (!afluid && C.bmode == 1) return;  // mDBC boundary: no pair terms (Eq 38 instead)
   const float cs = C.csf;
   const unsigned r2max_u = __float_as_uint(C.r2max) - 1u;
   const float4 pa = posc[i];
@@ -2260,17 +2271,19 @@ void launch_corrector(int n, const uint32_t *perm2, const uint32_t *keys_half,
 
 void launch_mdbc(int margin, int n, const int *nvalid, const uint32_t *keys, State st,
                  float *press, const uint32_t *cstart, int nbits, const CaseConst *cc,
-                 const CaseDyn *dyn, int stage, cudaStream_t s) {
+                 const CaseDyn *dyn, int stage, cudaStream_t s, bool list) {
   if (n <= 0) return;
-  if (margin == 1)
-    k_mdbc<1><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, press, cstart, nbits, cc, dyn,
-                                           stage);
-  else if (margin == 3)
-    k_mdbc<3><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, press, cstart, nbits, cc, dyn,
-                                           stage);
-  else
-    k_mdbc<2><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, press, cstart, nbits, cc, dyn,
-                                           stage);
+#define SPH_MD(MM, LL)                                                                    \
+  k_mdbc<MM, LL><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, st, press, cstart, nbits, cc, \
+                                              dyn, stage)
+  if (margin == 1) {
+    if (list) SPH_MD(1, true); else SPH_MD(1, false);
+  } else if (margin == 3) {
+    if (list) SPH_MD(3, true); else SPH_MD(3, false);
+  } else {
+    if (list) SPH_MD(2, true); else SPH_MD(2, false);
+  }
+#undef SPH_MD
 }
 
 void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,

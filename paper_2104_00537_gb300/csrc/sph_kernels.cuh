@@ -37,10 +37,11 @@ void launch_predictor(int n, const uint32_t *keys_in, State src, const float4 *a
                       const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
                       float4 *velrho_out, uint32_t *keys_out, cudaStream_t s);
 // mDBC boundary values (Eq 38-39) on the sorted state st, before an
-// interaction; stage 0: wall velocity at t, 1: at t + dt/2.
+// interaction; stage 0: wall velocity at t, 1: at t + dt/2.  list: st is in
+// the cells of a neighbour list's build (offsets up to skin/2 outside them).
 void launch_mdbc(int margin, int n, const int *nvalid, const uint32_t *keys, State st,
                  float *press, const uint32_t *cstart, int nbits, const CaseConst *cc,
-                 const CaseDyn *dyn, int stage, cudaStream_t s);
+                 const CaseDyn *dyn, int stage, cudaStream_t s, bool list = false);
 // Neighbour list (Symplectic scheme, boundary_mode 0): build on state n
 // with radius 2h + skin; interaction over the list; predictor and corrector
 // that keep the order and the cells of the build.

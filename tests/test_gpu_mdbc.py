@@ -79,11 +79,15 @@ def test_mdbc_one_evaluation(slip):
     eng.destroy()
 
 
-def test_mdbc_moving_tank_matches_oracle():
+@pytest.mark.parametrize("variant", [5, 4, 0])
+def test_mdbc_moving_tank_matches_oracle(variant):
     """Translating tank (Eq 37) with no-slip walls: 20 steps against the
-    oracle, then one evaluation."""
+    oracle, then one evaluation; on the list kept across steps, the per-step
+    list (the ghost-node pass on states in the build's cells) and two lists
+    per step."""
     c = cases.sloshing_tank(3000, 0.3, 0.03, 1.2, boundary_mode=1, mdbc_slip=1)
     eng = sph.Engine.create(c)
+    eng.set_options(pi_variant=variant)
     eng.step(20)
     st = eng.get_state()
     o = oracle.OracleState(c)
@@ -95,10 +99,11 @@ def test_mdbc_moving_tank_matches_oracle():
     eng.destroy()
 
 
-def test_mdbc_dam_break_100_steps():
+@pytest.mark.parametrize("variant", [5, 4, 0])
+def test_mdbc_dam_break_100_steps(variant):
     c = cases.dam_break(0.02, boundary_mode=1)
     eng = sph.Engine.create(c)
-    eng.set_options(use_graph=1)
+    eng.set_options(use_graph=1, pi_variant=variant)
     eng.step(100)
     s = eng.stats()
     st = eng.get_state()
@@ -139,8 +144,10 @@ def test_mdbc_still_tank_hydrostatic_gpu():
 def test_mdbc_raw_resume_and_pool():
     c = cases.dam_break(0.04, boundary_mode=1, mdbc_slip=1, seed=3)
     a = sph.Engine.create(c)
+    a.set_options(pi_variant=4)           # the pool's path
     a.step(6)
     b = sph.Engine.from_raw(c, a.get_raw())
+    b.set_options(pi_variant=4)
     a.step(5)
     b.step(5)
     sa, sb = a.get_state(), b.get_state()
@@ -156,3 +163,17 @@ def test_mdbc_raw_resume_and_pool():
     a.destroy()
     b.destroy()
     pool.destroy()
+
+
+@pytest.mark.parametrize("variant", [5, 4])
+def test_mdbc_list_finds_every_pair(variant):
+    """mDBC cases on a neighbour list: brute-force check of every evaluation
+    (fluid targets; boundary targets take Eq 38 and have no pair terms)."""
+    c = cases.sloshing_tank(3000, 0.3, 0.04, 1.2, boundary_mode=1, mdbc_slip=1, seed=6)
+    eng = sph.Engine.create(c)
+    eng.set_options(pi_variant=variant, check_list=1)
+    eng.step(120)
+    li, st = eng.list_info(), eng.stats()
+    assert li["check_bad"] == 0
+    assert li["check_pairs"] == st["interactions"]
+    eng.destroy()
