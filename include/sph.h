@@ -150,8 +150,9 @@ typedef struct {
                        * builds it with a larger skin and keeps it (and the
                        * particle order and cells) across steps until a
                        * particle could leave the skin, decided on the
-                       * device (Symplectic scheme and boundary_mode 0;
-                       * else 3-5 fall back to 0)                         */
+                       * device (5 also serves the Verlet scheme; 3 and 4
+                       * with Verlet, and any list beyond 2^25 particles,
+                       * fall back to 0)                                 */
   int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
   int32_t timing;     /* 1: time every PI launch with CUDA events              */
   float list_skin;    /* pi_variant 5: skin added for the steps the list is

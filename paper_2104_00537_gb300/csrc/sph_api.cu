@@ -316,9 +316,9 @@ int list_records_needed(int cell_mode, double h, double dp) {
   return std::min(4096, ((int)std::ceil(1.2 * worst) + 31) / 32 * 32);
 }
 
-// A neighbour list applies to this step: Symplectic scheme, no mDBC case, a
-// list variant chosen (3, 4: one list per step; 5: kept across steps) and
-// the list allocated.
+// A neighbour list applies to this step: a list variant chosen (3, 4: one
+// list per Symplectic step; 5: kept across steps, either scheme) and the
+// list allocated.
 bool use_list(sph_engine e) {
   if (!e->list_ok) return false;
   if (e->integrator == 1) return e->opt.pi_variant == 5;  // Verlet: one PI per step
