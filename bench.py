@@ -336,7 +336,7 @@ def run_served(args):
     results = {}
     for name, slots in (("served", 64), ("plain", 1)):
         pool = sph.Engine.pool(max_p, max_cells, slots, stream=stream)
-        pool.set_options(use_graph=1)
+        pool.set_options(use_graph=1, pi_variant=args.pi_variant, list_skin=args.list_skin)
         reqs = [serve.Request(i, a, c, te) for i, (a, c, te) in enumerate(trace)]
         srv = serve.Server(pool, chunk=args.chunk)
         torch.cuda.synchronize()
@@ -353,7 +353,8 @@ def run_served(args):
            "config": {"workload": "sloshing tanks, Poisson %.0f req/s, %d requests, fluid "
                                   "10k-%d log-uniform, t_end %.3g s"
                                   % (args.rate, args.requests, args.max_fluid, args.t_end),
-                      "chunk_steps": args.chunk, "cell_mode": args.cell_mode},
+                      "chunk_steps": args.chunk, "cell_mode": args.cell_mode,
+                      "pi_variant": args.pi_variant if args.pi_variant >= 0 else 5},
            "served": results["served"], "plain": results["plain"],
            "throughput_ratio": results["served"]["throughput_req_s"] /
            results["plain"]["throughput_req_s"],
@@ -421,9 +422,9 @@ def main():
             sph.Engine.create(cs[0], stream=stream)
     eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin)
     n_particles = sum(c.n for c in cs)
-    # the pi_variant the engine runs (its default: 5 for one case, 4 for a Symplectic batch)
+    # the pi_variant the engine runs (its default: 5, the list kept across steps)
     list_ok = n_particles < (1 << 25)
-    default_var = 5 if len(cs) == 1 else (4 if args.integrator == "symplectic" else 0)
+    default_var = 5
     eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4, 5) else (
         default_var if list_ok else 0)
     if eff_var in (3, 4, 5) and not list_ok:

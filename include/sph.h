@@ -137,9 +137,9 @@ typedef void (*sph_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 /* Engine-wide launch options (the autotuner's knobs). */
 typedef struct {
   int32_t pi_block;   /* threads per block of the interaction kernel (0: default) */
-  int32_t pi_variant; /* interaction pair loop: -1 the engine default (where a
-                       * list is supported 5 for one case, 4 for a batch or
-                       * pool, else 0); 0 compacted hit masks; 1 test
+  int32_t pi_variant; /* interaction pair loop: -1 the engine default (5 where
+                       * a list is supported, else 0); 0 compacted hit
+                       * masks; 1 test
                        * and evaluate inline; 2 hit masks queued per lane
                        * across rows (same sums as 0, bit for bit); 3, 4
                        * and 5 a neighbour list: candidates within 2h + skin
@@ -150,9 +150,12 @@ typedef struct {
                        * builds it with a larger skin and keeps it (and the
                        * particle order and cells) across steps until a
                        * particle could leave the skin, decided on the
-                       * device (5 also serves the Verlet scheme; 3 and 4
-                       * with Verlet, and any list beyond 2^25 particles,
-                       * fall back to 0)                                 */
+                       * device, for all the cases of the engine at once
+                       * (so a case of a batch or pool stays within FP32
+                       * rounding of its run alone; with 4 it is equal bit
+                       * for bit).  5 also serves the Verlet scheme; 3 and
+                       * 4 with Verlet, and any list beyond 2^25 particles,
+                       * fall back to 0                                  */
   int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
   int32_t timing;     /* 1: time every PI launch with CUDA events              */
   float list_skin;    /* pi_variant 5: skin added for the steps the list is

@@ -199,7 +199,7 @@ struct sph_engine_t {
   int rbx_key = -1;
   cudaError_t cap_err = cudaSuccess;  // first error while building a conditional node
   bool capturing = false;             // enqueue_step runs under stream capture
-  int list_default = 4;               // pi_variant -1 with a list: 5 one case, 4 batch / pool
+  int list_default = 5;               // pi_variant -1 with a list: the kept list
   int64_t builds_seen = 0;            // ctl->builds at the last check_flags
   float4 *tau4 = nullptr;  // (tau/rho) of Eq 25 in sorted order: xx, yy, zz, xy
   float2 *tau2 = nullptr;  //   xz, yz
@@ -549,9 +549,9 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     for (int c = 0; c < ncases; c++)
       cap = std::max(cap, list_records_needed(params[c].cell_mode, params[c].h, params[c].dp));
     e->list_cap = cap;
-    // one case: the list kept across steps; several: one list per step, so
-    // that every case of a batch takes the same steps as alone, bit for bit
-    e->list_default = ncases == 1 ? 5 : 4;
+    // the list kept across steps (one list per step, 4, makes every case of a
+    // batch take the same steps as alone, bit for bit)
+    e->list_default = 5;
   }
   e->opt.pi_variant = resolve_variant(e, -1);
   rc = allocate(e);
@@ -1503,8 +1503,8 @@ int sph_pool_create(int64_t max_particles, int64_t max_cells, int32_t max_cases,
   if (e->list_ok) {
     const double hq = 1.2 * std::sqrt(3.0);
     for (int cm = 0; cm < 3; cm++) e->list_cap = std::max(e->list_cap, list_records_needed(cm, hq, 1.0));
-    e->list_default = 4;  // pools: one list per step (cases equal alone, bit for bit)
-    e->opt.pi_variant = 4;
+    e->list_default = 5;  // the list kept across steps (4: cases equal alone, bit for bit)
+    e->opt.pi_variant = 5;
   }
   rc = allocate(e);
   if (rc == SPH_OK) {

@@ -302,8 +302,9 @@ class Engine:
     def set_options(self, pi_block=0, pi_variant=-1, use_graph=0, timing=0, list_skin=-1.0,
                     check_list=0):
         """pi_variant -1 keeps the engine default (where the engine supports
-        a neighbour list: kept across steps, 5, for one case, one per step,
-        4, for a batch or pool; else the compacted loop, 0); list_skin:
+        a neighbour list: kept across steps, 5; else the compacted loop, 0;
+        4, one list per step, keeps batch and pool cases equal to their runs
+        alone bit for bit); list_skin:
         variant 5's added skin as a fraction of 2h (< 0: the default, 0.04);
         check_list: brute-force check of every list evaluation (list_info)."""
         o = Options(pi_block, pi_variant, use_graph, timing, list_skin, check_list)

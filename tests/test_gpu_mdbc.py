@@ -154,6 +154,7 @@ def test_mdbc_raw_resume_and_pool():
     for k in ("pos", "vel", "rho"):
         assert np.array_equal(sa[k], sb[k]), k
     pool = sph.Engine.pool(400000, 2000000, 4)
+    pool.set_options(pi_variant=4)         # one list per step: bit for bit
     pool.admit(cases.dam_break(0.04, seed=5, boundary_mode=1), t_end=1.0)
     s = pool.admit(c, t_end=1.0)
     pool.pool_step(11)

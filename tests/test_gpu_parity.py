@@ -401,7 +401,8 @@ def test_raw_checkpoint_resume_is_bit_exact(c0):
 def test_batch_equals_alone():
     cs = [cases.dam_break(0.04, seed=1), cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
           cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
-    bat = sph.Engine.batch(cs)            # one list per step (variant 4)
+    bat = sph.Engine.batch(cs)
+    bat.set_options(pi_variant=4)          # one list per step: bit for bit
     bat.step(12)
     for i, c in enumerate(cs):
         e = sph.Engine.create(c)
@@ -419,6 +420,7 @@ def test_pool_mix_equals_alone():
     ca = cases.dam_break(0.04, seed=5)
     cb = cases.sloshing_tank(2500, 0.3, 0.03, 1.1, seed=6)
     pool = sph.Engine.pool(200000, 2000000, 8)
+    pool.set_options(pi_variant=4)         # one list per step: bit for bit
     sa = pool.admit(ca, t_end=1.0)
     pool.pool_step(5)
     sb = pool.admit(cb, t_end=1.0)   # admitted while case a runs
@@ -499,6 +501,7 @@ def test_empty_case_and_empty_batch_member():
     assert e.stats()["n"] == 0 and e.stats()["step"] == 0
     e.destroy()
     bat = sph.Engine.batch([full, empty])
+    bat.set_options(pi_variant=4)
     bat.step(4)
     alone = sph.Engine.create(full)
     alone.set_options(pi_variant=4)      # the batch's path
@@ -562,7 +565,7 @@ def test_list_kept_across_steps_in_a_batch():
     cs = [cases.dam_break(0.04, seed=1), cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
           cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
     bat = sph.Engine.batch(cs)
-    bat.set_options(pi_variant=5, check_list=1)
+    bat.set_options(check_list=1)          # the default: the kept list
     bat.step(40)
     assert bat.list_info()["check_bad"] == 0
     for i, c in enumerate(cs):
@@ -587,3 +590,30 @@ def test_list_skin_option_is_validated(c0):
     eng.step(20)
     assert 10 <= eng.list_info()["builds"] <= 20
     eng.destroy()
+
+
+def test_pool_on_kept_list_matches_alone():
+    """Continuous batching on the default path (the list kept across steps):
+    a case admitted while another runs, which then leaves, ends within FP32
+    rounding of its run alone; every pair of every evaluation is listed."""
+    ca = cases.dam_break(0.04, seed=5)
+    cb = cases.sloshing_tank(2500, 0.3, 0.03, 1.1, seed=6)
+    pool = sph.Engine.pool(200000, 2000000, 8)
+    pool.set_options(use_graph=1, check_list=1)
+    sa = pool.admit(ca, t_end=1.0)
+    pool.pool_step(5)
+    sb = pool.admit(cb, t_end=1.0)
+    pool.pool_step(27)
+    pool.release(sa)
+    pool.pool_step(13)
+    assert pool.list_info()["check_bad"] == 0
+    eb = sph.Engine.create(cb)
+    eb.step(40)
+    a, b = pool.get_state(sb), eb.get_state()
+    dp = cb.params["dp"]
+    assert a["step"] == b["step"] == 40
+    assert np.abs(a["pos"] - b["pos"]).max() < 1e-3 * dp
+    assert np.abs(a["rho"] - b["rho"]).max() < 1e-3 * cb.params["rho0"]
+    assert a["t"] == pytest.approx(b["t"], rel=1e-6)
+    eb.destroy()
+    pool.destroy()

@@ -88,6 +88,7 @@ def test_pool_sps_case_equals_alone():
     c = sps_case(0.04, seed=4)
     other = cases.dam_break(0.04, seed=5)
     pool = sph.Engine.pool(200000, 2000000, 4)
+    pool.set_options(pi_variant=4)         # one list per step: bit for bit
     pool.admit(other, t_end=1.0)
     s = pool.admit(c, t_end=1.0)
     pool.pool_step(8)
