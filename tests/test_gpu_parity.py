@@ -617,3 +617,22 @@ def test_pool_on_kept_list_matches_alone():
     assert a["t"] == pytest.approx(b["t"], rel=1e-6)
     eb.destroy()
     pool.destroy()
+
+
+def test_kept_list_exact_through_the_splash():
+    """The kept list through the dam break's collapse and splash (1,200
+    steps of a 0.015 m case: the front reaches the far wall, particles fly
+    at the highest speeds of the run): every pair of every evaluation is in
+    the list (brute force), the rebuild rate follows the flow, no flag."""
+    c = cases.dam_break(0.015, seed=9, tank=(0.9, 0.45, 0.6), column=(0.3, 0.3, 0.3))
+    eng = sph.Engine.create(c)
+    eng.set_options(use_graph=1, check_list=1)
+    eng.step(600)
+    b600 = eng.list_info()["builds"]
+    eng.step(600)
+    li, st = eng.list_info(), eng.stats()
+    assert li["check_bad"] == 0
+    assert li["check_pairs"] == st["interactions"]
+    assert st["flags"] == 0
+    assert 0 < b600 < li["builds"] - b600 < 600      # faster flow, more rebuilds
+    eng.destroy()
