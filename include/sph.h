@@ -177,10 +177,15 @@ int sph_create(const sph_case_params *params, const sph_particles *parts,
                void *stream, sph_alloc_fn alloc, sph_free_fn free_fn,
                void *alloc_ctx, sph_engine *out);
 
-/* sph_step: advance every case of the engine by nsteps Symplectic steps
- * (Eq 33-34), each: NL -> PI (state n) -> dt (Eq 35) -> predictor -> NL ->
- * PI (state n+1/2) -> corrector.  Work is queued on the engine's stream;
- * the call returns after synchronising and checking the failure flags. */
+/* sph_step: advance every case of the engine by nsteps steps of its scheme:
+ * Symplectic (Eq 33-34): PI (state n) -> dt (Eq 35) -> predictor -> PI
+ * (state n+1/2) -> corrector; Verlet (Eq 30-31): PI -> dt -> update.  The
+ * neighbour list behind each PI is rebuilt as pi_variant says (0-2: a cell
+ * walk per PI; 3, 4: one list per step; 5: a list kept until a particle
+ * could leave its skin, rebuilt at the start of every call).  Work is queued
+ * on the engine's stream; the call returns after synchronising and checking
+ * the failure flags (a list overflow or skin violation is an error, never a
+ * dropped pair). */
 int sph_step(sph_engine e, int64_t nsteps);
 
 /* sph_get_state: copy case `icase` (0 for a single case) to host arrays in
