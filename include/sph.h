@@ -150,12 +150,11 @@ typedef struct {
                        * builds it with a larger skin and keeps it (and the
                        * particle order and cells) across steps until a
                        * particle could leave the skin, decided on the
-                       * device, for all the cases of the engine at once
-                       * (so a case of a batch or pool stays within FP32
-                       * rounding of its run alone; with 4 it is equal bit
-                       * for bit).  5 also serves the Verlet scheme; 3 and
-                       * 4 with Verlet, and any list beyond 2^25 particles,
-                       * fall back to 0                                  */
+                       * device per case (a case of a batch or pool takes
+                       * the steps it takes alone, bit for bit, however
+                       * the steps are split into calls).  5 also serves
+                       * the Verlet scheme; 3 and 4 with Verlet, and any
+                       * list beyond 2^25 particles, fall back to 0      */
   int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
   int32_t timing;     /* 1: time every PI launch with CUDA events              */
   float list_skin;    /* pi_variant 5: skin added for the steps the list is
@@ -181,8 +180,10 @@ int sph_create(const sph_case_params *params, const sph_particles *parts,
  * Symplectic (Eq 33-34): PI (state n) -> dt (Eq 35) -> predictor -> PI
  * (state n+1/2) -> corrector; Verlet (Eq 30-31): PI -> dt -> update.  The
  * neighbour list behind each PI is rebuilt as pi_variant says (0-2: a cell
- * walk per PI; 3, 4: one list per step; 5: a list kept until a particle
- * could leave its skin, rebuilt at the start of every call).  Work is queued
+ * walk per PI; 3, 4: one list per step; 5: a case's list kept until one of
+ * its particles could leave the skin; a call continues the previous call's
+ * lists unless cases were admitted or released, a snapshot was taken or a
+ * parity helper re-sorted the state, which rebuild them).  Work is queued
  * on the engine's stream; the call returns after synchronising and checking
  * the failure flags (a list overflow or skin violation is an error, never a
  * dropped pair). */

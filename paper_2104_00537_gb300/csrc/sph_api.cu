@@ -190,6 +190,9 @@ struct sph_engine_t {
   uint2 *nlist = nullptr;
   uint16_t *ncount = nullptr;
   float4 *posc_ref = nullptr;  // positions at the list's build (pi_variant 5)
+  float4 *posc_ref2 = nullptr; //   the same gathered into a rebuild's new order
+  bool list_dirty = true;      // the next kept-list step starts with a rebuild event
+  bool list_stale = true;      //   in which every case rebuilds (sorted state overwritten)
   ListCtl *ctl = nullptr;      // rebuild request, build count, list check
   cudaStream_t s2 = nullptr;   // captures the bodies of conditional graph nodes
   // pi_variant 5 without a captured step graph: the two guarded parts of a
@@ -386,6 +389,7 @@ int allocate(sph_engine e) {
     e->nlist = (uint2 *)A(sizeof(uint2) * (size_t)e->list_cap * (size_t)N);
     e->ncount = (uint16_t *)A(2 * N);
     e->posc_ref = (float4 *)A(16 * N);
+    e->posc_ref2 = (float4 *)A(16 * N);
     e->ctl = (ListCtl *)A(sizeof(ListCtl));
   }
   if (e->sps || e->pool) {
@@ -492,7 +496,9 @@ int set_slot(sph_engine e, int slot, const sph_case_params *p, const sph_particl
   CaseDyn d;
   std::memset(&d, 0, sizeof(d));
   d.dtmin_bits = kFloatInfBits;
+  d.need = 1u;  // a new case builds its list
   CUDA_TRY(cudaMemcpyAsync(e->ddyn + slot, &d, sizeof(CaseDyn), cudaMemcpyHostToDevice, e->s));
+  e->list_dirty = true;
   CUDA_TRY(cudaStreamSynchronize(e->s));
   return SPH_OK;
 }
@@ -616,15 +622,17 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
                 e->ddyn, 0, s);
   if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
     if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
-    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, s);
+    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
+                      s);
     launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                       e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                      e->list_cap, e->ncount, nullptr, s);
+                      e->list_cap, e->ncount, nullptr, nullptr, s);
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                          e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
   } else {
-    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, s);
+    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
+                      s);
     if (ev) cudaEventRecord(ev[0], s);
     launch_interact_build(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                           e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
@@ -652,6 +660,35 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   launch_corrector_list(nl, e->keysB, e->keysC, Y, Z.velrho, e->ace, e->dconst, e->ddyn,
                         e->nbits, X, e->keysA, s);
   launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
+}
+
+// The two guarded parts of a kept-list rebuild event.  The sort: cases that
+// need no rebuild enter it with their build keys and build-cell state (so
+// their order and cells stay), the others with the normalised state in X;
+// the reorder also gathers the build positions into the new order.
+void enqueue_rebuild_sort(sph_engine e, cudaStream_t q) {
+  const int n = (int)e->n_phys;
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &X = e->S[0], &Y = e->S[1];
+  launch_select(n, X.cid, e->dconst, e->ddyn, e->keysB, Y.posc, e->keysA, X.posc, q);
+  radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, q);
+  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
+                 X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, q, e->posc_ref,
+                 e->posc_ref2);
+  launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, q);
+}
+
+// The list: per-case skin and build mode, then the build (a case that needs
+// it from its state, one whose indices moved from its build positions, the
+// rest keep their records).
+void enqueue_rebuild_list(sph_engine e, float extra, cudaStream_t q) {
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &Y = e->S[1];
+  launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, extra, 0, e->cstart, e->cells_hw,
+                    q);
+  launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
+                    e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
+                    e->list_cap, e->ncount, e->posc_ref, e->posc_ref2, q);
 }
 
 // Appends to the graph being captured on e->s a k_decide kernel and an IF
@@ -745,18 +782,8 @@ void enqueue_step_reuse(sph_engine e, cudaEvent_t *ev) {
   State &X = e->S[0], &Y = e->S[1], &Z = e->S[2];
   cudaStream_t s = e->s;
   const float extra = e->opt.list_skin >= 0.f ? e->opt.list_skin : 0.04f;
-  auto nl_part = [=](cudaStream_t q) {
-    radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, q);
-    launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
-                   X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, q);
-    launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, q);
-  };
-  auto list_part = [=](cudaStream_t q) {
-    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, extra, q);
-    launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
-                      e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                      e->list_cap, e->ncount, e->posc_ref, q);
-  };
+  auto nl_part = [=](cudaStream_t q) { enqueue_rebuild_sort(e, q); };
+  auto list_part = [=](cudaStream_t q) { enqueue_rebuild_list(e, extra, q); };
   if (e->capturing) {
     capture_if_rebuild(e, nl_part);
     capture_if_rebuild(e, list_part);
@@ -806,18 +833,8 @@ void enqueue_step_verlet_reuse(sph_engine e, cudaEvent_t *ev) {
   State &X = e->S[0], &Y = e->S[1];
   cudaStream_t s = e->s;
   const float extra = e->opt.list_skin >= 0.f ? e->opt.list_skin : 0.04f;
-  auto nl_part = [=](cudaStream_t q) {
-    radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, q);
-    launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
-                   X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, q);
-    launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, q);
-  };
-  auto list_part = [=](cudaStream_t q) {
-    launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, extra, q);
-    launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
-                      e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                      e->list_cap, e->ncount, e->posc_ref, q);
-  };
+  auto nl_part = [=](cudaStream_t q) { enqueue_rebuild_sort(e, q); };
+  auto list_part = [=](cudaStream_t q) { enqueue_rebuild_list(e, extra, q); };
   if (e->capturing) {
     capture_if_rebuild(e, nl_part);
     capture_if_rebuild(e, list_part);
@@ -899,8 +916,10 @@ void enqueue_step(sph_engine e, cudaEvent_t *ev) {
   launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
 }
 
-// NL only, on the current state: keysA/X -> keysB/Y + cell table.
+// NL only, on the current state: keysA/X -> keysB/Y + cell table (the kept
+// list's sorted state is gone: its next step rebuilds every case).
 void enqueue_nl(sph_engine e) {
+  e->list_stale = true;
   const int n = (int)e->n_phys;
   const int nl = (int)(e->n_phys - e->n_dead);
   State &X = e->S[0], &Y = e->S[1];
@@ -983,6 +1002,7 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
     return fail(SPH_ERR_ARG, "list_skin must be at most 0.25 (or < 0 for the default)");
   e->opt = *opt;
   e->opt.pi_variant = resolve_variant(e, opt->pi_variant);
+  e->list_stale = true;  // another pair loop may have run in between
   e->drop_graphs();
   return SPH_OK;
 }
@@ -1008,9 +1028,13 @@ int sph_step(sph_engine e, int64_t nsteps) {
   int64_t k = 0;
   const bool reuse = use_list(e) && e->opt.pi_variant == 5;
   if (reuse) {
-    // every call starts from the state in X (the API's view): build first
     if (!e->s2) CUDA_TRY(cudaStreamCreateWithFlags(&e->s2, cudaStreamNonBlocking));
-    CUDA_TRY(cudaMemsetAsync(&e->ctl->rebuild, 1, sizeof(unsigned int), e->s));
+    // a call continues the kept list as if the steps had not been split,
+    // unless the cases or the sorted state changed since the last step
+    if (e->list_stale) launch_need_all(e->cap_cases, e->ddyn, e->s);
+    if (e->list_stale || e->list_dirty)
+      CUDA_TRY(cudaMemsetAsync(&e->ctl->rebuild, 1, sizeof(unsigned int), e->s));
+    e->list_stale = e->list_dirty = false;
   }
   e->cap_err = cudaSuccess;
   if (!timing && e->opt.use_graph && e->n_dead == 0) {
@@ -1207,6 +1231,9 @@ int sph_get_raw(sph_engine e, int32_t icase, void *buf, size_t *bytes) {
   }
   if (*bytes < need) return fail(SPH_ERR_ARG, "raw buffer too small");
   *bytes = need;
+  // a snapshot holds the normalised state only: the next step rebuilds every
+  // case's list, as the first step of an engine resumed from it does
+  e->list_stale = true;
   // device order of the case = order in X, filtered by slot (host-side)
   const int64_t np = e->n_phys;
   std::vector<uint32_t> keys(np), ids(np);
@@ -1617,6 +1644,7 @@ int sph_pool_release(sph_engine e, int32_t slot) {
   for (auto &s : e->slots)
     if (s.used) e->cells_hw = std::max<int64_t>(e->cells_hw, (int64_t)s.cellbase + s.ncells);
   e->drop_graphs();
+  e->list_dirty = true;  // the other cases' indices move: their lists are re-expressed
   return SPH_OK;
 }
 

@@ -70,6 +70,12 @@ struct CaseDyn {
   int n_out;
   unsigned int v2max_bits;  // float bits of max |v|^2 over in-domain particles at the last reorder
   float skin;               // neighbour-list path: skin of the list built last (set by k_list_begin)
+  // list kept across steps, per case: need = the case's list must be rebuilt
+  // (set by the corrector, at admission, by the host); lmode = what the
+  // current build does for the case (0 keep the records, 1 build from the
+  // state, 2 rebuild from the build positions after an index shift);
+  // startF / startB = first fluid / boundary index of the case at its build
+  unsigned int need, lmode, startF, startB;
   double mot[kMaxMotions][4];  // displacement and velocity at t+dt/2 and t+dt
 };
 

@@ -135,7 +135,9 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
                           const float4 *__restrict__ vrprev_src,
                           const float4 *__restrict__ ghost_src, State dst,
                           float *__restrict__ press, const CaseConst *__restrict__ cc,
-                          CaseDyn *__restrict__ dyn, int nbits) {
+                          CaseDyn *__restrict__ dyn, int nbits,
+                          const float4 *__restrict__ ref_src = nullptr,
+                          float4 *__restrict__ ref_dst = nullptr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int cidx = -1;
   unsigned v2 = 0u;
@@ -158,6 +160,7 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
     dst.code[i] = code_src[p];
     if (vrprev_src) dst.vrprev[i] = vrprev_src[p];
     if (ghost_src) dst.ghost[i] = ghost_src[p];
+    if (ref_dst) ref_dst[i] = ref_src[p];  // kept list: build positions follow the order
     press[i] = tait_pressure(C, vr.w) / vr.w;
   }
   // max |v|^2 per case (for the neighbour list's skin): one atomic per warp
@@ -453,8 +456,15 @@ __device__ __forceinline__ void finish_target(const CaseConst &C, int i, int n, 
 // plus 1e-3 h; the 25 % covers the change of a wall's imposed speed over
 // dt / 2.  A list kept across steps adds extra x 2h.  The build's rows reach
 // 2h + cs, so the skin is capped at 0.95 cs (kFlagSkin if one step needs more).
+// Also sets each case's build mode: with fresh_all (one list per step) every
+// case builds from its state; else a case that needs a rebuild does (and
+// takes a new skin), one whose particles moved in the sorted order (another
+// case's particle left the domain, a case was admitted or released) rebuilds
+// its records from its build positions with its old skin, and the rest keep
+// their records.  Clears the rebuild request and counts the build.
 __global__ void k_list_begin(int ncases, const CaseConst *__restrict__ cc,
-                             CaseDyn *__restrict__ dyn, ListCtl *__restrict__ ctl, float extra) {
+                             CaseDyn *__restrict__ dyn, ListCtl *__restrict__ ctl, float extra,
+                             int fresh_all, const uint32_t *__restrict__ cstart, uint32_t cap1) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c == 0 && ctl) {
     ctl->rebuild = 0u;
@@ -463,10 +473,42 @@ __global__ void k_list_begin(int ncases, const CaseConst *__restrict__ cc,
   if (c >= ncases || !cc[c].active) return;
   const CaseConst &C = cc[c];
   CaseDyn &D = dyn[c];
-  const float need = fmaf(C.list_k, sqrtf(__uint_as_float(D.v2max_bits)), 1e-3f * C.h);
-  const float smax = 0.95f * C.csf;
-  if (need > smax) D.flags |= kFlagSkin;
-  D.skin = fminf(fmaf(extra, 2.f * C.h, need), smax);
+  const uint32_t sF = cstart[C.cellbase], sB = cstart[cap1 + C.cellbase];
+  if (fresh_all || D.need) {
+    const float need = fmaf(C.list_k, sqrtf(__uint_as_float(D.v2max_bits)), 1e-3f * C.h);
+    const float smax = 0.95f * C.csf;
+    if (need > smax) D.flags |= kFlagSkin;
+    D.skin = fminf(fmaf(extra, 2.f * C.h, need), smax);
+    D.lmode = 1u;
+  } else {
+    D.lmode = (sF != D.startF || sB != D.startB) ? 2u : 0u;
+  }
+  D.need = 0u;
+  D.startF = sF;
+  D.startB = sB;
+}
+
+// Before the sort of a kept-list rebuild: the cases that need no rebuild
+// enter it with their build keys and their state in the build's cells (y),
+// so that they keep their particle order and cells; the others with the
+// normalised state the corrector wrote into x.
+__global__ void k_select(int n, const uint16_t *__restrict__ cid,
+                         const CaseConst *__restrict__ cc, const CaseDyn *__restrict__ dyn,
+                         const uint32_t *__restrict__ keys_build, const float4 *__restrict__ posc_build,
+                         uint32_t *__restrict__ keys, float4 *__restrict__ posc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = cid[i];
+  if (!cc[c].active || dyn[c].need) return;
+  keys[i] = keys_build[i];
+  posc[i] = posc_build[i];
+}
+
+// Marks every case's list for a rebuild (after the sorted state was
+// overwritten outside the step, or the pair loop changed).
+__global__ void k_need_all(int ncases, CaseDyn *__restrict__ dyn) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncases) dyn[c].need = 1u;
 }
 
 // One thread per particle a in sorted order (all fluid targets first, then
@@ -491,7 +533,10 @@ __global__ void k_list_begin(int ncases, const CaseConst *__restrict__ cc,
 // index | row offset, mask of those candidates) to list[i cap + c].  The
 // list's rows reach one cell further than the 2h support (M + 1 cells, so
 // 2h + cs >= 2h + skin), clipped to the case's grid.  ref, if set, receives
-// the target's position at the build (the list kept across steps).
+// the target's position at the build (the list kept across steps), and the
+// case's build mode applies (k_list_begin): 0 keeps the target's records, 1
+// builds from posc, 2 rebuilds from the previous build positions (ref_src,
+// gathered into the new order) with the case's old skin.
 template <int M, int VARIANT, int EXT = 0, int LIST = 0>
 __global__ void __launch_bounds__(128, EXT == 2 ? 6 : 0)
 k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
@@ -502,7 +547,8 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
            float4 *__restrict__ ace, float *__restrict__ mu_out, int want_dt,
            const float4 *__restrict__ tau4 = nullptr, const float2 *__restrict__ tau2 = nullptr,
            uint2 *__restrict__ list = nullptr, int cap = 0,
-           uint16_t *__restrict__ count = nullptr, float4 *__restrict__ ref = nullptr) {
+           uint16_t *__restrict__ count = nullptr, float4 *__restrict__ ref = nullptr,
+           const float4 *__restrict__ ref_src = nullptr) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -526,13 +572,15 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   const unsigned r2l_u = __float_as_uint(r2l) - 1u;
   const float r2prune = r2l * 1.0001f;  // conservative: pruning never drops a pair
   int lcnt = 0;                          // LIST: records written
-  const float4 pa = has ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int lmode = (LIST == 2 && ref) ? (int)dyn[cidx].lmode : 1;
+  const float4 *__restrict__ P = lmode == 2 ? ref_src : posc;  // positions walked
+  const float4 pa = has ? P[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float4 va = has ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
   const float Pa = has ? press[i] * va.w : 0.f;  // press holds P / rho
   const float kv = C.kvisc * va.w;
   const bool ddt_on = C.ddt != 0;
   // boundary targets of an mDBC case take their density from Eq 38, not Eq 36
-  const bool work = has && (afluid || C.bmode == 0);
+  const bool work = has && (afluid || C.bmode == 0) && lmode != 0;
   Ext X;
   X.C = &C;
   X.hyd = EXT >= 1 && C.ddt == 2;
@@ -553,7 +601,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   const bool warp_plain = __all_sync(full, (afluid || !has) && !X.hyd && !X.sps);
   Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
   constexpr int MR = LIST ? M + 1 : M;  // rows reach MR cells
-  if (LIST && ref && i < n) ref[i] = pa;
+  if (LIST && ref && i < n) ref[i] = lmode == 1 ? pa : ref_src[i];
   // rows dy, dz in [-M, M]; a list build adds row -(M+1) (M+1) for the
   // targets within the skin of their cell's lower (upper) face, over the
   // warp's union of those ranges
@@ -611,7 +659,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
 #pragma unroll 8
           for (int k = 0; k < nk; k++) {
             if (base + k < len) {
-              const float4 pb = posc[lo + base + k];
+              const float4 pb = P[lo + base + k];
               const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
               const float ry = sy - pb.y, rz = sz - pb.z;
               const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
@@ -686,7 +734,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
     }
   }
 
-  if (LIST && i < n) {
+  if (LIST && i < n && lmode != 0) {
     count[i] = (uint16_t)min(lcnt, cap);
     if (has && lcnt > cap) atomicOr(&dyn[cidx].flags, kFlagListFull);
   }
@@ -1752,6 +1800,7 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
                             (float)(cz * C.cs + pn.z), 0.f);
     x.velrho[i] = vn;
     keys_next[i] = key_out(nbits);
+    dyn[cidx].need = 1u;
     ctl->rebuild = 1u;
     return;
   }
@@ -1764,6 +1813,7 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
   x.velrho[i] = vnew;
   keys_next[i] = kn;
   if (kn >= key_out(nbits)) {  // left at the full step: frozen in x
+    dyn[cidx].need = 1u;
     ctl->rebuild = 1u;
     return;
   }
@@ -1776,7 +1826,10 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
   const float dx = pu.x - r.x, dy = pu.y - r.y, dz = pu.z - r.z;
   const float v = sqrtf(fmaf(vnew.x, vnew.x, fmaf(vnew.y, vnew.y, vnew.z * vnew.z)));
   const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + 0.5f * C.list_k * v;
-  if (e > 0.5f * (D.skin - 1e-3f * C.h)) ctl->rebuild = 1u;
+  if (e > 0.5f * (D.skin - 1e-3f * C.h)) {
+    dyn[cidx].need = 1u;
+    ctl->rebuild = 1u;
+  }
 }
 
 // Sets the condition of the graph's IF node that guards a list build: the
@@ -1927,6 +1980,7 @@ __global__ void k_verlet(int n, const uint32_t *__restrict__ keys_in, State src,
   keys_out[i] = kn;
   if (REUSE) {
     if (left) {
+      dyn[cidx].need = 1u;
       ctl->rebuild = 1u;
       return;
     }
@@ -1938,8 +1992,10 @@ __global__ void k_verlet(int n, const uint32_t *__restrict__ keys_in, State src,
     press[i] = tait_pressure(C, vnew.w) / vnew.w;
     const float4 r = ref[i];
     const float dx = pu.x - r.x, dy = pu.y - r.y, dz = pu.z - r.z;
-    if (sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) > 0.5f * (D.skin - 1e-3f * C.h))
+    if (sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) > 0.5f * (D.skin - 1e-3f * C.h)) {
+      dyn[cidx].need = 1u;
       ctl->rebuild = 1u;
+    }
   }
 }
 
@@ -2161,10 +2217,12 @@ void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
                     const float4 *posc, const float4 *velrho, const uint32_t *id,
                     const uint16_t *cid, const uint8_t *code, const float4 *vrprev,
                     const float4 *ghost, State dst, float *press, const CaseConst *cc,
-                    CaseDyn *dyn, int nbits, cudaStream_t s) {
+                    CaseDyn *dyn, int nbits, cudaStream_t s, const float4 *ref_src,
+                    float4 *ref_dst) {
   if (n > 0)
     k_reorder<<<nblk(n, 256), 256, 0, s>>>(n, perm, keys_sorted, posc, velrho, id, cid, code,
-                                           vrprev, ghost, dst, press, cc, dyn, nbits);
+                                           vrprev, ghost, dst, press, cc, dyn, nbits, ref_src,
+                                           ref_dst);
 }
 
 size_t cells_temp_words(int64_t cap_cells) {
@@ -2309,20 +2367,33 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
 }
 
 void launch_list_begin(int ncases, const CaseConst *cc, CaseDyn *dyn, ListCtl *ctl,
-                       float extra, cudaStream_t s) {
-  k_list_begin<<<(ncases + 127) / 128, 128, 0, s>>>(ncases, cc, dyn, ctl, extra);
+                       float extra, int fresh_all, const uint32_t *cstart, int64_t cap_cells,
+                       cudaStream_t s) {
+  k_list_begin<<<(ncases + 127) / 128, 128, 0, s>>>(ncases, cc, dyn, ctl, extra, fresh_all,
+                                                     cstart, (uint32_t)(cap_cells + 1));
+}
+
+void launch_select(int n, const uint16_t *cid, const CaseConst *cc, const CaseDyn *dyn,
+                   const uint32_t *keys_build, const float4 *posc_build, uint32_t *keys,
+                   float4 *posc, cudaStream_t s) {
+  if (n > 0)
+    k_select<<<nblk(n, 256), 256, 0, s>>>(n, cid, cc, dyn, keys_build, posc_build, keys, posc);
+}
+
+void launch_need_all(int ncases, CaseDyn *dyn, cudaStream_t s) {
+  k_need_all<<<(ncases + 127) / 128, 128, 0, s>>>(ncases, dyn);
 }
 
 void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *keys,
                        const float4 *posc, const float4 *velrho, const float *press,
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
-                       uint16_t *count, float4 *ref, cudaStream_t s) {
+                       uint16_t *count, float4 *ref, const float4 *ref_src, cudaStream_t s) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_BL_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 0, \
-      nullptr, nullptr, list, cap, count, ref
+      nullptr, nullptr, list, cap, count, ref, ref_src
   if (margin == 1)
     k_interact<1, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
   else if (margin == 3)

@@ -8,11 +8,13 @@ void launch_upload(int n, const double *pos, const float *vel, const float *rho,
                    const uint8_t *type, const int32_t *group, int slot, uint32_t id_base,
                    const CaseConst *cc, CaseDyn *dyn, int nbits, State st, uint32_t *keys,
                    int dst0, const float *ghost, cudaStream_t s);
+// ref_src / ref_dst (or null): also gather the kept list's build positions.
 void launch_reorder(int n, const uint32_t *perm, const uint32_t *keys_sorted,
                     const float4 *posc, const float4 *velrho, const uint32_t *id,
                     const uint16_t *cid, const uint8_t *code, const float4 *vrprev,
                     const float4 *ghost, State dst, float *press, const CaseConst *cc,
-                    CaseDyn *dyn, int nbits, cudaStream_t s);
+                    CaseDyn *dyn, int nbits, cudaStream_t s, const float4 *ref_src = nullptr,
+                    float4 *ref_dst = nullptr);
 // Words of temporary storage launch_cells needs for cap_cells cells.
 size_t cells_temp_words(int64_t cap_cells);
 // Cell start table of the sorted keys (and nvalid); returns kernels launched.
@@ -45,17 +47,27 @@ void launch_mdbc(int margin, int n, const int *nvalid, const uint32_t *keys, Sta
 // Neighbour list (Symplectic scheme, boundary_mode 0): build on state n
 // with radius 2h + skin; interaction over the list; predictor and corrector
 // that keep the order and the cells of the build.
-// Per-case skin of the next build (extra x 2h added for a list kept across
-// steps); clears the rebuild request and counts the build.
+// Per-case skin and build mode of the next build (fresh_all: every case
+// builds from its state; else only the cases that need it, after the cell
+// table of the sort); clears the rebuild request and counts the build.
 void launch_list_begin(int ncases, const CaseConst *cc, CaseDyn *dyn, ListCtl *ctl,
-                       float extra, cudaStream_t s);
+                       float extra, int fresh_all, const uint32_t *cstart, int64_t cap_cells,
+                       cudaStream_t s);
+// Kept list, before a rebuild's sort: the cases that need no rebuild enter
+// the sort with their build keys and build-cell state.
+void launch_select(int n, const uint16_t *cid, const CaseConst *cc, const CaseDyn *dyn,
+                   const uint32_t *keys_build, const float4 *posc_build, uint32_t *keys,
+                   float4 *posc, cudaStream_t s);
+// Marks every case's kept list for a rebuild.
+void launch_need_all(int ncases, CaseDyn *dyn, cudaStream_t s);
 // The list alone (the candidate test of the compacted loop, no pair terms);
-// ref (or null) receives every target's position at the build.
+// ref (or null) receives every target's position at the build, and then the
+// cases' build modes apply (ref_src: the previous build positions, gathered).
 void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *keys,
                        const float4 *posc, const float4 *velrho, const float *press,
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
-                       uint16_t *count, float4 *ref, cudaStream_t s);
+                       uint16_t *count, float4 *ref, const float4 *ref_src, cudaStream_t s);
 // First evaluation of the list step: the compacted pair loop on state n that
 // also writes every target's list (chunk records, radius 2h + skin) and count.
 void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t *keys,
