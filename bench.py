@@ -275,8 +275,8 @@ def run_batched(args):
     eng.destroy()
     # plain: one case at a time, each in its own engine: the batch's pair
     # loop with one launch per kernel and with each step replayed from a
-    # graph, and the single-case default (the list kept across steps) the
-    # same two ways; the speedups are quoted against the fastest plain path
+    # graph, and the list kept across steps (the default) the same two ways;
+    # the speedups are quoted against the fastest plain path
     ms_p, ms_pg, ms_pk, ms_pkg, pp = 0.0, 0.0, 0.0, 0.0, 0
     for c in cs:
         e = sph.Engine.create(c, stream=stream)

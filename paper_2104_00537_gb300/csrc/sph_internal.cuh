@@ -99,9 +99,10 @@ __host__ __device__ inline void list_row_decode(uint32_t x, int &dy, int &dz) {
 }
 
 // Engine-wide control of the neighbour list kept across steps: rebuild is
-// requested by the corrector (or by the host at the start of every
-// sph_step call) and cleared by the build; builds counts the builds;
-// check_pairs / check_bad are the optional brute-force check of the list.
+// requested by the corrector (a case needs a new list) or by the host (cases
+// admitted or released, the sorted state overwritten) and cleared by the
+// build; builds counts the rebuild events; check_pairs / check_bad are the
+// optional brute-force check of the list.
 struct ListCtl {
   unsigned int rebuild;
   unsigned int pad;

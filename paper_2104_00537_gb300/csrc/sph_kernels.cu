@@ -1461,18 +1461,21 @@ __global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
   keys_next[i] = kn;
 }
 
-// ---- per-step neighbour list (pi_variant 3) ---------------------------------------
+// ---- neighbour lists (pi_variant 3-5) ---------------------------------------------
 //
 // The Symplectic step evaluates the interaction on state n and on state n+1/2.
-// Instead of sorting again for n+1/2, the candidate test runs once per step,
-// on state n, with radius 2h + skin, and writes every candidate that passes
-// into a per-target list (entry = index | row offset); both evaluations then
-// walk the list and keep the pairs with 0 < r^2 < (2h)^2 at their own state.
-// The half-step state keeps the cells of state n (offsets may leave [0, cs)
-// by a half-step displacement), so relative positions stay cell + offset in
-// FP32.  The skin covers twice the largest half-step displacement, which the
-// predictor checks (kFlagSkin).  The pair set of each evaluation is the same
-// as with a fresh neighbour list; only the order of the sums differs.
+// Instead of sorting again for n+1/2, the candidate test runs on state n with
+// radius 2h + skin and writes every chunk of candidates that passes as a
+// record (first index | row code, mask) into a per-target list; both
+// evaluations walk the records and keep the pairs with 0 < r^2 < (2h)^2 at
+// their own state.  The half-step state keeps the cells of state n (offsets
+// may leave [0, cs) by a half-step displacement), so relative positions stay
+// cell + offset in FP32.  The skin covers twice the largest displacement since
+// the build, which the predictor checks (kFlagSkin).  Variants 3 and 4 build
+// the list every step; 5 keeps it, with the particle order and cells, until a
+// particle of the case could leave the skin.  The pair set of each evaluation
+// is the same as with a fresh neighbour list; only the order of the sums
+// differs.
 
 
 // The interaction over a target's list (state n or n+1/2, same order and
