@@ -491,7 +491,8 @@ def test_boundary_only_case(variant):
     eng.destroy()
 
 
-def test_empty_case_and_empty_batch_member():
+@pytest.mark.parametrize("variant", [5, 4])
+def test_empty_case_and_empty_batch_member(variant):
     """A case without particles: creation, steps and stats are no-ops; as a
     member of a batch it does not disturb the others."""
     full = cases.dam_break(0.04, seed=7)
@@ -501,10 +502,10 @@ def test_empty_case_and_empty_batch_member():
     assert e.stats()["n"] == 0 and e.stats()["step"] == 0
     e.destroy()
     bat = sph.Engine.batch([full, empty])
-    bat.set_options(pi_variant=4)
+    bat.set_options(pi_variant=variant)
     bat.step(4)
     alone = sph.Engine.create(full)
-    alone.set_options(pi_variant=4)      # the batch's path
+    alone.set_options(pi_variant=variant)
     alone.step(4)
     a, b = alone.get_state(), bat.get_state(0)
     for k in ("pos", "vel", "rho"):
@@ -635,5 +636,28 @@ def test_pool_on_kept_list_matches_alone():
     for k in ("pos", "vel", "rho"):
         assert np.array_equal(a[k], b[k]), k
     assert a["t"] == b["t"]
+    eb.destroy()
+    pool.destroy()
+
+
+def test_pool_emptied_and_refilled_on_kept_list():
+    """A pool whose only case leaves and whose next case arrives afterwards:
+    the new case steps as it does alone, bit for bit."""
+    ca = cases.dam_break(0.04, seed=11)
+    cb = cases.sloshing_tank(2200, 0.28, 0.02, 0.9, seed=12)
+    pool = sph.Engine.pool(200000, 2000000, 4)
+    sa = pool.admit(ca, t_end=1.0)
+    pool.pool_step(9)
+    pool.release(sa)
+    pool.pool_step(3)                 # nothing to step
+    sb = pool.admit(cb, t_end=1.0)
+    pool.pool_step(11)
+    pool.pool_step(6)
+    eb = sph.Engine.create(cb)
+    eb.step(17)
+    a, b = pool.get_state(sb), eb.get_state()
+    for k in ("pos", "vel", "rho"):
+        assert np.array_equal(a[k], b[k]), k
+    assert pool.usage()["cases"] == 1
     eb.destroy()
     pool.destroy()
