@@ -141,29 +141,34 @@ def test_mdbc_still_tank_hydrostatic_gpu():
     eng.destroy()
 
 
-def test_mdbc_raw_resume_and_pool():
+@pytest.mark.parametrize("variant", [5, 4])
+def test_mdbc_raw_resume_and_pool(variant):
     c = cases.dam_break(0.04, boundary_mode=1, mdbc_slip=1, seed=3)
     a = sph.Engine.create(c)
-    a.set_options(pi_variant=4)           # the pool's path
+    a.set_options(pi_variant=variant)
     a.step(6)
     b = sph.Engine.from_raw(c, a.get_raw())
-    b.set_options(pi_variant=4)
+    b.set_options(pi_variant=variant)
     a.step(5)
     b.step(5)
     sa, sb = a.get_state(), b.get_state()
     for k in ("pos", "vel", "rho"):
         assert np.array_equal(sa[k], sb[k]), k
+    # in a pool beside another mDBC case, as alone (a snapshot rebuilds the
+    # kept list, so the reference runs its 11 steps without one)
+    ref = sph.Engine.create(c)
+    ref.set_options(pi_variant=variant)
+    ref.step(11)
     pool = sph.Engine.pool(400000, 2000000, 4)
-    pool.set_options(pi_variant=4)         # one list per step: bit for bit
+    pool.set_options(pi_variant=variant)
     pool.admit(cases.dam_break(0.04, seed=5, boundary_mode=1), t_end=1.0)
     s = pool.admit(c, t_end=1.0)
     pool.pool_step(11)
-    sp = pool.get_state(s)
+    sp, sr = pool.get_state(s), ref.get_state()
     for k in ("pos", "vel", "rho"):
-        assert np.array_equal(sp[k], sa[k]), k
-    a.destroy()
-    b.destroy()
-    pool.destroy()
+        assert np.array_equal(sp[k], sr[k]), k
+    for e in (a, b, ref, pool):
+        e.destroy()
 
 
 @pytest.mark.parametrize("variant", [5, 4])

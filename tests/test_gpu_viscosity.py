@@ -84,16 +84,17 @@ def test_mixed_physics_batch_matches_oracle():
     bat.destroy()
 
 
-def test_pool_sps_case_equals_alone():
+@pytest.mark.parametrize("variant", [5, 4])
+def test_pool_sps_case_equals_alone(variant):
     c = sps_case(0.04, seed=4)
     other = cases.dam_break(0.04, seed=5)
     pool = sph.Engine.pool(200000, 2000000, 4)
-    pool.set_options(pi_variant=4)         # one list per step: bit for bit
+    pool.set_options(pi_variant=variant)
     pool.admit(other, t_end=1.0)
     s = pool.admit(c, t_end=1.0)
     pool.pool_step(8)
     e = sph.Engine.create(c)
-    e.set_options(pi_variant=4)          # the pool's path
+    e.set_options(pi_variant=variant)
     e.step(8)
     a, b = pool.get_state(s), e.get_state()
     for k in ("pos", "vel", "rho"):
