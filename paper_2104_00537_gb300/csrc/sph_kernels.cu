@@ -1537,25 +1537,32 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
   unsigned cm = 0u;
   int cbase = 0;
   float sy = 0.f, sz = 0.f;
+  // the next record of the lane: base index, candidate mask, row offsets
+  auto next_record = [&]() {
+    const uint2 rec = mine[r++];
+    cbase = (int)(rec.x & kListIndexMask);
+    cm = rec.y;
+    int rdy, rdz;
+    list_row_decode(rec.x, rdy, rdz);
+    sy = fmaf(-(float)rdy, cs, pa.y);
+    sz = fmaf(-(float)rdz, cs, pa.z);
+  };
 #pragma unroll 1
   for (;;) {
-    if (cm == 0u && r < nrec) {
-      const uint2 rec = mine[r++];
-      cbase = (int)(rec.x & kListIndexMask);
-      cm = rec.y;
-      int rdy, rdz;
-      list_row_decode(rec.x, rdy, rdz);
-      sy = fmaf(-(float)rdy, cs, pa.y);
-      sz = fmaf(-(float)rdz, cs, pa.z);
-    }
+    if (cm == 0u && r < nrec) next_record();
     if (!__any_sync(full, cm != 0u)) break;
     if (cm) {
+      // the lane's next two candidates in list order; the second may open the
+      // next record, so no slot idles at the end of an odd record
       const int k1 = 31 - __clz(cm);
       cm ^= 1u << k1;
+      const int j1 = cbase + k1;
+      const float sy1 = sy, sz1 = sz;
+      if (cm == 0u && r < nrec) next_record();
       const bool h2 = cm != 0u;
       const int k2 = h2 ? 31 - __clz(cm) : k1;
       if (h2) cm ^= 1u << k2;
-      const int j1 = cbase + k1, j2 = cbase + k2;
+      const int j2 = h2 ? cbase + k2 : j1;
       const float4 pb1 = posc[j1];
       const float4 pb2 = posc[j2];
       const float4 vb1 = velrho[j1];
@@ -1567,7 +1574,7 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
         const float4 vb = u ? vb2 : vb1;
         const int j = u ? j2 : j1;
         const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
-        const float ry = sy - pb.y, rz = sz - pb.z;
+        const float ry = (u ? sy : sy1) - pb.y, rz = (u ? sz : sz1) - pb.z;
         const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
         if ((u == 0 || h2) && __float_as_uint(r2) - 1u < r2max_u) {
           const bool bfluid = j < jb;
