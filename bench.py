@@ -63,7 +63,8 @@ def measured_traffic(cell_mode, workload_name, variant, builds_per_step=1.0):
     """DRAM bytes per interaction launch, as bench.py times it, from the
     committed ncu capture of the list kernels (profiles/k_interact_list_traffic.json),
     or None when the capture does not match (other workload / cell size /
-    variant, or the kernel source changed since the counters were taken).
+    variant, or the kernel source or the build flags changed since the
+    counters were taken).
     Variant 4: (build + two evaluations) / 2; variant 5: one evaluation plus
     half the build times the builds per step."""
     import hashlib
@@ -74,6 +75,12 @@ def measured_traffic(cell_mode, workload_name, variant, builds_per_step=1.0):
     except (OSError, ValueError, KeyError):
         return None
     if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+        return None
+    try:
+        flags = open(os.path.join(ROOT, d["build"]), "rb").read()
+    except (OSError, KeyError):
+        return None
+    if hashlib.sha256(flags).hexdigest() != d.get("build_sha256"):
         return None
     if workload_name != "dam_break" or cell_mode != 1:
         return None
