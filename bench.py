@@ -59,34 +59,46 @@ def fp32_peak_tflops(mhz=SM_MAX_MHZ):
     return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
-def measured_traffic(cell_mode, workload_name, variant, builds_per_step=1.0):
-    """DRAM bytes per interaction launch, as bench.py times it, from the
-    committed ncu capture of the list kernels (profiles/k_interact_list_traffic.json),
-    or None when the capture does not match (other workload / cell size /
-    variant, or the kernel source or the build flags changed since the
-    counters were taken).
-    Variant 4: (build + two evaluations) / 2; variant 5: one evaluation plus
-    half the build times the builds per step."""
+def list_capture(cell_mode, workload_name, variant):
+    """The committed ncu capture of the list kernels for this variant
+    (profiles/k_interact_list_traffic.json), or None when it does not match:
+    another workload / cell size / variant, or the kernel source or the build
+    flags changed since the counters were taken."""
     import hashlib
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "k_interact_list_traffic.json")))
         src = open(os.path.join(ROOT, d["source"]), "rb").read()
+        flags = open(os.path.join(ROOT, d["build"]), "rb").read()
         v = d["variants"][str(variant)]
     except (OSError, ValueError, KeyError):
         return None
     if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
         return None
-    try:
-        flags = open(os.path.join(ROOT, d["build"]), "rb").read()
-    except (OSError, KeyError):
-        return None
     if hashlib.sha256(flags).hexdigest() != d.get("build_sha256"):
         return None
     if workload_name != "dam_break" or cell_mode != 1:
         return None
+    return v
+
+
+def measured_traffic(cell_mode, workload_name, variant, builds_per_step=1.0):
+    """DRAM bytes per interaction launch, as bench.py times it, from the
+    committed capture (None when it does not match, see list_capture).
+    Variant 4: (build + two evaluations) / 2; variant 5: one evaluation plus
+    half the build times the builds per step."""
+    v = list_capture(cell_mode, workload_name, variant)
+    if v is None:
+        return None
     if variant == 4:
         return (v["build_bytes"] + 2 * v["eval_bytes"]) / 2
     return v["eval_bytes"] + builds_per_step * v["build_bytes"] / 2
+
+
+def measured_limiter(cell_mode, workload_name, variant):
+    """The hardware unit that bounds the list evaluation in the committed
+    capture, with its utilisation (None when the capture does not match)."""
+    v = list_capture(cell_mode, workload_name, variant)
+    return None if v is None else v.get("limiter")
 
 
 def workload(name, rank=0, **kw):
@@ -489,12 +501,14 @@ def main():
     pi_avg_s = tm["pi_ms"] / 1000.0 / launches
     achieved = flops / launches / pi_avg_s / 1e12
     peak = fp32_peak_tflops()
+    captured = ((args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) ==
+                (1, "symplectic", 0, 0) and eff_var in (4, 5))
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": measured_traffic(args.cell_mode, args.workload, eff_var,
-                                            builds / args.steps)
-                if (args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) ==
-                (1, "symplectic", 0, 0) and eff_var in (4, 5) else None,
+                                            builds / args.steps) if captured else None,
+                "limiter": measured_limiter(args.cell_mode, args.workload, eff_var)
+                if captured else None,
                 "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
                 "pi_ms_per_launch": 1000 * pi_avg_s,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal max clock)"}

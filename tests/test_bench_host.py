@@ -60,3 +60,39 @@ def test_reference_arm_prints_one_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "interactions/s"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["higher_is_better"] is True
+
+
+def test_profile_figures_follow_their_capture(tmp_path, monkeypatch):
+    """traffic and limiter come from the committed capture only while the
+    kernel source and the build flags are the ones it was taken with, and
+    only for its workload (a copy of the repository layout under tmp_path)."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "k.cu").write_text("kernel source")
+    (tmp_path / "build.py").write_text("FLAGS = ['-ftz=true']")
+    sha = lambda p: hashlib.sha256(p.read_bytes()).hexdigest()
+    lim = {"unit": "L1 data pipe", "pct_of_peak": 89.0}
+    d = {"source": "k.cu", "source_sha256": sha(tmp_path / "k.cu"),
+         "build": "build.py", "build_sha256": sha(tmp_path / "build.py"),
+         "variants": {"4": {"eval_bytes": 300, "build_bytes": 200, "limiter": lim},
+                      "5": {"eval_bytes": 330, "build_bytes": 200, "limiter": lim}}}
+    (tmp_path / "profiles" / "k_interact_list_traffic.json").write_text(json.dumps(d))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic(1, "dam_break", 4) == (200 + 2 * 300) / 2
+    assert bench.measured_traffic(1, "dam_break", 5, 0.25) == 330 + 0.25 * 200 / 2
+    assert bench.measured_limiter(1, "dam_break", 5) == lim
+    # another workload, cell size or variant: nothing
+    assert bench.measured_traffic(1, "wave_flume", 5) is None
+    assert bench.measured_traffic(0, "dam_break", 5) is None
+    assert bench.measured_limiter(1, "dam_break", 0) is None
+    # the flags changed since the capture: nothing
+    (tmp_path / "build.py").write_text("FLAGS = []")
+    assert bench.measured_traffic(1, "dam_break", 5) is None
+    assert bench.measured_limiter(1, "dam_break", 5) is None
+    # the kernel source changed: nothing
+    (tmp_path / "build.py").write_text("FLAGS = ['-ftz=true']")
+    assert bench.measured_traffic(1, "dam_break", 4) is not None
+    (tmp_path / "k.cu").write_text("kernel source, edited")
+    assert bench.measured_traffic(1, "dam_break", 4) is None
