@@ -478,6 +478,15 @@ def main():
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     p1 = totals()
+    # per-step device times of the timed steps (CUDA events on the engine's
+    # stream, start of one step's first interaction to the next's)
+    st_ms = eng.step_times()
+    step_time = None
+    if len(st_ms):
+        step_time = {"p50": max_over_ranks(float(np.percentile(st_ms, 50)), dist),
+                     "p99": max_over_ranks(float(np.percentile(st_ms, 99)), dist),
+                     "max": max_over_ranks(float(st_ms.max()), dist), "unit": "ms",
+                     "steps": int(len(st_ms))}
     tm = eng.timing(reset=True)
     builds = eng.list_info()["builds"] - builds0
     pairs = p1[0] - p0[0]
@@ -552,7 +561,7 @@ def main():
                       "parallelism": "replicas" if world > 1 else "single"},
            "steps_per_s": steps_per_s, "interactions_per_step": pairs / args.steps,
            "gpu_launches": tm["kernel_launches"], "roofline": roofline, "clocks": clk,
-           "step_bound": step_bound}
+           "step_bound": step_bound, "step_time": step_time}
 
     if rank == 0 and not args.no_e2e:
         # end to end through the public API from pinned host memory: create

@@ -208,6 +208,16 @@ int sph_set_options(sph_engine e, const sph_options *opt);
 int sph_get_timing(sph_engine e, double *pi_ms, int64_t *pi_launches,
                    double *step_ms, int64_t *kernel_launches, int32_t reset);
 
+/* sph_get_step_times: with timing on, the device time of each step timed
+ * since the last reset of sph_get_timing, in ms (CUDA events on the engine's
+ * stream: from the start of a step's first interaction evaluation to the
+ * start of the next step's; for the last step of an sph_step call, to the
+ * end of that call).  Copies min(*n, cap) values to the caller-owned host
+ * array ms (NULL or cap = 0: none); *n (may be NULL) receives the number of
+ * steps stored, at most 1,048,576 between resets.  SPH_ERR_ARG for a null
+ * engine or cap < 0.  Used for the p50/p99 step time of a run. */
+int sph_get_step_times(sph_engine e, float *ms, int64_t cap, int64_t *n);
+
 /* sph_list_info: neighbour-list builds since the engine was created (the
  * rebuilds of pi_variant 5, or one per step for 3 and 4), and with
  * check_list on the pairs found by brute force and the number of targets

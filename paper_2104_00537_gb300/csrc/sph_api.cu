@@ -235,6 +235,7 @@ struct sph_engine_t {
   int graph_ext = 0;  // ext + 2 sps + 4 mdbc + 8 list of the captured graph
   std::vector<cudaEvent_t> evs;
   double pi_ms = 0, step_ms = 0;
+  std::vector<float> step_times;  // per timed step (ms), at most kMaxStepTimes
   int64_t pi_launches = 0, kernel_launches = 0;
 
   void *dalloc(size_t bytes) {
@@ -286,6 +287,7 @@ int bits_for(int64_t cap_cells) { return key_bits(cap_cells); }
 // particle type; x 1.2, rounded up to a multiple of 32.  skin: the largest
 // list kept across steps (kListExtraMax x 2h) plus 0.1 h for one step.
 constexpr double kListExtraMax = 0.25;
+constexpr int64_t kMaxStepTimes = 1 << 20;  // per-step times kept between timing resets
 
 double slab_gap_h(int d, double o, double cs) {
   return d > 0 ? d * cs - o : (d < 0 ? o - (d + 1) * cs : 0.0);
@@ -1097,12 +1099,16 @@ int sph_step(sph_engine e, int64_t nsteps) {
   CUDA_TRY(cudaStreamSynchronize(e->s));
   if (timing) {
     for (int64_t j = 0; j < nsteps; j++) {
-      float a = 0.f, b = 0.f;
+      float a = 0.f, b = 0.f, d = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&a, e->evs[4 * j], e->evs[4 * j + 1]));
       if (e->integrator != 1)
         CUDA_TRY(cudaEventElapsedTime(&b, e->evs[4 * j + 2], e->evs[4 * j + 3]));
       e->pi_ms += a + b;
       e->pi_launches += e->integrator == 1 ? 1 : 2;
+      // step j: from the start of its first interaction to the start of the
+      // next step's (the call's last step: to the end of the call)
+      CUDA_TRY(cudaEventElapsedTime(&d, e->evs[4 * j], j + 1 < nsteps ? e->evs[4 * (j + 1)] : t1));
+      if ((int64_t)e->step_times.size() < kMaxStepTimes) e->step_times.push_back(d);
     }
     float tot = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&tot, t0, t1));
@@ -1125,7 +1131,17 @@ int sph_get_timing(sph_engine e, double *pi_ms, int64_t *pi_launches, double *st
     e->pi_ms = e->step_ms = 0;
     e->pi_launches = 0;
     e->kernel_launches = 0;
+    e->step_times.clear();
   }
+  return SPH_OK;
+}
+
+int sph_get_step_times(sph_engine e, float *ms, int64_t cap, int64_t *n) {
+  if (!e) return fail(SPH_ERR_ARG, "null engine");
+  if (cap < 0) return fail(SPH_ERR_ARG, "cap must be >= 0");
+  const int64_t have = (int64_t)e->step_times.size();
+  if (ms && cap > 0) std::copy_n(e->step_times.begin(), std::min(have, cap), ms);
+  if (n) *n = have;
   return SPH_OK;
 }
 

@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         "sph_set_options": (C.c_int, [vp, C.POINTER(Options)]),
         "sph_get_timing": (C.c_int, [vp, dp, C.POINTER(i64), dp, C.POINTER(i64), i32]),
         "sph_list_info": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
+        "sph_get_step_times": (C.c_int, [vp, vp, i64, C.POINTER(i64)]),
         "sph_get_raw": (C.c_int, [vp, i32, vp, C.POINTER(C.c_size_t)]),
         "sph_create_from_raw": (C.c_int, [C.POINTER(CaseParams), C.POINTER(Particles), vp,
                                           C.c_size_t, vp, ALLOC_FN, FREE_FN, vp,
@@ -323,6 +324,15 @@ class Engine:
                                       int(reset)))
         return dict(pi_ms=pm.value, pi_launches=ln.value, step_ms=sm.value,
                     kernel_launches=kl.value)
+
+    def step_times(self):
+        """Device time of each step timed since the last timing reset (ms)."""
+        n = C.c_int64()
+        check(self.lib.sph_get_step_times(self.h, None, 0, C.byref(n)))
+        out = np.zeros(n.value, np.float32)
+        check(self.lib.sph_get_step_times(self.h, out.ctypes.data_as(C.c_void_p), n.value,
+                                          C.byref(n)))
+        return out
 
     def _n(self, icase):
         return self.sizes[icase]

@@ -661,3 +661,28 @@ def test_pool_emptied_and_refilled_on_kept_list():
     assert pool.usage()["cases"] == 1
     eb.destroy()
     pool.destroy()
+
+
+@pytest.mark.parametrize("variant", [5, 0])
+def test_step_times_cover_the_timed_steps(c0, variant):
+    """Per-step device times (sph_get_step_times): one per timed step over
+    several calls, each positive, together no more than the calls' own device
+    time and most of it; a timing reset clears them; untimed steps add none."""
+    eng = sph.Engine.create(c0)
+    eng.set_options(pi_variant=variant, timing=1)
+    eng.step(3)
+    eng.timing(reset=True)
+    eng.step(7)
+    eng.step(13)
+    st = eng.step_times()
+    tm = eng.timing()
+    assert st.shape == (20,)
+    assert (st > 0).all()
+    assert st.sum() <= tm["step_ms"] * (1 + 1e-3) + 1e-3
+    assert st.sum() >= 0.5 * tm["step_ms"]
+    eng.timing(reset=True)
+    assert eng.step_times().shape == (0,)
+    eng.set_options(pi_variant=variant, timing=0)
+    eng.step(5)
+    assert eng.step_times().shape == (0,)
+    eng.destroy()
