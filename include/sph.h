@@ -78,10 +78,10 @@ typedef struct {
                                * offsets, sph_particles.ghost)             */
   double nu0;                 /* kinematic viscosity of Eq 23 (m^2/s)       */
   int32_t mdbc_slip;          /* mDBC boundary velocity: 0 the imposed one
-                               * (Eq 37); 1 no-slip, 2 v_wall - v_G; 2 free
-                               * slip: tangential part of v_G with the
-                               * normal part of 2 v_wall - v_G (normal along
-                               * the ghost offset)                          */
+                               * (Eq 37); 1 no-slip, v_B = 2 v_wall - v_G;
+                               * 2 free slip: the tangential part of v_G
+                               * with the normal part of 2 v_wall - v_G
+                               * (normal along the ghost offset)            */
   int32_t pad2_;
 } sph_case_params;
 
@@ -156,7 +156,9 @@ typedef struct {
                        * the Verlet scheme; 3 and 4 with Verlet, and any
                        * list beyond 2^25 particles, fall back to 0      */
   int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
-  int32_t timing;     /* 1: time every PI launch with CUDA events              */
+  int32_t timing;     /* 1: time every PI launch and every step with CUDA
+                       * events (sph_get_timing, sph_get_step_times); the
+                       * steps then run without the captured step graph   */
   float list_skin;    /* pi_variant 5: skin added for the steps the list is
                        * kept, as a fraction of 2h, in [0, 0.25]; < 0: the
                        * default (0.04)                                    */
