@@ -5,6 +5,8 @@ quadrature, a closed form, a conservation law, a continuum limit of the SPH
 operators, or a brute-force enumeration.
 """
 import math
+import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -15,7 +17,45 @@ from paper_2104_00537_gb300 import cases
 from tests.lattice import centre_index, lattice_case, random_cloud
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def paper_constants():
+    """The constants the paper prints (tests/golden/paper_constants.txt, each
+    line citing its passage), as exact fractions by name."""
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_constants.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                name, value = line.split()[:2]
+                out[name] = Fraction(value)
+    return out
+
+
 # ---- Eq 11: Wendland C2 kernel -------------------------------------------
+
+def test_wendland_normalisation_is_the_printed_one():
+    """Eq 11 at q = 0 gives W = a_D, with a_D as the paper prints it for 3-D."""
+    a = float(paper_constants()["wendland_aD_3d_times_pi_h3"])
+    for h in (0.01, 0.0346, 1.0):
+        assert oracle.wendland_w(0.0, h) == pytest.approx(a / (math.pi * h ** 3), rel=1e-14)
+
+
+def test_case_defaults_are_the_printed_constants():
+    """The generators' physics constants are the paper's: gamma (Eq 28),
+    c_s = 10 |v|max with |v|max read as sqrt(g H) (Sect. 2.4), C_CFL in the
+    printed range (Eq 35), eta^2 = 0.001 h^2 (Eq 21), N_S = 40 (Eq 31)."""
+    k = paper_constants()
+    depth = 0.4
+    p = cases.default_params(0.02, depth, (0, 0, 0), (1, 1, 1))
+    assert p["gamma"] == float(k["tait_gamma"])
+    assert p["cs0"] == pytest.approx(float(k["sound_speed_factor"]) * math.sqrt(cases.G * depth),
+                                     rel=1e-15)
+    assert float(k["cfl_min"]) <= p["cfl"] <= float(k["cfl_max"])
+    assert p["eta2"] == pytest.approx(float(k["eta2_over_h2"]) * p["h"] ** 2, rel=1e-15)
+    assert p["verlet_steps"] == int(k["verlet_ns"])
+
+
 
 @pytest.mark.parametrize("h", [0.01, 0.0346, 1.0])
 def test_wendland_normalises_to_one(h):
@@ -76,7 +116,6 @@ def test_tait_isothermal_special_case():
 
 def test_tait_exact_rational_value():
     """rho/rho0 = 101/100, gamma = 7: compare with exact rational arithmetic."""
-    from fractions import Fraction
     p = cases.default_params(0.02, 0.4, (0, 0, 0), (1, 1, 1), cs0=20.0)
     B = Fraction(400) * 1000 / 7
     exact = B * (Fraction(101, 100) ** 7 - 1)
@@ -240,9 +279,11 @@ def test_sps_stress_of_a_simple_shear():
     c.vel[:, 0] = gam * (c.pos[:, 1] - c.pos[ic, 1])
     T = oracle.sps_tau(c.params, c.pos, c.vel, c.rho, c.ptype)[ic]
     dp = c.params["dp"]
-    assert T[3] == pytest.approx((0.12 * dp) ** 2 * gam ** 2 / 2, rel=2e-2)
+    kc = paper_constants()
+    c_s, c_l = float(kc["sps_smagorinsky_cs"]), float(kc["sps_blin_cl"])
+    assert T[3] == pytest.approx((c_s * dp) ** 2 * gam ** 2 / 2, rel=2e-2)
     for k in range(3):
-        assert T[k] == pytest.approx(-(2 / 3) * 0.0066 * dp ** 2 * gam ** 2 / 4, rel=4e-2)
+        assert T[k] == pytest.approx(-(2 / 3) * c_l * dp ** 2 * gam ** 2 / 4, rel=4e-2)
     assert abs(T[4]) < 1e-6 * T[3] and abs(T[5]) < 1e-6 * T[3]
 
 
