@@ -9,6 +9,7 @@ A *case* is any object with the attributes produced by the seeded input
 generators (``params`` dict, ``pos`` [n,3] float64, ``vel`` [n,3], ``rho`` [n],
 ``ptype`` [n] uint8, ``group`` [n] int32 and ``motions`` list of dicts).
 """
+import contextlib
 import ctypes as C
 import os
 
@@ -46,52 +47,71 @@ def lib():
     """Load (building first if needed) the oracle shared library."""
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        P = C.POINTER(OrcParams)
-        L.orc_wendland_w.restype = C.c_double
-        L.orc_wendland_w.argtypes = [C.c_double, C.c_double]
-        L.orc_wendland_gradfac.restype = C.c_double
-        L.orc_wendland_gradfac.argtypes = [C.c_double, C.c_double]
-        L.orc_tait.restype = C.c_double
-        L.orc_tait.argtypes = [P, C.c_double]
-        L.orc_sps_tau.restype = C.c_int
-        L.orc_sps_tau.argtypes = [P, C.c_int64, _D, _D, _D, _U8, C.c_void_p, _D]
-        L.orc_rho_hydro.restype = C.c_double
-        L.orc_rho_hydro.argtypes = [P, C.POINTER(C.c_double)]
-        L.orc_grid.restype = C.c_int
-        L.orc_grid.argtypes = [P, _D, C.POINTER(C.c_double), _I64, C.POINTER(C.c_int32)]
-        L.orc_cells.restype = C.c_int
-        L.orc_cells.argtypes = [P, C.c_int64, _D, _I64]
-        L.orc_sort.restype = C.c_int64
-        L.orc_sort.argtypes = [P, C.c_int64, _D, _U8, C.c_void_p, C.c_void_p, _I64]
-        L.orc_pairs.restype = C.c_int64
-        L.orc_pairs.argtypes = [P, C.c_int64, _D, C.c_void_p, C.c_int, _I64, _U64,
-                                C.c_void_p, C.c_int64]
-        L.orc_interact.restype = C.c_int64
-        L.orc_interact.argtypes = [P, C.c_int64, _D, _D, _D, _U8, C.c_void_p, C.c_int,
-                                   _D, _D, _D]
-        L.orc_interact_range.restype = C.c_int64
-        L.orc_interact_range.argtypes = [P, C.c_int64, _D, _D, _D, _U8, C.c_void_p, C.c_int,
-                                         C.c_int64, C.c_int64, _D, _D, _D]
-        L.orc_dt.restype = C.c_double
-        L.orc_dt.argtypes = [P, C.c_int64, _D, _D, _U8, C.c_void_p]
-        L.orc_step.restype = C.c_int64
-        L.orc_step.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _U8,
-                               _I32, _U8, C.c_void_p, C.POINTER(C.c_double),
-                               C.POINTER(C.c_double), C.c_int64, _D]
-        L.orc_mdbc.restype = C.c_int
-        L.orc_mdbc.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _U8, _I32,
-                               C.c_void_p, _D, C.c_double, C.c_void_p]
-        L.orc_step_verlet.restype = C.c_int64
-        L.orc_step_verlet.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _D, _D,
-                                      _U8, _I32, _U8, C.c_void_p, C.POINTER(C.c_double),
-                                      C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32,
-                                      C.c_int64, _D]
-        L.orc_diag.restype = C.c_int
-        L.orc_diag.argtypes = [P, C.c_int64, _D, _D, _U8, C.c_void_p, _D]
-        _lib = L
+        _lib = load_library(_build.build())
     return _lib
+
+
+@contextlib.contextmanager
+def library(path):
+    """Route every call of this module to another build of sph_oracle.c for
+    the duration of the block.  The mutation tests compile a copy with one
+    plausible mistake planted and check that a pin fails on it."""
+    global _lib
+    saved = _lib
+    _lib = load_library(path)
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def load_library(path):
+    """A build of the oracle at `path`, with the ctypes signatures of this
+    module's calls."""
+    L = C.CDLL(path)
+    P = C.POINTER(OrcParams)
+    L.orc_wendland_w.restype = C.c_double
+    L.orc_wendland_w.argtypes = [C.c_double, C.c_double]
+    L.orc_wendland_gradfac.restype = C.c_double
+    L.orc_wendland_gradfac.argtypes = [C.c_double, C.c_double]
+    L.orc_tait.restype = C.c_double
+    L.orc_tait.argtypes = [P, C.c_double]
+    L.orc_sps_tau.restype = C.c_int
+    L.orc_sps_tau.argtypes = [P, C.c_int64, _D, _D, _D, _U8, C.c_void_p, _D]
+    L.orc_rho_hydro.restype = C.c_double
+    L.orc_rho_hydro.argtypes = [P, C.POINTER(C.c_double)]
+    L.orc_grid.restype = C.c_int
+    L.orc_grid.argtypes = [P, _D, C.POINTER(C.c_double), _I64, C.POINTER(C.c_int32)]
+    L.orc_cells.restype = C.c_int
+    L.orc_cells.argtypes = [P, C.c_int64, _D, _I64]
+    L.orc_sort.restype = C.c_int64
+    L.orc_sort.argtypes = [P, C.c_int64, _D, _U8, C.c_void_p, C.c_void_p, _I64]
+    L.orc_pairs.restype = C.c_int64
+    L.orc_pairs.argtypes = [P, C.c_int64, _D, C.c_void_p, C.c_int, _I64, _U64,
+                            C.c_void_p, C.c_int64]
+    L.orc_interact.restype = C.c_int64
+    L.orc_interact.argtypes = [P, C.c_int64, _D, _D, _D, _U8, C.c_void_p, C.c_int,
+                               _D, _D, _D]
+    L.orc_interact_range.restype = C.c_int64
+    L.orc_interact_range.argtypes = [P, C.c_int64, _D, _D, _D, _U8, C.c_void_p, C.c_int,
+                                     C.c_int64, C.c_int64, _D, _D, _D]
+    L.orc_dt.restype = C.c_double
+    L.orc_dt.argtypes = [P, C.c_int64, _D, _D, _U8, C.c_void_p]
+    L.orc_step.restype = C.c_int64
+    L.orc_step.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _U8,
+                           _I32, _U8, C.c_void_p, C.POINTER(C.c_double),
+                           C.POINTER(C.c_double), C.c_int64, _D]
+    L.orc_mdbc.restype = C.c_int
+    L.orc_mdbc.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _U8, _I32,
+                           C.c_void_p, _D, C.c_double, C.c_void_p]
+    L.orc_step_verlet.restype = C.c_int64
+    L.orc_step_verlet.argtypes = [P, C.c_void_p, C.c_int32, C.c_int64, _D, _D, _D, _D, _D,
+                                  _U8, _I32, _U8, C.c_void_p, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32,
+                                  C.c_int64, _D]
+    L.orc_diag.restype = C.c_int
+    L.orc_diag.argtypes = [P, C.c_int64, _D, _D, _U8, C.c_void_p, _D]
+    return L
 
 
 def make_params(p: dict) -> OrcParams:

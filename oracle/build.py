@@ -19,13 +19,19 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)):
         return LIB
     tmp = LIB + ".%d.tmp" % os.getpid()
-    # -ffp-contract=off: no fused multiply-add, so x86 and Arm hosts give the
-    # same FP64 rounding.
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-Wall", "-o", tmp, SRC, "-lm"]
-    subprocess.check_call(cmd)
+    compile_source(SRC, tmp)
     os.replace(tmp, LIB)
     return LIB
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile one oracle source (sph_oracle.c, or a test's patched copy of
+    it) into the shared library `out`.  -ffp-contract=off: no fused
+    multiply-add, so x86 and Arm hosts give the same FP64 rounding."""
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-Wall", "-I", HERE, "-o", out, src, "-lm"]
+    subprocess.check_call(cmd)
+    return out
 
 
 if __name__ == "__main__":

@@ -224,6 +224,37 @@ def test_viscosity_vanishes_for_receding_pairs():
     assert mu[0] == pytest.approx(h * 0.6 / 0.02, rel=4e-3)
 
 
+def test_artificial_viscosity_two_particle_value():
+    """Eq 21-22 for two approaching fluid particles a distance h apart (q = 1,
+    where grad_a W_ab = -(5 a_D / h^2)(1/8) r_ab), with unequal densities:
+    the viscous part of dv_a/dt (the acceleration minus that with alpha = 0)
+    has the closed form m alpha cs0 u 5 a_D / (8 (1 + eta^2/h^2) rho_bar h)
+    along r_ab, u the closing speed and rho_bar = (rho_a + rho_b)/2.  A
+    dropped h in mu_ab, rho_a in place of the mean, or eta in place of eta^2
+    each moves the value by far more than the 1e-12 allowed."""
+    c = random_cloud(N=2, L=0.01, seed=1)
+    p = c.params
+    h, dp, alpha, cs0 = p["h"], p["dp"], p["alpha"], p["cs0"]
+    u = 0.7
+    c.pos[:] = [[0.05 + h, 0.05, 0.05], [0.05, 0.05, 0.05]]  # r_ab = +h e_x
+    c.vel[:] = [[-u / 2, 0.0, 0.0], [u / 2, 0.0, 0.0]]       # v_ab . r_ab = -u h
+    c.rho[:] = [1010.0, 990.0]
+    acc, _, mu, n = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
+    acc0, _, _, _ = oracle.interact(dict(p, alpha=0.0), c.pos, c.vel, c.rho, c.ptype)
+    assert n == 2
+    m = p["rho0"] * dp ** 3
+    a_d = 21.0 / (16.0 * math.pi * h ** 3)
+    eta2_h2 = p["eta2"] / (h * h)
+    rho_bar = 1000.0
+    expect = m * alpha * cs0 * u * 5.0 * a_d / (8.0 * (1.0 + eta2_h2) * rho_bar * h)
+    visc = acc - acc0
+    assert visc[0, 0] == pytest.approx(expect, rel=1e-12)
+    assert visc[1, 0] == pytest.approx(-expect, rel=1e-12)  # Pi_ab = Pi_ba
+    assert np.all(visc[:, 1:] == 0.0)
+    # Eq 35's inner maximum for the pair: h |v_ab . r_ab| / (r^2 + eta^2)
+    assert mu[0] == pytest.approx(u / (1.0 + eta2_h2), rel=1e-12)
+
+
 def test_continuity_uniform_dilation():
     """Eq 15 on a lattice with v = eps r: drho/dt -> -rho div v = -3 eps rho."""
     n = 11
@@ -416,6 +447,37 @@ def test_mdbc_reproduces_a_linear_density_field():
     np.testing.assert_array_equal(rho_b[f], rho[f])  # fluid untouched
 
 
+def test_mdbc_non_positive_extrapolation_takes_the_shepard_value():
+    """Eq 38 extrapolates rho_B = rho_G + (r_B - r_G) . grad rho_G.  For a
+    fluid density field that is steep enough (rho = 1000 + 4e4 z kg/m^3, all
+    fluid densities positive), that line crosses zero below the fluid, so for
+    the bottom-wall particles Eq 38 gives rho_B <= 0, for which Eq 28 has no
+    pressure (Eq 16 divides by rho_b) and the method is undefined.  Exactly
+    there the reading takes the Shepard density at the ghost node, a convex
+    combination of fluid densities; where the line stays positive (side
+    walls, and the whole tank for a gentler slope) Eq 38 is used as printed."""
+    c = mdbc_tank()
+    f, b = c.ptype == 0, c.ptype == 1
+    rho = c.rho.copy()
+    for slope, expect_fallback in ((4e4, True), (30.0, False)):
+        lin = lambda r: 1000.0 + slope * r[:, 2]
+        rho[f] = lin(c.pos[f])
+        assert rho[f].min() > 0
+        rho_b, _, dets = oracle.mdbc(c, c.pos, c.vel, rho, with_dets=True)
+        reg = b & (np.abs(dets) >= 1e-3)
+        line = lin(c.pos)
+        neg = reg & (line <= 0.0)
+        pos_ = reg & (line > 0.0)
+        np.testing.assert_allclose(rho_b[pos_], line[pos_], rtol=1e-10)
+        if expect_fallback:
+            assert neg.sum() > 10
+            assert np.all(rho_b[neg] > 0)
+            assert np.all(rho_b[neg] >= rho[f].min() * (1 - 1e-12))
+            assert np.all(rho_b[neg] <= rho[f].max() * (1 + 1e-12))
+        else:
+            assert neg.sum() == 0
+
+
 def test_mdbc_reproduces_a_constant_field_everywhere():
     """Constant density and velocity: corrected and Shepard branches both
     return the constant; no-slip mirrors the velocity about a fixed wall."""
@@ -506,15 +568,19 @@ def test_boundary_particles_dbc():
 
 # ---- Eq 33-35: time step and Symplectic integrator ------------------------
 
-def test_time_step_isolated_particle_closed_form():
-    """Eq 35 for an isolated particle: C_CFL min(sqrt(h/g), h/cs0)."""
-    c = cases.free_particle()
+@pytest.mark.parametrize("g", [9.81, 2.0e4])
+def test_time_step_isolated_particle_closed_form(g):
+    """Eq 35 for an isolated particle: C_CFL min(sqrt(h/g), h/cs0).  With
+    g = 9.81 the sound-speed term h/cs0 is the smaller, with g = 2e4 m/s^2
+    the force term sqrt(h/|f|), so both branches are pinned."""
+    c = cases.free_particle(gravity=(0.0, 0.0, -g))
     p = c.params
     acc, drho, mu, n = oracle.interact(p, c.pos, c.vel, c.rho, c.ptype)
     assert n == 0 and mu[0] == 0
     dt = oracle.time_step(p, acc, mu, c.ptype)
-    assert dt == pytest.approx(p["cfl"] * min(math.sqrt(p["h"] / 9.81), p["h"] / p["cs0"]),
-                               rel=1e-14)
+    dt_f, dt_cv = math.sqrt(p["h"] / g), p["h"] / p["cs0"]
+    assert (dt_f < dt_cv) == (g > 1e3)
+    assert dt == pytest.approx(p["cfl"] * min(dt_f, dt_cv), rel=1e-14)
 
 
 def test_free_fall_is_exact():
@@ -547,6 +613,87 @@ def test_imposed_motion_follows_law():
     np.testing.assert_allclose(s.vel[b, 0], m["amp"] * m["omega"] * math.cos(m["omega"] * t),
                                atol=1e-12)
     np.testing.assert_allclose(s.pos[b, 1:], c.pos[b, 1:], atol=0)
+
+
+def two_passing_particles(dt, T, u=1.0, offset=0.5):
+    """Two fluid particles passing each other at the constant closing speed u
+    (impact parameter offset x h), with no force acting: cs0 = 0 makes the
+    Tait pressure of Eq 28 vanish, alpha = delta = 0 and g = 0.  Their
+    densities then follow Eq 15 exactly as rho(t) = rho(0) + m (W(r(t)) -
+    W(r(0))), since v_ab . grad_a W_ab = dW(|r_ab|)/dt and rho_a = rho_b by
+    symmetry.  Returns (Symplectic rho_a after T, the closed form, the state)."""
+    c = lattice_case(n=2)
+    p = c.params
+    h, dp = p["h"], p["dp"]
+    c.pos = np.array([[0.1, 0.1, 0.1], [0.1 + 3.0 * h, 0.1 + offset * h, 0.1]])
+    c.vel = np.array([[u / 2, 0.0, 0.0], [-u / 2, 0.0, 0.0]])
+    c.rho = np.full(2, p["rho0"])
+    c.ptype = np.zeros(2, np.uint8)
+    c.group = np.full(2, -1, np.int32)
+    p.update(cs0=0.0, alpha=0.0, delta=0.0, ddt_mode=0, dt_fixed=dt,
+             domain_min=(-1.0, -1.0, -1.0), domain_max=(1.0, 1.0, 1.0))
+    s = oracle.OracleState(c)
+    s.step(int(round(T / dt)))
+    m = p["rho0"] * dp ** 3
+    r0 = np.linalg.norm(c.pos[0] - c.pos[1])
+    r1 = np.linalg.norm(s.pos[0] - s.pos[1])
+    exact = p["rho0"] + m * (oracle.wendland_w(r1, h) - oracle.wendland_w(r0, h))
+    return s.rho[0], exact, s
+
+
+def test_symplectic_density_update_against_the_closed_form():
+    """Eq 34 (rho^{n+1} = rho^n (2 - eps)/(2 + eps), eps = -(R^{n+1/2} /
+    rho^{n+1/2}) dt, predictor rho^{n+1/2} = rho^n + dt R^n / 2) on the
+    two-particle exact solution: the error after T = 0.06 s (the particles
+    cross each other's support) falls 4x per halving of dt (second order)
+    and is below 2e-3 kg/m^3 at dt = 1e-3 s.  (1 - eps) in place of the
+    fraction, or R^n in eps, is first order (2x per halving); rho^{n+1/2}
+    as the base does not converge."""
+    errs = []
+    for dt in (2e-3, 1e-3, 5e-4, 2.5e-4):
+        rho, exact, s = two_passing_particles(dt, 0.06)
+        assert s.t.value == pytest.approx(0.06, rel=1e-12)
+        assert rho == s.rho[1]  # symmetric pair
+        errs.append(abs(rho - exact))
+    # the closed form must matter: the density changes by a few kg/m^3
+    assert abs(exact - 1000.0) > 1.0
+    ratios = [errs[k] / errs[k + 1] for k in range(3)]
+    assert all(3.8 < r < 4.2 for r in ratios), ratios
+    assert errs[1] < 2e-3 * 1.1
+    # positions and velocities: no force, so exact to rounding
+    np.testing.assert_array_equal(s.vel, [[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]])
+
+
+def smooth_blob(dt, T, n=8):
+    """n^3 fluid particles (lattice with 5 % jitter) with a smooth density
+    perturbation of 0.4 % and a smooth velocity field, falling under gravity
+    with alpha = 0 (the min(v.r, 0) of Eq 21 is not smooth), advanced with a
+    fixed dt to time T by the Symplectic scheme."""
+    c = lattice_case(n=n, jitter=0.05, seed=5, alpha=0.0, gravity=(0.0, 0.0, -9.81))
+    p = c.params
+    x = (c.pos - c.pos.mean(0)) / (n * p["dp"])
+    c.rho = p["rho0"] * (1.0 + 0.004 * np.sin(2 * np.pi * x[:, 0]) * np.cos(np.pi * x[:, 1]))
+    c.vel = 0.05 * np.stack([np.sin(np.pi * x[:, 1]), np.cos(np.pi * x[:, 2]),
+                             np.sin(np.pi * x[:, 0])], 1)
+    p.update(dt_fixed=dt, domain_min=(-1.0, -1.0, -1.0), domain_max=(1.0, 1.0, 1.0))
+    s = oracle.OracleState(c)
+    s.step(int(round(T / dt)))
+    return s
+
+
+def test_symplectic_scheme_is_second_order():
+    """Eq 33-34 form a second-order scheme (Sect. 2.5.2): with dt = T/24,
+    T/48, T/96 and T/192 the differences between successive halvings of a
+    smooth pressure-driven flow shrink about 4x in r, v and rho (measured
+    3.6-4.2).  F^n in place of F^{n+1/2} in the velocity corrector, or r^{n+1}
+    = r^n + dt v^n, makes the scheme first order (about 2x)."""
+    T = 0.012
+    S = [smooth_blob(T / k, T) for k in (24, 48, 96, 192)]
+    for name in ("pos", "vel", "rho"):
+        d = [np.abs(getattr(S[k], name) - getattr(S[k + 1], name)).max() for k in range(3)]
+        assert d[2] > 0
+        ratios = [d[k] / d[k + 1] for k in range(2)]
+        assert all(r > 3.2 for r in ratios), (name, ratios)
 
 
 # ---- Eq 30-31: Verlet scheme ------------------------------------------------
