@@ -249,6 +249,32 @@ int sph_create_from_raw(const sph_case_params *params, const sph_particles *part
 int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho,
                     float *mumax, double *dt, int64_t *pairs);
 
+/* sph_eval_step: one interaction evaluation of the next step of the engine's
+ * scheme, through the very launches sph_step makes (Sect. 5.1, Fig. 7; Eq 15-18,
+ * 21-22, 35-36), without advancing the engine.  stage 0: the step's first
+ * evaluation, on state n; stage 1: its second, on the half-step state of
+ * Eq 33-34 (dt of Eq 35 from stage 0, then the predictor).  With a neighbour
+ * list (pi_variant 3-5) both walk the list's chunk records, and with the list
+ * kept across steps (5) state n and state n+1/2 are those kept in the order
+ * and cells of the list's build (cell offsets up to half the skin outside
+ * [0, cs)).  The part of the next step before its first evaluation runs for
+ * real -- a pending rebuild of the kept list, or the sort of a per-step list
+ * or cell walk -- and everything else the next step reads is restored, so
+ * sph_step afterwards takes the steps it would have taken (bit for bit).
+ * Outputs, caller-owned host buffers in the caller's particle order, any may
+ * be NULL: pos [3n] (FP64, from the evaluated cell + offset), vel [3n], rho [n]
+ * the evaluated state; acc [3n] dv/dt of Eq 22 + f (zero for B), drho [n]
+ * (Eq 15 with D_a; Eq 36 for B), mumax [n] the inner max of Eq 35 (zero for
+ * B); *dt the Eq 35 step of the step's first evaluation; *pairs the ordered
+ * pairs of this evaluation (Eq 4 support).  Particles frozen outside the
+ * domain report zero results.  SPH_ERR_ARG for a stage other than 0 or 1,
+ * or stage 1 on a cell walk (pi_variant 0-2) or the Verlet scheme (one
+ * evaluation per step); SPH_ERR_UNSTABLE (NaN/Inf, or the half step left the
+ * skin) and SPH_ERR_STATE (list overflow) as sph_step reports them. */
+int sph_eval_step(sph_engine e, int32_t icase, int32_t stage, double *pos, float *vel,
+                  float *rho, float *acc, float *drho, float *mumax, double *dt,
+                  int64_t *pairs);
+
 
 /* sph_eval_sps: tau / rho of Eq 25 (the SPS stress of Eq 24-25 with the
  * velocity gradient of the SPH estimate over b in P) for every particle of

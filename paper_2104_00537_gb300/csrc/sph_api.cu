@@ -606,14 +606,12 @@ void enqueue_step_verlet(sph_engine e, cudaEvent_t *ev) {
   launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
 }
 
-// One Symplectic step with the per-step neighbour list: NL on state n (Y),
-// the list (written by the first PI, variant 3, or built alone and then
-// evaluated, variant 4), Δt, half step in Y's order and cells (Z), PI over the
-// list, full step into X.  ev: 4 events around the two evaluations.
-void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
+// The sort of a per-step neighbour list (pi_variant 3, 4): NL on state n
+// (X -> Y) with the cell table, and the Eq 38-39 boundary values on it.
+void enqueue_list_nl(sph_engine e) {
   const int n = (int)e->n_phys;
   const int nl = (int)(e->n_phys - e->n_dead);
-  State &X = e->S[0], &Y = e->S[1], &Z = e->S[2];
+  State &X = e->S[0], &Y = e->S[1];
   cudaStream_t s = e->s;
   radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, s);
   launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
@@ -622,7 +620,26 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   if (e->mdbc)  // boundary values of Eq 38-39 on state n
     launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
                 e->ddyn, 0, s);
-  if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
+}
+
+// The first evaluation of a list step, on state n (Y, keysB): pi_variant 4
+// builds the list alone and walks it, 3 writes it during a compacted
+// evaluation, 5 walks the kept list (its Eq 38-39 boundary values first, in
+// the build's cells).  ev: events 0 and 1 (variant 5 records event 0 in its
+// guarded rebuild); mu (or null) receives mu_max of Eq 35 per particle.
+void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &Y = e->S[1];
+  cudaStream_t s = e->s;
+  float4 *tau4 = e->sps ? e->tau4 : nullptr;
+  if (e->opt.pi_variant == 5) {
+    if (e->mdbc)  // boundary values of Eq 38-39 on state n (the build's cells)
+      launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits,
+                  e->dconst, e->ddyn, 0, s, true);
+    launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
+                         e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
+                         e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu);
+  } else if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
     if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
                       s);
@@ -631,37 +648,59 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
                       e->list_cap, e->ncount, nullptr, nullptr, s);
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
-                         e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
+                         e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu);
   } else {
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
                       s);
     if (ev) cudaEventRecord(ev[0], s);
     launch_interact_build(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                           e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
-                          e->nlist, e->list_cap, e->ncount, e->ext,
-                          e->sps ? e->tau4 : nullptr, e->tau2, s);
+                          e->nlist, e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu);
   }
   if (ev) cudaEventRecord(ev[1], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
                       e->list_cap, e->ncount, e->ctl, s);
+}
+
+// The rest of a list step up to its second evaluation: dt (Eq 35), the half
+// step into Z in Y's order and cells (Eq 33-34; with the kept list checked
+// against the build positions), the Eq 38-39 boundary values on it, and the
+// interaction over the list on state n+1/2 (keysC).  ev: events 2 and 3.
+void enqueue_list_half(sph_engine e, cudaEvent_t *ev, float *mu) {
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &Y = e->S[1], &Z = e->S[2];
+  cudaStream_t s = e->s;
   launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
   launch_predictor_list(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
-                        e->keysC, e->press, nullptr, s);
+                        e->keysC, e->press, e->opt.pi_variant == 5 ? e->posc_ref : nullptr, s);
   if (e->mdbc)  // boundary values of Eq 38-39 on state n+1/2 (Y's cells)
     launch_mdbc(e->margin, nl, e->nvalid, e->keysC, half_state(Y, Z), e->press, e->cstart,
                 e->nbits, e->dconst, e->ddyn, 1, s, true);
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
-                       e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
+                       e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s,
+                       mu);
   if (ev) cudaEventRecord(ev[3], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysC, Z.posc, Y.cid, e->dconst, e->nbits, e->nlist,
                       e->list_cap, e->ncount, e->ctl, s);
+}
+
+// One Symplectic step with the per-step neighbour list: NL on state n (Y),
+// the list (written by the first PI, variant 3, or built alone and then
+// evaluated, variant 4), dt, half step in Y's order and cells (Z), PI over the
+// list, full step into X.  ev: 4 events around the two evaluations.
+void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &X = e->S[0], &Y = e->S[1], &Z = e->S[2];
+  enqueue_list_nl(e);
+  enqueue_list_first(e, ev, nullptr);
+  enqueue_list_half(e, ev, nullptr);
   launch_corrector_list(nl, e->keysB, e->keysC, Y, Z.velrho, e->ace, e->dconst, e->ddyn,
-                        e->nbits, X, e->keysA, s);
-  launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
+                        e->nbits, X, e->keysA, e->s);
+  launch_end_step(e->cap_cases, e->dconst, e->ddyn, e->s);
 }
 
 // The two guarded parts of a kept-list rebuild event.  The sort: cases that
@@ -770,6 +809,26 @@ void eager_if_rebuild(sph_engine e, int which, F fn) {
   if (err) e->cap_err = err;
 }
 
+// The guarded part of a step on the kept list: while a rebuild is requested,
+// the sort, reorder and cell table of the current state (X -> Y), then the
+// skin and the list on Y with every target's position (posc_ref); as IF nodes
+// of the captured step graph, or as small graphs launched eagerly (ev[0]
+// then sits between the two parts, so that the first evaluation's time
+// includes the list build).
+void enqueue_reuse_rebuild(sph_engine e, cudaEvent_t *ev) {
+  const float extra = e->opt.list_skin >= 0.f ? e->opt.list_skin : 0.04f;
+  auto nl_part = [=](cudaStream_t q) { enqueue_rebuild_sort(e, q); };
+  auto list_part = [=](cudaStream_t q) { enqueue_rebuild_list(e, extra, q); };
+  if (e->capturing) {
+    capture_if_rebuild(e, nl_part);
+    capture_if_rebuild(e, list_part);
+  } else {
+    eager_if_rebuild(e, 0, nl_part);
+    if (ev) cudaEventRecord(ev[0], e->s);
+    eager_if_rebuild(e, 1, list_part);
+  }
+}
+
 // One Symplectic step over the neighbour list kept across steps (pi_variant
 // 5).  Guarded by the rebuild request: sort, reorder and cell table of the
 // current state (X -> Y), then the skin and the list on Y with every target's
@@ -779,49 +838,14 @@ void eager_if_rebuild(sph_engine e, int which, F fn) {
 // step could leave the skin.  ev: 4 events around the two evaluations (the
 // first one's time includes the list build when it runs).
 void enqueue_step_reuse(sph_engine e, cudaEvent_t *ev) {
-  const int n = (int)e->n_phys;
   const int nl = (int)(e->n_phys - e->n_dead);
   State &X = e->S[0], &Y = e->S[1], &Z = e->S[2];
-  cudaStream_t s = e->s;
-  const float extra = e->opt.list_skin >= 0.f ? e->opt.list_skin : 0.04f;
-  auto nl_part = [=](cudaStream_t q) { enqueue_rebuild_sort(e, q); };
-  auto list_part = [=](cudaStream_t q) { enqueue_rebuild_list(e, extra, q); };
-  if (e->capturing) {
-    capture_if_rebuild(e, nl_part);
-    capture_if_rebuild(e, list_part);
-  } else {
-    eager_if_rebuild(e, 0, nl_part);
-    if (ev) cudaEventRecord(ev[0], s);
-    eager_if_rebuild(e, 1, list_part);
-  }
-  float4 *tau4 = e->sps ? e->tau4 : nullptr;
-  if (e->mdbc)  // boundary values of Eq 38-39 on state n (the build's cells)
-    launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
-                e->ddyn, 0, s, true);
-  launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
-                       e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
-                       e->list_cap, e->ncount, e->ext, tau4, e->tau2, s);
-  if (ev) cudaEventRecord(ev[1], s);
-  if (e->opt.check_list)
-    launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_cap, e->ncount, e->ctl, s);
-  launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
-  launch_predictor_list(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, Z.posc, Z.velrho,
-                        e->keysC, e->press, e->posc_ref, s);
-  if (e->mdbc)  // boundary values of Eq 38-39 on state n+1/2
-    launch_mdbc(e->margin, nl, e->nvalid, e->keysC, half_state(Y, Z), e->press, e->cstart,
-                e->nbits, e->dconst, e->ddyn, 1, s, true);
-  if (ev) cudaEventRecord(ev[2], s);
-  launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
-                       e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
-                       e->list_cap, e->ncount, e->ext, tau4, e->tau2, s);
-  if (ev) cudaEventRecord(ev[3], s);
-  if (e->opt.check_list)
-    launch_list_check(nl, e->nvalid, e->keysC, Z.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_cap, e->ncount, e->ctl, s);
+  enqueue_reuse_rebuild(e, ev);
+  enqueue_list_first(e, ev, nullptr);
+  enqueue_list_half(e, ev, nullptr);
   launch_corrector_reuse(nl, e->keysB, e->keysC, Y, Z.velrho, e->ace, e->posc_ref, e->dconst,
-                         e->ddyn, e->nbits, X, e->keysA, e->press, e->ctl, s);
-  launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
+                         e->ddyn, e->nbits, X, e->keysA, e->press, e->ctl, e->s);
+  launch_end_step(e->cap_cases, e->dconst, e->ddyn, e->s);
 }
 
 // One Verlet step over the list kept across steps: the guarded sort +
@@ -830,35 +854,14 @@ void enqueue_step_reuse(sph_engine e, cudaEvent_t *ev) {
 // Y and requests a rebuild when a particle is farther than (skin - 1e-3 h)/2
 // from its build position.  ev: 2 events around the PI (the build included).
 void enqueue_step_verlet_reuse(sph_engine e, cudaEvent_t *ev) {
-  const int n = (int)e->n_phys;
   const int nl = (int)(e->n_phys - e->n_dead);
   State &X = e->S[0], &Y = e->S[1];
-  cudaStream_t s = e->s;
-  const float extra = e->opt.list_skin >= 0.f ? e->opt.list_skin : 0.04f;
-  auto nl_part = [=](cudaStream_t q) { enqueue_rebuild_sort(e, q); };
-  auto list_part = [=](cudaStream_t q) { enqueue_rebuild_list(e, extra, q); };
-  if (e->capturing) {
-    capture_if_rebuild(e, nl_part);
-    capture_if_rebuild(e, list_part);
-  } else {
-    eager_if_rebuild(e, 0, nl_part);
-    if (ev) cudaEventRecord(ev[0], s);
-    eager_if_rebuild(e, 1, list_part);
-  }
-  if (e->mdbc)  // boundary values of Eq 38-39 on state n (the build's cells)
-    launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits, e->dconst,
-                e->ddyn, 0, s, true);
-  launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
-                       e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
-                       e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
-  if (ev) cudaEventRecord(ev[1], s);
-  if (e->opt.check_list)
-    launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_cap, e->ncount, e->ctl, s);
-  launch_dt(e->cap_cases, e->dconst, e->ddyn, s);
+  enqueue_reuse_rebuild(e, ev);
+  enqueue_list_first(e, ev, nullptr);
+  launch_dt(e->cap_cases, e->dconst, e->ddyn, e->s);
   launch_verlet_reuse(nl, e->keysB, Y, e->ace, e->dconst, e->ddyn, e->nbits, X, e->keysA,
-                      e->posc_ref, e->press, e->ctl, s);
-  launch_end_step(e->cap_cases, e->dconst, e->ddyn, s);
+                      e->posc_ref, e->press, e->ctl, e->s);
+  launch_end_step(e->cap_cases, e->dconst, e->ddyn, e->s);
 }
 
 // One Symplectic step (all cases).  ev: 4 events around the two PI launches.
@@ -1425,6 +1428,141 @@ int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho, float 
     }
   }
   if (pairs) *pairs = (int64_t)d.pairs;
+  return SPH_OK;
+}
+
+int sph_eval_step(sph_engine e, int32_t icase, int32_t stage, double *pos, float *vel,
+                  float *rho, float *acc, float *drho, float *mumax, double *dt,
+                  int64_t *pairs) {
+  int rc = valid_case(e, icase);
+  if (rc) return rc;
+  if (stage != 0 && stage != 1) return fail(SPH_ERR_ARG, "stage must be 0 or 1");
+  const bool listed = use_list(e);
+  if (stage == 1 && (!listed || e->integrator == 1))
+    return fail(SPH_ERR_ARG,
+                "stage 1 is the half-step evaluation of a Symplectic step over a neighbour "
+                "list (pi_variant 3-5); the cell walks (0-2) evaluate it with the stage-0 "
+                "kernel on a re-sorted state");
+  const int64_t n = e->slots[icase].n;
+  const int nl = (int)(e->n_phys - e->n_dead);
+  State &Y = e->S[1], &Z = e->S[2];
+  cudaStream_t s = e->s;
+  const bool reuse = listed && e->opt.pi_variant == 5;
+  // the part of the next step that precedes its first evaluation, run for
+  // real: the kept list's pending rebuild (which the next step then does not
+  // repeat), or the sort of a per-step list or cell walk
+  if (reuse) {
+    if (!e->s2) CUDA_TRY(cudaStreamCreateWithFlags(&e->s2, cudaStreamNonBlocking));
+    if (e->list_stale) launch_need_all(e->cap_cases, e->ddyn, s);
+    if (e->list_stale || e->list_dirty)
+      CUDA_TRY(cudaMemsetAsync(&e->ctl->rebuild, 1, sizeof(unsigned int), s));
+    e->list_stale = e->list_dirty = false;
+    e->cap_err = cudaSuccess;
+    enqueue_reuse_rebuild(e, nullptr);
+    if (e->cap_err != cudaSuccess) {
+      cudaStreamSynchronize(s);
+      return fail(SPH_ERR_CUDA, std::string("conditional graph node: ") +
+                                    cudaGetErrorString(e->cap_err));
+    }
+  } else if (listed) {
+    enqueue_list_nl(e);
+    e->list_stale = true;
+  } else {
+    enqueue_nl(e);
+    if (e->mdbc)
+      launch_mdbc(e->margin, nl, e->nvalid, e->keysB, Y, e->press, e->cstart, e->nbits,
+                  e->dconst, e->ddyn, 0, s);
+  }
+  // from here on nothing the next step reads is left changed: the per-case
+  // values, the list control and P/rho are restored afterwards
+  std::vector<CaseDyn> saved(e->cap_cases), d0(e->cap_cases), d1;
+  ListCtl ctl_saved{};
+  CUDA_TRY(cudaMemcpyAsync(saved.data(), e->ddyn, sizeof(CaseDyn) * e->cap_cases,
+                           cudaMemcpyDeviceToHost, s));
+  if (e->ctl)
+    CUDA_TRY(cudaMemcpyAsync(&ctl_saved, e->ctl, sizeof(ListCtl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<CaseDyn> fresh = saved;
+  for (auto &d : fresh) {
+    d.dtmin_bits = kFloatInfBits;
+    d.pairs = d.pairs_fb = d.pairs_bf = 0;
+    d.flags = 0;
+  }
+  CUDA_TRY(cudaMemcpyAsync(e->ddyn, fresh.data(), sizeof(CaseDyn) * e->cap_cases,
+                           cudaMemcpyHostToDevice, s));
+  float *press_saved = (float *)e->keysD;  // unused by the list steps' launches
+  if (nl > 0)
+    CUDA_TRY(cudaMemcpyAsync(press_saved, e->press, 4 * (size_t)nl, cudaMemcpyDeviceToDevice, s));
+  if (listed)
+    enqueue_list_first(e, nullptr, e->mu);
+  else
+    launch_interact(e->margin, e->opt.pi_variant, nl, e->nvalid, e->keysB, Y.posc, Y.velrho,
+                    e->press, Y.cid, e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn,
+                    e->ace, e->mu, 1, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s);
+  CUDA_TRY(cudaMemcpyAsync(d0.data(), e->ddyn, sizeof(CaseDyn) * e->cap_cases,
+                           cudaMemcpyDeviceToHost, s));
+  if (stage == 1) {
+    d1.resize(e->cap_cases);
+    enqueue_list_half(e, nullptr, e->mu);
+    CUDA_TRY(cudaMemcpyAsync(d1.data(), e->ddyn, sizeof(CaseDyn) * e->cap_cases,
+                             cudaMemcpyDeviceToHost, s));
+  }
+  // results and the evaluated state, in the caller's order
+  const uint32_t *keys = stage == 1 ? e->keysC : e->keysB;
+  const State st = stage == 1 ? half_state(Y, Z) : Y;
+  char *p = e->io;
+  double *d_pos = (double *)p;
+  p += align256(24 * n);
+  float *d_vel = (float *)p;
+  p += align256(12 * n);
+  float *d_rho = (float *)p;
+  p += align256(4 * n);
+  float *d_acc = (float *)p;
+  p += align256(12 * n);
+  float *d_drho = (float *)p;
+  p += align256(4 * n);
+  float *d_mu = (float *)p;
+  launch_scatter_forces(nl, Y.cid, Y.id, icase, 0, e->nvalid, e->ace, e->mu, d_acc, d_drho, d_mu,
+                        s, keys, e->nbits);
+  launch_export((int)e->n_phys, keys, st, e->dconst, icase, 0, e->nbits, d_pos, d_vel, d_rho,
+                nullptr, s);
+  CUDA_TRY(cudaGetLastError());
+  if (pos) CUDA_TRY(cudaMemcpyAsync(pos, d_pos, 24 * n, cudaMemcpyDeviceToHost, s));
+  if (vel) CUDA_TRY(cudaMemcpyAsync(vel, d_vel, 12 * n, cudaMemcpyDeviceToHost, s));
+  if (rho) CUDA_TRY(cudaMemcpyAsync(rho, d_rho, 4 * n, cudaMemcpyDeviceToHost, s));
+  if (acc) CUDA_TRY(cudaMemcpyAsync(acc, d_acc, 12 * n, cudaMemcpyDeviceToHost, s));
+  if (drho) CUDA_TRY(cudaMemcpyAsync(drho, d_drho, 4 * n, cudaMemcpyDeviceToHost, s));
+  if (mumax) CUDA_TRY(cudaMemcpyAsync(mumax, d_mu, 4 * n, cudaMemcpyDeviceToHost, s));
+  // restore
+  if (nl > 0)
+    CUDA_TRY(cudaMemcpyAsync(e->press, press_saved, 4 * (size_t)nl, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(e->ddyn, saved.data(), sizeof(CaseDyn) * e->cap_cases,
+                           cudaMemcpyHostToDevice, s));
+  if (e->ctl)
+    CUDA_TRY(cudaMemcpyAsync(e->ctl, &ctl_saved, sizeof(ListCtl), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const std::vector<CaseDyn> &dl = stage == 1 ? d1 : d0;
+  const unsigned bad = dl[icase].flags;
+  if (bad & kFlagNaN) return fail(SPH_ERR_UNSTABLE, "NaN/Inf in the interaction");
+  if (bad & kFlagListFull)
+    return fail(SPH_ERR_STATE, "a particle has more neighbour-list candidates than the list holds");
+  if (bad & kFlagSkin)
+    return fail(SPH_ERR_UNSTABLE, "the half step left the neighbour list's skin");
+  const CaseConst &C = e->hconst[icase];
+  if (dt) {
+    const unsigned bits = d0[icase].dtmin_bits;
+    if (C.dt_fixed > 0)
+      *dt = C.dt_fixed;
+    else if (bits >= kFloatInfBits)
+      *dt = C.cfl * C.h_d / C.cs0_d;
+    else {
+      float m;
+      std::memcpy(&m, &bits, 4);
+      *dt = C.cfl * (double)m;
+    }
+  }
+  if (pairs)
+    *pairs = (int64_t)(stage == 1 ? d1[icase].pairs - d0[icase].pairs : d0[icase].pairs);
   return SPH_OK;
 }
 

@@ -1492,7 +1492,7 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
                 float4 *__restrict__ ace, int want_dt, const uint2 *__restrict__ list,
                 int cap, const uint16_t *__restrict__ count,
                 const float4 *__restrict__ tau4 = nullptr,
-                const float2 *__restrict__ tau2 = nullptr) {
+                const float2 *__restrict__ tau2 = nullptr, float *__restrict__ mu_out = nullptr) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -1590,7 +1590,7 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
       }
     }
   }
-  finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, nullptr, dyn);
+  finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
 }
 
 
@@ -2084,11 +2084,13 @@ __global__ void k_scatter_forces(int n, const uint16_t *__restrict__ cid,
                                  const uint32_t *__restrict__ id, int slot, uint32_t id_base,
                                  const int *__restrict__ nvalid_p, const float4 *__restrict__ ace,
                                  const float *__restrict__ mu, float *__restrict__ acc_out,
-                                 float *__restrict__ drho_out, float *__restrict__ mu_out) {
+                                 float *__restrict__ drho_out, float *__restrict__ mu_out,
+                                 const uint32_t *__restrict__ keys, int nbits) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || cid[i] != slot) return;
   const uint32_t lid = id[i] - id_base;
-  const bool valid = i < *nvalid_p;
+  // keys (or null): the evaluated state's keys; a particle frozen there has no forces
+  const bool valid = i < *nvalid_p && (!keys || keys[i] < key_out(nbits));
   const float4 a = valid ? ace[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   if (acc_out) {
     acc_out[3 * lid] = a.x;
@@ -2359,11 +2361,11 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const uint32_t *cstart, int64_t cap_cells, int nbits,
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
                           const uint2 *list, int cap, const uint16_t *count, bool ext,
-                          float4 *tau4, float2 *tau2, cudaStream_t s) {
+                          float4 *tau4, float2 *tau2, cudaStream_t s, float *mu) {
   if (n <= 0) return;
 #define SPH_IL_ARGS                                                                      \
   n, nvalid, keys, posc, velrho, press, cid, cstart, (uint32_t)(cap_cells + 1), nbits, cc, \
-      dyn, ace, want_dt, list, cap, count, tau4, tau2
+      dyn, ace, want_dt, list, cap, count, tau4, tau2, mu
   if (tau4) {  // laminar + SPS cases present: strain pass over the list first
     k_strain_list<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, nbits, cc,
                                                list, cap, count, tau4, tau2);
@@ -2418,11 +2420,11 @@ void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t 
                            const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
                            int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
                            uint2 *list, int cap, uint16_t *count, bool ext, float4 *tau4,
-                           float2 *tau2, cudaStream_t s) {
+                           float2 *tau2, cudaStream_t s, float *mu) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_IB_ARGS                                                                        \
-  n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 1, \
+  n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, mu, 1, \
       tau4, tau2, list, cap, count
   if (tau4) {  // laminar + SPS cases: strain pass on state n, then EXT 2
     if (margin == 1) {
@@ -2537,10 +2539,10 @@ void launch_import_raw(int n, const int32_t *cell, const float4 *posc, const flo
 void launch_scatter_forces(int n, const uint16_t *cid, const uint32_t *id, int slot,
                            uint32_t id_base, const int *nvalid, const float4 *ace,
                            const float *mu, float *acc_out, float *drho_out, float *mu_out,
-                           cudaStream_t s) {
+                           cudaStream_t s, const uint32_t *keys, int nbits) {
   if (n > 0)
     k_scatter_forces<<<nblk(n, 256), 256, 0, s>>>(n, cid, id, slot, id_base, nvalid, ace, mu,
-                                                  acc_out, drho_out, mu_out);
+                                                  acc_out, drho_out, mu_out, keys, nbits);
 }
 
 // tau/rho (sorted order, tau4/tau2) to the original order of one case: [6 n].

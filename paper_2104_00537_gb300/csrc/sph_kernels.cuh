@@ -75,13 +75,13 @@ void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t 
                            const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
                            int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
                            uint2 *list, int cap, uint16_t *count, bool ext, float4 *tau4,
-                           float2 *tau2, cudaStream_t s);
+                           float2 *tau2, cudaStream_t s, float *mu = nullptr);
 void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
                           const float4 *velrho, const float *press, const uint16_t *cid,
                           const uint32_t *cstart, int64_t cap_cells, int nbits,
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
                           const uint2 *list, int cap, const uint16_t *count, bool ext,
-                          float4 *tau4, float2 *tau2, cudaStream_t s);
+                          float4 *tau4, float2 *tau2, cudaStream_t s, float *mu = nullptr);
 void launch_predictor_list(int n, const uint32_t *keys_in, State src, const float4 *ace,
                            const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
                            float4 *velrho_out, uint32_t *keys_out, float *press,
@@ -127,7 +127,7 @@ void launch_import_raw(int n, const int32_t *cell, const float4 *posc, const flo
 void launch_scatter_forces(int n, const uint16_t *cid, const uint32_t *id, int slot,
                            uint32_t id_base, const int *nvalid, const float4 *ace,
                            const float *mu, float *acc_out, float *drho_out, float *mu_out,
-                           cudaStream_t s);
+                           cudaStream_t s, const uint32_t *keys = nullptr, int nbits = 0);
 void launch_pair_stats(int n, const int *nvalid, const uint32_t *keys, State st,
                        const uint32_t *cstart, int64_t cap_cells, int nbits, const CaseConst *cc,
                        int slot, uint32_t id_base, long long *count, unsigned long long *hash,

@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True):
                                           C.c_size_t, vp, ALLOC_FN, FREE_FN, vp,
                                           C.POINTER(vp)]),
         "sph_eval_forces": (C.c_int, [vp, i32, vp, vp, vp, dp, C.POINTER(i64)]),
+        "sph_eval_step": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, vp, vp, dp,
+                                    C.POINTER(i64)]),
         "sph_eval_sps": (C.c_int, [vp, i32, vp]),
         "sph_eval_boundary": (C.c_int, [vp, i32, vp, vp]),
         "sph_get_order": (C.c_int, [vp, i32, vp, vp, C.POINTER(i64)]),
@@ -367,6 +369,25 @@ class Engine:
         check(self.lib.sph_eval_forces(self.h, icase, acc.ctypes.data, drho.ctypes.data,
                                        mu.ctypes.data, C.byref(dt), C.byref(pairs)))
         return dict(acc=acc, drho=drho, mumax=mu, dt=dt.value, pairs=pairs.value)
+
+    def eval_step(self, stage=0, icase=0):
+        """One evaluation of the next step through the step's own launches
+        (stage 0: state n; 1: the half-step state of a list step), without
+        advancing: the evaluated state and its results, original order."""
+        n = self._n(icase)
+        pos = np.zeros((n, 3), np.float64)
+        vel = np.zeros((n, 3), np.float32)
+        rho = np.zeros(n, np.float32)
+        acc = np.zeros((n, 3), np.float32)
+        drho = np.zeros(n, np.float32)
+        mu = np.zeros(n, np.float32)
+        dt, pairs = C.c_double(), C.c_int64()
+        check(self.lib.sph_eval_step(self.h, icase, int(stage), pos.ctypes.data,
+                                     vel.ctypes.data, rho.ctypes.data, acc.ctypes.data,
+                                     drho.ctypes.data, mu.ctypes.data, C.byref(dt),
+                                     C.byref(pairs)))
+        return dict(pos=pos, vel=vel, rho=rho, acc=acc, drho=drho, mumax=mu, dt=dt.value,
+                    pairs=pairs.value)
 
     def eval_sps(self, icase=0):
         """tau / rho of Eq 25 per particle (original order): xx, yy, zz, xy, xz, yz."""

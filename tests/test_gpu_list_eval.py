@@ -1,0 +1,231 @@
+"""The interaction kernel that sph_step times -- the neighbour-list walk --
+against the FP64 oracle, one evaluation at a time (Sect. 2, Eq 15-18, 21-22,
+35-36; Sect. 5.1).
+
+sph_eval_step runs the step's own launches without advancing the engine:
+stage 0 is the first evaluation of the next step (state n), stage 1 the second
+(the half-step state of Eq 33-34).  With the list kept across steps (the
+default) both states are those kept in the order and cells of the list's
+build, with cell offsets up to half the skin outside [0, cs), and both walks
+go over the chunk records with the two-candidate carry-over; the library is
+built with FP32 flush-to-zero.  The oracle evaluates Eq 15-18, 21-22 and 36 in
+FP64 on the evaluated state (positions from the GPU's cell + offset, velocity
+and density as stored), so the comparison isolates the evaluation itself.
+
+Tolerances: dv/dt, drho/dt and mu_max within 1e-4 of max|.| (FP32 against
+FP64); dt of Eq 35 within 1e-4 relative; the pair count equal up to the pairs
+within 1e-6 (relative) of (2h)^2, on which FP32 and FP64 may disagree (their
+kernel weight is ~1e-18).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_00537_gb300 import cases, sph
+from tests.test_gpu_parity import n_ambiguous, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def n_band(case, pos):
+    """Ordered pairs (all types) with |r^2 - (2h)^2| < 1e-6 (2h)^2: an upper
+    bound of the pairs on which FP32 and FP64 may disagree, counted without
+    listing pairs (for the full-size cases)."""
+    from scipy.spatial import cKDTree
+    R2 = 4.0 * case.params["h"] ** 2
+    tree = cKDTree(pos)
+    lo, hi = tree.count_neighbors(tree, np.sqrt(R2 * np.array([1 - 1e-6, 1 + 1e-6])))
+    return int(hi - lo)
+
+
+def check_step_eval(case, eng, stage, icase=0, exact_pairs=True):
+    """One evaluation of the next step (stage 0 or 1) against the oracle on
+    the evaluated state; returns the GPU results."""
+    g = eng.eval_step(stage, icase)
+    vel = g["vel"].astype(np.float64)
+    rho = g["rho"].astype(np.float64)
+    acc, drho, mu, npairs = oracle.interact(case.params, g["pos"], vel, rho, case.ptype)
+    f = case.ptype == 0
+    b = ~f
+    amb = n_ambiguous(case, g["pos"]) if exact_pairs else n_band(case, g["pos"])
+    assert abs(g["pairs"] - npairs) <= amb, (g["pairs"], npairs, amb)
+    assert rel_err(g["acc"][f], acc[f]) < TOL
+    assert np.all(g["acc"][b] == 0)
+    if case.params.get("boundary_mode", 0) == 1:  # Eq 38 sets boundary densities
+        assert rel_err(g["drho"][f], drho[f]) < TOL
+        assert np.all(g["drho"][b] == 0)
+    else:
+        assert rel_err(g["drho"], drho) < TOL
+    assert rel_err(g["mumax"][f], mu[f]) < TOL
+    assert np.all(g["mumax"][b] == 0)
+    if stage == 0:
+        dt = oracle.time_step(case.params, acc, mu, case.ptype)
+        assert abs(g["dt"] - dt) < TOL * dt
+    return g
+
+
+def mid_list_eval(case, eng, stage):
+    """check_step_eval on a state kept since an earlier list build: asserts
+    that the evaluation did not rebuild the list (so the state is in the
+    build's cells), returning False where it had to (a pending rebuild)."""
+    b0 = eng.list_info()["builds"]
+    check_step_eval(case, eng, stage)
+    return eng.list_info()["builds"] == b0
+
+
+@pytest.mark.parametrize("variant", [3, 4, 5])
+@pytest.mark.parametrize("cell_mode", [0, 1, 2])
+def test_list_evaluation_at_rest(cell_mode, variant):
+    """t = 0: both evaluations of the first step (the list built on state n)."""
+    case = cases.dam_break(0.02, cell_mode=cell_mode)
+    eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=variant)
+    for stage in (0, 1):
+        check_step_eval(case, eng, stage)
+    eng.destroy()
+
+
+@pytest.mark.parametrize("variant", [3, 4, 5])
+def test_list_evaluation_in_motion(variant):
+    """After 60 steps the column moves: the viscosity and diffusion terms and
+    mu_max are active, and the kept list has been walked for several steps."""
+    case = cases.dam_break(0.02)
+    eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=variant, use_graph=1)
+    eng.step(60)
+    for stage in (0, 1):
+        g = check_step_eval(case, eng, stage)
+        assert np.abs(g["mumax"]).max() > 0
+    if variant == 5:
+        assert eng.list_info()["builds"] < 60
+    eng.destroy()
+
+
+def test_kept_list_evaluation_through_the_splash():
+    """The dam break through its collapse and splash (~1,050 steps, t ~ 0.3 s),
+    with the list kept across steps and rebuilt as the flow needs: both
+    evaluations at seven points of the run.  Where a point falls on a step
+    that starts with a rebuild, the run goes on a step at a time until an
+    evaluation is in the middle of a kept list (state in the build's cells),
+    so that all seven points test that state."""
+    case = cases.dam_break(0.02)
+    eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=5, use_graph=1)
+    done = 0
+    for chunk in (150,) * 7:
+        eng.step(chunk)
+        done += chunk
+        for _ in range(8):
+            kept = mid_list_eval(case, eng, 0)
+            check_step_eval(case, eng, 1)
+            if kept:
+                break
+            eng.step(1)
+            done += 1
+        assert kept, done
+    builds = eng.list_info()["builds"]
+    assert 5 < builds < done // 2, builds
+    assert eng.stats()["t"] > 0.25
+    eng.destroy()
+
+
+def test_evaluation_does_not_perturb_the_run():
+    """sph_eval_step leaves the engine as it found it: a run with evaluations
+    of both stages in its middle (one of them at a pending rebuild) takes the
+    same steps, bit for bit, as a run without."""
+    case = cases.dam_break(0.02)
+    a = sph.Engine.create(case)
+    b = sph.Engine.create(case)
+    for e in (a, b):
+        e.set_options(pi_variant=5, use_graph=1)
+    a.step(250)
+    a.eval_step(0)
+    a.eval_step(1)
+    a.step(1)
+    a.eval_step(1)
+    a.step(49)
+    b.step(300)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("pos", "vel", "rho"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert sa["t"] == sb["t"] and sa["step"] == sb["step"] == 300
+    assert a.list_info()["builds"] == b.list_info()["builds"]
+    a.destroy()
+    b.destroy()
+
+
+@pytest.mark.parametrize("physics", ["fourtakas", "sps", "mdbc"])
+def test_list_evaluation_extended_physics(physics):
+    """The list kernels of the Eq 19-20 diffusion (EXT 1), of laminar + SPS
+    viscosity (EXT 2, with its strain pass over the list) and the list walk of
+    an mDBC case (boundary values of Eq 38-39 in the build's cells)."""
+    kw = dict(fourtakas=dict(ddt_mode=2), sps=dict(visc_mode=1, nu0=1e-3),
+              mdbc=dict(boundary_mode=1))[physics]
+    case = cases.dam_break(0.02, **kw)
+    eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=5, use_graph=1)
+    eng.step(60)
+    for stage in (0, 1):
+        check_step_eval(case, eng, stage)
+    eng.destroy()
+
+
+def test_verlet_list_evaluation():
+    """The Verlet scheme's one evaluation per step (Eq 30-31) over the kept list."""
+    case = cases.dam_break(0.02, integrator=1)
+    eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=5, use_graph=1)
+    eng.step(60)
+    check_step_eval(case, eng, 0)
+    with pytest.raises(sph.SphError):
+        eng.eval_step(1)
+    eng.destroy()
+
+
+def test_list_evaluation_wave_flume_fiftieth_scale():
+    """The piston-wavemaker flume on its 1/50-particle-count copy (768k
+    particles): the piston's imposed velocity (Eq 37) enters the viscosity of
+    its fluid neighbours; both evaluations after 20 steps."""
+    case = cases.wave_flume(0.008 * 50 ** (1 / 3))
+    eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=5, use_graph=1)
+    eng.step(20)
+    for stage in (0, 1):
+        g = check_step_eval(case, eng, stage, exact_pairs=False)
+    piston = case.group >= 0
+    assert np.abs(g["vel"][piston, 0]).max() > 0
+    eng.destroy()
+
+
+def test_full_size_dam_break_order_and_evaluation():
+    """The 1.48M-particle dam break (dp = 0.004 m) in the bench's launch
+    configuration (kept list, CUDA-graph replay): the cell order after the
+    3-pass radix sort of 23-bit keys bit-exact at t = 0, then both
+    evaluations of step 21 against the oracle."""
+    case = cases.dam_break(0.004, cell_mode=1)
+    eng = sph.Engine.create(case)
+    ids, cells, ninside = eng.order()
+    order, inside = oracle.sort_order(case.params, case.pos, case.ptype)
+    assert ninside == inside == case.n
+    assert np.array_equal(ids, order)
+    assert np.array_equal(cells, oracle.cells(case.params, case.pos)[order])
+    eng.set_options(pi_variant=5, use_graph=1)
+    eng.step(20)
+    for stage in (0, 1):
+        check_step_eval(case, eng, stage, exact_pairs=False)
+    eng.destroy()
+
+
+def test_eval_step_rejects_what_it_cannot_evaluate():
+    case = cases.dam_break(0.02)
+    eng = sph.Engine.create(case)
+    with pytest.raises(sph.SphError):
+        eng.eval_step(2)
+    eng.set_options(pi_variant=0)
+    check_step_eval(case, eng, 0)  # the cell walk's first evaluation
+    with pytest.raises(sph.SphError) as ex:
+        eng.eval_step(1)
+    assert ex.value.code == -1
+    eng.destroy()
