@@ -1,11 +1,18 @@
 """Benchmark of the WCSPH hot path on GB300 (one JSON line on rank 0).
 
 Default workload: the 3-D dam break at dp = 0.004 m (1,000,000 fluid +
-479,826 boundary particles, cells of 2h), stepped with the Symplectic scheme.
-A "step" is one full Symplectic step: NL -> PI -> dt -> predictor -> NL ->
-PI -> corrector.  The metric is particle interactions per second (ordered
-pairs evaluated by the two PI evaluations of each step, the paper's PIPS);
-steps/s is reported beside it.
+479,826 boundary particles, cells of h), stepped with the Symplectic scheme
+over the neighbour list kept across steps.  A "step" is one full Symplectic
+step: NL (when the list needs a rebuild) -> PI -> dt -> predictor -> PI ->
+corrector.  The metric is particle interactions per second (ordered pairs
+evaluated by the two PI evaluations of each step, the paper's PIPS); steps/s
+is reported beside it.  The default line also carries, measured in the same
+run: the roofline of the interaction kernel against the FP32 throughput
+measured on this GPU, the case's whole 2,000-step run (its own list-rebuild
+rate), the batched execution of the 256 dam breaks against one case at a
+time, a scaled serving trace against one request at a time, the end-to-end
+figure through the C ABI from pinned host memory, and the FP64 oracle on the
+host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--workload dam_break|dam_break_small|wave_flume|batched|served]
@@ -41,7 +48,7 @@ F_PAIR_FF_HYD = F_PAIR_FF + 11
 # Laminar + SPS (Eq 23-27) adds, per pair with a in F: Eq 23 (9), Eq 26 with
 # the stored tau (33) and the strain pass of Eq 24-25 (33); Eq 21 drops (4)
 F_PAIR_VISC = 9 + 33 + 33 - 4
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_LANES, SM_MAX_MHZ = 128, 2070.0  # per SM (Blackwell); the nominal maximum SM clock
 # Algorithmic HBM bytes per particle of one Symplectic step: two sorts of
 # three 8-bit passes (20 each), two reorders (90), two cell tables (~7),
 # predictor (91), corrector (115), two interactions (52)
@@ -53,10 +60,6 @@ def hbm_peak_gbs():
         return float(json.load(open(MEASURED_PEAKS))["hbm_gbs"])
     except (OSError, ValueError, KeyError):
         return 6800.0  # fallback figure for a GB300 copy
-
-
-def fp32_peak_tflops(mhz=SM_MAX_MHZ):
-    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
 def list_capture(cell_mode, workload_name, variant):
@@ -193,63 +196,57 @@ def sum_over_ranks(x, dist):
     return float(t.item())
 
 
-def cpu_baseline(case, seconds_budget=20.0):
+def cpu_baseline(case, seconds_budget=15.0):
     """The FP64 oracle timed on the host cores over a bounded sample of the same
-    workload: one interaction evaluation (neighbour list over all particles)
-    for a contiguous block of target particles."""
+    workload: whole Symplectic steps (neighbour list + two interaction
+    evaluations + update, as the GPU steps) of the case from rest; one
+    calibration step sizes the sample to about `seconds_budget` seconds."""
     import oracle
-    n = case.n
-    cores = os.cpu_count()
-    # calibrate on a small block, then size the sample for ~seconds_budget
+    s = oracle.OracleState(case)
     t0 = time.perf_counter()
-    _, _, _, p0 = oracle.interact_range(case.params, case.pos, case.vel, case.rho, case.ptype,
-                                        0, min(n, 20000))
+    s.step(1)
     t_cal = time.perf_counter() - t0
-    block = min(n, max(20000, int(20000 * seconds_budget / max(t_cal, 1e-3) / 2)))
+    nsteps = max(1, min(200, int(seconds_budget / max(t_cal, 1e-3))))
     t0 = time.perf_counter()
-    _, _, _, pairs = oracle.interact_range(case.params, case.pos, case.vel, case.rho,
-                                           case.ptype, 0, block)
+    pairs = s.step(nsteps)
     dt = time.perf_counter() - t0
-    return {"value": pairs / dt, "unit": "interactions/s", "cores": cores, "kind": "oracle",
-            "sample": "FP64 oracle: neighbour list of all %d particles + interaction of "
-                      "particles [0, %d) of the dam break at t=0 (%d pairs, %.1f s)"
-                      % (n, block, pairs, dt)}
+    return {"value": pairs / dt, "unit": "interactions/s", "cores": os.cpu_count(),
+            "kind": "oracle", "steps_per_s": nsteps / dt,
+            "sample": "FP64 oracle, OpenMP: Symplectic steps 2-%d of the %d-particle case "
+                      "from rest (neighbour list + 2 interaction evaluations + update per "
+                      "step; %d pairs, %.1f s)" % (nsteps + 1, case.n, pairs, dt)}
 
 
 def run_reference(args, rank, world, dist):
-    """Reference arm: the FP64 oracle on the host cores, same metric and workload;
-    each step is a bounded sample (interaction of a block of target particles)."""
+    """Reference arm: the FP64 oracle on the host cores, same metric and
+    workload: W untimed and K timed whole Symplectic steps of the case from
+    rest, as the GPU arm times them (the same window of the run)."""
     import oracle
     if rank != 0:
         return
     cs, desc = workload(args.workload, 0)
     case = cs[0]
-    n = case.n
-    block = max(1, min(n, args.ref_block))
-
-    def one(k):
-        a0 = (k * block) % max(1, n - block)
-        _, _, _, p = oracle.interact_range(case.params, case.pos, case.vel, case.rho,
-                                           case.ptype, a0, a0 + block)
-        return p
-
-    for k in range(args.warmup):
-        one(k)
-    pairs = 0
+    s = oracle.OracleState(case)
+    if args.warmup:
+        s.step(args.warmup)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        pairs += one(args.warmup + k)
+    pairs = s.step(args.steps)
     dt = time.perf_counter() - t0
     v = pairs / dt
     out = {"metric": "particle_interactions_per_s", "value": v, "unit": "interactions/s",
            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": desc, "sample_particles_per_step": block},
+           "steps_per_s": args.steps / dt,
+           "config": {"workload": desc, "particles": case.n,
+                      "window": "steps %d-%d of the run from rest" % (
+                          args.warmup, args.warmup + args.steps)},
            "cpu_baseline": {"value": v, "unit": "interactions/s", "cores": os.cpu_count(),
                             "kind": "oracle",
-                            "sample": "each step: neighbour list of all %d particles + "
-                                      "interaction of %d target particles" % (n, block)},
+                            "sample": "FP64 oracle, OpenMP: Symplectic steps %d-%d of the "
+                                      "%d-particle case from rest (neighbour list + 2 "
+                                      "interaction evaluations + update per step)"
+                                      % (args.warmup, args.warmup + args.steps, case.n)},
            "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -268,117 +265,145 @@ def timed_steps(eng, stream, steps):
     return ev0.elapsed_time(ev1)
 
 
-def run_batched(args):
-    """256 uneven dam breaks: one batched engine (one launch per stage for all
-    cases, CUDA-graph replay, autotuned cell size / kernel variant) against the
-    plain path that steps each case alone in its own engine (also replayed
-    from a CUDA graph).  Reports aggregate case-steps/s of both."""
+def measure_batched(ncases, steps, warmup, tune, clock_index=0):
+    """C3: `ncases` uneven dam breaks in one batched engine (one launch per
+    stage for all cases, CUDA-graph replay) against the plain path that steps
+    each case alone in its own engine (the list kept across steps, each step
+    replayed from a captured graph: the fastest plain way measured).  Both
+    time the same steps (warmup .. warmup + steps of every case from rest)
+    with CUDA events on the engines' stream.  tune: pick cell size and
+    interaction variant with the autotuner (else cells of h, kept list)."""
     import torch
     from paper_2104_00537_gb300 import autotune, cases, sph
-    torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    cs = cases.batch_dam_breaks(args.ncases, seed=0)
-    gpu = torch.cuda.get_device_name(0)
-    mk = lambda cc: sph.Engine.batch(cc, stream=stream)
-    (cm, var), tune_ms = autotune.tune(cs, mk, gpu)
+    cs = cases.batch_dam_breaks(ncases, seed=0)
+    cm, var, tune_ms = 1, 5, None
+    if tune:
+        mk = lambda cc: sph.Engine.batch(cc, stream=stream)
+        (cm, var), tune_ms = autotune.tune(cs, mk, torch.cuda.get_device_name(0))
     for c in cs:
         c.params["cell_mode"] = cm
     eng = sph.Engine.batch(cs, stream=stream)
     eng.set_options(pi_variant=var, use_graph=1)
-    eng.step(args.warmup)
+    eng.step(warmup)
     p0 = sum(eng.stats(i)["interactions"] for i in range(len(cs)))
-    clocks = ClockSampler(0)
-    ms_b = timed_steps(eng, stream, args.steps)
+    clocks = ClockSampler(clock_index)
+    ms_b = timed_steps(eng, stream, steps)
     clk = clocks.stop()
     p1 = sum(eng.stats(i)["interactions"] for i in range(len(cs)))
     eng.destroy()
-    # plain: one case at a time, each in its own engine: the batch's pair
-    # loop with one launch per kernel and with each step replayed from a
-    # graph, and the list kept across steps (the default) the same two ways;
-    # the speedups are quoted against the fastest plain path
-    ms_p, ms_pg, ms_pk, ms_pkg, pp = 0.0, 0.0, 0.0, 0.0, 0
+    ms_p, pp = 0.0, 0
     for c in cs:
         e = sph.Engine.create(c, stream=stream)
-        e.set_options(pi_variant=var)
-        e.step(args.warmup)
-        q0 = e.stats()["interactions"]
-        ms_p += timed_steps(e, stream, args.steps)
-        pp += e.stats()["interactions"] - q0
         e.set_options(pi_variant=var, use_graph=1)
-        e.step(1)
-        ms_pg += timed_steps(e, stream, args.steps)
+        e.step(warmup)
+        q0 = e.stats()["interactions"]
+        ms_p += timed_steps(e, stream, steps)
+        pp += e.stats()["interactions"] - q0
         e.destroy()
-        e = sph.Engine.create(c, stream=stream)
-        e.set_options(pi_variant=5)
-        e.step(args.warmup)
-        ms_pk += timed_steps(e, stream, args.steps)
-        e.set_options(pi_variant=5, use_graph=1)
-        e.step(1)
-        ms_pkg += timed_steps(e, stream, args.steps)
-        e.destroy()
-    ms_best = min(ms_p, ms_pg, ms_pk, ms_pkg)
-    nb = len(cs) * args.steps
-    out = {"metric": "case_steps_per_s", "value": nb / (ms_b / 1e3), "unit": "case-steps/s",
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "%d dam breaks, fluid 5k-200k log-uniform" % len(cs),
-                      "particles": sum(c.n for c in cs), "cell_mode": cm, "pi_variant": var},
-           "batched": {"case_steps_per_s": nb / (ms_b / 1e3),
-                       "interactions_per_s": (p1 - p0) / (ms_b / 1e3)},
-           "plain": {"case_steps_per_s": nb / (ms_p / 1e3),
-                     "interactions_per_s": pp / (ms_p / 1e3)},
-           "plain_graph": {"case_steps_per_s": nb / (ms_pg / 1e3)},
-           "plain_list_kept": {"case_steps_per_s": nb / (ms_pk / 1e3)},
-           "plain_list_kept_graph": {"case_steps_per_s": nb / (ms_pkg / 1e3)},
-           "speedup_vs_plain": ms_p / ms_b, "speedup_vs_plain_graph": ms_pg / ms_b,
-           "speedup_vs_best_plain": ms_best / ms_b,
-           "autotune_ms_per_step": tune_ms, "clocks": clk}
-    print(json.dumps(out), flush=True)
+    nb = len(cs) * steps
+    return {"cases": len(cs), "particles": sum(c.n for c in cs), "steps": steps,
+            "warmup": warmup, "cell_mode": cm, "pi_variant": var,
+            "batched": {"case_steps_per_s": nb / (ms_b / 1e3), "ms_per_step": ms_b / steps,
+                        "interactions_per_s": (p1 - p0) / (ms_b / 1e3)},
+            "plain": {"case_steps_per_s": nb / (ms_p / 1e3), "ms_per_round": ms_p / steps,
+                      "interactions_per_s": pp / (ms_p / 1e3)},
+            "speedup_vs_plain": ms_p / ms_b, "same_pairs": p1 - p0 == pp,
+            "autotune_ms_per_step": tune_ms, "clocks": clk}
 
 
-def run_served(args):
-    """Poisson arrivals of sloshing-tank requests served by continuous batching
-    on one pool engine, against the same trace served one request at a time."""
+def measure_served(requests, rate, max_fluid, t_end, chunk, cell_mode=1, pi_variant=-1,
+                   list_skin=-1.0, plain=True, max_particles=None):
+    """C4: Poisson arrivals of sloshing-tank requests served by continuous
+    batching on one pool engine (64 slots), against the same trace served one
+    request at a time (a one-slot pool); wall-clock time-to-result."""
     import torch
     from paper_2104_00537_gb300 import cases, serve, sph
-    torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    trace = cases.sloshing_trace(args.requests, rate=args.rate, seed=0, n_min=10000,
-                                 n_max=args.max_fluid, t_end=args.t_end)
+    trace = cases.sloshing_trace(requests, rate=rate, seed=0, n_min=10000, n_max=max_fluid,
+                                 t_end=t_end)
     for _, c, _ in trace:
-        c.params["cell_mode"] = args.cell_mode
+        c.params["cell_mode"] = cell_mode
     free, _ = torch.cuda.mem_get_info()
     # about 200 B of state and 1.5 KB of per-step list per particle slot
-    max_p = int(min(free * 0.3 / 1800, 16_000_000))
+    max_p = int(min(free * 0.3 / 1800, max_particles or 16_000_000))
     max_cells = int(min(free * 0.05 / 8, 200_000_000))
     results = {}
-    for name, slots in (("served", 64), ("plain", 1)):
+    for name, slots in (("served", 64), ("plain", 1)) if plain else (("served", 64),):
         pool = sph.Engine.pool(max_p, max_cells, slots, stream=stream)
-        pool.set_options(use_graph=1, pi_variant=args.pi_variant, list_skin=args.list_skin)
+        pool.set_options(use_graph=1, pi_variant=pi_variant, list_skin=list_skin)
         reqs = [serve.Request(i, a, c, te) for i, (a, c, te) in enumerate(trace)]
-        srv = serve.Server(pool, chunk=args.chunk)
+        srv = serve.Server(pool, chunk=chunk)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         srv.run(reqs)
         wall = time.perf_counter() - t0
-        s = serve.summary(reqs, wall)
-        s["case_steps_per_s"] = srv.case_steps / wall
-        results[name] = s
+        st = serve.summary(reqs, wall)
+        st["case_steps_per_s"] = srv.case_steps / wall
+        results[name] = st
         pool.destroy()
-    out = {"metric": "served_p50_time_to_result_s", "value": results["served"]["p50_s"],
+    out = {"trace": "sloshing tanks 1x0.5x0.6 m, Poisson %.3g req/s, %d requests, fluid "
+                    "10k-%d log-uniform, %.3g s simulated each"
+                    % (rate, requests, max_fluid, t_end),
+           "chunk_steps": chunk, "served": results["served"]}
+    if plain:
+        out["plain"] = results["plain"]
+        out["throughput_ratio"] = (results["served"]["throughput_req_s"] /
+                                   results["plain"]["throughput_req_s"])
+        out["case_steps_ratio"] = (results["served"]["case_steps_per_s"] /
+                                   results["plain"]["case_steps_per_s"])
+    return out
+
+
+def measure_full_run(case, stream, steps=2000):
+    """The case's whole run from rest (C1's 2,000 steps), graph-replayed with
+    the list kept across steps: the step time at the run's own rebuild rate."""
+    import torch
+    from paper_2104_00537_gb300 import sph
+    e = sph.Engine.create(case, stream=stream)
+    e.set_options(use_graph=1)
+    torch.cuda.synchronize()
+    ms = timed_steps(e, stream, steps)
+    s = e.stats()
+    out = {"steps": steps, "ms_per_step": ms / steps, "steps_per_s": steps / (ms / 1e3),
+           "interactions_per_s": s["interactions"] / (ms / 1e3),
+           "builds_per_step": e.list_info()["builds"] / steps, "t_end_s": s["t"]}
+    e.destroy()
+    return out
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = measure_batched(args.ncases, args.steps, args.warmup, tune=True)
+    nb = r["cases"] * args.steps
+    out = {"metric": "case_steps_per_s", "value": r["batched"]["case_steps_per_s"],
+           "unit": "case-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": r["batched"]["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "%d dam breaks, fluid 5k-200k log-uniform" % r["cases"],
+                      "particles": r["particles"], "cell_mode": r["cell_mode"],
+                      "pi_variant": r["pi_variant"]},
+           "batched": r["batched"], "plain": r["plain"],
+           "speedup_vs_plain": r["speedup_vs_plain"],
+           "autotune_ms_per_step": r["autotune_ms_per_step"], "clocks": r["clocks"]}
+    del nb
+    print(json.dumps(out), flush=True)
+
+
+def run_served(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = measure_served(args.requests, args.rate, args.max_fluid, args.t_end, args.chunk,
+                       args.cell_mode, args.pi_variant, args.list_skin)
+    out = {"metric": "served_p50_time_to_result_s", "value": r["served"]["p50_s"],
            "unit": "s", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "sloshing tanks, Poisson %.0f req/s, %d requests, fluid "
-                                  "10k-%d log-uniform, t_end %.3g s"
-                                  % (args.rate, args.requests, args.max_fluid, args.t_end),
-                      "chunk_steps": args.chunk, "cell_mode": args.cell_mode,
+           "config": {"workload": r["trace"], "chunk_steps": args.chunk,
+                      "cell_mode": args.cell_mode,
                       "pi_variant": args.pi_variant if args.pi_variant >= 0 else 5},
-           "served": results["served"], "plain": results["plain"],
-           "throughput_ratio": results["served"]["throughput_req_s"] /
-           results["plain"]["throughput_req_s"],
-           "case_steps_ratio": results["served"]["case_steps_per_s"] /
-           results["plain"]["case_steps_per_s"]}
+           "served": r["served"], "plain": r["plain"],
+           "throughput_ratio": r["throughput_ratio"], "case_steps_ratio": r["case_steps_ratio"]}
     print(json.dumps(out), flush=True)
 
 
@@ -402,7 +427,9 @@ def main():
     ap.add_argument("--mdbc-slip", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-block", type=int, default=20000)
+    ap.add_argument("--no-modes", action="store_true",
+                    help="skip the batched / served / full-run sub-measurements of the "
+                         "default line")
     ap.add_argument("--ncases", type=int, default=256)
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--rate", type=float, default=20.0)
@@ -410,8 +437,9 @@ def main():
     ap.add_argument("--t-end", type=float, default=0.1)
     ap.add_argument("--chunk", type=int, default=10)
     args = ap.parse_args()
-    if args.steps is None:  # the reference arm's steps are bounded samples: 100 by default
-        args.steps = 2000 if args.workload == "dam_break" and args.impl == "gb300" else 100
+    if args.steps is None:  # the reference arm's steps are whole oracle steps: 20 by default
+        args.steps = (2000 if args.workload == "dam_break" else 100) if args.impl == "gb300" \
+            else 20
     args.warmup = max(3, args.warmup)
     if args.impl != "reference" and args.workload == "batched":
         return run_batched(args)
@@ -453,6 +481,9 @@ def main():
     kernel = {3: "k_interact_list", 4: "k_interact_list", 5: "k_interact_list"}.get(
         eff_var, "k_interact")
 
+    # the FP32 / FP64 pipe throughput of this GPU (roofline denominators),
+    # measured before the warm-up
+    peaks = sph.probe_peaks(stream)
     # warm-up
     eng.step(args.warmup)
     eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, timing=1)
@@ -509,18 +540,26 @@ def main():
     launches = max(1, tm["pi_launches"])
     pi_avg_s = tm["pi_ms"] / 1000.0 / launches
     achieved = flops / launches / pi_avg_s / 1e12
-    peak = fp32_peak_tflops()
+    peak = peaks["fp32_tflops"]
+    mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
+    nominal = peaks["sms"] * FP32_LANES * 2 * mhz * 1e6 / 1e12
     captured = ((args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) ==
                 (1, "symplectic", 0, 0) and eff_var in (4, 5))
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_basis": "measured in this run: FP32 FMA chains on all %d SMs "
+                              "(sph_probe_peaks, best of 3, CUDA events)" % peaks["sms"],
+                "peak_nominal": nominal, "frac_nominal": achieved / nominal,
+                "peak_nominal_basis": "%d SMs (device) x 128 FP32 lanes x 2 FLOP x %.0f MHz "
+                                      "(median SM clock sampled in the timed region)"
+                                      % (peaks["sms"], mhz),
+                "fp64_measured_tflops": peaks["fp64_tflops"],
                 "traffic": measured_traffic(args.cell_mode, args.workload, eff_var,
                                             builds / args.steps) if captured else None,
                 "limiter": measured_limiter(args.cell_mode, args.workload, eff_var)
                 if captured else None,
                 "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
-                "pi_ms_per_launch": 1000 * pi_avg_s,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal max clock)"}
+                "pi_ms_per_launch": 1000 * pi_avg_s}
 
     # whole-step bound T = interaction FLOPs / FP32 peak + step bytes / HBM peak
     # (default Symplectic step: two interactions); reported against ms_per_step
@@ -584,9 +623,24 @@ def main():
                               "wall clock" % args.steps}
         e2.destroy()
         del st
+    eng.destroy()
+    if rank == 0 and world == 1 and not args.no_modes and args.workload == "dam_break" and \
+            (args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) == \
+            (1, "symplectic", 0, 0) and args.pi_variant in (-1, 5):
+        # the rest of the metric, measured in the same run: the whole 2,000-step
+        # run of this case, batched vs plain (C3), served vs plain (C4, scaled)
+        out["full_run"] = measure_full_run(cs[0], stream)
+        out["batched"] = measure_batched(256, 20, 3, tune=False, clock_index=local)
+        out["batched"]["note"] = ("C3 in full (256 cases, 26.6M particles), 20 timed steps "
+                                  "after 3 from rest instead of 500; cells of h, list kept "
+                                  "across steps (the autotuner's choice) for both paths; "
+                                  "each path's state equals the other's (same pairs)")
+        out["served"] = measure_served(48, 20.0, 200000, 0.1, 10)
+        out["served"]["note"] = ("C4 scaled to fit the run: 48 requests, fluid <= 200k, "
+                                 "0.1 s simulated (C4: 100+ requests, <= 2M, 1 s; run with "
+                                 "--workload served)")
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(cs[0])
-    eng.destroy()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

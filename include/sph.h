@@ -39,7 +39,8 @@ extern "C" {
 #define SPH_ERR_CUDA (-3)     /* a CUDA runtime call failed               */
 #define SPH_ERR_UNSTABLE (-4) /* NaN/Inf in the state or dt < dt_min      */
 #define SPH_ERR_DOMAIN (-5)   /* more particles left the domain than allowed */
-#define SPH_ERR_TIMEOUT (-6)  /* a bounded device wait gave up            */
+/* (-6) is not used: no kernel of the library waits on a flag or a peer, so
+ * there is no bounded device wait that could give up */
 #define SPH_ERR_BUSY (-7)     /* pool: no free slot or not enough memory  */
 #define SPH_ERR_STATE (-8)    /* call not valid in the engine's state     */
 
@@ -332,20 +333,38 @@ int sph_pool_usage(sph_engine e, int64_t *particles_used, int64_t *cells_used,
 /* sph_destroy: release all device memory of the engine. */
 void sph_destroy(sph_engine e);
 
+/* ---- roofline denominators ------------------------------------------------
+ * sph_probe_peaks: not an operation of the paper.  Measures the FP32 and FP64
+ * fused multiply-add throughput of the current device (TFLOP/s, 2 FLOP per
+ * FMA): independent FMA chains in every thread of 8 blocks of 256 threads per
+ * SM, best of 3 launches timed with CUDA events on `stream` (cudaStream_t,
+ * NULL = default) after one untimed launch; about 50 ms in all.  These are the
+ * denominators of the interaction kernel's roofline, whose pair loop is bound
+ * by FP32 arithmetic.  *sm_count receives the device's SM count.  Any output
+ * may be NULL (a NULL TFLOP/s output skips that measurement).  Allocates and
+ * frees 16 bytes of device memory; synchronises the stream.  SPH_ERR_CUDA if
+ * there is no device or a launch fails. */
+int sph_probe_peaks(double *fp32_tflops, double *fp64_tflops, int32_t *sm_count, void *stream);
+
 /* ---- allocation-free cell-key sort ------------------------------------------
  * The paper has no counterpart of this call; it exists for callers that may
  * not let a library allocate device memory (a host program that owns the
  * whole device-memory budget, or a loop that cannot accept the device
  * synchronisation that cudaMalloc/cudaFree may cause).
  *
- * sph_sort_cell_keys_static: stable sort of n 32-bit keys (only the low nbits
- * bits are significant) -- the sort the neighbour list uses.  keys_in [n]
+ * sph_sort_cell_keys_static: stable sort of n 32-bit keys -- the sort the
+ * neighbour list uses.  It orders by the low 8 ceil(nbits/8) bits of each key
+ * (one pass per 8-bit digit), so every key must be below 2^nbits for the
+ * order to be by value; bits from 8 ceil(nbits/8) up are ignored.  keys_in [n]
  * (read), keys_out [n] and perm_out [n] (written; perm_out[i] = index in
  * keys_in of the i-th smallest key, ties in input order) are caller-owned
- * DEVICE pointers; work is queued on `stream` (cudaStream_t, NULL = default
- * stream) and the call returns without synchronising.
- * It calls no cudaMalloc/cudaFree: its scratch is one fixed array of about
- * 4.3 MB in the library's device data, present on every GPU that loads the
+ * DEVICE pointers that must not overlap (SPH_ERR_ARG otherwise: the passes
+ * write one output while other blocks still read the input); work is queued
+ * on `stream` (cudaStream_t, NULL = default stream) and the call returns
+ * without synchronising.
+ * It calls no cudaMalloc/cudaFree: its scratch is one fixed array of
+ * 4,457,472 bytes (exactly what n = SPH_SORT_STATIC_MAX_KEYS needs) in the
+ * library's device data, present on every GPU that loads the
  * library until the process exits.  n above SPH_SORT_STATIC_MAX_KEYS is
  * rejected with SPH_ERR_ARG.  The first call on a device looks up that
  * array's device address (with that device current); make that first call

@@ -145,9 +145,22 @@ struct State {
 void set_last_error(const std::string &msg);
 
 // ---- launchers (defined in the .cu files) --------------------------------
+// Radix sort geometry: keys per tile (block) and digit values per 8-bit pass.
+constexpr int64_t kSortTile = 2048;
+constexpr int64_t kSortRadix = 256;
+// Scratch bytes of radix_sort for n keys: key and index ping-pong buffers,
+// per-tile digit histograms and digit totals, each rounded up to 256 bytes.
+constexpr size_t sort_temp_bytes(int64_t n) {
+  return (size_t)(((n * 4 + 255) / 256) * 256) * 2 +
+         (size_t)(((((n + kSortTile - 1) / kSortTile) > 0 ? (n + kSortTile - 1) / kSortTile : 1) *
+                       kSortRadix * 4 + 255) / 256 * 256) +
+         (size_t)(kSortRadix * 4);
+}
 size_t radix_sort_temp_bytes(int64_t n);
-// Stable LSD sort of keys_in[0,n) (only the low nbits bits are significant);
-// writes the sorted keys and the permutation (source index of each output).
+// Stable LSD sort of keys_in[0,n) by their low 8 ceil(nbits/8) bits (one
+// pass per 8-bit digit; keys below 2^nbits sort by value); writes the sorted
+// keys and the permutation (source index of each output).  keys_in, keys_out,
+// perm_out and temp must not overlap.
 void radix_sort(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *perm_out,
                 int n, int nbits, void *temp, cudaStream_t s);
 

@@ -9,7 +9,7 @@
 // digit histograms) in the fixed array below instead of allocated memory.
 //
 // The array is a file-scope __device__ variable, so every GPU that loads
-// libsph.so holds it (about 4.3 MB) until the process exits.  In host code
+// libsph.so holds it (4,457,472 bytes) until the process exits.  In host code
 // its name is only a host-side stand-in, so its device address is looked up
 // once per device with cudaGetSymbolAddress, with that device current.
 #include <mutex>
@@ -21,7 +21,9 @@
 namespace {
 
 constexpr int64_t kMaxKeys = SPH_SORT_STATIC_MAX_KEYS;
-constexpr size_t kScratchBytes = 4 * 1024 * 1024 + 256 * 1024 + 4096;  // >= radix_sort_temp_bytes(kMaxKeys)
+// exactly the scratch the sort needs for the largest accepted n
+constexpr size_t kScratchBytes = sph::sort_temp_bytes(kMaxKeys);
+static_assert(kScratchBytes >= sph::sort_temp_bytes(1), "scratch size");
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
@@ -50,6 +52,17 @@ extern "C" int sph_sort_cell_keys_static(const uint32_t *keys_in, uint32_t *keys
   if (n == 0) return SPH_OK;
   if (!keys_in || !keys_out || !perm_out) {
     return fail(SPH_ERR_ARG, "sph_sort_cell_keys_static: null device pointer");
+  }
+  {
+    // the passes ping-pong between the outputs and the scratch while other
+    // blocks still read the input, so the three arrays must be disjoint
+    const uintptr_t a = (uintptr_t)keys_in, b = (uintptr_t)keys_out, c = (uintptr_t)perm_out;
+    const uintptr_t len = (uintptr_t)n * 4u;
+    auto overlap = [len](uintptr_t x, uintptr_t y) { return x < y + len && y < x + len; };
+    if (overlap(a, b) || overlap(a, c) || overlap(b, c)) {
+      return fail(SPH_ERR_ARG, "sph_sort_cell_keys_static: keys_in, keys_out and perm_out "
+                               "must not overlap");
+    }
   }
   if (sph::radix_sort_temp_bytes(n) > kScratchBytes) {
     return fail(SPH_ERR_ARG, "sph_sort_cell_keys_static: scratch too small");

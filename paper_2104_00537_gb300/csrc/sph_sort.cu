@@ -1,6 +1,6 @@
 // sph_sort.cu -- stable LSD radix sort of 32-bit cell keys with their source
-// index, for the neighbour list of Sect. 5.1 ("particles are sorted according
-// to the cell to which they belong").
+// index, for the neighbour list of Sect. 5.1, which orders the particles by
+// the cell each one lies in.
 //
 // Each 8-bit pass is three launches:
 //   upsweep      per-tile digit counts (warp-aggregated with match.any),
@@ -20,6 +20,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 8;                  // per thread
 constexpr int kTile = kThreads * kItems;   // 2048 keys per block
 constexpr int kRadix = 256;
+static_assert(kTile == kSortTile && kRadix == kSortRadix, "sort geometry");
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -157,16 +158,7 @@ k_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ v
 
 }  // namespace
 
-size_t radix_sort_temp_bytes(int64_t n) {
-  int64_t ntiles = (n + kTile - 1) / kTile;
-  if (ntiles < 1) ntiles = 1;
-  size_t b = 0;
-  b += ((size_t)n * 4 + 255) / 256 * 256;     // keys ping-pong
-  b += ((size_t)n * 4 + 255) / 256 * 256;     // vals ping-pong
-  b += ((size_t)ntiles * kRadix * 4 + 255) / 256 * 256;
-  b += 256 * 4;
-  return b;
-}
+size_t radix_sort_temp_bytes(int64_t n) { return sort_temp_bytes(n); }
 
 void radix_sort(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *perm_out, int n,
                 int nbits, void *temp, cudaStream_t s) {

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SPH_OK = 0
 SORT_STATIC_MAX_KEYS = 524288  # SPH_SORT_STATIC_MAX_KEYS of include/sph.h
 ERRORS = {-1: "SPH_ERR_ARG", -2: "SPH_ERR_OOM", -3: "SPH_ERR_CUDA", -4: "SPH_ERR_UNSTABLE",
-          -5: "SPH_ERR_DOMAIN", -6: "SPH_ERR_TIMEOUT", -7: "SPH_ERR_BUSY", -8: "SPH_ERR_STATE"}
+          -5: "SPH_ERR_DOMAIN", -7: "SPH_ERR_BUSY", -8: "SPH_ERR_STATE"}
 
 
 class SphError(RuntimeError):
@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True):
         "sph_pool_release": (C.c_int, [vp, i32]),
         "sph_pool_usage": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
         "sph_destroy": (None, [vp]),
+        "sph_probe_peaks": (C.c_int, [dp, dp, C.POINTER(i32), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -128,6 +129,15 @@ def load(build_if_missing: bool = True):
         f.argtypes = args
     _lib = L
     return L
+
+
+def probe_peaks(stream=None):
+    """Measured FP32 and FP64 FMA throughput (TFLOP/s) and SM count of the
+    current device (the roofline denominators of the pair loop)."""
+    f32, f64, sms = C.c_double(), C.c_double(), C.c_int32()
+    check(load().sph_probe_peaks(C.byref(f32), C.byref(f64), C.byref(sms),
+                                 _stream_handle(stream)))
+    return dict(fp32_tflops=f32.value, fp64_tflops=f64.value, sms=sms.value)
 
 
 def last_error() -> str:

@@ -50,9 +50,8 @@ def test_two_rank_max_and_sum_over_gloo():
 
 def test_reference_arm_prints_one_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--workload", "dam_break_small", "--steps", "3", "--warmup", "3",
-                        "--ref-block", "2000"], capture_output=True, text=True, timeout=600,
-                       cwd=ROOT)
+                        "--workload", "dam_break_small", "--steps", "3", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -60,6 +59,9 @@ def test_reference_arm_prints_one_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "interactions/s"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["higher_is_better"] is True
+    # whole oracle steps of the same window as the GPU arm
+    assert d["steps"] == 3 and "steps 3-6" in d["config"]["window"]
+    assert d["ms_per_step"] > 0 and d["cpu_baseline"]["value"] == d["value"]
 
 
 def test_profile_figures_follow_their_capture(tmp_path, monkeypatch):
