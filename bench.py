@@ -420,6 +420,8 @@ def main():
     ap.add_argument("--ddt-mode", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--pi-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5])
     ap.add_argument("--list-skin", type=float, default=-1.0)
+    ap.add_argument("--pi-block", type=int, default=0,
+                    help="threads per block of the list walk (0: the engine default)")
     ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "verlet"])
     ap.add_argument("--visc-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--nu0", type=float, default=1e-6)
@@ -467,7 +469,7 @@ def main():
     with torch.cuda.stream(stream):
         eng = sph.Engine.batch(cs, stream=stream) if len(cs) > 1 else \
             sph.Engine.create(cs[0], stream=stream)
-    eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin)
+    eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, pi_block=args.pi_block)
     n_particles = sum(c.n for c in cs)
     # the pi_variant the engine runs (its default: 5, the list kept across steps)
     list_ok = n_particles < (1 << 25)
@@ -486,7 +488,8 @@ def main():
     peaks = sph.probe_peaks(stream)
     # warm-up
     eng.step(args.warmup)
-    eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, timing=1)
+    eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, timing=1,
+                    pi_block=args.pi_block)
     eng.timing(reset=True)
     builds0 = eng.list_info()["builds"]
 

@@ -137,7 +137,9 @@ typedef void (*sph_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 
 /* Engine-wide launch options (the autotuner's knobs). */
 typedef struct {
-  int32_t pi_block;   /* threads per block of the interaction kernel (0: default) */
+  int32_t pi_block;   /* threads per block of the list walk of the default
+                       * physics: 0 (default: 128), 128, 256, 512 or 1024;
+                       * the other interaction kernels use 128 */
   int32_t pi_variant; /* interaction pair loop: -1 the engine default (5 where
                        * a list is supported, else 0); 0 compacted hit
                        * masks; 1 test

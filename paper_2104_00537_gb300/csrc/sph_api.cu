@@ -638,29 +638,32 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
                   e->dconst, e->ddyn, 0, s, true);
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
-                         e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu);
+                         e->list_ld, e->ncount, e->ext, tau4, e->tau2, s, mu,
+                         e->opt.pi_block);
   } else if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
     if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
                       s);
     launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                       e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                      e->list_cap, e->ncount, nullptr, nullptr, s);
+                      e->list_cap, e->list_ld, e->ncount, nullptr, nullptr, s);
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
-                         e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu);
+                         e->list_ld, e->ncount, e->ext, tau4, e->tau2, s, mu,
+                         e->opt.pi_block);
   } else {
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
                       s);
     if (ev) cudaEventRecord(ev[0], s);
     launch_interact_build(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                           e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
-                          e->nlist, e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu);
+                          e->nlist, e->list_cap, e->list_ld, e->ncount, e->ext, tau4, e->tau2, s,
+                          mu);
   }
   if (ev) cudaEventRecord(ev[1], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_cap, e->ncount, e->ctl, s);
+                      e->list_ld, e->ncount, e->ctl, s);
 }
 
 // The rest of a list step up to its second evaluation: dt (Eq 35), the half
@@ -680,12 +683,12 @@ void enqueue_list_half(sph_engine e, cudaEvent_t *ev, float *mu) {
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
-                       e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s,
-                       mu);
+                       e->list_ld, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s,
+                       mu, e->opt.pi_block);
   if (ev) cudaEventRecord(ev[3], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysC, Z.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_cap, e->ncount, e->ctl, s);
+                      e->list_ld, e->ncount, e->ctl, s);
 }
 
 // One Symplectic step with the per-step neighbour list: NL on state n (Y),
@@ -729,7 +732,7 @@ void enqueue_rebuild_list(sph_engine e, float extra, cudaStream_t q) {
                     q);
   launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                     e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                    e->list_cap, e->ncount, e->posc_ref, e->posc_ref2, q);
+                    e->list_cap, e->list_ld, e->ncount, e->posc_ref, e->posc_ref2, q);
 }
 
 // Appends to the graph being captured on e->s a k_decide kernel and an IF
@@ -996,8 +999,9 @@ int sph_batch_create(const sph_case_params *params, const sph_particles *parts, 
 
 int sph_set_options(sph_engine e, const sph_options *opt) {
   if (!e || !opt) return fail(SPH_ERR_ARG, "null argument");
-  if (opt->pi_block != 0 && opt->pi_block != 128)
-    return fail(SPH_ERR_ARG, "pi_block must be 0 (default) or 128");
+  if (opt->pi_block != 0 && opt->pi_block != 128 && opt->pi_block != 256 &&
+      opt->pi_block != 512 && opt->pi_block != 1024)
+    return fail(SPH_ERR_ARG, "pi_block must be 0 (default), 128, 256, 512 or 1024");
   if (opt->pi_variant < -1 || opt->pi_variant > 5)
     return fail(SPH_ERR_ARG,
                 "pi_variant must be -1 (engine default), 0 (compacted), 1 (inline), 2 (queued), "

@@ -11,6 +11,7 @@
 //   k_corrector   Symplectic full step (Eq 33-34)
 //   k_end_step    t += dt in FP64
 //   k_export / k_diag / k_pair_stats   read-out and parity helpers
+#include <algorithm>
 #include <cfloat>
 
 #include "sph_internal.cuh"
@@ -530,7 +531,9 @@ __global__ void k_need_all(int ncases, CaseDyn *__restrict__ dyn) {
 // LIST (VARIANT 0): 1 also writes the target's neighbour list, 2 writes
 // only the list (no pair terms, no outputs besides the list and ref): for
 // every tested chunk with a candidate within 2h + skin, one record (first
-// index | row offset, mask of those candidates) to list[i cap + c].  The
+// index | row offset, mask of those candidates) to list[c ld + i] (record c of
+// every target in one row of ld entries, so that the lanes of a warp read and
+// write adjacent words), at most cap records per target.  The
 // list's rows reach one cell further than the 2h support (M + 1 cells, so
 // 2h + cs >= 2h + skin), clipped to the case's grid.  ref, if set, receives
 // the target's position at the build (the list kept across steps), and the
@@ -548,7 +551,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
            const float4 *__restrict__ tau4 = nullptr, const float2 *__restrict__ tau2 = nullptr,
            uint2 *__restrict__ list = nullptr, int cap = 0,
            uint16_t *__restrict__ count = nullptr, float4 *__restrict__ ref = nullptr,
-           const float4 *__restrict__ ref_src = nullptr) {
+           const float4 *__restrict__ ref_src = nullptr, int64_t ld = 0) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -668,7 +671,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
             }
           }
           if (LIST && ml) {
-            if (lcnt < cap) list[(int64_t)i * cap + lcnt] = make_uint2((uint32_t)(lo + base) | rowbits, ml);
+            if (lcnt < cap) list[(int64_t)lcnt * ld + i] = make_uint2((uint32_t)(lo + base) | rowbits, ml);
             lcnt++;
           }
           if (LIST != 2) {
@@ -1482,19 +1485,54 @@ __global__ void k_corrector(int n, const uint32_t *__restrict__ perm2,
 // cells): the pair terms of k_interact for the entries inside 2h.  EXT 1
 // adds the Eq 19-20 density diffusion, EXT 2 also laminar + SPS (tau4/tau2
 // from k_strain_list), for the cases that use them.
+// Arguments of the interaction over the neighbour list (one struct, so that
+// the one-target body below serves both launch forms).
+struct ListArgs {
+  int n;
+  const int *nvalid_p;
+  const uint32_t *keys;
+  const float4 *posc, *velrho;
+  const float *press;
+  const uint16_t *cid;
+  const uint32_t *cstart;
+  uint32_t cap1;
+  int nbits;
+  const CaseConst *cc;
+  CaseDyn *dyn;
+  float4 *ace;
+  int want_dt;
+  const uint2 *list;
+  int64_t ld;
+  const uint16_t *count;
+  const float4 *tau4;
+  const float2 *tau2;
+  float *mu_out;
+};
+
+// One target i of the list walk (all 32 lanes of the warp call it together).
 template <int EXT>
-__global__ void __launch_bounds__(128, EXT == 2 ? 6 : 0)
-k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
-                const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
-                const float *__restrict__ press, const uint16_t *__restrict__ cid,
-                const uint32_t *__restrict__ cstart, uint32_t cap1, int nbits,
-                const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
-                float4 *__restrict__ ace, int want_dt, const uint2 *__restrict__ list,
-                int cap, const uint16_t *__restrict__ count,
-                const float4 *__restrict__ tau4 = nullptr,
-                const float2 *__restrict__ tau2 = nullptr, float *__restrict__ mu_out = nullptr) {
+__device__ __forceinline__ void list_target(const int i, const ListArgs &a) {
   const unsigned full = 0xffffffffu;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = a.n;
+  const int *__restrict__ nvalid_p = a.nvalid_p;
+  const uint32_t *__restrict__ keys = a.keys;
+  const float4 *__restrict__ posc = a.posc;
+  const float4 *__restrict__ velrho = a.velrho;
+  const float *__restrict__ press = a.press;
+  const uint16_t *__restrict__ cid = a.cid;
+  const uint32_t *__restrict__ cstart = a.cstart;
+  const uint32_t cap1 = a.cap1;
+  const int nbits = a.nbits;
+  const CaseConst *__restrict__ cc = a.cc;
+  CaseDyn *__restrict__ dyn = a.dyn;
+  float4 *__restrict__ ace = a.ace;
+  const int want_dt = a.want_dt;
+  const uint2 *__restrict__ list = a.list;
+  const int64_t ld = a.ld;
+  const uint16_t *__restrict__ count = a.count;
+  const float4 *__restrict__ tau4 = a.tau4;
+  const float2 *__restrict__ tau2 = a.tau2;
+  float *__restrict__ mu_out = a.mu_out;
   const int nvalid = *nvalid_p;
   const uint32_t key = i < nvalid ? keys[i] : key_out(nbits);
   const bool has = key < key_out(nbits);  // not frozen at this state
@@ -1529,7 +1567,7 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
   const int nrec = has ? (int)count[i] : 0;
   const bool warp_fluid = __all_sync(full, afluid || !has);
   Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
-  const uint2 *__restrict__ mine = list + (int64_t)i * cap;
+  const uint2 *__restrict__ mine = list + i;  // record r at mine[r ld]
   // two candidates per lane per iteration (their loads issued together),
   // records taken in order: the warp waits only for its lane with the most
   // candidates in total
@@ -1539,7 +1577,7 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
   float sy = 0.f, sz = 0.f;
   // the next record of the lane: base index, candidate mask, row offsets
   auto next_record = [&]() {
-    const uint2 rec = mine[r++];
+    const uint2 rec = mine[(int64_t)(r++) * ld];
     cbase = (int)(rec.x & kListIndexMask);
     cm = rec.y;
     int rdy, rdz;
@@ -1593,6 +1631,14 @@ k_interact_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restr
   finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
 }
 
+// One thread per target, in the key order of the targets.
+template <int EXT>
+__global__ void __launch_bounds__(EXT == 0 ? 1024 : 128, EXT == 2 ? 6 : (EXT == 0 ? 1 : 0))
+k_interact_list(const ListArgs a) {
+  list_target<EXT>(blockIdx.x * blockDim.x + threadIdx.x, a);
+}
+
+
 
 // The strain pass of the laminar + SPS model (as k_strain) over the target's
 // list records, for the half-step state kept in the order and cells of state n.
@@ -1600,7 +1646,7 @@ __global__ void __launch_bounds__(128)
 k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
               const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
               const uint16_t *__restrict__ cid, int nbits, const CaseConst *__restrict__ cc,
-              const uint2 *__restrict__ list, int cap, const uint16_t *__restrict__ count,
+              const uint2 *__restrict__ list, int64_t ld, const uint16_t *__restrict__ count,
               float4 *__restrict__ tau4, float2 *__restrict__ tau2) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1621,7 +1667,7 @@ k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restric
   const float4 pa = act ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float4 va = act ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
   const int nrec = act ? (int)count[i] : 0;
-  const uint2 *__restrict__ mine = list + (int64_t)i * cap;
+  const uint2 *__restrict__ mine = list + i;  // record r at mine[r ld]
   float gxx = 0.f, gyy = 0.f, gzz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
   int r = 0;
   unsigned cm = 0u;
@@ -1630,7 +1676,7 @@ k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restric
 #pragma unroll 1
   for (;;) {
     if (cm == 0u && r < nrec) {
-      const uint2 rec = mine[r++];
+      const uint2 rec = mine[(int64_t)(r++) * ld];
       cbase = (int)(rec.x & kListIndexMask);
       cm = rec.y;
       int rdy, rdz;
@@ -1858,7 +1904,7 @@ __global__ void k_decide(cudaGraphConditionalHandle h, const ListCtl *__restrict
 __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
                              const uint32_t *__restrict__ keys, const float4 *__restrict__ posc,
                              const uint16_t *__restrict__ cid, const CaseConst *__restrict__ cc,
-                             int nbits, const uint2 *__restrict__ list, int cap,
+                             int nbits, const uint2 *__restrict__ list, int64_t ld,
                              const uint16_t *__restrict__ count, ListCtl *__restrict__ ctl) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -1887,9 +1933,8 @@ __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
     const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
     if (__float_as_uint(r2) - 1u < r2max_u) nb++;
   }
-  const uint2 *mine = list + (int64_t)i * cap;
   for (int r = 0; r < (int)count[i]; r++) {
-    const uint2 rec = mine[r];
+    const uint2 rec = list[(int64_t)r * ld + i];
     const int cbase = (int)(rec.x & kListIndexMask);
     int rdy, rdz;
     list_row_decode(rec.x, rdy, rdz);
@@ -2360,22 +2405,23 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const float4 *velrho, const float *press, const uint16_t *cid,
                           const uint32_t *cstart, int64_t cap_cells, int nbits,
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
-                          const uint2 *list, int cap, const uint16_t *count, bool ext,
-                          float4 *tau4, float2 *tau2, cudaStream_t s, float *mu) {
+                          const uint2 *list, int64_t ld, const uint16_t *count, bool ext,
+                          float4 *tau4, float2 *tau2, cudaStream_t s, float *mu, int block) {
   if (n <= 0) return;
-#define SPH_IL_ARGS                                                                      \
-  n, nvalid, keys, posc, velrho, press, cid, cstart, (uint32_t)(cap_cells + 1), nbits, cc, \
-      dyn, ace, want_dt, list, cap, count, tau4, tau2, mu
-  if (tau4) {  // laminar + SPS cases present: strain pass over the list first
+  const ListArgs a{n,   nvalid, keys, posc, velrho, press, cid,   cstart, (uint32_t)(cap_cells + 1),
+                   nbits, cc,   dyn,  ace,  want_dt, list,  ld,    count,  tau4, tau2, mu};
+  if (tau4)  // laminar + SPS cases present: strain pass over the list first
     k_strain_list<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, nbits, cc,
-                                               list, cap, count, tau4, tau2);
-    k_interact_list<2><<<nblk(n, 128), 128, 0, s>>>(SPH_IL_ARGS);
-  } else if (ext) {
-    k_interact_list<1><<<nblk(n, 128), 128, 0, s>>>(SPH_IL_ARGS);
-  } else {
-    k_interact_list<0><<<nblk(n, 128), 128, 0, s>>>(SPH_IL_ARGS);
-  }
-#undef SPH_IL_ARGS
+                                               list, ld, count, tau4, tau2);
+  // one thread per target; block size 128 (default) to 1024 for the default
+  // kernel (EXT 1 and 2: 128, by their registers)
+  const int b0 = block >= 128 && block <= 1024 && block % 32 == 0 ? block : 128;
+  if (tau4)
+    k_interact_list<2><<<nblk(n, 128), 128, 0, s>>>(a);
+  else if (ext)
+    k_interact_list<1><<<nblk(n, 128), 128, 0, s>>>(a);
+  else
+    k_interact_list<0><<<nblk(n, b0), b0, 0, s>>>(a);
 }
 
 void launch_list_begin(int ncases, const CaseConst *cc, CaseDyn *dyn, ListCtl *ctl,
@@ -2400,12 +2446,13 @@ void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *key
                        const float4 *posc, const float4 *velrho, const float *press,
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
-                       uint16_t *count, float4 *ref, const float4 *ref_src, cudaStream_t s) {
+                       int64_t ld, uint16_t *count, float4 *ref, const float4 *ref_src,
+                       cudaStream_t s) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_BL_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 0, \
-      nullptr, nullptr, list, cap, count, ref, ref_src
+      nullptr, nullptr, list, cap, count, ref, ref_src, ld
   if (margin == 1)
     k_interact<1, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
   else if (margin == 3)
@@ -2419,13 +2466,13 @@ void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t 
                            const float4 *posc, const float4 *velrho, const float *press,
                            const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
                            int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
-                           uint2 *list, int cap, uint16_t *count, bool ext, float4 *tau4,
-                           float2 *tau2, cudaStream_t s, float *mu) {
+                           uint2 *list, int cap, int64_t ld, uint16_t *count, bool ext,
+                           float4 *tau4, float2 *tau2, cudaStream_t s, float *mu) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_IB_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, mu, 1, \
-      tau4, tau2, list, cap, count
+      tau4, tau2, list, cap, count, nullptr, nullptr, ld
   if (tau4) {  // laminar + SPS cases: strain pass on state n, then EXT 2
     if (margin == 1) {
       k_strain<1><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
@@ -2487,9 +2534,9 @@ void launch_decide(cudaGraphConditionalHandle h, const ListCtl *ctl, cudaStream_
 
 void launch_list_check(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
                        const uint16_t *cid, const CaseConst *cc, int nbits, const uint2 *list,
-                       int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s) {
+                       int64_t ld, const uint16_t *count, ListCtl *ctl, cudaStream_t s) {
   if (n > 0)
-    k_list_check<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, cid, cc, nbits, list, cap,
+    k_list_check<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, cid, cc, nbits, list, ld,
                                               count, ctl);
 }
 

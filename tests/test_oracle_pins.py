@@ -150,7 +150,10 @@ def test_pairs_are_symmetric_and_strict():
 
 
 def test_sort_is_stable_by_type_then_cell():
-    """Neighbour-list order: fluid by cell, then boundary by cell, ties in prior order."""
+    """Neighbour-list order: fluid by cell, then boundary by cell, ties in prior
+    order.  The paper orders particles by cell only; the split by type first
+    is a convention of this build (both sides), so this checks the oracle's
+    implementation of that convention, not a passage of the paper."""
     p = cases.default_params(0.02, 0.4, (0, 0, 0), (1, 1, 1))
     cs = 2 * p["h"]
     pos = np.array([[0.5 * cs, 0.5 * cs, 0.5 * cs],   # cell A
