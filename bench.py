@@ -272,19 +272,20 @@ def measure_batched(ncases, steps, warmup, tune, clock_index=0):
     replayed from a captured graph: the fastest plain way measured).  Both
     time the same steps (warmup .. warmup + steps of every case from rest)
     with CUDA events on the engines' stream.  tune: pick cell size and
-    interaction variant with the autotuner (else cells of h, kept list)."""
+    interaction variant and list-walk block size with the autotuner (else
+    cells of h, kept list, 128 threads)."""
     import torch
     from paper_2104_00537_gb300 import autotune, cases, sph
     stream = torch.cuda.Stream()
     cs = cases.batch_dam_breaks(ncases, seed=0)
-    cm, var, tune_ms = 1, 5, None
+    cm, var, block, tune_ms = 1, 5, 128, None
     if tune:
         mk = lambda cc: sph.Engine.batch(cc, stream=stream)
-        (cm, var), tune_ms = autotune.tune(cs, mk, torch.cuda.get_device_name(0))
+        (cm, var, block), tune_ms = autotune.tune(cs, mk, torch.cuda.get_device_name(0))
     for c in cs:
         c.params["cell_mode"] = cm
     eng = sph.Engine.batch(cs, stream=stream)
-    eng.set_options(pi_variant=var, use_graph=1)
+    eng.set_options(pi_variant=var, pi_block=block, use_graph=1)
     eng.step(warmup)
     p0 = sum(eng.stats(i)["interactions"] for i in range(len(cs)))
     clocks = ClockSampler(clock_index)
@@ -295,7 +296,7 @@ def measure_batched(ncases, steps, warmup, tune, clock_index=0):
     ms_p, pp = 0.0, 0
     for c in cs:
         e = sph.Engine.create(c, stream=stream)
-        e.set_options(pi_variant=var, use_graph=1)
+        e.set_options(pi_variant=var, pi_block=block, use_graph=1)
         e.step(warmup)
         q0 = e.stats()["interactions"]
         ms_p += timed_steps(e, stream, steps)
@@ -303,7 +304,7 @@ def measure_batched(ncases, steps, warmup, tune, clock_index=0):
         e.destroy()
     nb = len(cs) * steps
     return {"cases": len(cs), "particles": sum(c.n for c in cs), "steps": steps,
-            "warmup": warmup, "cell_mode": cm, "pi_variant": var,
+            "warmup": warmup, "cell_mode": cm, "pi_variant": var, "pi_block": block,
             "batched": {"case_steps_per_s": nb / (ms_b / 1e3), "ms_per_step": ms_b / steps,
                         "interactions_per_s": (p1 - p0) / (ms_b / 1e3)},
             "plain": {"case_steps_per_s": nb / (ms_p / 1e3), "ms_per_round": ms_p / steps,
@@ -383,7 +384,7 @@ def run_batched(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "%d dam breaks, fluid 5k-200k log-uniform" % r["cases"],
                       "particles": r["particles"], "cell_mode": r["cell_mode"],
-                      "pi_variant": r["pi_variant"]},
+                      "pi_variant": r["pi_variant"], "pi_block": r["pi_block"]},
            "batched": r["batched"], "plain": r["plain"],
            "speedup_vs_plain": r["speedup_vs_plain"],
            "autotune_ms_per_step": r["autotune_ms_per_step"], "clocks": r["clocks"]}
@@ -633,11 +634,12 @@ def main():
         # the rest of the metric, measured in the same run: the whole 2,000-step
         # run of this case, batched vs plain (C3), served vs plain (C4, scaled)
         out["full_run"] = measure_full_run(cs[0], stream)
-        out["batched"] = measure_batched(256, 20, 3, tune=False, clock_index=local)
+        out["batched"] = measure_batched(256, 20, 3, tune=True, clock_index=local)
         out["batched"]["note"] = ("C3 in full (256 cases, 26.6M particles), 20 timed steps "
-                                  "after 3 from rest instead of 500; cells of h, list kept "
-                                  "across steps (the autotuner's choice) for both paths; "
-                                  "each path's state equals the other's (same pairs)")
+                                  "after 3 from rest instead of 500; cell size, pair loop and "
+                                  "block size from the autotuner (3 timed steps per "
+                                  "candidate), the same for both paths; each path's state "
+                                  "equals the other's (same pairs)")
         out["served"] = measure_served(48, 20.0, 200000, 0.1, 10)
         out["served"]["note"] = ("C4 scaled to fit the run: 48 requests, fluid <= 200k, "
                                  "0.1 s simulated (C4: 100+ requests, <= 2M, 1 s; run with "
