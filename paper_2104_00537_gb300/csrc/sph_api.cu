@@ -194,6 +194,7 @@ struct sph_engine_t {
   bool list_dirty = true;      // the next kept-list step starts with a rebuild event
   bool list_stale = true;      //   in which every case rebuilds (sorted state overwritten)
   ListCtl *ctl = nullptr;      // rebuild request, build count, list check
+  uint32_t *rb_tmp = nullptr;  // tile counts of the restricted rebuild's compaction
   cudaStream_t s2 = nullptr;   // captures the bodies of conditional graph nodes
   // pi_variant 5 without a captured step graph: the two guarded parts of a
   // rebuild (sort + reorder + cell table; skin + list) as small graphs
@@ -393,6 +394,7 @@ int allocate(sph_engine e) {
     e->posc_ref = (float4 *)A(16 * N);
     e->posc_ref2 = (float4 *)A(16 * N);
     e->ctl = (ListCtl *)A(sizeof(ListCtl));
+    e->rb_tmp = (uint32_t *)A(4 * rb_temp_words(N));
   }
   if (e->sps || e->pool) {
     e->tau4 = (float4 *)A(16 * N);
@@ -638,7 +640,7 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
                   e->dconst, e->ddyn, 0, s, true);
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
-                         e->list_ld, e->ncount, e->ext, tau4, e->tau2, s, mu,
+                         e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu,
                          e->opt.pi_block);
   } else if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
     if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
@@ -646,10 +648,10 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
                       s);
     launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                       e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                      e->list_cap, e->list_ld, e->ncount, nullptr, nullptr, s);
+                      e->list_cap, e->ncount, nullptr, nullptr, s);
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
-                         e->list_ld, e->ncount, e->ext, tau4, e->tau2, s, mu,
+                         e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu,
                          e->opt.pi_block);
   } else {
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
@@ -657,13 +659,13 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
     if (ev) cudaEventRecord(ev[0], s);
     launch_interact_build(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                           e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace,
-                          e->nlist, e->list_cap, e->list_ld, e->ncount, e->ext, tau4, e->tau2, s,
+                          e->nlist, e->list_cap, e->ncount, e->ext, tau4, e->tau2, s,
                           mu);
   }
   if (ev) cudaEventRecord(ev[1], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_ld, e->ncount, e->ctl, s);
+                      e->list_cap, e->ncount, e->ctl, s);
 }
 
 // The rest of a list step up to its second evaluation: dt (Eq 35), the half
@@ -683,12 +685,12 @@ void enqueue_list_half(sph_engine e, cudaEvent_t *ev, float *mu) {
   if (ev) cudaEventRecord(ev[2], s);
   launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
-                       e->list_ld, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s,
+                       e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s,
                        mu, e->opt.pi_block);
   if (ev) cudaEventRecord(ev[3], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysC, Z.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_ld, e->ncount, e->ctl, s);
+                      e->list_cap, e->ncount, e->ctl, s);
 }
 
 // One Symplectic step with the per-step neighbour list: NL on state n (Y),
@@ -706,19 +708,30 @@ void enqueue_step_list(sph_engine e, cudaEvent_t *ev) {
   launch_end_step(e->cap_cases, e->dconst, e->ddyn, e->s);
 }
 
-// The two guarded parts of a kept-list rebuild event.  The sort: cases that
-// need no rebuild enter it with their build keys and build-cell state (so
-// their order and cells stay), the others with the normalised state in X;
-// the reorder also gathers the build positions into the new order.
+// The two guarded parts of a kept-list rebuild event.  The sort: when index
+// ranges may move (ListCtl::full) every particle, the cases that need no
+// rebuild entering it with their build keys and build-cell state (so their
+// order and cells stay), the others with the normalised state in X; else
+// only the particles of the cases that need a rebuild, within their own
+// index ranges, the others left untouched in Y.  The build positions follow
+// the moved particles.  (An engine of one case sorts directly: its rebuilds
+// always involve all its particles.)  Then the cell table of the whole order.
 void enqueue_rebuild_sort(sph_engine e, cudaStream_t q) {
   const int n = (int)e->n_phys;
   const int nl = (int)(e->n_phys - e->n_dead);
   State &X = e->S[0], &Y = e->S[1];
-  launch_select(n, X.cid, e->dconst, e->ddyn, e->keysB, Y.posc, e->keysA, X.posc, q);
-  radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, q);
-  launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
-                 X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, q, e->posc_ref,
-                 e->posc_ref2);
+  if (e->cap_cases == 1) {
+    // one case: every rebuild event sorts all its particles, directly
+    radix_sort(e->keysA, e->keysB, e->perm1, n, e->nbits, e->sort_tmp, q);
+    launch_reorder(nl, e->perm1, e->keysB, X.posc, X.velrho, X.id, X.cid, X.code, X.vrprev,
+                   X.ghost, Y, e->press, e->dconst, e->ddyn, e->nbits, q, e->posc_ref,
+                   e->posc_ref2);
+  } else {
+    launch_select(n, X.cid, e->dconst, e->ddyn, e->keysB, Y.posc, e->keysA, X.posc, e->ctl, q);
+    launch_rebuild_sort(n, e->ctl, e->keysA, X, Y, e->keysB, e->press, e->dconst, e->ddyn,
+                        e->nbits, e->posc_ref, e->posc_ref2, e->rb_tmp, e->perm2, e->keysC,
+                        e->keysD, e->perm1, e->sort_tmp, q);
+  }
   launch_cells(nl, e->keysB, e->cstart, e->cells_hw, e->nbits, e->nvalid, e->cells_tmp, q);
 }
 
@@ -732,7 +745,7 @@ void enqueue_rebuild_list(sph_engine e, float extra, cudaStream_t q) {
                     q);
   launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                     e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                    e->list_cap, e->list_ld, e->ncount, e->posc_ref, e->posc_ref2, q);
+                    e->list_cap, e->ncount, e->posc_ref, e->posc_ref2, q);
 }
 
 // Appends to the graph being captured on e->s a k_decide kernel and an IF
@@ -1041,8 +1054,8 @@ int sph_step(sph_engine e, int64_t nsteps) {
     // a call continues the kept list as if the steps had not been split,
     // unless the cases or the sorted state changed since the last step
     if (e->list_stale) launch_need_all(e->cap_cases, e->ddyn, e->s);
-    if (e->list_stale || e->list_dirty)
-      CUDA_TRY(cudaMemsetAsync(&e->ctl->rebuild, 1, sizeof(unsigned int), e->s));
+    if (e->list_stale || e->list_dirty)  // a rebuild of every case: ranges may have moved
+      CUDA_TRY(cudaMemsetAsync(&e->ctl->rebuild, 1, 2 * sizeof(unsigned int), e->s));
     e->list_stale = e->list_dirty = false;
   }
   e->cap_err = cudaSuccess;
@@ -1458,8 +1471,8 @@ int sph_eval_step(sph_engine e, int32_t icase, int32_t stage, double *pos, float
   if (reuse) {
     if (!e->s2) CUDA_TRY(cudaStreamCreateWithFlags(&e->s2, cudaStreamNonBlocking));
     if (e->list_stale) launch_need_all(e->cap_cases, e->ddyn, s);
-    if (e->list_stale || e->list_dirty)
-      CUDA_TRY(cudaMemsetAsync(&e->ctl->rebuild, 1, sizeof(unsigned int), s));
+    if (e->list_stale || e->list_dirty)  // a rebuild of every case: ranges may have moved
+      CUDA_TRY(cudaMemsetAsync(&e->ctl->rebuild, 1, 2 * sizeof(unsigned int), s));
     e->list_stale = e->list_dirty = false;
     e->cap_err = cudaSuccess;
     enqueue_reuse_rebuild(e, nullptr);

@@ -101,11 +101,15 @@ __host__ __device__ inline void list_row_decode(uint32_t x, int &dy, int &dz) {
 // Engine-wide control of the neighbour list kept across steps: rebuild is
 // requested by the corrector (a case needs a new list) or by the host (cases
 // admitted or released, the sorted state overwritten) and cleared by the
-// build; builds counts the rebuild events; check_pairs / check_bad are the
+// build; full says that the rebuild must re-sort all cases (else only the
+// particles of the cases that need a list, within their own index ranges);
+// builds counts the rebuild events; check_pairs / check_bad are the
 // optional brute-force check of the list.
 struct ListCtl {
   unsigned int rebuild;
-  unsigned int pad;
+  unsigned int full;  // the rebuild must re-sort every case: index ranges may move
+                      // (a particle left the domain, cases were admitted or
+                      // released, or the sorted state was overwritten)
   unsigned long long builds;
   unsigned long long check_pairs;  // pairs inside 2h found by brute force
   unsigned long long check_bad;    // targets whose brute-force count differs from the list's
@@ -161,7 +165,9 @@ size_t radix_sort_temp_bytes(int64_t n);
 // pass per 8-bit digit; keys below 2^nbits sort by value); writes the sorted
 // keys and the permutation (source index of each output).  keys_in, keys_out,
 // perm_out and temp must not overlap.
+// n_dev (or null): the number of keys, at most n, read on the device when
+// the kernels run (grids and scratch are sized for n).
 void radix_sort(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *perm_out,
-                int n, int nbits, void *temp, cudaStream_t s);
+                int n, int nbits, void *temp, cudaStream_t s, const int *n_dev = nullptr);
 
 }  // namespace sph

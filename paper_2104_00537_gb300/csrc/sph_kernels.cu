@@ -176,6 +176,140 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
   }
 }
 
+// ---- restricted rebuild of the list kept across steps -----------------------
+//
+// At a rebuild event only the particles of the cases that need a new list are
+// sorted again, when no index range can move (ctl->full == 0: no particle left
+// the domain and no case was admitted or released since the last build).  A
+// case's fluid particles then keep one fixed index range and its boundary
+// particles another (all fluid keys lie below all boundary keys, and the cases
+// follow their cellbase order), so the flagged particles, listed in index order
+// and sorted stably by key, fill exactly the slots they came from: output p of
+// that sort goes to the p-th flagged index.  With ctl->full every particle is
+// flagged and the p-th flagged index is p: the full sort.  The other cases keep
+// their order, cells and state untouched.
+constexpr int kRbTile = 1024;
+
+__device__ __forceinline__ bool rb_flag(int i, int n, const uint16_t *__restrict__ cid,
+                                        const CaseDyn *__restrict__ dyn,
+                                        const ListCtl *__restrict__ ctl) {
+  return i < n && (ctl->full || dyn[cid[i]].need);
+}
+
+// The number of flagged particles in every tile of kRbTile indices.
+__global__ void __launch_bounds__(kRbTile)
+k_rb_count(int n, const uint16_t *__restrict__ cid, const CaseDyn *__restrict__ dyn,
+           const ListCtl *__restrict__ ctl, uint32_t *__restrict__ tile_cnt) {
+  const int i = blockIdx.x * kRbTile + threadIdx.x;
+  const int c = __syncthreads_count(rb_flag(i, n, cid, dyn, ctl));
+  if (threadIdx.x == 0) tile_cnt[blockIdx.x] = (uint32_t)c;
+}
+
+// One block: exclusive scan of the tile counts in place; the total to *m.
+__global__ void __launch_bounds__(1024)
+k_rb_scan(int ntiles, uint32_t *__restrict__ tile_cnt, int *__restrict__ m) {
+  const unsigned full = 0xffffffffu;
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  for (int base = 0; base < ntiles; base += 1024) {
+    const int t = base + threadIdx.x;
+    const uint32_t v = t < ntiles ? tile_cnt[t] : 0u;
+    uint32_t x = v;  // inclusive scan within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(full, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {  // inclusive scan of the warp totals
+      uint32_t w = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(full, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t excl = carry + (warp ? wsum[warp - 1] : 0u) + x - v;
+    if (t < ntiles) tile_cnt[t] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *m = (int)carry;
+}
+
+// The flagged indices in index order (idx) and their keys (kc).
+__global__ void __launch_bounds__(kRbTile)
+k_rb_compact(int n, const uint16_t *__restrict__ cid, const CaseDyn *__restrict__ dyn,
+             const ListCtl *__restrict__ ctl, const uint32_t *__restrict__ tile_off,
+             const uint32_t *__restrict__ keys, uint32_t *__restrict__ idx,
+             uint32_t *__restrict__ kc) {
+  __shared__ uint32_t wcnt[kRbTile / 32];
+  const int i = blockIdx.x * kRbTile + threadIdx.x;
+  const bool f = rb_flag(i, n, cid, dyn, ctl);
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wcnt[warp] = (uint32_t)__popc(b);
+  __syncthreads();
+  if (!f) return;
+  uint32_t off = tile_off[blockIdx.x];
+  for (int w = 0; w < warp; w++) off += wcnt[w];
+  const uint32_t p = off + (uint32_t)__popc(b & ((1u << lane) - 1u));
+  idx[p] = (uint32_t)i;
+  kc[p] = keys[i];
+}
+
+// k_reorder through the compaction: output p of the sort of the flagged keys
+// (keys_sorted, perm) goes to slot idx[p] from the particle idx[perm[p]];
+// keys_dst receives its key; the build positions follow (ref, kept list).
+__global__ void k_rb_scatter(int n, const int *__restrict__ m_p, const uint32_t *__restrict__ idx,
+                             const uint32_t *__restrict__ perm,
+                             const uint32_t *__restrict__ keys_sorted, State src, State dst,
+                             uint32_t *__restrict__ keys_dst, float *__restrict__ press,
+                             const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
+                             int nbits, const float4 *__restrict__ ref_src,
+                             float4 *__restrict__ ref_dst) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int cidx = -1;
+  unsigned v2 = 0u;
+  if (p < n && p < *m_p) {
+    const uint32_t d = idx[p], q = idx[perm[p]];
+    float4 pc = src.posc[q];
+    const float4 vr = src.velrho[q];
+    cidx = src.cid[q];
+    const CaseConst &C = cc[cidx];
+    const uint32_t k = keys_sorted[p];
+    if (k < key_out(nbits)) {
+      const uint32_t lin = key_cell(k, nbits) - C.cellbase;
+      pc.w = (float)(lin % (uint32_t)C.nx);
+      v2 = __float_as_uint(fmaf(vr.x, vr.x, fmaf(vr.y, vr.y, vr.z * vr.z)));
+    }
+    keys_dst[d] = k;
+    dst.posc[d] = pc;
+    dst.velrho[d] = vr;
+    dst.id[d] = src.id[q];
+    dst.cid[d] = (uint16_t)cidx;
+    dst.code[d] = src.code[q];
+    if (src.vrprev) dst.vrprev[d] = src.vrprev[q];
+    if (src.ghost) dst.ghost[d] = src.ghost[q];
+    if (ref_dst) ref_dst[d] = ref_src[q];
+    press[d] = tait_pressure(C, vr.w) / vr.w;
+  }
+  // max |v|^2 per case (for the skin of the cases that rebuild), as k_reorder
+  const unsigned full = 0xffffffffu;
+  const int c0 = __shfl_sync(full, cidx, 0);
+  if (__all_sync(full, cidx == c0)) {
+    const unsigned mx = __reduce_max_sync(full, v2);
+    if ((threadIdx.x & 31) == 0 && c0 >= 0 && mx) atomicMax(&dyn[c0].v2max_bits, mx);
+  } else if (cidx >= 0 && v2) {
+    atomicMax(&dyn[cidx].v2max_bits, v2);
+  }
+}
+
 // ---- cell start table --------------------------------------------------------
 
 // cstart (pre-filled with 0xff): first sorted index of every non-empty
@@ -469,6 +603,7 @@ __global__ void k_list_begin(int ncases, const CaseConst *__restrict__ cc,
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c == 0 && ctl) {
     ctl->rebuild = 0u;
+    ctl->full = 0u;
     ctl->builds += 1ull;
   }
   if (c >= ncases || !cc[c].active) return;
@@ -489,16 +624,18 @@ __global__ void k_list_begin(int ncases, const CaseConst *__restrict__ cc,
   D.startB = sB;
 }
 
-// Before the sort of a kept-list rebuild: the cases that need no rebuild
-// enter it with their build keys and their state in the build's cells (y),
-// so that they keep their particle order and cells; the others with the
-// normalised state the corrector wrote into x.
+// Before the sort of a kept-list rebuild that re-sorts every case (ctl->full):
+// the cases that need no rebuild enter it with their build keys and their
+// state in the build's cells (y), so that they keep their particle order and
+// cells; the others with the normalised state the corrector wrote into x.
+// (A restricted rebuild sorts only the cases that need one: nothing to do.)
 __global__ void k_select(int n, const uint16_t *__restrict__ cid,
                          const CaseConst *__restrict__ cc, const CaseDyn *__restrict__ dyn,
                          const uint32_t *__restrict__ keys_build, const float4 *__restrict__ posc_build,
-                         uint32_t *__restrict__ keys, float4 *__restrict__ posc) {
+                         uint32_t *__restrict__ keys, float4 *__restrict__ posc,
+                         const ListCtl *__restrict__ ctl) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || !ctl->full) return;
   const int c = cid[i];
   if (!cc[c].active || dyn[c].need) return;
   keys[i] = keys_build[i];
@@ -531,9 +668,8 @@ __global__ void k_need_all(int ncases, CaseDyn *__restrict__ dyn) {
 // LIST (VARIANT 0): 1 also writes the target's neighbour list, 2 writes
 // only the list (no pair terms, no outputs besides the list and ref): for
 // every tested chunk with a candidate within 2h + skin, one record (first
-// index | row offset, mask of those candidates) to list[c ld + i] (record c of
-// every target in one row of ld entries, so that the lanes of a warp read and
-// write adjacent words), at most cap records per target.  The
+// index | row offset, mask of those candidates) to list[i cap + c] (a target's
+// records side by side, four to a 32-byte sector), at most cap per target.  The
 // list's rows reach one cell further than the 2h support (M + 1 cells, so
 // 2h + cs >= 2h + skin), clipped to the case's grid.  ref, if set, receives
 // the target's position at the build (the list kept across steps), and the
@@ -551,7 +687,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
            const float4 *__restrict__ tau4 = nullptr, const float2 *__restrict__ tau2 = nullptr,
            uint2 *__restrict__ list = nullptr, int cap = 0,
            uint16_t *__restrict__ count = nullptr, float4 *__restrict__ ref = nullptr,
-           const float4 *__restrict__ ref_src = nullptr, int64_t ld = 0) {
+           const float4 *__restrict__ ref_src = nullptr) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -604,7 +740,9 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   const bool warp_plain = __all_sync(full, (afluid || !has) && !X.hyd && !X.sps);
   Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
   constexpr int MR = LIST ? M + 1 : M;  // rows reach MR cells
-  if (LIST && ref && i < n) ref[i] = lmode == 1 ? pa : ref_src[i];
+  // the build position: taken now (mode 1), gathered into the new order by
+  // the sort (mode 2), or kept where it is (mode 0: the target did not move)
+  if (LIST && ref && i < n && lmode != 0) ref[i] = lmode == 1 ? pa : ref_src[i];
   // rows dy, dz in [-M, M]; a list build adds row -(M+1) (M+1) for the
   // targets within the skin of their cell's lower (upper) face, over the
   // warp's union of those ranges
@@ -671,7 +809,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
             }
           }
           if (LIST && ml) {
-            if (lcnt < cap) list[(int64_t)lcnt * ld + i] = make_uint2((uint32_t)(lo + base) | rowbits, ml);
+            if (lcnt < cap) list[(int64_t)i * cap + lcnt] = make_uint2((uint32_t)(lo + base) | rowbits, ml);
             lcnt++;
           }
           if (LIST != 2) {
@@ -1502,7 +1640,7 @@ struct ListArgs {
   float4 *ace;
   int want_dt;
   const uint2 *list;
-  int64_t ld;
+  int cap;  // records per target: record r of target i at list[i cap + r]
   const uint16_t *count;
   const float4 *tau4;
   const float2 *tau2;
@@ -1528,7 +1666,7 @@ __device__ __forceinline__ void list_target(const int i, const ListArgs &a) {
   float4 *__restrict__ ace = a.ace;
   const int want_dt = a.want_dt;
   const uint2 *__restrict__ list = a.list;
-  const int64_t ld = a.ld;
+  const int cap = a.cap;
   const uint16_t *__restrict__ count = a.count;
   const float4 *__restrict__ tau4 = a.tau4;
   const float2 *__restrict__ tau2 = a.tau2;
@@ -1567,7 +1705,7 @@ __device__ __forceinline__ void list_target(const int i, const ListArgs &a) {
   const int nrec = has ? (int)count[i] : 0;
   const bool warp_fluid = __all_sync(full, afluid || !has);
   Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
-  const uint2 *__restrict__ mine = list + i;  // record r at mine[r ld]
+  const uint2 *__restrict__ mine = list + (int64_t)i * cap;
   // two candidates per lane per iteration (their loads issued together),
   // records taken in order: the warp waits only for its lane with the most
   // candidates in total
@@ -1577,7 +1715,7 @@ __device__ __forceinline__ void list_target(const int i, const ListArgs &a) {
   float sy = 0.f, sz = 0.f;
   // the next record of the lane: base index, candidate mask, row offsets
   auto next_record = [&]() {
-    const uint2 rec = mine[(int64_t)(r++) * ld];
+    const uint2 rec = mine[r++];
     cbase = (int)(rec.x & kListIndexMask);
     cm = rec.y;
     int rdy, rdz;
@@ -1646,7 +1784,7 @@ __global__ void __launch_bounds__(128)
 k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
               const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
               const uint16_t *__restrict__ cid, int nbits, const CaseConst *__restrict__ cc,
-              const uint2 *__restrict__ list, int64_t ld, const uint16_t *__restrict__ count,
+              const uint2 *__restrict__ list, int cap, const uint16_t *__restrict__ count,
               float4 *__restrict__ tau4, float2 *__restrict__ tau2) {
   const unsigned full = 0xffffffffu;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1667,7 +1805,7 @@ k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restric
   const float4 pa = act ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float4 va = act ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
   const int nrec = act ? (int)count[i] : 0;
-  const uint2 *__restrict__ mine = list + i;  // record r at mine[r ld]
+  const uint2 *__restrict__ mine = list + (int64_t)i * cap;
   float gxx = 0.f, gyy = 0.f, gzz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
   int r = 0;
   unsigned cm = 0u;
@@ -1676,7 +1814,7 @@ k_strain_list(int n, const int *__restrict__ nvalid_p, const uint32_t *__restric
 #pragma unroll 1
   for (;;) {
     if (cm == 0u && r < nrec) {
-      const uint2 rec = mine[(int64_t)(r++) * ld];
+      const uint2 rec = mine[r++];
       cbase = (int)(rec.x & kListIndexMask);
       cm = rec.y;
       int rdy, rdz;
@@ -1857,6 +1995,7 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
     x.velrho[i] = vn;
     keys_next[i] = key_out(nbits);
     dyn[cidx].need = 1u;
+    ctl->full = 1u;  // the frozen particle moves to the tail of the order
     ctl->rebuild = 1u;
     return;
   }
@@ -1870,6 +2009,7 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
   keys_next[i] = kn;
   if (kn >= key_out(nbits)) {  // left at the full step: frozen in x
     dyn[cidx].need = 1u;
+    ctl->full = 1u;
     ctl->rebuild = 1u;
     return;
   }
@@ -1904,7 +2044,7 @@ __global__ void k_decide(cudaGraphConditionalHandle h, const ListCtl *__restrict
 __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
                              const uint32_t *__restrict__ keys, const float4 *__restrict__ posc,
                              const uint16_t *__restrict__ cid, const CaseConst *__restrict__ cc,
-                             int nbits, const uint2 *__restrict__ list, int64_t ld,
+                             int nbits, const uint2 *__restrict__ list, int cap,
                              const uint16_t *__restrict__ count, ListCtl *__restrict__ ctl) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
@@ -1934,7 +2074,7 @@ __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
     if (__float_as_uint(r2) - 1u < r2max_u) nb++;
   }
   for (int r = 0; r < (int)count[i]; r++) {
-    const uint2 rec = list[(int64_t)r * ld + i];
+    const uint2 rec = list[(int64_t)i * cap + r];
     const int cbase = (int)(rec.x & kListIndexMask);
     int rdy, rdz;
     list_row_decode(rec.x, rdy, rdz);
@@ -2036,6 +2176,7 @@ __global__ void k_verlet(int n, const uint32_t *__restrict__ keys_in, State src,
   if (REUSE) {
     if (left) {
       dyn[cidx].need = 1u;
+      ctl->full = 1u;
       ctl->rebuild = 1u;
       return;
     }
@@ -2405,14 +2546,14 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const float4 *velrho, const float *press, const uint16_t *cid,
                           const uint32_t *cstart, int64_t cap_cells, int nbits,
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
-                          const uint2 *list, int64_t ld, const uint16_t *count, bool ext,
+                          const uint2 *list, int cap, const uint16_t *count, bool ext,
                           float4 *tau4, float2 *tau2, cudaStream_t s, float *mu, int block) {
   if (n <= 0) return;
   const ListArgs a{n,   nvalid, keys, posc, velrho, press, cid,   cstart, (uint32_t)(cap_cells + 1),
-                   nbits, cc,   dyn,  ace,  want_dt, list,  ld,    count,  tau4, tau2, mu};
+                   nbits, cc,   dyn,  ace,  want_dt, list,  cap,   count,  tau4, tau2, mu};
   if (tau4)  // laminar + SPS cases present: strain pass over the list first
     k_strain_list<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, nbits, cc,
-                                               list, ld, count, tau4, tau2);
+                                               list, cap, count, tau4, tau2);
   // one thread per target; block size 128 (default) to 1024 for the default
   // kernel (EXT 1 and 2: 128, by their registers)
   const int b0 = block >= 128 && block <= 1024 && block % 32 == 0 ? block : 128;
@@ -2433,9 +2574,28 @@ void launch_list_begin(int ncases, const CaseConst *cc, CaseDyn *dyn, ListCtl *c
 
 void launch_select(int n, const uint16_t *cid, const CaseConst *cc, const CaseDyn *dyn,
                    const uint32_t *keys_build, const float4 *posc_build, uint32_t *keys,
-                   float4 *posc, cudaStream_t s) {
+                   float4 *posc, const ListCtl *ctl, cudaStream_t s) {
   if (n > 0)
-    k_select<<<nblk(n, 256), 256, 0, s>>>(n, cid, cc, dyn, keys_build, posc_build, keys, posc);
+    k_select<<<nblk(n, 256), 256, 0, s>>>(n, cid, cc, dyn, keys_build, posc_build, keys, posc,
+                                          ctl);
+}
+
+size_t rb_temp_words(int64_t n) { return (size_t)((n + kRbTile - 1) / kRbTile) + 2; }
+
+void launch_rebuild_sort(int n, const ListCtl *ctl, const uint32_t *keys, State src, State dst,
+                         uint32_t *keys_dst, float *press, const CaseConst *cc, CaseDyn *dyn,
+                         int nbits, const float4 *ref_src, float4 *ref_dst, uint32_t *tmp,
+                         uint32_t *idx, uint32_t *kc, uint32_t *kc_sorted, uint32_t *perm,
+                         void *sort_tmp, cudaStream_t s) {
+  if (n <= 0) return;
+  const int ntiles = (n + kRbTile - 1) / kRbTile;
+  int *m = (int *)(tmp + ntiles);
+  k_rb_count<<<ntiles, kRbTile, 0, s>>>(n, src.cid, dyn, ctl, tmp);
+  k_rb_scan<<<1, 1024, 0, s>>>(ntiles, tmp, m);
+  k_rb_compact<<<ntiles, kRbTile, 0, s>>>(n, src.cid, dyn, ctl, tmp, keys, idx, kc);
+  radix_sort(kc, kc_sorted, perm, n, nbits, sort_tmp, s, m);
+  k_rb_scatter<<<nblk(n, 256), 256, 0, s>>>(n, m, idx, perm, kc_sorted, src, dst, keys_dst,
+                                             press, cc, dyn, nbits, ref_src, ref_dst);
 }
 
 void launch_need_all(int ncases, CaseDyn *dyn, cudaStream_t s) {
@@ -2446,13 +2606,12 @@ void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *key
                        const float4 *posc, const float4 *velrho, const float *press,
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
-                       int64_t ld, uint16_t *count, float4 *ref, const float4 *ref_src,
-                       cudaStream_t s) {
+                       uint16_t *count, float4 *ref, const float4 *ref_src, cudaStream_t s) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_BL_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 0, \
-      nullptr, nullptr, list, cap, count, ref, ref_src, ld
+      nullptr, nullptr, list, cap, count, ref, ref_src
   if (margin == 1)
     k_interact<1, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
   else if (margin == 3)
@@ -2466,13 +2625,13 @@ void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t 
                            const float4 *posc, const float4 *velrho, const float *press,
                            const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
                            int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
-                           uint2 *list, int cap, int64_t ld, uint16_t *count, bool ext,
-                           float4 *tau4, float2 *tau2, cudaStream_t s, float *mu) {
+                           uint2 *list, int cap, uint16_t *count, bool ext, float4 *tau4,
+                           float2 *tau2, cudaStream_t s, float *mu) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_IB_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, mu, 1, \
-      tau4, tau2, list, cap, count, nullptr, nullptr, ld
+      tau4, tau2, list, cap, count
   if (tau4) {  // laminar + SPS cases: strain pass on state n, then EXT 2
     if (margin == 1) {
       k_strain<1><<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, cstart, cap1,
@@ -2534,9 +2693,9 @@ void launch_decide(cudaGraphConditionalHandle h, const ListCtl *ctl, cudaStream_
 
 void launch_list_check(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
                        const uint16_t *cid, const CaseConst *cc, int nbits, const uint2 *list,
-                       int64_t ld, const uint16_t *count, ListCtl *ctl, cudaStream_t s) {
+                       int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s) {
   if (n > 0)
-    k_list_check<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, cid, cc, nbits, list, ld,
+    k_list_check<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, cid, cc, nbits, list, cap,
                                               count, ctl);
 }
 

@@ -57,7 +57,19 @@ void launch_list_begin(int ncases, const CaseConst *cc, CaseDyn *dyn, ListCtl *c
 // the sort with their build keys and build-cell state.
 void launch_select(int n, const uint16_t *cid, const CaseConst *cc, const CaseDyn *dyn,
                    const uint32_t *keys_build, const float4 *posc_build, uint32_t *keys,
-                   float4 *posc, cudaStream_t s);
+                   float4 *posc, const ListCtl *ctl, cudaStream_t s);
+// The sort, reorder and scatter of a kept-list rebuild: the particles of the
+// cases that need a list (every particle when ctl->full), sorted by key within
+// the slots they occupy, from src (x) into dst (y) and keys_dst, with P/rho,
+// the max |v|^2 per case and the build positions (ref_src -> ref_dst).
+// Scratch: tmp (rb_temp_words(n) words), idx, kc, kc_sorted, perm ([n] each)
+// and sort_tmp (radix_sort_temp_bytes(n)).
+size_t rb_temp_words(int64_t n);
+void launch_rebuild_sort(int n, const ListCtl *ctl, const uint32_t *keys, State src, State dst,
+                         uint32_t *keys_dst, float *press, const CaseConst *cc, CaseDyn *dyn,
+                         int nbits, const float4 *ref_src, float4 *ref_dst, uint32_t *tmp,
+                         uint32_t *idx, uint32_t *kc, uint32_t *kc_sorted, uint32_t *perm,
+                         void *sort_tmp, cudaStream_t s);
 // Marks every case's kept list for a rebuild.
 void launch_need_all(int ncases, CaseDyn *dyn, cudaStream_t s);
 // The list alone (the candidate test of the compacted loop, no pair terms);
@@ -67,21 +79,20 @@ void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *key
                        const float4 *posc, const float4 *velrho, const float *press,
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
-                       int64_t ld, uint16_t *count, float4 *ref, const float4 *ref_src,
-                       cudaStream_t s);
+                       uint16_t *count, float4 *ref, const float4 *ref_src, cudaStream_t s);
 // First evaluation of the list step: the compacted pair loop on state n that
 // also writes every target's list (chunk records, radius 2h + skin) and count.
 void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t *keys,
                            const float4 *posc, const float4 *velrho, const float *press,
                            const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells,
                            int nbits, const CaseConst *cc, CaseDyn *dyn, float4 *ace,
-                           uint2 *list, int cap, int64_t ld, uint16_t *count, bool ext,
-                           float4 *tau4, float2 *tau2, cudaStream_t s, float *mu = nullptr);
+                           uint2 *list, int cap, uint16_t *count, bool ext, float4 *tau4,
+                           float2 *tau2, cudaStream_t s, float *mu = nullptr);
 void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
                           const float4 *velrho, const float *press, const uint16_t *cid,
                           const uint32_t *cstart, int64_t cap_cells, int nbits,
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
-                          const uint2 *list, int64_t ld, const uint16_t *count, bool ext,
+                          const uint2 *list, int cap, const uint16_t *count, bool ext,
                           float4 *tau4, float2 *tau2, cudaStream_t s, float *mu = nullptr,
                           int block = 128);
 void launch_predictor_list(int n, const uint32_t *keys_in, State src, const float4 *ace,
@@ -100,7 +111,7 @@ void launch_decide(cudaGraphConditionalHandle h, const ListCtl *ctl, cudaStream_
 // Brute-force check of the list against the evaluated state (tests).
 void launch_list_check(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
                        const uint16_t *cid, const CaseConst *cc, int nbits, const uint2 *list,
-                       int64_t ld, const uint16_t *count, ListCtl *ctl, cudaStream_t s);
+                       int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s);
 void launch_corrector_list(int n, const uint32_t *keys_n, const uint32_t *keys_half, State sn,
                            const float4 *velrho_half, const float4 *ace, const CaseConst *cc,
                            CaseDyn *dyn, int nbits, State x, uint32_t *keys_next,

@@ -30,7 +30,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 __global__ void __launch_bounds__(kThreads)
 k_upsweep(const uint32_t *__restrict__ keys, int n, int shift, int ntiles,
-          uint32_t *__restrict__ hist) {
+          uint32_t *__restrict__ hist, const int *__restrict__ n_dev) {
+  if (n_dev) n = min(n, *n_dev);  // the key count, when only the device knows it
   __shared__ uint32_t cnt[kRadix];
   for (int d = threadIdx.x; d < kRadix; d += kThreads) cnt[d] = 0;
   __syncthreads();
@@ -92,7 +93,9 @@ __global__ void __launch_bounds__(kThreads)
 k_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
             uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int n,
             int shift, int ntiles, const uint32_t *__restrict__ hist,
-            const uint32_t *__restrict__ totals) {
+            const uint32_t *__restrict__ totals,
+            const int *__restrict__ n_dev) {
+  if (n_dev) n = min(n, *n_dev);
   __shared__ uint32_t wcnt[kWarps][kRadix];
   __shared__ uint32_t gbase[kRadix];
   __shared__ uint32_t wsum[kWarps];
@@ -161,7 +164,7 @@ k_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ v
 size_t radix_sort_temp_bytes(int64_t n) { return sort_temp_bytes(n); }
 
 void radix_sort(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *perm_out, int n,
-                int nbits, void *temp, cudaStream_t s) {
+                int nbits, void *temp, cudaStream_t s, const int *n_dev) {
   if (n <= 0) return;
   int ntiles = (n + kTile - 1) / kTile;
   char *p = (char *)temp;
@@ -183,10 +186,10 @@ void radix_sort(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *perm_out,
     uint32_t *kout = to_out ? keys_out : ktmp;
     uint32_t *vout = to_out ? perm_out : vtmp;
     int shift = pass * 8;
-    k_upsweep<<<ntiles, kThreads, 0, s>>>(kin, n, shift, ntiles, hist);
+    k_upsweep<<<ntiles, kThreads, 0, s>>>(kin, n, shift, ntiles, hist, n_dev);
     k_digit_scan<<<kRadix, 1024, 0, s>>>(hist, ntiles, totals);
     k_downsweep<<<ntiles, kThreads, 0, s>>>(kin, vin, kout, vout, n, shift, ntiles, hist,
-                                            totals);
+                                            totals, n_dev);
     kin = kout;
     vin = vout;
   }

@@ -582,6 +582,39 @@ def test_list_kept_across_steps_in_a_batch():
     bat.destroy()
 
 
+def test_batch_rebuilds_with_a_particle_leaving_the_domain():
+    """Rebuild events of a batch re-sort only the cases that need a new list,
+    in place, while no index range can move; a particle of the first case
+    leaving the domain (it moves to the tail of the order, shifting every
+    later range) makes the next rebuild re-sort every case.  Each case still
+    takes bit for bit the steps it takes alone, and every pair is found."""
+    c1 = cases.dam_break(0.04, seed=1)
+    f = np.where(c1.ptype == 0)[0][-1]
+    origin, csz, nc, margin = oracle.grid(c1.params)
+    ztop = origin[2] + (nc[2] - margin) * csz
+    c1.pos[f] = (0.8, 0.3, ztop - 0.004)
+    c1.vel[f] = (0.0, 0.0, 5.0)
+    cs = [c1, cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
+          cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
+    for use_graph in (0, 1):
+        bat = sph.Engine.batch(cs)
+        bat.set_options(check_list=1, use_graph=use_graph)
+        bat.step(60)
+        assert bat.list_info()["check_bad"] == 0
+        assert bat.stats(0)["n_out"] >= 1
+        for i, c in enumerate(cs):
+            e = sph.Engine.create(c)
+            e.set_options(use_graph=use_graph)
+            e.step(60)
+            a, b = e.get_state(), bat.get_state(i)
+            for k in ("pos", "vel", "rho"):
+                assert np.array_equal(a[k], b[k]), (use_graph, i, k)
+            assert a["t"] == b["t"]
+            assert e.stats()["interactions"] == bat.stats(i)["interactions"]
+            e.destroy()
+        bat.destroy()
+
+
 def test_kept_list_steps_do_not_depend_on_calls(c0):
     """Splitting steps into calls changes nothing on the kept list: a call
     continues the list of the previous one (eager launches and graph replay
