@@ -104,8 +104,11 @@ def measured_limiter(cell_mode, workload_name, variant):
     return None if v is None else v.get("limiter")
 
 
-def workload(name, rank=0, **kw):
+def workload(name, rank=0, dp=None, **kw):
     from paper_2104_00537_gb300 import cases
+    if name == "wave_flume" and dp:
+        c = cases.wave_flume(dp, seed=rank, **kw)
+        return [c], "wave flume 25x1x1.2 m dp=%g (%.1fM particles)" % (dp, c.n / 1e6)
     if name == "dam_break":
         return [cases.dam_break(0.004, seed=rank, **kw)], "3-D dam break dp=0.004 (1.48M particles)"
     if name == "dam_break_small":
@@ -430,6 +433,8 @@ def main():
     ap.add_argument("--mdbc-slip", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dp", type=float, default=None,
+                    help="particle spacing of the wave flume (default 0.008 m)")
     ap.add_argument("--no-modes", action="store_true",
                     help="skip the batched / served / full-run sub-measurements of the "
                          "default line")
@@ -458,7 +463,7 @@ def main():
     from paper_2104_00537_gb300 import sph
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    cs, desc = workload(args.workload, rank, boundary_mode=args.boundary_mode)
+    cs, desc = workload(args.workload, rank, dp=args.dp, boundary_mode=args.boundary_mode)
     for c in cs:
         c.params["cell_mode"] = args.cell_mode
         c.params["ddt_mode"] = args.ddt_mode

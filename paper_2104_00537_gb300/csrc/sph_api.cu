@@ -1136,7 +1136,12 @@ int sph_step(sph_engine e, int64_t nsteps) {
   }
   const int64_t builds0 = e->builds_seen;
   const int rc = check_flags(e);
-  if (reuse) e->kernel_launches += (e->builds_seen - builds0) * (3 * passes + 1 + 4 + 1 + 1);
+  // per rebuild event: the sort (3 kernels per pass), the reorder (one case) or
+  // select + count + scan + compact + scatter (several), the cell table (4),
+  // the skin and the list build
+  if (reuse)
+    e->kernel_launches += (e->builds_seen - builds0) *
+                          (3 * passes + (e->cap_cases == 1 ? 1 : 5) + 4 + 1 + 1);
   return rc;
 }
 
