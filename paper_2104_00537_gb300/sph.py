@@ -173,6 +173,19 @@ def make_params(p: dict) -> CaseParams:
     return c
 
 
+def state_buffers(n, pinned=False):
+    """Host arrays of n particles for Engine.get_state(out=...); pinned: in
+    page-locked memory (kept alive by the returned dict's "_keep")."""
+    out = dict(pos=np.zeros((n, 3), np.float64), vel=np.zeros((n, 3), np.float32),
+               rho=np.zeros(n, np.float32), press=np.zeros(n, np.float32))
+    if pinned:
+        import torch
+        keep = [torch.from_numpy(a).pin_memory() for a in out.values()]
+        out = dict(zip(out.keys(), (t.numpy() for t in keep)))
+        out["_keep"] = keep
+    return out
+
+
 class HostParticles:
     """Keeps the host arrays of one case alive while the C struct points at them."""
 
@@ -253,9 +266,10 @@ class Engine:
 
     # ---- constructors
     @classmethod
-    def create(cls, case, stream=None, torch_alloc=True, pinned=False):
+    def create(cls, case, stream=None, torch_alloc=True, pinned=False, host=None):
+        """host: a HostParticles of the case prepared beforehand (e.g. pinned)."""
         L = load()
-        hp = HostParticles(case, pinned=pinned)
+        hp = host if host is not None else HostParticles(case, pinned=pinned)
         prm = make_params(case.params)
         al = TorchAllocator() if torch_alloc else None
         h = C.c_void_p()
@@ -349,12 +363,14 @@ class Engine:
     def _n(self, icase):
         return self.sizes[icase]
 
-    def get_state(self, icase=0):
+    def get_state(self, icase=0, out=None):
+        """The case's state in the caller's order; out: arrays from
+        state_buffers(n) to fill instead of new ones."""
         n = self._n(icase)
-        pos = np.zeros((n, 3), np.float64)
-        vel = np.zeros((n, 3), np.float32)
-        rho = np.zeros(n, np.float32)
-        press = np.zeros(n, np.float32)
+        if out is None:
+            out = state_buffers(n)
+        pos, vel, rho, press = out["pos"], out["vel"], out["rho"], out["press"]
+        assert pos.shape == (n, 3) and rho.shape == (n,)
         t, st, dt = C.c_double(), C.c_int64(), C.c_double()
         check(self.lib.sph_get_state(self.h, icase, pos.ctypes.data, vel.ctypes.data,
                                      rho.ctypes.data, press.ctypes.data, C.byref(t),
