@@ -422,10 +422,12 @@ def main():
     ap.add_argument("--workload", default="dam_break")
     ap.add_argument("--cell-mode", type=int, default=1)
     ap.add_argument("--ddt-mode", type=int, default=1, choices=[0, 1, 2])
-    ap.add_argument("--pi-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5])
+    ap.add_argument("--pi-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6])
     ap.add_argument("--list-skin", type=float, default=-1.0)
     ap.add_argument("--pi-block", type=int, default=0,
                     help="threads per block of the list walk (0: the engine default)")
+    ap.add_argument("--pi-lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="threads per target of the list walk (0: the engine default)")
     ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "verlet"])
     ap.add_argument("--visc-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--nu0", type=float, default=1e-6)
@@ -475,19 +477,20 @@ def main():
     with torch.cuda.stream(stream):
         eng = sph.Engine.batch(cs, stream=stream) if len(cs) > 1 else \
             sph.Engine.create(cs[0], stream=stream)
-    eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, pi_block=args.pi_block)
+    eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, pi_block=args.pi_block,
+                    pi_lanes=args.pi_lanes)
     n_particles = sum(c.n for c in cs)
     # the pi_variant the engine runs (its default: 5, the list kept across steps)
     list_ok = n_particles < (1 << 25)
     default_var = 5
-    eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4, 5) else (
+    eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4, 5, 6) else (
         default_var if list_ok else 0)
     if eff_var in (3, 4, 5) and not list_ok:
         eff_var = 0
     if args.integrator == "verlet" and eff_var in (3, 4):
         eff_var = 0
-    kernel = {3: "k_interact_list", 4: "k_interact_list", 5: "k_interact_list"}.get(
-        eff_var, "k_interact")
+    kernel = {3: "k_interact_list", 4: "k_interact_list", 5: "k_interact_list",
+              6: "k_interact_tile"}.get(eff_var, "k_interact")
 
     # the FP32 / FP64 pipe throughput of this GPU (roofline denominators),
     # measured before the warm-up
@@ -495,7 +498,7 @@ def main():
     # warm-up
     eng.step(args.warmup)
     eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, timing=1,
-                    pi_block=args.pi_block)
+                    pi_block=args.pi_block, pi_lanes=args.pi_lanes)
     eng.timing(reset=True)
     builds0 = eng.list_info()["builds"]
 
@@ -552,8 +555,10 @@ def main():
     peak = peaks["fp32_tflops"]
     mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
     nominal = peaks["sms"] * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    # the committed capture is of the default physics and launch shape
     captured = ((args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) ==
-                (1, "symplectic", 0, 0) and eff_var in (4, 5))
+                (1, "symplectic", 0, 0) and eff_var in (4, 5) and
+                args.pi_block in (0, 128) and args.pi_lanes in (0, 1) and args.list_skin < 0)
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_basis": "measured in this run: FP32 FMA chains on all %d SMs "

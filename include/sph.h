@@ -157,7 +157,12 @@ typedef struct {
                        * the steps it takes alone, bit for bit, however
                        * the steps are split into calls).  5 also serves
                        * the Verlet scheme; 3 and 4 with Verlet, and any
-                       * list beyond 2^25 particles, fall back to 0      */
+                       * list beyond 2^25 particles, fall back to 0; 6 the
+                       * cell walk with warp-shared candidate tiles: the
+                       * lanes of a warp in one row of cells stage the
+                       * union of their candidates 32 at a time in shared
+                       * memory and each tests every staged candidate
+                       * (default physics; the extended terms take 0)    */
   int32_t use_graph;  /* 1: replay each step from a captured CUDA graph        */
   int32_t timing;     /* 1: time every PI launch and every step with CUDA
                        * events (sph_get_timing, sph_get_step_times); the
@@ -168,6 +173,12 @@ typedef struct {
   int32_t check_list; /* 1: after every list evaluation, count the pairs of
                        * every target by brute force and compare (tests;
                        * sph_list_info reports the result)                */
+  int32_t pi_lanes;   /* threads that share one target in the list walk
+                       * (pi_variant 3-5): 0 (default: 1), 1, 2, 4 or 8;
+                       * thread k of a target takes the candidates at bit
+                       * positions k, k + lanes, ... of each chunk record and
+                       * the partial sums are added at the end, so the sums'
+                       * order (not the pair set) depends on it           */
 } sph_options;
 
 /* Last error message of the calling thread ("" if none). */

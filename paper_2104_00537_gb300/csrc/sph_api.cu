@@ -230,7 +230,7 @@ struct sph_engine_t {
   char *io = nullptr;
   size_t io_bytes = 0;
   // options, graph, timing
-  sph_options opt{0, 0, 0, 0, -1.f, 0};  // list_skin < 0: the default
+  sph_options opt{0, 0, 0, 0, -1.f, 0, 0};  // list_skin < 0: the default
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_n = -1, graph_dead = -1;  // n_phys and cells_hw of the captured graph
   int graph_ext = 0;  // ext + 2 sps + 4 mdbc + 8 list of the captured graph
@@ -336,7 +336,7 @@ bool use_list(sph_engine e) {
 // list allocated, or 3 and 4 with the Verlet scheme).
 int resolve_variant(sph_engine e, int v) {
   if (v == -1) v = e->list_ok ? e->list_default : 0;
-  if (v >= 3 && (!e->list_ok || (e->integrator == 1 && v != 5))) v = 0;
+  if (v >= 3 && v <= 5 && (!e->list_ok || (e->integrator == 1 && v != 5))) v = 0;
   return v;
 }
 
@@ -641,7 +641,7 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                          e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu,
-                         e->opt.pi_block);
+                         e->opt.pi_block, e->opt.pi_lanes);
   } else if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
     if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
@@ -652,7 +652,7 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                          e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu,
-                         e->opt.pi_block);
+                         e->opt.pi_block, e->opt.pi_lanes);
   } else {
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
                       s);
@@ -686,7 +686,7 @@ void enqueue_list_half(sph_engine e, cudaEvent_t *ev, float *mu) {
   launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
                        e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s,
-                       mu, e->opt.pi_block);
+                       mu, e->opt.pi_block, e->opt.pi_lanes);
   if (ev) cudaEventRecord(ev[3], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysC, Z.posc, Y.cid, e->dconst, e->nbits, e->nlist,
@@ -1015,11 +1015,14 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
   if (opt->pi_block != 0 && opt->pi_block != 128 && opt->pi_block != 256 &&
       opt->pi_block != 512 && opt->pi_block != 1024)
     return fail(SPH_ERR_ARG, "pi_block must be 0 (default), 128, 256, 512 or 1024");
-  if (opt->pi_variant < -1 || opt->pi_variant > 5)
+  if (opt->pi_lanes != 0 && opt->pi_lanes != 1 && opt->pi_lanes != 2 && opt->pi_lanes != 4 &&
+      opt->pi_lanes != 8)
+    return fail(SPH_ERR_ARG, "pi_lanes must be 0 (default), 1, 2, 4 or 8");
+  if (opt->pi_variant < -1 || opt->pi_variant > 6)
     return fail(SPH_ERR_ARG,
                 "pi_variant must be -1 (engine default), 0 (compacted), 1 (inline), 2 (queued), "
                 "3 (per-step list written by the first evaluation), 4 (per-step list built "
-                "alone) or 5 (list kept across steps)");
+                "alone), 5 (list kept across steps) or 6 (warp-shared candidate tiles)");
   if (opt->list_skin > (float)kListExtraMax)
     return fail(SPH_ERR_ARG, "list_skin must be at most 0.25 (or < 0 for the default)");
   e->opt = *opt;

@@ -550,10 +550,13 @@ __device__ __forceinline__ void pair_boundary(const float4 &va, float hih, float
 // Final values of target a from its accumulators: dv/dt (Eq 22 with g), drho/dt
 // (Eq 15 with the Eq 17-18 term, or Eq 36), mu_max and the Eq 35 candidate
 // time step; then the warp's per-case reduction of counts, dt and flags.
+// With several lanes per target (all holding the same totals) only the lead
+// lane writes and counts.
 __device__ __forceinline__ void finish_target(const CaseConst &C, int i, int n, int cidx, bool has,
                                               bool afluid, const float4 &va, const Acc &A,
                                               int want_dt, float4 *__restrict__ ace,
-                                              float *__restrict__ mu_out, CaseDyn *dyn) {
+                                              float *__restrict__ mu_out, CaseDyn *dyn,
+                                              bool lead = true) {
   unsigned npairs = 0, nfb = 0, nbf = 0, dtbits = kFloatInfBits;
   bool bad = false;
   if (has) {
@@ -579,8 +582,12 @@ __device__ __forceinline__ void finish_target(const CaseConst &C, int i, int n, 
       mumax = 0.f;
       bad = !isfinite(out.w);
     }
-    ace[i] = out;
-    if (mu_out) mu_out[i] = mumax;
+    if (lead) {
+      ace[i] = out;
+      if (mu_out) mu_out[i] = mumax;
+    } else {
+      npairs = nfb = nbf = 0u;
+    }
   }
   reduce_case(i < n ? cidx : -1, has, npairs, nfb, nbf, dtbits, bad, dyn);
 }
@@ -1024,6 +1031,124 @@ k_interact_q(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict
     }
   }
   while (__any_sync(full, cur != 0u || head != tail)) pair_step();
+  finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
+}
+
+// Warp-shared candidate tiles (pi_variant 6): the lanes of a warp whose
+// targets lie in one row of cells (same cell y and z of the same case) walk
+// the union of their candidate ranges together.  Per row of neighbour cells
+// the candidates [lo, hi) of the union are staged 32 at a time in shared
+// memory, one coalesced load per array (position, velocity-density, P/rho),
+// and every lane tests each staged candidate (a broadcast read) against its
+// own target and evaluates the pairs inside 2h.  A candidate lies in one
+// absolute row, visited once per group, so every pair is taken once; the
+// exact cut-off test makes the pair set that of the other walks.
+template <int M>
+__global__ void __launch_bounds__(128)
+k_interact_tile(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
+                const float4 *__restrict__ posc, const float4 *__restrict__ velrho,
+                const float *__restrict__ press, const uint16_t *__restrict__ cid,
+                const uint32_t *__restrict__ cstart, uint32_t cap1, int nbits,
+                const CaseConst *__restrict__ cc, CaseDyn *__restrict__ dyn,
+                float4 *__restrict__ ace, float *__restrict__ mu_out, int want_dt) {
+  __shared__ float4 t_pos[128];
+  __shared__ float4 t_vel[128];
+  __shared__ float t_q[128];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int wb = threadIdx.x & ~31;  // the warp's slice of the tiles
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvalid = *nvalid_p;
+  const bool has = i < nvalid;
+  const int cidx = i < n ? (int)cid[i] : 0;
+  const CaseConst &C = cc[cidx];
+  const uint32_t key = has ? keys[i] : 0u;
+  const bool afluid = has && !key_boundary(key, nbits);
+  const int gc = (int)key_cell(key, nbits);
+  const int nx = C.nx, nxy = C.nx * C.ny;
+  const float cs = C.csf, ics = C.inv_csf, r2max = C.r2max, eta2 = C.eta2, hih = C.half_inv_h;
+  const float r2prune = r2max * 1.0001f;
+  const unsigned r2max_u = __float_as_uint(r2max) - 1u;
+  const float4 pa = has ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 va = has ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+  const float Pa = has ? press[i] * va.w : 0.f;
+  const float kv = C.kvisc * va.w;
+  const bool ddt_on = C.ddt != 0;
+  const bool work = has && (afluid || C.bmode == 0);
+  // the cell of x = 0 in the target's row of cells: the group key
+  const int cx = has ? (gc - (int)C.cellbase) % nx : 0;
+  const int rowkey = work ? gc - cx : -1;
+  Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u};
+  constexpr int W = 2 * M + 1;
+
+  unsigned todo = __ballot_sync(full, work);
+#pragma unroll 1
+  while (todo) {
+    const int key0 = __shfl_sync(full, rowkey, __ffs(todo) - 1);
+    const unsigned gmask = __ballot_sync(full, work && rowkey == key0);
+    todo &= ~gmask;
+    const bool in = (gmask >> lane) & 1u;
+    const bool gfluid = __any_sync(full, in && afluid);
+#pragma unroll 1
+    for (int row = 0; row < W * W; row++) {
+      const int dy = row % W - M, dz = row / W - M;
+      const float gy = slab_gap(dy, pa.y, cs), gz = slab_gap(dz, pa.z, cs);
+      const float d2 = fmaf(gy, gy, gz * gz);
+      const bool reach = in && d2 < r2prune;  // this lane's sphere reaches the row
+      int c0 = INT_MAX, c1 = INT_MIN;
+      if (reach) {
+        const float L = sqrtf(r2prune - d2);
+        const int kx0 = max(-M, (int)floorf((pa.x - L) * ics));
+        const int kx1 = min(M, (int)floorf((pa.x + L) * ics));
+        c0 = gc + dz * nxy + dy * nx + kx0;
+        c1 = gc + dz * nxy + dy * nx + kx1 + 1;
+      }
+      // the group's union of cells in this row (one contiguous range)
+      const int u0 = __reduce_min_sync(full, c0);
+      const int u1 = __reduce_max_sync(full, c1);
+      if (u0 >= u1) continue;
+      const float sy = fmaf(-(float)dy, cs, pa.y), sz = fmaf(-(float)dz, cs, pa.z);
+#pragma unroll 1
+      for (int part = 0; part < 2; part++) {  // fluid neighbours, then boundary ones
+        if (part == 1 && !gfluid) break;
+        const int lo = (int)cstart[part * cap1 + u0];
+        const int hi = (int)cstart[part * cap1 + u1];
+        const bool mine = reach && (part == 0 || afluid);
+        const bool ddt = ddt_on && part == 0;
+#pragma unroll 1
+        for (int base = lo; base < hi; base += 32) {
+          const int j = base + lane;
+          if (j < hi) {
+            t_pos[wb + lane] = posc[j];
+            t_vel[wb + lane] = velrho[j];
+            t_q[wb + lane] = press[j];
+          }
+          __syncwarp();
+          const int nk = min(32, hi - base);
+          if (mine) {
+#pragma unroll 2
+            for (int k = 0; k < nk; k++) {
+              const float4 pb = t_pos[wb + k];
+              const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+              const float ry = sy - pb.y, rz = sz - pb.z;
+              const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+              if (__float_as_uint(r2) - 1u < r2max_u) {
+                const float4 vb = t_vel[wb + k];
+                if (afluid) {
+                  pair_fluid(va, Pa, kv, hih, eta2, rx, ry, rz, r2, vb, t_q[wb + k], ddt, A);
+                  if (part) A.cntb++; else A.cnt++;
+                } else {
+                  pair_boundary(va, hih, rx, ry, rz, r2, vb, A);
+                  A.cnt++;
+                }
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
   finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
 }
 
@@ -1648,8 +1773,13 @@ struct ListArgs {
 };
 
 // One target i of the list walk (all 32 lanes of the warp call it together).
-template <int EXT>
-__device__ __forceinline__ void list_target(const int i, const ListArgs &a) {
+// G lanes share a target (G = 1, 2, 4 or 8; sub = the lane's rank among
+// them): lane sub takes the candidates of each record at the bit positions
+// sub, sub + G, sub + 2G, ..., so the lanes of a target load neighbouring
+// candidates together (fewer L1 wavefronts per gather), and the G partial
+// sums are combined by a butterfly over the G lanes at the end.
+template <int EXT, int G>
+__device__ __forceinline__ void list_target(const int i, const int sub, const ListArgs &a) {
   const unsigned full = 0xffffffffu;
   const int n = a.n;
   const int *__restrict__ nvalid_p = a.nvalid_p;
@@ -1714,10 +1844,13 @@ __device__ __forceinline__ void list_target(const int i, const ListArgs &a) {
   int cbase = 0;
   float sy = 0.f, sz = 0.f;
   // the next record of the lane: base index, candidate mask, row offsets
+  // the lane's bit positions within a record
+  const unsigned sel = (G == 1 ? 0xffffffffu : G == 2 ? 0x55555555u : G == 4 ? 0x11111111u
+                                                                    : 0x01010101u) << sub;
   auto next_record = [&]() {
     const uint2 rec = mine[r++];
     cbase = (int)(rec.x & kListIndexMask);
-    cm = rec.y;
+    cm = rec.y & sel;
     int rdy, rdz;
     list_row_decode(rec.x, rdy, rdz);
     sy = fmaf(-(float)rdy, cs, pa.y);
@@ -1725,7 +1858,13 @@ __device__ __forceinline__ void list_target(const int i, const ListArgs &a) {
   };
 #pragma unroll 1
   for (;;) {
-    if (cm == 0u && r < nrec) next_record();
+    // (a record holds at least one candidate, but with G > 1 maybe none of
+    // this lane's)
+    if (G == 1) {
+      if (cm == 0u && r < nrec) next_record();
+    } else {
+      while (cm == 0u && r < nrec) next_record();
+    }
     if (!__any_sync(full, cm != 0u)) break;
     if (cm) {
       // the lane's next two candidates in list order; the second may open the
@@ -1734,7 +1873,11 @@ __device__ __forceinline__ void list_target(const int i, const ListArgs &a) {
       cm ^= 1u << k1;
       const int j1 = cbase + k1;
       const float sy1 = sy, sz1 = sz;
-      if (cm == 0u && r < nrec) next_record();
+      if (G == 1) {
+        if (cm == 0u && r < nrec) next_record();
+      } else {
+        while (cm == 0u && r < nrec) next_record();
+      }
       const bool h2 = cm != 0u;
       const int k2 = h2 ? 31 - __clz(cm) : k1;
       if (h2) cm ^= 1u << k2;
@@ -1766,14 +1909,30 @@ __device__ __forceinline__ void list_target(const int i, const ListArgs &a) {
       }
     }
   }
-  finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
+  if (G > 1) {
+    // the G lanes' partial sums; every lane of the target ends with the same
+    // totals (each addition is commutative: lanes pair the same operands)
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      A.ax += __shfl_xor_sync(full, A.ax, o);
+      A.ay += __shfl_xor_sync(full, A.ay, o);
+      A.az += __shfl_xor_sync(full, A.az, o);
+      A.s1 += __shfl_xor_sync(full, A.s1, o);
+      A.s2 += __shfl_xor_sync(full, A.s2, o);
+      A.mur = fmaxf(A.mur, __shfl_xor_sync(full, A.mur, o));
+      A.cnt += __shfl_xor_sync(full, A.cnt, o);
+      A.cntb += __shfl_xor_sync(full, A.cntb, o);
+    }
+  }
+  finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn, sub == 0);
 }
 
-// One thread per target, in the key order of the targets.
-template <int EXT>
+// G threads per target, in the key order of the targets.
+template <int EXT, int G>
 __global__ void __launch_bounds__(EXT == 0 ? 1024 : 128, EXT == 2 ? 6 : (EXT == 0 ? 1 : 0))
 k_interact_list(const ListArgs a) {
-  list_target<EXT>(blockIdx.x * blockDim.x + threadIdx.x, a);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  list_target<EXT, G>(t / G, t % G, a);
 }
 
 
@@ -2476,21 +2635,27 @@ void launch_interact(int margin, int variant, int n, const int *nvalid, const ui
     }
 #undef SPH_EXT
   } else if (margin == 1) {
-    if (variant == 2)
+    if (variant == 6)
+      k_interact_tile<1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+    else if (variant == 2)
       k_interact_q<1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else if (variant == 1)
       k_interact<1, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else
       k_interact<1, 0><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
   } else if (margin == 3) {
-    if (variant == 2)
+    if (variant == 6)
+      k_interact_tile<3><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+    else if (variant == 2)
       k_interact_q<3><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else if (variant == 1)
       k_interact<3, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else
       k_interact<3, 0><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
   } else {
-    if (variant == 2)
+    if (variant == 6)
+      k_interact_tile<2><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
+    else if (variant == 2)
       k_interact_q<2><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
     else if (variant == 1)
       k_interact<2, 1><<<nblk(n, b), b, 0, s>>>(SPH_PI_ARGS);
@@ -2547,22 +2712,35 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const uint32_t *cstart, int64_t cap_cells, int nbits,
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
                           const uint2 *list, int cap, const uint16_t *count, bool ext,
-                          float4 *tau4, float2 *tau2, cudaStream_t s, float *mu, int block) {
+                          float4 *tau4, float2 *tau2, cudaStream_t s, float *mu, int block,
+                          int lanes) {
   if (n <= 0) return;
+  if (lanes != 2 && lanes != 4 && lanes != 8) lanes = 1;
   const ListArgs a{n,   nvalid, keys, posc, velrho, press, cid,   cstart, (uint32_t)(cap_cells + 1),
                    nbits, cc,   dyn,  ace,  want_dt, list,  cap,   count,  tau4, tau2, mu};
   if (tau4)  // laminar + SPS cases present: strain pass over the list first
     k_strain_list<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, nbits, cc,
                                                list, cap, count, tau4, tau2);
-  // one thread per target; block size 128 (default) to 1024 for the default
-  // kernel (EXT 1 and 2: 128, by their registers)
+  // G = lanes threads per target; block size 128 (default) to 1024 for the
+  // default kernel (EXT 1 and 2: 128, by their registers)
   const int b0 = block >= 128 && block <= 1024 && block % 32 == 0 ? block : 128;
-  if (tau4)
-    k_interact_list<2><<<nblk(n, 128), 128, 0, s>>>(a);
-  else if (ext)
-    k_interact_list<1><<<nblk(n, 128), 128, 0, s>>>(a);
-  else
-    k_interact_list<0><<<nblk(n, b0), b0, 0, s>>>(a);
+  const int64_t nt = (int64_t)n * lanes;
+  const int g1 = (int)((nt + 127) / 128), g0 = (int)((nt + b0 - 1) / b0);
+#define SPH_LIST(EXT, GRID, BLK)                                                      \
+  switch (lanes) {                                                                  \
+    case 2: k_interact_list<EXT, 2><<<GRID, BLK, 0, s>>>(a); break;                 \
+    case 4: k_interact_list<EXT, 4><<<GRID, BLK, 0, s>>>(a); break;                 \
+    case 8: k_interact_list<EXT, 8><<<GRID, BLK, 0, s>>>(a); break;                 \
+    default: k_interact_list<EXT, 1><<<GRID, BLK, 0, s>>>(a); break;                \
+  }
+  if (tau4) {
+    SPH_LIST(2, g1, 128)
+  } else if (ext) {
+    SPH_LIST(1, g1, 128)
+  } else {
+    SPH_LIST(0, g0, b0)
+  }
+#undef SPH_LIST
 }
 
 void launch_list_begin(int ncases, const CaseConst *cc, CaseDyn *dyn, ListCtl *ctl,

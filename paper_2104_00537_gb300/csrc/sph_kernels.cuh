@@ -94,7 +94,7 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
                           const uint2 *list, int cap, const uint16_t *count, bool ext,
                           float4 *tau4, float2 *tau2, cudaStream_t s, float *mu = nullptr,
-                          int block = 128);
+                          int block = 128, int lanes = 1);
 void launch_predictor_list(int n, const uint32_t *keys_in, State src, const float4 *ace,
                            const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
                            float4 *velrho_out, uint32_t *keys_out, float *press,

@@ -103,6 +103,35 @@ def test_list_evaluation_in_motion(variant):
     eng.destroy()
 
 
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_list_evaluation_lanes_per_target(lanes):
+    """pi_lanes threads per target: thread k takes the candidates at bit
+    positions k, k + lanes, ... of each record (a record may hold none of a
+    thread's) and the partial sums are added at the end.  On the same state
+    the pair set is that of one thread per target (first evaluation from
+    rest); both evaluations after 60 steps against the oracle; the run stays
+    within rounding of the run with one thread per target (its sums are added
+    in another order)."""
+    case = cases.dam_break(0.02)
+    eng = sph.Engine.create(case)
+    one = sph.Engine.create(case)
+    eng.set_options(pi_variant=5, use_graph=1, pi_lanes=lanes)
+    one.set_options(pi_variant=5, use_graph=1, pi_lanes=1)
+    ga, gb = eng.eval_step(0), one.eval_step(0)
+    assert ga["pairs"] == gb["pairs"]
+    assert rel_err(ga["acc"], gb["acc"]) < 1e-5
+    eng.step(60)
+    one.step(60)
+    for stage in (0, 1):
+        check_step_eval(case, eng, stage)
+    sa, sb = eng.get_state(), one.get_state()
+    assert np.abs(sa["pos"] - sb["pos"]).max() < 1e-3 * case.params["dp"]
+    pa, pb = eng.stats()["interactions"], one.stats()["interactions"]
+    assert abs(pa - pb) <= 1e-6 * pb, (pa, pb)
+    eng.destroy()
+    one.destroy()
+
+
 def test_kept_list_evaluation_through_the_splash():
     """The dam break through its collapse and splash (~1,050 steps, t ~ 0.3 s),
     with the list kept across steps and rebuilt as the flow needs: both
@@ -156,16 +185,18 @@ def test_evaluation_does_not_perturb_the_run():
     b.destroy()
 
 
+@pytest.mark.parametrize("lanes", [0, 4])
 @pytest.mark.parametrize("physics", ["fourtakas", "sps", "mdbc"])
-def test_list_evaluation_extended_physics(physics):
+def test_list_evaluation_extended_physics(physics, lanes):
     """The list kernels of the Eq 19-20 diffusion (EXT 1), of laminar + SPS
     viscosity (EXT 2, with its strain pass over the list) and the list walk of
-    an mDBC case (boundary values of Eq 38-39 in the build's cells)."""
+    an mDBC case (boundary values of Eq 38-39 in the build's cells), with the
+    default threads per target and with four."""
     kw = dict(fourtakas=dict(ddt_mode=2), sps=dict(visc_mode=1, nu0=1e-3),
               mdbc=dict(boundary_mode=1))[physics]
     case = cases.dam_break(0.02, **kw)
     eng = sph.Engine.create(case)
-    eng.set_options(pi_variant=5, use_graph=1)
+    eng.set_options(pi_variant=5, use_graph=1, pi_lanes=lanes)
     eng.step(60)
     for stage in (0, 1):
         check_step_eval(case, eng, stage)

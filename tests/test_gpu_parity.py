@@ -134,7 +134,7 @@ def test_pair_sets_are_bit_exact(cell_mode):
 
 # ---- particle interaction ----------------------------------------------------
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 6])
 @pytest.mark.parametrize("cell_mode", [0, 1, 2])
 def test_one_evaluation_at_rest(c0, cell_mode, variant):
     case = cases.dam_break(0.02, cell_mode=cell_mode)
@@ -144,7 +144,7 @@ def test_one_evaluation_at_rest(c0, cell_mode, variant):
     eng.destroy()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 6])
 def test_one_evaluation_in_motion(c0, variant):
     """After 60 steps the column moves: viscosity and DDT terms are active."""
     eng = sph.Engine.create(c0)
@@ -189,7 +189,7 @@ def test_still_tank_hydrostatic_gpu(ddt_mode):
     eng.destroy()
 
 
-@pytest.mark.parametrize("variant", [0, 2])
+@pytest.mark.parametrize("variant", [0, 2, 6])
 def test_one_evaluation_ragged_sizes(variant):
     """Random clouds of awkward sizes (not multiples of any tile)."""
     from tests.lattice import random_cloud
@@ -220,7 +220,7 @@ def c0_100(c0):
     return o
 
 
-@pytest.mark.parametrize("variant", [5, 4, 3, 0])
+@pytest.mark.parametrize("variant", [5, 4, 3, 0, 6])
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_dam_break_100_steps(c0, c0_100, use_graph, variant):
     """Variants 4 (the default here) and 3: one neighbour list per step on
@@ -398,15 +398,19 @@ def test_raw_checkpoint_resume_is_bit_exact(c0):
     assert sa["t"] == sb["t"] and sa["step"] == sb["step"] == 25
 
 
-def test_batch_equals_alone():
+@pytest.mark.parametrize("variant", [4, 6])
+def test_batch_equals_alone(variant):
+    """One list per step (4), and the warp-shared tiles (6: a lane adds its
+    pairs row by row in candidate order, whichever lanes share its tiles):
+    bit for bit."""
     cs = [cases.dam_break(0.04, seed=1), cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
           cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
     bat = sph.Engine.batch(cs)
-    bat.set_options(pi_variant=4)          # one list per step: bit for bit
+    bat.set_options(pi_variant=variant)
     bat.step(12)
     for i, c in enumerate(cs):
         e = sph.Engine.create(c)
-        e.set_options(pi_variant=4)
+        e.set_options(pi_variant=variant)
         e.step(12)
         sa, sb = e.get_state(), bat.get_state(i)
         for k in ("pos", "vel", "rho"):
@@ -559,19 +563,23 @@ def test_list_finds_every_pair_brute_force(variant, use_graph):
         eng.destroy()
 
 
-def test_list_kept_across_steps_in_a_batch():
+@pytest.mark.parametrize("lanes", [0, 1, 4, 8])
+def test_list_kept_across_steps_in_a_batch(lanes):
     """A batch on the kept list (the default): rebuilds are decided per case
     (a case that needs none keeps its order, cells and records through the
     others' rebuilds), so every case takes bit for bit the steps it takes
-    alone; every pair is found."""
+    alone; every pair is found.  With several threads per target the split of
+    a record's candidates follows the bit positions of the record, which start
+    at the row's first particle, so it too is the same alone and in a batch."""
     cs = [cases.dam_break(0.04, seed=1), cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
           cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
     bat = sph.Engine.batch(cs)
-    bat.set_options(check_list=1)
+    bat.set_options(check_list=1, pi_lanes=lanes)
     bat.step(40)
     assert bat.list_info()["check_bad"] == 0
     for i, c in enumerate(cs):
         e = sph.Engine.create(c)
+        e.set_options(pi_lanes=lanes)
         e.step(40)
         a, b = e.get_state(), bat.get_state(i)
         for k in ("pos", "vel", "rho"):
