@@ -359,13 +359,14 @@ def measure_served(requests, rate, max_fluid, t_end, chunk, cell_mode=1, pi_vari
     return out
 
 
-def measure_full_run(case, stream, steps=2000):
+def measure_full_run(case, stream, steps=2000, pair_once=0):
     """The case's whole run from rest (C1's 2,000 steps), graph-replayed with
-    the list kept across steps: the step time at the run's own rebuild rate."""
+    the list kept across steps: the step time at the run's own rebuild rate.
+    pair_once: each pair evaluated once (atomic sums, not bit-reproducible)."""
     import torch
     from paper_2104_00537_gb300 import sph
     e = sph.Engine.create(case, stream=stream)
-    e.set_options(use_graph=1)
+    e.set_options(use_graph=1, pair_once=pair_once)
     torch.cuda.synchronize()
     ms = timed_steps(e, stream, steps)
     s = e.stats()
@@ -428,6 +429,8 @@ def main():
                     help="threads per block of the list walk (0: the engine default)")
     ap.add_argument("--pi-lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="threads per target of the list walk (0: the engine default)")
+    ap.add_argument("--pair-once", type=int, default=0, choices=[0, 1],
+                    help="1: evaluate each pair once (atomic sums, not bit-reproducible)")
     ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "verlet"])
     ap.add_argument("--visc-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--nu0", type=float, default=1e-6)
@@ -478,7 +481,7 @@ def main():
         eng = sph.Engine.batch(cs, stream=stream) if len(cs) > 1 else \
             sph.Engine.create(cs[0], stream=stream)
     eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, pi_block=args.pi_block,
-                    pi_lanes=args.pi_lanes)
+                    pi_lanes=args.pi_lanes, pair_once=args.pair_once)
     n_particles = sum(c.n for c in cs)
     # the pi_variant the engine runs (its default: 5, the list kept across steps)
     list_ok = n_particles < (1 << 25)
@@ -498,7 +501,7 @@ def main():
     # warm-up
     eng.step(args.warmup)
     eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, timing=1,
-                    pi_block=args.pi_block, pi_lanes=args.pi_lanes)
+                    pi_block=args.pi_block, pi_lanes=args.pi_lanes, pair_once=args.pair_once)
     eng.timing(reset=True)
     builds0 = eng.list_info()["builds"]
 
@@ -558,7 +561,8 @@ def main():
     # the committed capture is of the default physics and launch shape
     captured = ((args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) ==
                 (1, "symplectic", 0, 0) and eff_var in (4, 5) and
-                args.pi_block in (0, 128) and args.pi_lanes in (0, 1) and args.list_skin < 0)
+                args.pi_block in (0, 128) and args.pi_lanes in (0, 1) and args.list_skin < 0 and
+                not args.pair_once)
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_basis": "measured in this run: FP32 FMA chains on all %d SMs "
@@ -600,6 +604,7 @@ def main():
                                      "verlet": "Verlet, Eq 30-31, N_S = 40 (1 PI per step)"}[
                           args.integrator],
                       "pi_variant": eff_var,
+                      "pair_once": bool(args.pair_once),
                       "window": "steps %d-%d of the run from rest" % (
                           args.warmup, args.warmup + args.steps),
                       "neighbour_list": (
@@ -626,7 +631,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2 = sph.Engine.create(cs[0], stream=stream, host=hp)
-        e2.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin)
+        e2.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin,
+                       pi_block=args.pi_block, pi_lanes=args.pi_lanes, pair_once=args.pair_once)
         e2.step(args.steps)
         st = [e2.get_state(0, out=outbuf)]
         e2pairs = e2.stats(0)["interactions"]
@@ -647,6 +653,9 @@ def main():
         # the rest of the metric, measured in the same run: the whole 2,000-step
         # run of this case, batched vs plain (C3), served vs plain (C4, scaled)
         out["full_run"] = measure_full_run(cs[0], stream)
+        # the same run with each pair evaluated once (an option: its atomic
+        # sums are not the same bit for bit from run to run)
+        out["full_run_pair_once"] = measure_full_run(cs[0], stream, pair_once=1)
         out["batched"] = measure_batched(256, 500, 3, tune=True, clock_index=local)
         out["batched"]["note"] = ("C3 as configured (256 cases, 26.6M particles, 500 timed "
                                   "steps after 3 from rest); cell size, pair loop and block "

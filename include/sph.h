@@ -179,6 +179,16 @@ typedef struct {
                        * positions k, k + lanes, ... of each chunk record and
                        * the partial sums are added at the end, so the sums'
                        * order (not the pair set) depends on it           */
+  int32_t pair_once;  /* 1: the list walk (pi_variant 3-5) of an engine with
+                       * the default physics (Eq 18 or no diffusion,
+                       * Eq 21 viscosity, DBC) evaluates each pair once:
+                       * the target of lower index takes the pair and adds
+                       * the partner's share (Eq 22's antisymmetric
+                       * momentum term, its continuity term) by atomic
+                       * vector additions, so the sums are not the same
+                       * bit for bit from run to run, alone or in a batch;
+                       * other engines ignore it.  0 (default): every
+                       * target sums its own pairs, deterministically     */
 } sph_options;
 
 /* Last error message of the calling thread ("" if none). */

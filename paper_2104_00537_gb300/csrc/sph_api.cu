@@ -230,7 +230,10 @@ struct sph_engine_t {
   char *io = nullptr;
   size_t io_bytes = 0;
   // options, graph, timing
-  sph_options opt{0, 0, 0, 0, -1.f, 0, 0};  // list_skin < 0: the default
+  sph_options opt{0, 0, 0, 0, -1.f, 0, 0, 0};  // list_skin < 0: the default
+  // pair_once: per-particle sums of the pair-once walk (allocated on first use)
+  float4 *sym_sum = nullptr;
+  unsigned *sym_mu = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_n = -1, graph_dead = -1;  // n_phys and cells_hw of the captured graph
   int graph_ext = 0;  // ext + 2 sps + 4 mdbc + 8 list of the captured graph
@@ -334,6 +337,15 @@ bool use_list(sph_engine e) {
 // pi_variant as the engine runs it: -1 takes the engine's default; list
 // variants fall back to the compacted loop (0) where no list applies (no
 // list allocated, or 3 and 4 with the Verlet scheme).
+// The pair-once list walk applies: asked for, a list walk, default physics.
+// (Variants 4 and 5, whose lists are built alone and can be half lists;
+// not pools, whose physics may change with an admission while records are
+// kept.)
+bool sym_on(sph_engine e) {
+  return e->opt.pair_once && e->sym_sum && use_list(e) && e->opt.pi_variant != 3 && !e->ext &&
+         !e->sps && !e->mdbc && !e->pool;
+}
+
 int resolve_variant(sph_engine e, int v) {
   if (v == -1) v = e->list_ok ? e->list_default : 0;
   if (v >= 3 && v <= 5 && (!e->list_ok || (e->integrator == 1 && v != 5))) v = 0;
@@ -352,7 +364,8 @@ State half_state(const State &y, const State &z) {
 // Key of a captured step graph: everything that changes its launches.
 int graph_key(sph_engine e) {
   return (int)e->ext + 2 * (int)e->sps + 4 * (int)e->mdbc +
-         8 * (use_list(e) ? e->opt.pi_variant - 2 : 0) + 64 * (e->opt.check_list != 0);
+         8 * (use_list(e) ? e->opt.pi_variant - 2 : 0) + 64 * (e->opt.check_list != 0) +
+         128 * (int)sym_on(e);
 }
 
 int allocate(sph_engine e) {
@@ -641,18 +654,20 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                          e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu,
-                         e->opt.pi_block, e->opt.pi_lanes);
+                         e->opt.pi_block, e->opt.pi_lanes,
+                         sym_on(e) ? e->sym_sum : nullptr, e->sym_mu);
   } else if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
     if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
                       s);
     launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                       e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                      e->list_cap, e->ncount, nullptr, nullptr, s);
+                      e->list_cap, e->ncount, nullptr, nullptr, s, sym_on(e));
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                          e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu,
-                         e->opt.pi_block, e->opt.pi_lanes);
+                         e->opt.pi_block, e->opt.pi_lanes,
+                         sym_on(e) ? e->sym_sum : nullptr, e->sym_mu);
   } else {
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
                       s);
@@ -665,7 +680,7 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
   if (ev) cudaEventRecord(ev[1], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_cap, e->ncount, e->ctl, s);
+                      e->list_cap, e->ncount, e->ctl, s, sym_on(e));
 }
 
 // The rest of a list step up to its second evaluation: dt (Eq 35), the half
@@ -686,11 +701,12 @@ void enqueue_list_half(sph_engine e, cudaEvent_t *ev, float *mu) {
   launch_interact_list(nl, e->nvalid, e->keysC, Z.posc, Z.velrho, e->press, Y.cid, e->cstart,
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
                        e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s,
-                       mu, e->opt.pi_block, e->opt.pi_lanes);
+                       mu, e->opt.pi_block, e->opt.pi_lanes,
+                         sym_on(e) ? e->sym_sum : nullptr, e->sym_mu);
   if (ev) cudaEventRecord(ev[3], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysC, Z.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_cap, e->ncount, e->ctl, s);
+                      e->list_cap, e->ncount, e->ctl, s, sym_on(e));
 }
 
 // One Symplectic step with the per-step neighbour list: NL on state n (Y),
@@ -745,7 +761,7 @@ void enqueue_rebuild_list(sph_engine e, float extra, cudaStream_t q) {
                     q);
   launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                     e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                    e->list_cap, e->ncount, e->posc_ref, e->posc_ref2, q);
+                    e->list_cap, e->ncount, e->posc_ref, e->posc_ref2, q, sym_on(e));
 }
 
 // Appends to the graph being captured on e->s a k_decide kernel and an IF
@@ -1018,6 +1034,16 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
   if (opt->pi_lanes != 0 && opt->pi_lanes != 1 && opt->pi_lanes != 2 && opt->pi_lanes != 4 &&
       opt->pi_lanes != 8)
     return fail(SPH_ERR_ARG, "pi_lanes must be 0 (default), 1, 2, 4 or 8");
+  if (opt->pair_once != 0 && opt->pair_once != 1)
+    return fail(SPH_ERR_ARG, "pair_once must be 0 or 1");
+  if (opt->pair_once && !e->sym_sum) {
+    const int64_t N = e->cap_p > 0 ? e->cap_p : 1;
+    e->sym_sum = (float4 *)e->dalloc(16 * N);
+    e->sym_mu = (unsigned *)e->dalloc(4 * N);
+    if (!e->sym_sum || !e->sym_mu) return fail(SPH_ERR_OOM, "device allocation failed");
+    CUDA_TRY(cudaMemsetAsync(e->sym_sum, 0, 16 * N, e->s));
+    CUDA_TRY(cudaMemsetAsync(e->sym_mu, 0, 4 * N, e->s));
+  }
   if (opt->pi_variant < -1 || opt->pi_variant > 6)
     return fail(SPH_ERR_ARG,
                 "pi_variant must be -1 (engine default), 0 (compacted), 1 (inline), 2 (queued), "
@@ -1105,7 +1131,8 @@ int sph_step(sph_engine e, int64_t nsteps) {
                                                : 6 * passes + 2 + 8 + 2 + 4) +
                            (e->sps ? pis : 0) +  // strain pass before each interaction
                            (e->mdbc ? pis : 0) +  // ghost-node pass before each interaction
-                           (listed && e->opt.check_list ? pis : 0);
+                           (listed && e->opt.check_list ? pis : 0) +
+                           (sym_on(e) ? pis : 0);  // the pair-once finish
   e->kernel_launches += per_step * nsteps;
   for (; k < nsteps; k++) {
     enqueue_step(e, timing ? &e->evs[4 * k] : nullptr);

@@ -682,7 +682,9 @@ __global__ void k_need_all(int ncases, CaseDyn *__restrict__ dyn) {
 // the target's position at the build (the list kept across steps), and the
 // case's build mode applies (k_list_begin): 0 keeps the target's records, 1
 // builds from posc, 2 rebuilds from the previous build positions (ref_src,
-// gathered into the new order) with the case's old skin.
+// gathered into the new order) with the case's old skin.  3 is 2 with only
+// the candidates of larger index than the target (the half list of the
+// pair-once walk: a boundary target, after every fluid index, gets none).
 template <int M, int VARIANT, int EXT = 0, int LIST = 0>
 __global__ void __launch_bounds__(128, EXT == 2 ? 6 : 0)
 k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
@@ -718,7 +720,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   const unsigned r2l_u = __float_as_uint(r2l) - 1u;
   const float r2prune = r2l * 1.0001f;  // conservative: pruning never drops a pair
   int lcnt = 0;                          // LIST: records written
-  const int lmode = (LIST == 2 && ref) ? (int)dyn[cidx].lmode : 1;
+  const int lmode = (LIST >= 2 && ref) ? (int)dyn[cidx].lmode : 1;
   const float4 *__restrict__ P = lmode == 2 ? ref_src : posc;  // positions walked
   const float4 pa = has ? P[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float4 va = has ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
@@ -815,11 +817,15 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
               if (LIST && __float_as_uint(r2) - 1u < r2l_u) ml |= 1u << k;
             }
           }
+          if (LIST == 3) {  // half list: only candidates of larger index than the target
+            const int lowk = i - (lo + base) + 1;
+            if (lowk > 0) ml = lowk >= 32 ? 0u : ml & (0xffffffffu << lowk);
+          }
           if (LIST && ml) {
             if (lcnt < cap) list[(int64_t)i * cap + lcnt] = make_uint2((uint32_t)(lo + base) | rowbits, ml);
             lcnt++;
           }
-          if (LIST != 2) {
+          if (LIST < 2) {
           if (part) A.cntb += __popc(m); else A.cnt += __popc(m);
           if (warp_plain) {  // fluid targets, Eq 18 or no diffusion
             while (__any_sync(full, m != 0u)) {
@@ -886,7 +892,7 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
     count[i] = (uint16_t)min(lcnt, cap);
     if (has && lcnt > cap) atomicOr(&dyn[cidx].flags, kFlagListFull);
   }
-  if (LIST == 2) return;
+  if (LIST >= 2) return;
   finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn);
 }
 
@@ -1937,6 +1943,257 @@ k_interact_list(const ListArgs a) {
 
 
 
+// Each pair once (the default physics of Eq 15, 17-18, 21-22 and 36, DBC):
+// the momentum term of a pair is antisymmetric, -m cw F r_ab on a and
+// +m cw F r_ab on b with F = t^3 [(P_a + P_b)/(rho_a rho_b) + kvisc
+// min(v_ab.r_ab, 0)/((r^2 + eta^2)(rho_a + rho_b))], and the continuity
+// terms of a and b share t^3 v_ab.r_ab.  A fluid target walks its records
+// and takes only the candidates of larger index (in the fluid-first key
+// order every boundary particle has a larger index than every fluid one, so
+// boundary targets walk nothing); it adds its own terms in registers and the
+// partner's with one vector atomic add into sum[b] = (sum_c F_bc r_bc,
+// continuity / (m cw)), then its own sums the same way.  The order of the
+// atomic additions varies, so the sums are not reproducible bit for bit.
+// k_sym_finish turns the sums into dv/dt, drho/dt and the Eq 35 terms.
+__global__ void __launch_bounds__(128)
+k_interact_sym(const ListArgs a, float4 *__restrict__ sum, unsigned *__restrict__ mu_bits) {
+  const unsigned full = 0xffffffffu;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = a.n;
+  const int nbits = a.nbits;
+  const float4 *__restrict__ posc = a.posc;
+  const float4 *__restrict__ velrho = a.velrho;
+  const float *__restrict__ press = a.press;
+  const int nvalid = *a.nvalid_p;
+  const uint32_t key = i < nvalid ? a.keys[i] : key_out(nbits);
+  const bool has = key < key_out(nbits);
+  const int cidx = i < n ? (int)a.cid[i] : 0;
+  const CaseConst &C = a.cc[cidx];
+  const bool afluid = has && !key_boundary(key, nbits);
+  const float cs = C.csf, eta2 = C.eta2, hih = C.half_inv_h, kvisc = C.kvisc, kddt = C.kddt;
+  const unsigned r2max_u = __float_as_uint(C.r2max) - 1u;
+  const float4 pa = afluid ? posc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 va = afluid ? velrho[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+  const float Qa = afluid ? press[i] : 0.f;  // P_a / rho_a
+  const float ia = __fdividef(1.f, va.w);
+  const bool ddt_on = C.ddt != 0;
+  const int jb = (int)a.cstart[a.cap1 - 1];  // first boundary particle of the key order
+  const int nrec = afluid ? (int)a.count[i] : 0;
+  const uint2 *__restrict__ mine = a.list + (int64_t)i * a.cap;
+  float fx = 0.f, fy = 0.f, fz = 0.f, cont = 0.f, mur = 0.f;
+  unsigned nff = 0u, nfb = 0u;
+  int r = 0;
+  unsigned cm = 0u;
+  int cbase = 0;
+  float sy = 0.f, sz = 0.f;
+  // the next record of the lane, keeping only candidates of index > i
+  auto next_record = [&]() {
+    const uint2 rec = mine[r++];
+    cbase = (int)(rec.x & kListIndexMask);
+    const int lowk = i - cbase + 1;  // first bit of a larger index
+    cm = lowk <= 0 ? rec.y : (lowk >= 32 ? 0u : rec.y & (0xffffffffu << lowk));
+    int rdy, rdz;
+    list_row_decode(rec.x, rdy, rdz);
+    sy = fmaf(-(float)rdy, cs, pa.y);
+    sz = fmaf(-(float)rdz, cs, pa.z);
+  };
+#pragma unroll 1
+  for (;;) {
+    while (cm == 0u && r < nrec) next_record();
+    if (!__any_sync(full, cm != 0u)) break;
+    if (cm) {
+      const int k1 = 31 - __clz(cm);
+      cm ^= 1u << k1;
+      const int j1 = cbase + k1;
+      const float sy1 = sy, sz1 = sz;
+      while (cm == 0u && r < nrec) next_record();
+      const bool h2 = cm != 0u;
+      const int k2 = h2 ? 31 - __clz(cm) : k1;
+      if (h2) cm ^= 1u << k2;
+      const int j2 = h2 ? cbase + k2 : j1;
+      const float4 pb1 = posc[j1];
+      const float4 pb2 = posc[j2];
+      const float4 vb1 = velrho[j1];
+      const float4 vb2 = velrho[j2];
+      const float q1 = press[j1], q2 = press[j2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const float4 pb = u ? pb2 : pb1;
+        const float4 vb = u ? vb2 : vb1;
+        const int j = u ? j2 : j1;
+        const float rx = fmaf(pa.w - pb.w, cs, pa.x - pb.x);
+        const float ry = (u ? sy : sy1) - pb.y, rz = (u ? sz : sz1) - pb.z;
+        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        if ((u == 0 || h2) && __float_as_uint(r2) - 1u < r2max_u) {
+          const bool bfluid = j < jb;
+          const float rr = r2 * rsqrtf(r2);
+          const float t = fmaf(-hih, rr, 1.f);
+          const float t3 = t * t * t;
+          const float vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
+          const float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
+          const float ib = __fdividef(1.f, vb.w);
+          const float sab = va.w + vb.w;
+          const float ie = __fdividef(1.f, (r2 + eta2) * sab);
+          mur = fmaxf(mur, fabsf(vr * ie * sab));
+          const float pi = fminf(vr, 0.f) * ie;
+          const float F = t3 * fmaf(kvisc, pi, fmaf(Qa, ib, (u ? q2 : q1) * ia));
+          fx = fmaf(F, rx, fx);
+          fy = fmaf(F, ry, fy);
+          fz = fmaf(F, rz, fz);
+          // Eq 17-18 between fluid particles: d = rho_b - rho_a
+          const float d = (ddt_on && bfluid) ? vb.w - va.w : 0.f;
+          cont = fmaf(t3 * ib, fmaf(va.w, vr, -kddt * d), cont);
+          // b: -F r_ab (its r_ba = -r_ab), t^3/rho_a (rho_b v.r + kddt d)
+          const float cb = t3 * ia * fmaf(vb.w, vr, kddt * d);
+          atomicAdd(&sum[j], make_float4(-F * rx, -F * ry, -F * rz, cb));
+          // each particle's own mu_max (an output only when asked for; the
+          // Eq 35 minimum needs only the largest over all pairs)
+          if (a.mu_out) atomicMax(&mu_bits[j], __float_as_uint(fabsf(vr * ie * sab)));
+          if (bfluid) nff++; else nfb++;
+        }
+      }
+    }
+  }
+  if (afluid) {
+    atomicAdd(&sum[i], make_float4(fx, fy, fz, cont));
+    atomicMax(&mu_bits[i], __float_as_uint(mur));
+  }
+  // directed pairs: an unordered fluid pair is two, a fluid-boundary pair is
+  // one of each kind
+  reduce_case(i < n ? cidx : -1, has, 2u * nff + 2u * nfb, nfb, nfb, kFloatInfBits, false,
+              a.dyn);
+}
+
+// dv/dt = g - m cw sum.xyz for fluid particles (0 for boundary ones), drho/dt
+// = m cw sum.w, mu_max = h max|mu| (fluid), the Eq 35 candidate time step and
+// the non-finite flag, per case; clears the sums for the next evaluation.
+// A short, memory-latency-bound kernel: each thread takes kFinishPer
+// particles (a block's range of kFinishPer x kFinishThreads), all their
+// loads issued first; the per-case minimum is merged per warp, then per
+// block, so that one atomic per block of one case reaches the same address
+// (all warps of the kernel end together).
+constexpr int kFinishThreads = 512;
+constexpr int kFinishPer = 4;
+__global__ void __launch_bounds__(kFinishThreads)
+k_sym_finish(const ListArgs a, float4 *__restrict__ sum, unsigned *__restrict__ mu_bits) {
+  __shared__ int s_case[kFinishThreads / 32];
+  __shared__ unsigned s_dt[kFinishThreads / 32];
+  __shared__ unsigned s_bad[kFinishThreads / 32];
+  const unsigned full = 0xffffffffu;
+  const int n = a.n;
+  const int nbits = a.nbits;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)blockIdx.x * (kFinishThreads * kFinishPer) + threadIdx.x;
+  float4 sm[kFinishPer];
+  unsigned mb[kFinishPer];
+  uint32_t key[kFinishPer];
+  int cid[kFinishPer];
+#pragma unroll
+  for (int k = 0; k < kFinishPer; k++) {
+    const int64_t i = base + (int64_t)k * kFinishThreads;
+    sm[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    mb[k] = 0u;
+    key[k] = key_out(nbits);
+    cid[k] = 0;
+    if (i < n) {
+      sm[k] = sum[i];
+      mb[k] = mu_bits[i];
+      key[k] = a.keys[i];
+      cid[k] = (int)a.cid[i];
+    }
+  }
+  const int nvalid = *a.nvalid_p;
+  // lane 0's running per-case minimum of the warp (case -1: none yet)
+  int rc = -1;
+  unsigned rdt = kFloatInfBits, rbad = 0u;
+#pragma unroll
+  for (int k = 0; k < kFinishPer; k++) {
+    const int64_t i = base + (int64_t)k * kFinishThreads;
+    if (i < n) {  // cleared for the next evaluation
+      sum[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      mu_bits[i] = 0u;
+    }
+    const bool has = i < nvalid && key[k] < key_out(nbits);
+    const int cidx = cid[k];
+    unsigned dtbits = kFloatInfBits;
+    bool bad = false;
+    if (has) {
+      const CaseConst &C = a.cc[cidx];
+      const bool afluid = !key_boundary(key[k], nbits);
+      const float mcw = C.m * C.cw;
+      float4 out;
+      float mumax = C.h * __uint_as_float(mb[k]);
+      if (afluid) {
+        out.x = fmaf(-mcw, sm[k].x, C.g[0]);
+        out.y = fmaf(-mcw, sm[k].y, C.g[1]);
+        out.z = fmaf(-mcw, sm[k].z, C.g[2]);
+        out.w = mcw * sm[k].w;
+        const float f = sqrtf(out.x * out.x + out.y * out.y + out.z * out.z);
+        const float dtf = f > 0.f ? sqrtf(C.h / f) : INFINITY;
+        const float dtcv = C.h / (C.cs0f + mumax);
+        bad = !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) && isfinite(out.w));
+        if (a.want_dt) dtbits = __float_as_uint(fminf(dtf, dtcv));
+      } else {
+        out = make_float4(0.f, 0.f, 0.f, mcw * sm[k].w);
+        mumax = 0.f;
+        bad = !isfinite(out.w);
+      }
+      a.ace[i] = out;
+      if (a.mu_out) a.mu_out[i] = mumax;
+    }
+    const int c0 = __shfl_sync(full, has ? cidx : -1, 0);
+    const bool uniform = __all_sync(full, has && cidx == c0);
+    const unsigned m = __reduce_min_sync(full, dtbits);
+    const unsigned anybad = __any_sync(full, bad);
+    if (!uniform) {  // a warp across cases (or the tail): each lane for itself
+      if (has && dtbits < kFloatInfBits) atomicMin(&a.dyn[cidx].dtmin_bits, dtbits);
+      if (has && bad) atomicOr(&a.dyn[cidx].flags, kFlagNaN);
+    } else if (lane == 0) {
+      if (rc != c0 && rc >= 0) {  // another case: flush the running one
+        if (rdt < kFloatInfBits) atomicMin(&a.dyn[rc].dtmin_bits, rdt);
+        if (rbad) atomicOr(&a.dyn[rc].flags, kFlagNaN);
+        rdt = kFloatInfBits;
+        rbad = 0u;
+      }
+      rc = c0;
+      rdt = min(rdt, m);
+      rbad |= anybad;
+    }
+  }
+  if (lane == 0) {
+    s_case[w] = rc;
+    s_dt[w] = rdt;
+    s_bad[w] = rbad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = kFinishThreads / 32;
+    int cb = -1;
+    bool one = true;
+    for (int k = 0; k < nw; k++) {
+      if (s_case[k] < 0) continue;
+      if (cb < 0) cb = s_case[k];
+      else if (s_case[k] != cb) one = false;
+    }
+    if (one && cb >= 0) {  // the block's uniform warps are of one case
+      unsigned m = kFloatInfBits, b = 0u;
+      for (int k = 0; k < nw; k++) {
+        m = min(m, s_dt[k]);
+        b |= s_bad[k];
+      }
+      if (m < kFloatInfBits && m < *(volatile unsigned *)&a.dyn[cb].dtmin_bits)
+        atomicMin(&a.dyn[cb].dtmin_bits, m);
+      if (b) atomicOr(&a.dyn[cb].flags, kFlagNaN);
+    } else {
+      for (int k = 0; k < nw; k++) {
+        if (s_case[k] < 0) continue;
+        if (s_dt[k] < kFloatInfBits) atomicMin(&a.dyn[s_case[k]].dtmin_bits, s_dt[k]);
+        if (s_bad[k]) atomicOr(&a.dyn[s_case[k]].flags, kFlagNaN);
+      }
+    }
+  }
+}
+
 // The strain pass of the laminar + SPS model (as k_strain) over the target's
 // list records, for the half-step state kept in the order and cells of state n.
 __global__ void __launch_bounds__(128)
@@ -2204,7 +2461,8 @@ __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
                              const uint32_t *__restrict__ keys, const float4 *__restrict__ posc,
                              const uint16_t *__restrict__ cid, const CaseConst *__restrict__ cc,
                              int nbits, const uint2 *__restrict__ list, int cap,
-                             const uint16_t *__restrict__ count, ListCtl *__restrict__ ctl) {
+                             const uint16_t *__restrict__ count, ListCtl *__restrict__ ctl,
+                             int half) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
   if (i >= nvalid || i >= n) return;
@@ -2223,6 +2481,7 @@ __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
   for (int j = 0; j < nvalid; j++) {
     const uint32_t kj = keys[j];
     if (cid[j] != cidx || kj >= key_out(nbits) || (!afluid && key_boundary(kj, nbits))) continue;
+    if (half && j <= i) continue;  // a half list holds the larger indices only
     int jx, jy, jz;
     decode_cell(key_cell(kj, nbits) - C.cellbase, C.nx, C.ny, jx, jy, jz);
     const float4 pb = posc[j];
@@ -2713,11 +2972,17 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
                           const uint2 *list, int cap, const uint16_t *count, bool ext,
                           float4 *tau4, float2 *tau2, cudaStream_t s, float *mu, int block,
-                          int lanes) {
+                          int lanes, float4 *sym_sum, unsigned *sym_mu) {
   if (n <= 0) return;
   if (lanes != 2 && lanes != 4 && lanes != 8) lanes = 1;
   const ListArgs a{n,   nvalid, keys, posc, velrho, press, cid,   cstart, (uint32_t)(cap_cells + 1),
                    nbits, cc,   dyn,  ace,  want_dt, list,  cap,   count,  tau4, tau2, mu};
+  if (sym_sum && !ext && !tau4) {  // each pair once, then the per-particle values
+    k_interact_sym<<<nblk(n, 128), 128, 0, s>>>(a, sym_sum, sym_mu);
+    k_sym_finish<<<nblk(n, kFinishThreads * kFinishPer), kFinishThreads, 0, s>>>(a, sym_sum,
+                                                                                 sym_mu);
+    return;
+  }
   if (tau4)  // laminar + SPS cases present: strain pass over the list first
     k_strain_list<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, velrho, cid, nbits, cc,
                                                list, cap, count, tau4, tau2);
@@ -2784,13 +3049,21 @@ void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *key
                        const float4 *posc, const float4 *velrho, const float *press,
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
-                       uint16_t *count, float4 *ref, const float4 *ref_src, cudaStream_t s) {
+                       uint16_t *count, float4 *ref, const float4 *ref_src, cudaStream_t s,
+                       bool half) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_BL_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 0, \
       nullptr, nullptr, list, cap, count, ref, ref_src
-  if (margin == 1)
+  if (half) {
+    if (margin == 1)
+      k_interact<1, 0, 0, 3><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
+    else if (margin == 3)
+      k_interact<3, 0, 0, 3><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
+    else
+      k_interact<2, 0, 0, 3><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
+  } else if (margin == 1)
     k_interact<1, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
   else if (margin == 3)
     k_interact<3, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
@@ -2871,10 +3144,10 @@ void launch_decide(cudaGraphConditionalHandle h, const ListCtl *ctl, cudaStream_
 
 void launch_list_check(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
                        const uint16_t *cid, const CaseConst *cc, int nbits, const uint2 *list,
-                       int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s) {
+                       int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s, bool half) {
   if (n > 0)
     k_list_check<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, cid, cc, nbits, list, cap,
-                                              count, ctl);
+                                              count, ctl, half ? 1 : 0);
 }
 
 void launch_corrector_list(int n, const uint32_t *keys_n, const uint32_t *keys_half, State sn,

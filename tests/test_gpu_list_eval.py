@@ -132,6 +132,52 @@ def test_list_evaluation_lanes_per_target(lanes):
     one.destroy()
 
 
+@pytest.mark.parametrize("variant", [4, 5])
+def test_pair_once_evaluation(variant):
+    """pair_once: each pair evaluated once by the target of lower index over
+    a half list, the partner's share added atomically.  Both evaluations at
+    rest and after 60 steps against the oracle (dv/dt, drho/dt, mu_max per
+    particle, dt, the directed pair count), and the half lists checked by
+    brute force at every evaluation of the 60 steps."""
+    case = cases.dam_break(0.02)
+    eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=variant, use_graph=1, pair_once=1)
+    for stage in (0, 1):
+        check_step_eval(case, eng, stage)
+    # the half lists (candidates of larger index only) hold every such pair
+    eng.set_options(pi_variant=variant, use_graph=1, pair_once=1, check_list=1)
+    eng.step(60)
+    li = eng.list_info()
+    assert li["check_bad"] == 0 and li["check_pairs"] > 0
+    for stage in (0, 1):
+        g = check_step_eval(case, eng, stage)
+        assert np.abs(g["mumax"]).max() > 0
+    eng.destroy()
+
+
+def test_pair_once_through_the_splash_and_in_a_batch():
+    """pair_once over the collapse (600 steps, kept list with rebuilds) and
+    in a batch of three uneven cases (each case's evaluations against the
+    oracle; a case's partner shares never cross into another case)."""
+    case = cases.dam_break(0.02)
+    eng = sph.Engine.create(case)
+    eng.set_options(pi_variant=5, use_graph=1, pair_once=1)
+    eng.step(600)
+    for stage in (0, 1):
+        check_step_eval(case, eng, stage)
+    eng.destroy()
+    cs = [cases.dam_break(0.04, seed=1), cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
+          cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
+    bat = sph.Engine.batch(cs)
+    bat.set_options(use_graph=1, pair_once=1, check_list=1)
+    bat.step(40)
+    assert bat.list_info()["check_bad"] == 0
+    for i, c in enumerate(cs):
+        for stage in (0, 1):
+            check_step_eval(c, bat, stage, icase=i)
+    bat.destroy()
+
+
 def test_kept_list_evaluation_through_the_splash():
     """The dam break through its collapse and splash (~1,050 steps, t ~ 0.3 s),
     with the list kept across steps and rebuilt as the flow needs: both

@@ -398,6 +398,25 @@ def test_raw_checkpoint_resume_is_bit_exact(c0):
     assert sa["t"] == sb["t"] and sa["step"] == sb["step"] == 25
 
 
+def test_pair_once_100_steps(c0, c0_100):
+    """The pair-once list walk over 100 steps against the oracle (same bounds
+    as the deterministic walks)."""
+    eng = sph.Engine.create(c0)
+    eng.set_options(use_graph=1, pair_once=1)
+    eng.step(100)
+    s = eng.stats()
+    st = eng.get_state()
+    o = c0_100
+    od = o.diag()
+    dp = c0.params["dp"]
+    assert abs(s["t"] - o.t.value) < 1e-3 * o.t.value
+    assert abs(s["front"] - od["front"]) < 0.5 * dp
+    assert abs(s["ke"] - od["ke"]) < 0.01 * od["ke"]
+    assert np.abs(st["pos"] - o.pos).max() < 0.5 * dp
+    assert s["n_out"] == 0 and s["flags"] == 0
+    eng.destroy()
+
+
 @pytest.mark.parametrize("variant", [4, 6])
 def test_batch_equals_alone(variant):
     """One list per step (4), and the warp-shared tiles (6: a lane adds its
