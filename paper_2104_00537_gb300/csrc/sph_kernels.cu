@@ -170,7 +170,11 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ perm,
   const int c0 = __shfl_sync(full, cidx, 0);
   if (__all_sync(full, cidx == c0)) {
     const unsigned m = __reduce_max_sync(full, v2);
-    if ((threadIdx.x & 31) == 0 && c0 >= 0 && m) atomicMax(&dyn[c0].v2max_bits, m);
+    // (the maximum only grows: a warp whose value is not above the one it
+    // reads, maybe an older one, leaves it; fewer same-address atomics)
+    if ((threadIdx.x & 31) == 0 && c0 >= 0 && m &&
+        m > *(volatile const unsigned *)&dyn[c0].v2max_bits)
+      atomicMax(&dyn[c0].v2max_bits, m);
   } else if (cidx >= 0 && v2) {
     atomicMax(&dyn[cidx].v2max_bits, v2);
   }
@@ -304,7 +308,9 @@ __global__ void k_rb_scatter(int n, const int *__restrict__ m_p, const uint32_t 
   const int c0 = __shfl_sync(full, cidx, 0);
   if (__all_sync(full, cidx == c0)) {
     const unsigned mx = __reduce_max_sync(full, v2);
-    if ((threadIdx.x & 31) == 0 && c0 >= 0 && mx) atomicMax(&dyn[c0].v2max_bits, mx);
+    if ((threadIdx.x & 31) == 0 && c0 >= 0 && mx &&
+        mx > *(volatile const unsigned *)&dyn[c0].v2max_bits)
+      atomicMax(&dyn[c0].v2max_bits, mx);
   } else if (cidx >= 0 && v2) {
     atomicMax(&dyn[cidx].v2max_bits, v2);
   }
@@ -2284,10 +2290,14 @@ __global__ void k_predictor_list(int n, const uint32_t *__restrict__ keys_in, St
                                  float *__restrict__ press, const float4 *__restrict__ ref) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  // every load of the particle first (independent: one memory latency)
   const uint32_t k = keys_in[i];
   const float4 p = src.posc[i];
   const float4 v = src.velrho[i];
   const int cidx = src.cid[i];
+  const uint8_t code = src.code[i];
+  const float4 a = ace[i];
+  const float4 r = REF ? ref[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   const CaseConst &C = cc[cidx];
   if (k >= key_out(nbits)) {
     posc_out[i] = p;
@@ -2295,15 +2305,13 @@ __global__ void k_predictor_list(int n, const uint32_t *__restrict__ keys_in, St
     keys_out[i] = k;
     return;
   }
-  const uint8_t code = src.code[i];
   const CaseDyn &D = dyn[cidx];
   double disp[3];
   float4 vn;
-  predictor_core(C, D, code, v, ace[i], disp, vn);
+  predictor_core(C, D, code, v, a, disp, vn);
   const float hs = 0.5f * D.skin;
   float dx = (float)disp[0], dy = (float)disp[1], dz = (float)disp[2];
   if (REF) {
-    const float4 r = ref[i];
     dx = (float)((double)p.x + disp[0]) - r.x;
     dy = (float)((double)p.y + disp[1]) - r.y;
     dz = (float)((double)p.z + disp[2]) - r.z;
@@ -2387,11 +2395,16 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
                                   float *__restrict__ press, ListCtl *__restrict__ ctl) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  // every load of the particle first (independent: one memory latency)
   const uint32_t k = keys_n[i];
   const float4 pn = y.posc[i];
   const float4 vn = y.velrho[i];
   const int cidx = y.cid[i];
   const uint8_t code = y.code[i];
+  const uint32_t kh = keys_half[i];
+  const float rho_half = velrho_half[i].w;
+  const float4 a = ace[i];
+  const float4 r = ref[i];
   x.id[i] = y.id[i];
   x.cid[i] = (uint16_t)cidx;
   x.code[i] = code;
@@ -2403,7 +2416,7 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
     keys_next[i] = k;
     return;
   }
-  if (keys_half[i] >= key_out(nbits)) {  // left at the half step: frozen at state n
+  if (kh >= key_out(nbits)) {  // left at the half step: frozen at state n
     int cx, cy, cz;
     decode_cell(key_cell(k, nbits) - C.cellbase, C.nx, C.ny, cx, cy, cz);
     x.posc[i] = make_float4((float)(cx * C.cs + pn.x), (float)(cy * C.cs + pn.y),
@@ -2418,7 +2431,7 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
   const CaseDyn &D = dyn[cidx];
   float4 pnew, vnew;
   double disp[3];
-  const uint32_t kn = corrector_core(C, D, code, k, pn, vn, velrho_half[i].w, ace[i], nbits,
+  const uint32_t kn = corrector_core(C, D, code, k, pn, vn, rho_half, a, nbits,
                                      cidx, dyn, pnew, vnew, disp);
   x.posc[i] = pnew;
   x.velrho[i] = vnew;
@@ -2434,7 +2447,6 @@ __global__ void k_corrector_reuse(int n, const uint32_t *__restrict__ keys_n,
   y.posc[i] = pu;
   y.velrho[i] = vnew;
   press[i] = tait_pressure(C, vnew.w) / vnew.w;
-  const float4 r = ref[i];
   const float dx = pu.x - r.x, dy = pu.y - r.y, dz = pu.z - r.z;
   const float v = sqrtf(fmaf(vnew.x, vnew.x, fmaf(vnew.y, vnew.y, vnew.z * vnew.z)));
   const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + 0.5f * C.list_k * v;
@@ -2796,17 +2808,27 @@ __global__ void k_diag_partial(int n, const uint32_t *__restrict__ keys, State s
   if (threadIdx.x < 8) part[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void k_diag_final(int nparts, const double *__restrict__ part, double *__restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double v[8] = {0, 0, 0, 0, 0, 0, -1e300, 0};
-  for (int b = 0; b < nparts; b++)
-    for (int q = 0; q < 8; q++) {
-      if (q == 6)
-        v[q] = fmax(v[q], part[b * 8 + q]);
-      else
-        v[q] += part[b * 8 + q];
+// The blocks' partial sums combined by 256 threads (32 per quantity), in a
+// fixed order, so the result does not depend on timing.
+__global__ void __launch_bounds__(256)
+k_diag_final(int nparts, const double *__restrict__ part, double *__restrict__ out) {
+  __shared__ double sh[256];
+  const int q = threadIdx.x & 7, g = threadIdx.x >> 3;  // quantity, group of 32
+  double v = q == 6 ? -1e300 : 0.0;
+  for (int b = g; b < nparts; b += 32) {
+    const double x = part[b * 8 + q];
+    v = q == 6 ? fmax(v, x) : v + x;
+  }
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int st = 16; st > 0; st >>= 1) {
+    if (g < st) {
+      const double x = sh[(g + st) * 8 + q];
+      sh[g * 8 + q] = q == 6 ? fmax(sh[g * 8 + q], x) : sh[g * 8 + q] + x;
     }
-  for (int q = 0; q < 8; q++) out[q] = v[q];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) out[threadIdx.x] = sh[threadIdx.x];
 }
 
 // Release: particles of a slot get the dead key and leave at the next sort.
@@ -3258,7 +3280,7 @@ void launch_pair_stats(int n, const int *nvalid, const uint32_t *keys, State st,
 void launch_diag(int n, const uint32_t *keys, State st, const CaseConst *cc, int slot,
                  int nbits, double *part, int nparts, double *out, cudaStream_t s) {
   k_diag_partial<<<nparts, 256, 0, s>>>(n, keys, st, cc, slot, nbits, part);
-  k_diag_final<<<1, 32, 0, s>>>(nparts, part, out);
+  k_diag_final<<<1, 256, 0, s>>>(nparts, part, out);
 }
 
 void launch_release(int n, const uint16_t *cid, int slot, int nbits, uint32_t *keys,
