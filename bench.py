@@ -268,7 +268,7 @@ def timed_steps(eng, stream, steps):
     return ev0.elapsed_time(ev1)
 
 
-def measure_batched(ncases, steps, warmup, tune, clock_index=0):
+def measure_batched(ncases, steps, warmup, tune, clock_index=0, pair_once=0, fixed=None):
     """C3: `ncases` uneven dam breaks in one batched engine (one launch per
     stage for all cases, CUDA-graph replay) against the plain path that steps
     each case alone in its own engine (the list kept across steps, each step
@@ -276,19 +276,23 @@ def measure_batched(ncases, steps, warmup, tune, clock_index=0):
     time the same steps (warmup .. warmup + steps of every case from rest)
     with CUDA events on the engines' stream.  tune: pick cell size and
     interaction variant and list-walk block size with the autotuner (else
-    cells of h, kept list, 128 threads)."""
+    cells of h, kept list, 128 threads).  pair_once: both paths evaluate each
+    pair once (atomic sums: the two paths then agree to rounding, not bit for
+    bit, and their pair counts may differ by the pairs at the cut-off)."""
     import torch
     from paper_2104_00537_gb300 import autotune, cases, sph
     stream = torch.cuda.Stream()
     cs = cases.batch_dam_breaks(ncases, seed=0)
     cm, var, block, tune_ms = 1, 5, 128, None
-    if tune:
+    if fixed:  # (cell_mode, pi_variant, pi_block) of an earlier tuning
+        cm, var, block = fixed
+    elif tune:
         mk = lambda cc: sph.Engine.batch(cc, stream=stream)
         (cm, var, block), tune_ms = autotune.tune(cs, mk, torch.cuda.get_device_name(0))
     for c in cs:
         c.params["cell_mode"] = cm
     eng = sph.Engine.batch(cs, stream=stream)
-    eng.set_options(pi_variant=var, pi_block=block, use_graph=1)
+    eng.set_options(pi_variant=var, pi_block=block, use_graph=1, pair_once=pair_once)
     eng.step(warmup)
     p0 = sum(eng.stats(i)["interactions"] for i in range(len(cs)))
     clocks = ClockSampler(clock_index)
@@ -299,7 +303,7 @@ def measure_batched(ncases, steps, warmup, tune, clock_index=0):
     ms_p, pp = 0.0, 0
     for c in cs:
         e = sph.Engine.create(c, stream=stream)
-        e.set_options(pi_variant=var, pi_block=block, use_graph=1)
+        e.set_options(pi_variant=var, pi_block=block, use_graph=1, pair_once=pair_once)
         e.step(warmup)
         q0 = e.stats()["interactions"]
         ms_p += timed_steps(e, stream, steps)
@@ -308,6 +312,7 @@ def measure_batched(ncases, steps, warmup, tune, clock_index=0):
     nb = len(cs) * steps
     return {"cases": len(cs), "particles": sum(c.n for c in cs), "steps": steps,
             "warmup": warmup, "cell_mode": cm, "pi_variant": var, "pi_block": block,
+            "pair_once": bool(pair_once),
             "batched": {"case_steps_per_s": nb / (ms_b / 1e3), "ms_per_step": ms_b / steps,
                         "interactions_per_s": (p1 - p0) / (ms_b / 1e3)},
             "plain": {"case_steps_per_s": nb / (ms_p / 1e3), "ms_per_round": ms_p / steps,
@@ -317,10 +322,11 @@ def measure_batched(ncases, steps, warmup, tune, clock_index=0):
 
 
 def measure_served(requests, rate, max_fluid, t_end, chunk, cell_mode=1, pi_variant=-1,
-                   list_skin=-1.0, plain=True, max_particles=None):
+                   list_skin=-1.0, plain=True, max_particles=None, pair_once=0):
     """C4: Poisson arrivals of sloshing-tank requests served by continuous
     batching on one pool engine (64 slots), against the same trace served one
-    request at a time (a one-slot pool); wall-clock time-to-result."""
+    request at a time (a one-slot pool); wall-clock time-to-result.
+    pair_once: both evaluate each pair once."""
     import torch
     from paper_2104_00537_gb300 import cases, serve, sph
     stream = torch.cuda.Stream()
@@ -335,7 +341,8 @@ def measure_served(requests, rate, max_fluid, t_end, chunk, cell_mode=1, pi_vari
     results = {}
     for name, slots in (("served", 64), ("plain", 1)) if plain else (("served", 64),):
         pool = sph.Engine.pool(max_p, max_cells, slots, stream=stream)
-        pool.set_options(use_graph=1, pi_variant=pi_variant, list_skin=list_skin)
+        pool.set_options(use_graph=1, pi_variant=pi_variant, list_skin=list_skin,
+                         pair_once=pair_once)
         reqs = [serve.Request(i, a, c, te) for i, (a, c, te) in enumerate(trace)]
         srv = serve.Server(pool, chunk=chunk)
         torch.cuda.synchronize()
@@ -380,7 +387,8 @@ def measure_full_run(case, stream, steps=2000, pair_once=0):
 def run_batched(args):
     import torch
     torch.cuda.set_device(0)
-    r = measure_batched(args.ncases, args.steps, args.warmup, tune=True)
+    r = measure_batched(args.ncases, args.steps, args.warmup, tune=True,
+                        pair_once=args.pair_once)
     nb = r["cases"] * args.steps
     out = {"metric": "case_steps_per_s", "value": r["batched"]["case_steps_per_s"],
            "unit": "case-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -388,7 +396,8 @@ def run_batched(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "%d dam breaks, fluid 5k-200k log-uniform" % r["cases"],
                       "particles": r["particles"], "cell_mode": r["cell_mode"],
-                      "pi_variant": r["pi_variant"], "pi_block": r["pi_block"]},
+                      "pi_variant": r["pi_variant"], "pi_block": r["pi_block"],
+                      "pair_once": r["pair_once"]},
            "batched": r["batched"], "plain": r["plain"],
            "speedup_vs_plain": r["speedup_vs_plain"],
            "autotune_ms_per_step": r["autotune_ms_per_step"], "clocks": r["clocks"]}
@@ -400,7 +409,8 @@ def run_served(args):
     import torch
     torch.cuda.set_device(0)
     r = measure_served(args.requests, args.rate, args.max_fluid, args.t_end, args.chunk,
-                       args.cell_mode, args.pi_variant, args.list_skin)
+                       args.cell_mode, args.pi_variant, args.list_skin,
+                       pair_once=args.pair_once)
     out = {"metric": "served_p50_time_to_result_s", "value": r["served"]["p50_s"],
            "unit": "s", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -662,10 +672,19 @@ def main():
                                   "size from the autotuner (3 timed steps per candidate), the "
                                   "same for both paths; each path's state equals the other's "
                                   "(same pairs)")
+        # the same comparison with each pair evaluated once on both paths
+        b = out["batched"]
+        out["batched_pair_once"] = measure_batched(
+            256, 500, 3, tune=False, clock_index=local, pair_once=1,
+            fixed=(b["cell_mode"], b["pi_variant"], b["pi_block"]))
+        out["batched_pair_once"]["note"] = ("as batched, both paths with pair_once (the "
+                                            "autotuned configuration above)")
         out["served"] = measure_served(48, 20.0, 200000, 0.1, 10)
         out["served"]["note"] = ("C4 scaled to fit the run: 48 requests, fluid <= 200k, "
                                  "0.1 s simulated (C4: 100+ requests, <= 2M, 1 s; run with "
                                  "--workload served)")
+        out["served_pair_once"] = measure_served(48, 20.0, 200000, 0.1, 10, pair_once=1)
+        out["served_pair_once"]["note"] = "as served, pools of both modes with pair_once"
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(cs[0])
     if rank == 0:

@@ -186,9 +186,11 @@ typedef struct {
                        * the partner's share (Eq 22's antisymmetric
                        * momentum term, its continuity term) by atomic
                        * vector additions, so the sums are not the same
-                       * bit for bit from run to run, alone or in a batch;
-                       * other engines ignore it.  0 (default): every
-                       * target sums its own pairs, deterministically     */
+                       * bit for bit from run to run, alone, in a batch or
+                       * in a pool; other engines (and a pool once it has
+                       * admitted a case with other physics) evaluate as
+                       * with 0.  0 (default): every target sums its own
+                       * pairs, deterministically                         */
 } sph_options;
 
 /* Last error message of the calling thread ("" if none). */

@@ -338,12 +338,11 @@ bool use_list(sph_engine e) {
 // variants fall back to the compacted loop (0) where no list applies (no
 // list allocated, or 3 and 4 with the Verlet scheme).
 // The pair-once list walk applies: asked for, a list walk, default physics.
-// (Variants 4 and 5, whose lists are built alone and can be half lists;
-// not pools, whose physics may change with an admission while records are
-// kept.)
+// (Variants 4 and 5, whose lists are built alone and can be half lists.  A
+// pool's admission that turns it off makes every case build whole lists.)
 bool sym_on(sph_engine e) {
   return e->opt.pair_once && e->sym_sum && use_list(e) && e->opt.pi_variant != 3 && !e->ext &&
-         !e->sps && !e->mdbc && !e->pool;
+         !e->sps && !e->mdbc;
 }
 
 int resolve_variant(sph_engine e, int v) {
@@ -1767,12 +1766,15 @@ int sph_pool_admit(sph_engine e, const sph_case_params *params, const sph_partic
   if (params->integrator != 0)
     return fail(SPH_ERR_ARG, "pools run the Symplectic scheme (integrator 0)");
   // (the pool's tau buffers exist from creation; the flags only grow)
+  const bool sym0 = sym_on(e);
   e->ext = e->ext || params->ddt_mode == 2 || params->visc_mode == 1;
   e->sps = e->sps || params->visc_mode == 1;
   e->mdbc = e->mdbc || params->boundary_mode == 1;
   if (e->list_ok && list_records_needed(params->cell_mode, params->h, params->dp) > e->list_cap)
     e->list_ok = false;  // from now on the pool runs two neighbour lists per step
   e->opt.pi_variant = resolve_variant(e, e->opt.pi_variant);
+  // the half lists of the pair-once walk no longer serve: every case rebuilds
+  if (sym0 && !sym_on(e)) e->list_stale = true;
   if (used == 0) e->margin = g.margin;
   if (g.margin != e->margin) return fail(SPH_ERR_ARG, "cell_mode differs from the pool's cases");
   int free_slot = -1;

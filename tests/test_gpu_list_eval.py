@@ -231,29 +231,32 @@ def test_evaluation_does_not_perturb_the_run():
     b.destroy()
 
 
-@pytest.mark.parametrize("lanes", [0, 4])
+@pytest.mark.parametrize("lanes,pair_once", [(0, 0), (4, 0), (0, 1)])
 @pytest.mark.parametrize("physics", ["fourtakas", "sps", "mdbc"])
-def test_list_evaluation_extended_physics(physics, lanes):
+def test_list_evaluation_extended_physics(physics, lanes, pair_once):
     """The list kernels of the Eq 19-20 diffusion (EXT 1), of laminar + SPS
     viscosity (EXT 2, with its strain pass over the list) and the list walk of
     an mDBC case (boundary values of Eq 38-39 in the build's cells), with the
-    default threads per target and with four."""
+    default threads per target, with four, and with pair_once asked for (which
+    these physics ignore: their lists stay whole)."""
     kw = dict(fourtakas=dict(ddt_mode=2), sps=dict(visc_mode=1, nu0=1e-3),
               mdbc=dict(boundary_mode=1))[physics]
     case = cases.dam_break(0.02, **kw)
     eng = sph.Engine.create(case)
-    eng.set_options(pi_variant=5, use_graph=1, pi_lanes=lanes)
+    eng.set_options(pi_variant=5, use_graph=1, pi_lanes=lanes, pair_once=pair_once)
     eng.step(60)
     for stage in (0, 1):
         check_step_eval(case, eng, stage)
     eng.destroy()
 
 
-def test_verlet_list_evaluation():
-    """The Verlet scheme's one evaluation per step (Eq 30-31) over the kept list."""
+@pytest.mark.parametrize("pair_once", [0, 1])
+def test_verlet_list_evaluation(pair_once):
+    """The Verlet scheme's one evaluation per step (Eq 30-31) over the kept
+    list, with each target's own pairs and with each pair once."""
     case = cases.dam_break(0.02, integrator=1)
     eng = sph.Engine.create(case)
-    eng.set_options(pi_variant=5, use_graph=1)
+    eng.set_options(pi_variant=5, use_graph=1, pair_once=pair_once)
     eng.step(60)
     check_step_eval(case, eng, 0)
     with pytest.raises(sph.SphError):

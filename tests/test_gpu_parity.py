@@ -700,6 +700,37 @@ def test_pool_on_kept_list_matches_alone():
     pool.destroy()
 
 
+def test_pool_pair_once_and_an_admission_that_turns_it_off():
+    """A pool with pair_once: half lists while its cases have the default
+    physics (every pair found, each case within rounding of its run alone);
+    admitting a case with the Eq 19-20 diffusion turns the pair-once walk off,
+    and every case then rebuilds whole lists (every pair found again), with
+    the new case against its own run alone."""
+    ca = cases.dam_break(0.04, seed=5)
+    cb = cases.sloshing_tank(2500, 0.3, 0.03, 1.1, seed=6)
+    cc = cases.dam_break(0.04, seed=7, ddt_mode=2)
+    pool = sph.Engine.pool(300000, 3000000, 8)
+    pool.set_options(use_graph=1, check_list=1, pair_once=1)
+    sa = pool.admit(ca, t_end=1.0)
+    pool.pool_step(5)
+    sb = pool.admit(cb, t_end=1.0)
+    pool.pool_step(25)
+    assert pool.list_info()["check_bad"] == 0
+    sc = pool.admit(cc, t_end=1.0)
+    pool.pool_step(20)
+    li = pool.list_info()
+    assert li["check_bad"] == 0 and li["check_pairs"] > 0
+    for slot, c, n in ((sa, ca, 50), (sb, cb, 45), (sc, cc, 20)):
+        e = sph.Engine.create(c)
+        e.step(n)
+        a, b = pool.get_state(slot), e.get_state()
+        assert a["step"] == b["step"] == n
+        assert np.abs(a["pos"] - b["pos"]).max() < 0.05 * c.params["dp"], slot
+        assert abs(a["t"] - b["t"]) < 1e-3 * b["t"]
+        e.destroy()
+    pool.destroy()
+
+
 def test_pool_emptied_and_refilled_on_kept_list():
     """A pool whose only case leaves and whose next case arrives afterwards:
     the new case steps as it does alone, bit for bit."""
