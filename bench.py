@@ -493,8 +493,10 @@ def main():
     eng.set_options(pi_variant=args.pi_variant, list_skin=args.list_skin, pi_block=args.pi_block,
                     pi_lanes=args.pi_lanes, pair_once=args.pair_once)
     n_particles = sum(c.n for c in cs)
-    # the pi_variant the engine runs (its default: 5, the list kept across steps)
-    list_ok = n_particles < (1 << 25)
+    # the pi_variant the engine runs (its default: 5, the list kept across
+    # steps; beyond 2^25 particles with wide records, for the default physics)
+    default_physics = (args.ddt_mode != 2 and args.visc_mode == 0 and args.boundary_mode == 0)
+    list_ok = n_particles < (1 << 25) or default_physics
     default_var = 5
     eff_var = args.pi_variant if args.pi_variant in (0, 1, 2, 3, 4, 5, 6) else (
         default_var if list_ok else 0)
@@ -504,6 +506,9 @@ def main():
         eff_var = 0
     kernel = {3: "k_interact_list", 4: "k_interact_list", 5: "k_interact_list",
               6: "k_interact_tile"}.get(eff_var, "k_interact")
+    pair_once_on = bool(args.pair_once) and eff_var in (4, 5) and default_physics
+    if pair_once_on:
+        kernel = "k_interact_sym + k_sym_finish"
 
     # the FP32 / FP64 pipe throughput of this GPU (roofline denominators),
     # measured before the warm-up
@@ -575,6 +580,11 @@ def main():
                 not args.pair_once)
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
+                "flop_basis": "48 / 45 / 25 FLOP per directed fluid-fluid / fluid-boundary / "
+                              "boundary-fluid pair" + (
+                                  " (the work of the per-target walk; the pair-once walk "
+                                  "itself does about 56 FLOP per unordered pair)"
+                                  if pair_once_on else ""),
                 "peak_basis": "measured in this run: FP32 FMA chains on all %d SMs "
                               "(sph_probe_peaks, best of 3, CUDA events)" % peaks["sms"],
                 "peak_nominal": nominal, "frac_nominal": achieved / nominal,
@@ -619,6 +629,8 @@ def main():
                           args.warmup, args.warmup + args.steps),
                       "neighbour_list": (
                           {"builds_per_step": builds / args.steps,
+                           "records": "wide (32-bit index)" if n_particles >= (1 << 25)
+                           else "narrow (25-bit index + row code)",
                            "skin": "list_k |v|max + 1e-3 h + %g x 2h" % (
                                args.list_skin if args.list_skin >= 0 else 0.04)}
                           if eff_var == 5 else

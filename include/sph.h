@@ -191,6 +191,14 @@ typedef struct {
                        * admitted a case with other physics) evaluate as
                        * with 0.  0 (default): every target sums its own
                        * pairs, deterministically                         */
+  int32_t wide_records; /* 1: neighbour-list records with a 32-bit first
+                       * index and no row code (the walk takes a record's
+                       * row from its first candidate's cell) at any size;
+                       * 0: only where the engine needs them, beyond 2^25
+                       * particles.  The default physics only (Eq 18 or no
+                       * diffusion, Eq 21 viscosity, DBC); the pair set and
+                       * the order of the sums are those of the narrow
+                       * records, so results are the same bit for bit    */
 } sph_options;
 
 /* Last error message of the calling thread ("" if none). */

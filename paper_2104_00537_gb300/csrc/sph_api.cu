@@ -185,6 +185,8 @@ struct sph_engine_t {
   bool mdbc = false;   // a case uses the modified dynamic boundary condition
   // neighbour list (pi_variant 3-5): list_cap chunk records per target
   bool list_ok = false;
+  bool list_wide = false;  // wide records: beyond 2^25 particles (default physics only)
+  bool list_wide_needed = false;  // (then always; else as sph_options.wide_records)
   int list_cap = 0;
   int64_t list_ld = 0;
   uint2 *nlist = nullptr;
@@ -230,7 +232,7 @@ struct sph_engine_t {
   char *io = nullptr;
   size_t io_bytes = 0;
   // options, graph, timing
-  sph_options opt{0, 0, 0, 0, -1.f, 0, 0, 0};  // list_skin < 0: the default
+  sph_options opt{0, 0, 0, 0, -1.f, 0, 0, 0, 0};  // list_skin < 0: the default
   // pair_once: per-particle sums of the pair-once walk (allocated on first use)
   float4 *sym_sum = nullptr;
   unsigned *sym_mu = nullptr;
@@ -347,6 +349,7 @@ bool sym_on(sph_engine e) {
 
 int resolve_variant(sph_engine e, int v) {
   if (v == -1) v = e->list_ok ? e->list_default : 0;
+  if (v == 3 && e->list_wide) v = 4;  // variant 3's records are narrow
   if (v >= 3 && v <= 5 && (!e->list_ok || (e->integrator == 1 && v != 5))) v = 0;
   return v;
 }
@@ -564,8 +567,13 @@ int create_engine(const sph_case_params *params, const sph_particles *parts, int
     e->mdbc = e->mdbc || params[c].boundary_mode == 1;
   }
   // the neighbour list serves every physics option (the Verlet scheme only
-  // with the list kept across steps)
+  // with the list kept across steps); beyond 2^25 particles its records are
+  // wide (the default physics only: the other walks keep the narrow form)
   e->list_ok = np < kListMaxParticles;
+  if (!e->list_ok && !e->ext && !e->sps && !e->mdbc && np < ((int64_t)1 << 31)) {
+    e->list_ok = true;
+    e->list_wide = e->list_wide_needed = true;
+  }
   if (e->list_ok) {
     int cap = 32;
     for (int c = 0; c < ncases; c++)
@@ -654,19 +662,21 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                          e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu,
                          e->opt.pi_block, e->opt.pi_lanes,
-                         sym_on(e) ? e->sym_sum : nullptr, e->sym_mu);
+                         sym_on(e) ? e->sym_sum : nullptr, e->sym_mu,
+                         e->list_wide ? e->keysB : nullptr);
   } else if (e->opt.pi_variant == 4) {  // list alone, then both evaluations over it
     if (ev) cudaEventRecord(ev[0], s);  // the first evaluation's time includes the list
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
                       s);
     launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                       e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                      e->list_cap, e->ncount, nullptr, nullptr, s, sym_on(e));
+                      e->list_cap, e->ncount, nullptr, nullptr, s, sym_on(e), e->list_wide);
     launch_interact_list(nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid, e->cstart,
                          e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 1, e->nlist,
                          e->list_cap, e->ncount, e->ext, tau4, e->tau2, s, mu,
                          e->opt.pi_block, e->opt.pi_lanes,
-                         sym_on(e) ? e->sym_sum : nullptr, e->sym_mu);
+                         sym_on(e) ? e->sym_sum : nullptr, e->sym_mu,
+                         e->list_wide ? e->keysB : nullptr);
   } else {
     launch_list_begin(e->cap_cases, e->dconst, e->ddyn, e->ctl, 0.f, 1, e->cstart, e->cells_hw,
                       s);
@@ -679,7 +689,8 @@ void enqueue_list_first(sph_engine e, cudaEvent_t *ev, float *mu) {
   if (ev) cudaEventRecord(ev[1], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysB, Y.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_cap, e->ncount, e->ctl, s, sym_on(e));
+                      e->list_cap, e->ncount, e->ctl, s, sym_on(e),
+                      e->list_wide ? e->keysB : nullptr);
 }
 
 // The rest of a list step up to its second evaluation: dt (Eq 35), the half
@@ -701,11 +712,13 @@ void enqueue_list_half(sph_engine e, cudaEvent_t *ev, float *mu) {
                        e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, 0, e->nlist,
                        e->list_cap, e->ncount, e->ext, e->sps ? e->tau4 : nullptr, e->tau2, s,
                        mu, e->opt.pi_block, e->opt.pi_lanes,
-                         sym_on(e) ? e->sym_sum : nullptr, e->sym_mu);
+                         sym_on(e) ? e->sym_sum : nullptr, e->sym_mu,
+                         e->list_wide ? e->keysB : nullptr);
   if (ev) cudaEventRecord(ev[3], s);
   if (e->opt.check_list)
     launch_list_check(nl, e->nvalid, e->keysC, Z.posc, Y.cid, e->dconst, e->nbits, e->nlist,
-                      e->list_cap, e->ncount, e->ctl, s, sym_on(e));
+                      e->list_cap, e->ncount, e->ctl, s, sym_on(e),
+                      e->list_wide ? e->keysB : nullptr);
 }
 
 // One Symplectic step with the per-step neighbour list: NL on state n (Y),
@@ -760,7 +773,8 @@ void enqueue_rebuild_list(sph_engine e, float extra, cudaStream_t q) {
                     q);
   launch_build_list(e->margin, nl, e->nvalid, e->keysB, Y.posc, Y.velrho, e->press, Y.cid,
                     e->cstart, e->cells_hw, e->nbits, e->dconst, e->ddyn, e->ace, e->nlist,
-                    e->list_cap, e->ncount, e->posc_ref, e->posc_ref2, q, sym_on(e));
+                    e->list_cap, e->ncount, e->posc_ref, e->posc_ref2, q, sym_on(e),
+                    e->list_wide);
 }
 
 // Appends to the graph being captured on e->s a k_decide kernel and an IF
@@ -1035,6 +1049,8 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
     return fail(SPH_ERR_ARG, "pi_lanes must be 0 (default), 1, 2, 4 or 8");
   if (opt->pair_once != 0 && opt->pair_once != 1)
     return fail(SPH_ERR_ARG, "pair_once must be 0 or 1");
+  if (opt->wide_records != 0 && opt->wide_records != 1)
+    return fail(SPH_ERR_ARG, "wide_records must be 0 or 1");
   if (opt->pair_once && !e->sym_sum) {
     const int64_t N = e->cap_p > 0 ? e->cap_p : 1;
     e->sym_sum = (float4 *)e->dalloc(16 * N);
@@ -1051,6 +1067,9 @@ int sph_set_options(sph_engine e, const sph_options *opt) {
   if (opt->list_skin > (float)kListExtraMax)
     return fail(SPH_ERR_ARG, "list_skin must be at most 0.25 (or < 0 for the default)");
   e->opt = *opt;
+  // wide records where needed, or where asked for and the physics allows them
+  e->list_wide = e->list_wide_needed ||
+                 (opt->wide_records && e->list_ok && !e->ext && !e->sps && !e->mdbc && !e->pool);
   e->opt.pi_variant = resolve_variant(e, opt->pi_variant);
   e->list_stale = true;  // another pair loop may have run in between
   e->drop_graphs();

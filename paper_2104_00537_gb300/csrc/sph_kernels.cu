@@ -691,6 +691,9 @@ __global__ void k_need_all(int ncases, CaseDyn *__restrict__ dyn) {
 // gathered into the new order) with the case's old skin.  3 is 2 with only
 // the candidates of larger index than the target (the half list of the
 // pair-once walk: a boundary target, after every fluid index, gets none).
+// LIST | 4 (6, 7): wide records, the whole 32-bit first index with no row
+// code (engines beyond 2^25 particles; the walks find the row from the
+// first candidate's cell).
 template <int M, int VARIANT, int EXT = 0, int LIST = 0>
 __global__ void __launch_bounds__(128, EXT == 2 ? 6 : 0)
 k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__ keys,
@@ -823,12 +826,14 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
               if (LIST && __float_as_uint(r2) - 1u < r2l_u) ml |= 1u << k;
             }
           }
-          if (LIST == 3) {  // half list: only candidates of larger index than the target
+          if ((LIST & 3) == 3) {  // half list: only candidates of larger index than the target
             const int lowk = i - (lo + base) + 1;
             if (lowk > 0) ml = lowk >= 32 ? 0u : ml & (0xffffffffu << lowk);
           }
           if (LIST && ml) {
-            if (lcnt < cap) list[(int64_t)i * cap + lcnt] = make_uint2((uint32_t)(lo + base) | rowbits, ml);
+            if (lcnt < cap)
+              list[(int64_t)i * cap + lcnt] =
+                  make_uint2((uint32_t)(lo + base) | (LIST & 4 ? 0u : rowbits), ml);
             lcnt++;
           }
           if (LIST < 2) {
@@ -1782,6 +1787,10 @@ struct ListArgs {
   const float4 *tau4;
   const float2 *tau2;
   float *mu_out;
+  // wide records (beyond 2^25 particles): the keys of the build's cells,
+  // whose cell gives a record's row (valid for every candidate of a kept
+  // list, also where a particle left at the half step)
+  const uint32_t *row_keys;
 };
 
 // One target i of the list walk (all 32 lanes of the warp call it together).
@@ -1790,7 +1799,7 @@ struct ListArgs {
 // sub, sub + G, sub + 2G, ..., so the lanes of a target load neighbouring
 // candidates together (fewer L1 wavefronts per gather), and the G partial
 // sums are combined by a butterfly over the G lanes at the end.
-template <int EXT, int G>
+template <int EXT, int G, int W = 0>
 __device__ __forceinline__ void list_target(const int i, const int sub, const ListArgs &a) {
   const unsigned full = 0xffffffffu;
   const int n = a.n;
@@ -1859,12 +1868,26 @@ __device__ __forceinline__ void list_target(const int i, const int sub, const Li
   // the lane's bit positions within a record
   const unsigned sel = (G == 1 ? 0xffffffffu : G == 2 ? 0x55555555u : G == 4 ? 0x11111111u
                                                                     : 0x01010101u) << sub;
+  // wide records: the rows relative to the target's own cell
+  int tcy = 0, tcz = 0;
+  if (W && nrec) {
+    int tcx;
+    decode_cell(key_cell(a.row_keys[i], nbits) - C.cellbase, C.nx, C.ny, tcx, tcy, tcz);
+  }
   auto next_record = [&]() {
     const uint2 rec = mine[r++];
-    cbase = (int)(rec.x & kListIndexMask);
-    cm = rec.y & sel;
     int rdy, rdz;
-    list_row_decode(rec.x, rdy, rdz);
+    if (W) {
+      cbase = (int)rec.x;
+      int bx, by, bz;
+      decode_cell(key_cell(a.row_keys[cbase], nbits) - C.cellbase, C.nx, C.ny, bx, by, bz);
+      rdy = by - tcy;
+      rdz = bz - tcz;
+    } else {
+      cbase = (int)(rec.x & kListIndexMask);
+      list_row_decode(rec.x, rdy, rdz);
+    }
+    cm = rec.y & sel;
     sy = fmaf(-(float)rdy, cs, pa.y);
     sz = fmaf(-(float)rdz, cs, pa.z);
   };
@@ -1939,12 +1962,12 @@ __device__ __forceinline__ void list_target(const int i, const int sub, const Li
   finish_target(C, i, n, cidx, has, afluid, va, A, want_dt, ace, mu_out, dyn, sub == 0);
 }
 
-// G threads per target, in the key order of the targets.
-template <int EXT, int G>
+// G threads per target, in the key order of the targets (W: wide records).
+template <int EXT, int G, int W = 0>
 __global__ void __launch_bounds__(EXT == 0 ? 1024 : 128, EXT == 2 ? 6 : (EXT == 0 ? 1 : 0))
 k_interact_list(const ListArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  list_target<EXT, G>(t / G, t % G, a);
+  list_target<EXT, G, W>(t / G, t % G, a);
 }
 
 
@@ -1961,6 +1984,7 @@ k_interact_list(const ListArgs a) {
 // continuity / (m cw)), then its own sums the same way.  The order of the
 // atomic additions varies, so the sums are not reproducible bit for bit.
 // k_sym_finish turns the sums into dv/dt, drho/dt and the Eq 35 terms.
+template <int W>
 __global__ void __launch_bounds__(128)
 k_interact_sym(const ListArgs a, float4 *__restrict__ sum, unsigned *__restrict__ mu_bits) {
   const unsigned full = 0xffffffffu;
@@ -1993,13 +2017,25 @@ k_interact_sym(const ListArgs a, float4 *__restrict__ sum, unsigned *__restrict_
   int cbase = 0;
   float sy = 0.f, sz = 0.f;
   // the next record of the lane, keeping only candidates of index > i
+  int tcy = 0, tcz = 0;  // wide records: rows relative to the target's cell
+  if (W && nrec) {
+    int tcx;
+    decode_cell(key_cell(a.row_keys[i], nbits) - C.cellbase, C.nx, C.ny, tcx, tcy, tcz);
+  }
   auto next_record = [&]() {
     const uint2 rec = mine[r++];
-    cbase = (int)(rec.x & kListIndexMask);
+    cbase = W ? (int)rec.x : (int)(rec.x & kListIndexMask);
     const int lowk = i - cbase + 1;  // first bit of a larger index
     cm = lowk <= 0 ? rec.y : (lowk >= 32 ? 0u : rec.y & (0xffffffffu << lowk));
     int rdy, rdz;
-    list_row_decode(rec.x, rdy, rdz);
+    if (W) {
+      int bx, by, bz;
+      decode_cell(key_cell(a.row_keys[cbase], nbits) - C.cellbase, C.nx, C.ny, bx, by, bz);
+      rdy = by - tcy;
+      rdz = bz - tcz;
+    } else {
+      list_row_decode(rec.x, rdy, rdz);
+    }
     sy = fmaf(-(float)rdy, cs, pa.y);
     sz = fmaf(-(float)rdz, cs, pa.z);
   };
@@ -2474,7 +2510,7 @@ __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
                              const uint16_t *__restrict__ cid, const CaseConst *__restrict__ cc,
                              int nbits, const uint2 *__restrict__ list, int cap,
                              const uint16_t *__restrict__ count, ListCtl *__restrict__ ctl,
-                             int half) {
+                             int half, const uint32_t *__restrict__ row_keys) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nvalid = *nvalid_p;
   if (i >= nvalid || i >= n) return;
@@ -2505,9 +2541,17 @@ __global__ void k_list_check(int n, const int *__restrict__ nvalid_p,
   }
   for (int r = 0; r < (int)count[i]; r++) {
     const uint2 rec = list[(int64_t)i * cap + r];
-    const int cbase = (int)(rec.x & kListIndexMask);
+    const int cbase = row_keys ? (int)rec.x : (int)(rec.x & kListIndexMask);
     int rdy, rdz;
-    list_row_decode(rec.x, rdy, rdz);
+    if (row_keys) {  // wide records: the row from the first candidate's cell
+      int bx, by, bz, tx, ty, tz;
+      decode_cell(key_cell(row_keys[cbase], nbits) - C.cellbase, C.nx, C.ny, bx, by, bz);
+      decode_cell(key_cell(row_keys[i], nbits) - C.cellbase, C.nx, C.ny, tx, ty, tz);
+      rdy = by - ty;
+      rdz = bz - tz;
+    } else {
+      list_row_decode(rec.x, rdy, rdz);
+    }
     const float sy = fmaf(-(float)rdy, cs, pa.y);
     const float sz = fmaf(-(float)rdz, cs, pa.z);
     for (unsigned m = rec.y; m; m &= m - 1u) {
@@ -2994,13 +3038,25 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const CaseConst *cc, CaseDyn *dyn, float4 *ace, int want_dt,
                           const uint2 *list, int cap, const uint16_t *count, bool ext,
                           float4 *tau4, float2 *tau2, cudaStream_t s, float *mu, int block,
-                          int lanes, float4 *sym_sum, unsigned *sym_mu) {
+                          int lanes, float4 *sym_sum, unsigned *sym_mu,
+                          const uint32_t *wide_keys) {
   if (n <= 0) return;
   if (lanes != 2 && lanes != 4 && lanes != 8) lanes = 1;
-  const ListArgs a{n,   nvalid, keys, posc, velrho, press, cid,   cstart, (uint32_t)(cap_cells + 1),
-                   nbits, cc,   dyn,  ace,  want_dt, list,  cap,   count,  tau4, tau2, mu};
+  const ListArgs a{n,     nvalid, keys,  posc,  velrho, press,  cid,  cstart,
+                   (uint32_t)(cap_cells + 1), nbits, cc, dyn,  ace,  want_dt, list,
+                   cap,   count,  tau4,  tau2,  mu,     wide_keys};
+  if (wide_keys) {  // wide records: the default physics only, one thread per target
+    if (sym_sum) {
+      k_interact_sym<1><<<nblk(n, 128), 128, 0, s>>>(a, sym_sum, sym_mu);
+      k_sym_finish<<<nblk(n, kFinishThreads * kFinishPer), kFinishThreads, 0, s>>>(
+          a, sym_sum, sym_mu);
+    } else {
+      k_interact_list<0, 1, 1><<<nblk(n, 128), 128, 0, s>>>(a);
+    }
+    return;
+  }
   if (sym_sum && !ext && !tau4) {  // each pair once, then the per-particle values
-    k_interact_sym<<<nblk(n, 128), 128, 0, s>>>(a, sym_sum, sym_mu);
+    k_interact_sym<0><<<nblk(n, 128), 128, 0, s>>>(a, sym_sum, sym_mu);
     k_sym_finish<<<nblk(n, kFinishThreads * kFinishPer), kFinishThreads, 0, s>>>(a, sym_sum,
                                                                                  sym_mu);
     return;
@@ -3072,25 +3128,32 @@ void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *key
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
                        uint16_t *count, float4 *ref, const float4 *ref_src, cudaStream_t s,
-                       bool half) {
+                       bool half, bool wide) {
   if (n <= 0) return;
   const uint32_t cap1 = (uint32_t)(cap_cells + 1);
 #define SPH_BL_ARGS                                                                        \
   n, nvalid, keys, posc, velrho, press, cid, cstart, cap1, nbits, cc, dyn, ace, nullptr, 0, \
       nullptr, nullptr, list, cap, count, ref, ref_src
-  if (half) {
-    if (margin == 1)
-      k_interact<1, 0, 0, 3><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
-    else if (margin == 3)
-      k_interact<3, 0, 0, 3><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
-    else
-      k_interact<2, 0, 0, 3><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
+#define SPH_BL(L)                                                                \
+  if (margin == 1)                                                               \
+    k_interact<1, 0, 0, L><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);           \
+  else if (margin == 3)                                                          \
+    k_interact<3, 0, 0, L><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);           \
+  else                                                                           \
+    k_interact<2, 0, 0, L><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
+  if (wide && half) {
+    SPH_BL(7)
+  } else if (wide) {
+    SPH_BL(6)
+  } else if (half) {
+    SPH_BL(3)
   } else if (margin == 1)
     k_interact<1, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
   else if (margin == 3)
     k_interact<3, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
   else
     k_interact<2, 0, 0, 2><<<nblk(n, 128), 128, 0, s>>>(SPH_BL_ARGS);
+#undef SPH_BL
 #undef SPH_BL_ARGS
 }
 
@@ -3166,10 +3229,11 @@ void launch_decide(cudaGraphConditionalHandle h, const ListCtl *ctl, cudaStream_
 
 void launch_list_check(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
                        const uint16_t *cid, const CaseConst *cc, int nbits, const uint2 *list,
-                       int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s, bool half) {
+                       int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s, bool half,
+                       const uint32_t *wide_keys) {
   if (n > 0)
     k_list_check<<<nblk(n, 128), 128, 0, s>>>(n, nvalid, keys, posc, cid, cc, nbits, list, cap,
-                                              count, ctl, half ? 1 : 0);
+                                              count, ctl, half ? 1 : 0, wide_keys);
 }
 
 void launch_corrector_list(int n, const uint32_t *keys_n, const uint32_t *keys_half, State sn,

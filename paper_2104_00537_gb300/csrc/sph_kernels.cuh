@@ -80,7 +80,7 @@ void launch_build_list(int margin, int n, const int *nvalid, const uint32_t *key
                        const uint16_t *cid, const uint32_t *cstart, int64_t cap_cells, int nbits,
                        const CaseConst *cc, CaseDyn *dyn, float4 *ace, uint2 *list, int cap,
                        uint16_t *count, float4 *ref, const float4 *ref_src, cudaStream_t s,
-                       bool half = false);
+                       bool half = false, bool wide = false);
 // First evaluation of the list step: the compacted pair loop on state n that
 // also writes every target's list (chunk records, radius 2h + skin) and count.
 void launch_interact_build(int margin, int n, const int *nvalid, const uint32_t *keys,
@@ -96,7 +96,7 @@ void launch_interact_list(int n, const int *nvalid, const uint32_t *keys, const 
                           const uint2 *list, int cap, const uint16_t *count, bool ext,
                           float4 *tau4, float2 *tau2, cudaStream_t s, float *mu = nullptr,
                           int block = 128, int lanes = 1, float4 *sym_sum = nullptr,
-                          unsigned *sym_mu = nullptr);
+                          unsigned *sym_mu = nullptr, const uint32_t *wide_keys = nullptr);
 void launch_predictor_list(int n, const uint32_t *keys_in, State src, const float4 *ace,
                            const CaseConst *cc, CaseDyn *dyn, int nbits, float4 *posc_out,
                            float4 *velrho_out, uint32_t *keys_out, float *press,
@@ -114,7 +114,7 @@ void launch_decide(cudaGraphConditionalHandle h, const ListCtl *ctl, cudaStream_
 void launch_list_check(int n, const int *nvalid, const uint32_t *keys, const float4 *posc,
                        const uint16_t *cid, const CaseConst *cc, int nbits, const uint2 *list,
                        int cap, const uint16_t *count, ListCtl *ctl, cudaStream_t s,
-                       bool half = false);
+                       bool half = false, const uint32_t *wide_keys = nullptr);
 void launch_corrector_list(int n, const uint32_t *keys_n, const uint32_t *keys_half, State sn,
                            const float4 *velrho_half, const float4 *ace, const CaseConst *cc,
                            CaseDyn *dyn, int nbits, State x, uint32_t *keys_next,

@@ -68,7 +68,8 @@ class Options(C.Structure):
     _fields_ = [("pi_block", C.c_int32), ("pi_variant", C.c_int32),
                 ("use_graph", C.c_int32), ("timing", C.c_int32),
                 ("list_skin", C.c_float), ("check_list", C.c_int32),
-                ("pi_lanes", C.c_int32), ("pair_once", C.c_int32)]
+                ("pi_lanes", C.c_int32), ("pair_once", C.c_int32),
+                ("wide_records", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -328,7 +329,7 @@ class Engine:
         check(self.lib.sph_step(self.h, int(nsteps)))
 
     def set_options(self, pi_block=0, pi_variant=-1, use_graph=0, timing=0, list_skin=-1.0,
-                    check_list=0, pi_lanes=0, pair_once=0):
+                    check_list=0, pi_lanes=0, pair_once=0, wide_records=0):
         """pi_variant -1 keeps the engine default (where the engine supports
         a neighbour list: kept across steps, 5; else the compacted loop, 0;
         4, one list per step, keeps batch and pool cases equal to their runs
@@ -336,9 +337,10 @@ class Engine:
         variant 5's added skin as a fraction of 2h (< 0: the default, 0.04);
         check_list: brute-force check of every list evaluation (list_info);
         pi_lanes: threads per target of the list walk (0: the default);
-        pair_once: evaluate each pair once (atomic sums, not bit-reproducible)."""
+        pair_once: evaluate each pair once (atomic sums, not bit-reproducible);
+        wide_records: 32-bit list records at any size (else beyond 2^25 only)."""
         o = Options(pi_block, pi_variant, use_graph, timing, list_skin, check_list, pi_lanes,
-                    pair_once)
+                    pair_once, wide_records)
         check(self.lib.sph_set_options(self.h, C.byref(o)))
 
     def list_info(self):

@@ -178,6 +178,67 @@ def test_pair_once_through_the_splash_and_in_a_batch():
     bat.destroy()
 
 
+@pytest.mark.parametrize("variant,pair_once", [(5, 0), (4, 0), (5, 1)])
+def test_wide_records_equal_narrow(variant, pair_once):
+    """Wide list records (a 32-bit first index, the row taken from the first
+    candidate's cell: what an engine beyond 2^25 particles uses), asked for on
+    a small case: both evaluations against the oracle at rest and after 60
+    steps, every pair listed, and (with each target's own sums) the same steps
+    bit for bit as the narrow records."""
+    case = cases.dam_break(0.02)
+    wide = sph.Engine.create(case)
+    wide.set_options(pi_variant=variant, use_graph=1, wide_records=1, pair_once=pair_once)
+    for stage in (0, 1):
+        check_step_eval(case, wide, stage)
+    wide.set_options(pi_variant=variant, use_graph=1, wide_records=1, pair_once=pair_once,
+                     check_list=1)
+    wide.step(60)
+    li = wide.list_info()
+    assert li["check_bad"] == 0 and li["builds"] > 0
+    for stage in (0, 1):
+        check_step_eval(case, wide, stage)
+    if not pair_once:
+        narrow = sph.Engine.create(case)
+        narrow.set_options(pi_variant=variant, use_graph=1, check_list=1)
+        narrow.step(60)
+        a, b = wide.get_state(), narrow.get_state()
+        for k in ("pos", "vel", "rho"):
+            assert np.array_equal(a[k], b[k]), k
+        narrow.destroy()
+    wide.destroy()
+
+
+def test_wide_records_beyond_two_to_the_25():
+    """An engine beyond 2^25 particles (the wave flume at dp = 0.0077 m,
+    35.6M particles) walks wide records instead of falling back to the cell
+    walk: its list is built and both evaluations of a step match the oracle."""
+    case = cases.wave_flume(0.0077)
+    assert case.n >= 1 << 25
+    eng = sph.Engine.create(case)
+    eng.set_options(use_graph=1)
+    eng.step(3)
+    assert eng.list_info()["builds"] >= 1
+    f = case.ptype == 0
+    for stage in (0, 1):
+        g = eng.eval_step(stage)
+        acc, drho, mu, npairs = oracle.interact(case.params, g["pos"],
+                                                g["vel"].astype(np.float64),
+                                                g["rho"].astype(np.float64), case.ptype)
+        # pairs within FP32 rounding of the cut-off may differ (weight ~1e-18):
+        # at most the evaluated pairs with |r^2 - (2h)^2| < 1e-6 (2h)^2, counted
+        # by the oracle with the cut-off moved to either edge of that band
+        band = 0
+        for sgn in (1, -1):
+            p = dict(case.params, h=case.params["h"] * np.sqrt(1 + sgn * 1e-6))
+            band += sgn * oracle.interact(p, g["pos"], g["vel"].astype(np.float64),
+                                          g["rho"].astype(np.float64), case.ptype)[3]
+        assert abs(g["pairs"] - npairs) <= band, (g["pairs"], npairs, band)
+        assert rel_err(g["acc"][f], acc[f]) < TOL
+        assert rel_err(g["drho"], drho) < TOL
+        assert rel_err(g["mumax"][f], mu[f]) < TOL
+    eng.destroy()
+
+
 def test_kept_list_evaluation_through_the_splash():
     """The dam break through its collapse and splash (~1,050 steps, t ~ 0.3 s),
     with the list kept across steps and rebuilt as the flow needs: both
