@@ -62,7 +62,7 @@ def hbm_peak_gbs():
         return 6800.0  # fallback figure for a GB300 copy
 
 
-def list_capture(cell_mode, workload_name, variant):
+def list_capture(cell_mode, workload_name, variant, pair_once=False):
     """The committed ncu capture of the list kernels for this variant
     (profiles/k_interact_list_traffic.json), or None when it does not match:
     another workload / cell size / variant, or the kernel source or the build
@@ -72,7 +72,7 @@ def list_capture(cell_mode, workload_name, variant):
         d = json.load(open(os.path.join(ROOT, "profiles", "k_interact_list_traffic.json")))
         src = open(os.path.join(ROOT, d["source"]), "rb").read()
         flags = open(os.path.join(ROOT, d["build"]), "rb").read()
-        v = d["variants"][str(variant)]
+        v = d["variants"][str(variant) + ("p" if pair_once else "")]
     except (OSError, ValueError, KeyError):
         return None
     if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
@@ -84,12 +84,13 @@ def list_capture(cell_mode, workload_name, variant):
     return v
 
 
-def measured_traffic(cell_mode, workload_name, variant, builds_per_step=1.0):
+def measured_traffic(cell_mode, workload_name, variant, builds_per_step=1.0, pair_once=False):
     """DRAM bytes per interaction launch, as bench.py times it, from the
     committed capture (None when it does not match, see list_capture).
     Variant 4: (build + two evaluations) / 2; variant 5: one evaluation plus
-    half the build times the builds per step."""
-    v = list_capture(cell_mode, workload_name, variant)
+    half the build times the builds per step (pair_once: the pair-once walk
+    and its finish as the evaluation, the half-list build as the build)."""
+    v = list_capture(cell_mode, workload_name, variant, pair_once)
     if v is None:
         return None
     if variant == 4:
@@ -97,10 +98,10 @@ def measured_traffic(cell_mode, workload_name, variant, builds_per_step=1.0):
     return v["eval_bytes"] + builds_per_step * v["build_bytes"] / 2
 
 
-def measured_limiter(cell_mode, workload_name, variant):
+def measured_limiter(cell_mode, workload_name, variant, pair_once=False):
     """The hardware unit that bounds the list evaluation in the committed
     capture, with its utilisation (None when the capture does not match)."""
-    v = list_capture(cell_mode, workload_name, variant)
+    v = list_capture(cell_mode, workload_name, variant, pair_once)
     return None if v is None else v.get("limiter")
 
 
@@ -439,8 +440,10 @@ def main():
                     help="threads per block of the list walk (0: the engine default)")
     ap.add_argument("--pi-lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="threads per target of the list walk (0: the engine default)")
-    ap.add_argument("--pair-once", type=int, default=0, choices=[0, 1],
-                    help="1: evaluate each pair once (atomic sums, not bit-reproducible)")
+    ap.add_argument("--pair-once", type=int, default=1, choices=[0, 1],
+                    help="1 (default): evaluate each pair once (atomic sums, not "
+                         "bit-reproducible); 0: every target sums its own pairs (the "
+                         "library's default, reproducible bit for bit)")
     ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "verlet"])
     ap.add_argument("--visc-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--nu0", type=float, default=1e-6)
@@ -576,8 +579,7 @@ def main():
     # the committed capture is of the default physics and launch shape
     captured = ((args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) ==
                 (1, "symplectic", 0, 0) and eff_var in (4, 5) and
-                args.pi_block in (0, 128) and args.pi_lanes in (0, 1) and args.list_skin < 0 and
-                not args.pair_once)
+                args.pi_block in (0, 128) and args.pi_lanes in (0, 1) and args.list_skin < 0)
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "flop_basis": "48 / 45 / 25 FLOP per directed fluid-fluid / fluid-boundary / "
@@ -593,9 +595,10 @@ def main():
                                       % (peaks["sms"], mhz),
                 "fp64_measured_tflops": peaks["fp64_tflops"],
                 "traffic": measured_traffic(args.cell_mode, args.workload, eff_var,
+                                            pair_once=pair_once_on, builds_per_step=
                                             builds / args.steps) if captured else None,
-                "limiter": measured_limiter(args.cell_mode, args.workload, eff_var)
-                if captured else None,
+                "limiter": measured_limiter(args.cell_mode, args.workload, eff_var,
+                                            pair_once_on) if captured else None,
                 "pi_share_of_step": tm["pi_ms"] / max(tm["step_ms"], 1e-9),
                 "pi_ms_per_launch": 1000 * pi_avg_s}
 
@@ -673,30 +676,33 @@ def main():
             (args.ddt_mode, args.integrator, args.visc_mode, args.boundary_mode) == \
             (1, "symplectic", 0, 0) and args.pi_variant in (-1, 5):
         # the rest of the metric, measured in the same run: the whole 2,000-step
-        # run of this case, batched vs plain (C3), served vs plain (C4, scaled)
-        out["full_run"] = measure_full_run(cs[0], stream)
-        # the same run with each pair evaluated once (an option: its atomic
-        # sums are not the same bit for bit from run to run)
-        out["full_run_pair_once"] = measure_full_run(cs[0], stream, pair_once=1)
-        out["batched"] = measure_batched(256, 500, 3, tune=True, clock_index=local)
+        # run of this case, batched vs plain (C3), served vs plain (C4, scaled),
+        # each in the mode of the line (pair_once as given) and in the other
+        po = args.pair_once
+        other = "reproducible" if po else "pair_once"
+        out["full_run"] = measure_full_run(cs[0], stream, pair_once=po)
+        out["full_run_" + other] = measure_full_run(cs[0], stream, pair_once=1 - po)
+        out["batched"] = measure_batched(256, 500, 3, tune=True, clock_index=local,
+                                         pair_once=po)
         out["batched"]["note"] = ("C3 as configured (256 cases, 26.6M particles, 500 timed "
                                   "steps after 3 from rest); cell size, pair loop and block "
                                   "size from the autotuner (3 timed steps per candidate), the "
-                                  "same for both paths; each path's state equals the other's "
-                                  "(same pairs)")
-        # the same comparison with each pair evaluated once on both paths
+                                  "same for both paths" + (
+                                      "; each pair evaluated once on both paths (atomic "
+                                      "sums: the paths agree to rounding, and their pair "
+                                      "counts differ by pairs at the cut-off)" if po else
+                                      "; each path's state equals the other's (same pairs)"))
         b = out["batched"]
-        out["batched_pair_once"] = measure_batched(
-            256, 500, 3, tune=False, clock_index=local, pair_once=1,
+        out["batched_" + other] = measure_batched(
+            256, 500, 3, tune=False, clock_index=local, pair_once=1 - po,
             fixed=(b["cell_mode"], b["pi_variant"], b["pi_block"]))
-        out["batched_pair_once"]["note"] = ("as batched, both paths with pair_once (the "
-                                            "autotuned configuration above)")
-        out["served"] = measure_served(48, 20.0, 200000, 0.1, 10)
+        out["batched_" + other]["note"] = "as batched, both paths with pair_once = %d" % (1 - po)
+        out["served"] = measure_served(48, 20.0, 200000, 0.1, 10, pair_once=po)
         out["served"]["note"] = ("C4 scaled to fit the run: 48 requests, fluid <= 200k, "
                                  "0.1 s simulated (C4: 100+ requests, <= 2M, 1 s; run with "
                                  "--workload served)")
-        out["served_pair_once"] = measure_served(48, 20.0, 200000, 0.1, 10, pair_once=1)
-        out["served_pair_once"]["note"] = "as served, pools of both modes with pair_once"
+        out["served_" + other] = measure_served(48, 20.0, 200000, 0.1, 10, pair_once=1 - po)
+        out["served_" + other]["note"] = "as served, both modes with pair_once = %d" % (1 - po)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(cs[0])
     if rank == 0:

@@ -340,11 +340,13 @@ def test_list_evaluation_wave_flume_fiftieth_scale():
     eng.destroy()
 
 
-def test_full_size_dam_break_order_and_evaluation():
+@pytest.mark.parametrize("pair_once", [0, 1])
+def test_full_size_dam_break_order_and_evaluation(pair_once):
     """The 1.48M-particle dam break (dp = 0.004 m) in the bench's launch
-    configuration (kept list, CUDA-graph replay): the cell order after the
-    3-pass radix sort of 23-bit keys bit-exact at t = 0, then both
-    evaluations of step 21 against the oracle."""
+    configuration (kept list, CUDA-graph replay; each target's own sums, and
+    each pair once as the bench times it): the cell order after the 3-pass
+    radix sort of 23-bit keys bit-exact at t = 0, then both evaluations of
+    step 21 against the oracle."""
     case = cases.dam_break(0.004, cell_mode=1)
     eng = sph.Engine.create(case)
     ids, cells, ninside = eng.order()
@@ -352,7 +354,7 @@ def test_full_size_dam_break_order_and_evaluation():
     assert ninside == inside == case.n
     assert np.array_equal(ids, order)
     assert np.array_equal(cells, oracle.cells(case.params, case.pos)[order])
-    eng.set_options(pi_variant=5, use_graph=1)
+    eng.set_options(pi_variant=5, use_graph=1, pair_once=pair_once)
     eng.step(20)
     for stage in (0, 1):
         check_step_eval(case, eng, stage, exact_pairs=False)
