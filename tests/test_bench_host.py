@@ -79,12 +79,17 @@ def test_profile_figures_follow_their_capture(tmp_path, monkeypatch):
     d = {"source": "k.cu", "source_sha256": sha(tmp_path / "k.cu"),
          "build": "build.py", "build_sha256": sha(tmp_path / "build.py"),
          "variants": {"4": {"eval_bytes": 300, "build_bytes": 200, "limiter": lim},
-                      "5": {"eval_bytes": 330, "build_bytes": 200, "limiter": lim}}}
+                      "5": {"eval_bytes": 330, "build_bytes": 200, "limiter": lim},
+                      "5p": {"eval_bytes": 260, "build_bytes": 130, "limiter": lim}}}
     (tmp_path / "profiles" / "k_interact_list_traffic.json").write_text(json.dumps(d))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_traffic(1, "dam_break", 4) == (200 + 2 * 300) / 2
     assert bench.measured_traffic(1, "dam_break", 5, 0.25) == 330 + 0.25 * 200 / 2
     assert bench.measured_limiter(1, "dam_break", 5) == lim
+    # the pair-once mode has its own entry (and none for variant 4 here)
+    assert bench.measured_traffic(1, "dam_break", 5, 0.25, pair_once=True) == 260 + 0.25 * 130 / 2
+    assert bench.measured_limiter(1, "dam_break", 5, pair_once=True) == lim
+    assert bench.measured_traffic(1, "dam_break", 4, pair_once=True) is None
     # another workload, cell size or variant: nothing
     assert bench.measured_traffic(1, "wave_flume", 5) is None
     assert bench.measured_traffic(0, "dam_break", 5) is None
