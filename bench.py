@@ -390,7 +390,6 @@ def run_batched(args):
     torch.cuda.set_device(0)
     r = measure_batched(args.ncases, args.steps, args.warmup, tune=True,
                         pair_once=args.pair_once)
-    nb = r["cases"] * args.steps
     out = {"metric": "case_steps_per_s", "value": r["batched"]["case_steps_per_s"],
            "unit": "case-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": r["batched"]["ms_per_step"], "higher_is_better": True,
@@ -402,7 +401,6 @@ def run_batched(args):
            "batched": r["batched"], "plain": r["plain"],
            "speedup_vs_plain": r["speedup_vs_plain"],
            "autotune_ms_per_step": r["autotune_ms_per_step"], "clocks": r["clocks"]}
-    del nb
     print(json.dumps(out), flush=True)
 
 

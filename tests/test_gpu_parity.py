@@ -642,6 +642,51 @@ def test_batch_rebuilds_with_a_particle_leaving_the_domain():
         bat.destroy()
 
 
+@pytest.mark.parametrize("wide", [0, 1])
+def test_batch_pair_once_and_wide_records_with_a_particle_leaving(wide):
+    """The batch of the previous test with each pair once (and with wide
+    records): the restricted and the full re-sorts keep the half lists whole
+    (every pair found at every evaluation), and each case stays within
+    rounding of its run alone (atomic sums); with wide records and each
+    target's own pairs, the batch equals its narrow-record run bit for bit."""
+    c1 = cases.dam_break(0.04, seed=1)
+    f = np.where(c1.ptype == 0)[0][-1]
+    origin, csz, nc, margin = oracle.grid(c1.params)
+    ztop = origin[2] + (nc[2] - margin) * csz
+    c1.pos[f] = (0.8, 0.3, ztop - 0.004)
+    c1.vel[f] = (0.0, 0.0, 5.0)
+    cs = [c1, cases.sloshing_tank(2000, 0.25, 0.02, 1.0, seed=2),
+          cases.dam_break(0.03, seed=3, column=(0.3, 0.2, 0.3))]
+    bat = sph.Engine.batch(cs)
+    bat.set_options(check_list=1, use_graph=1, pair_once=1, wide_records=wide)
+    bat.step(60)
+    assert bat.list_info()["check_bad"] == 0
+    assert bat.stats(0)["n_out"] >= 1
+    for i, c in enumerate(cs):
+        e = sph.Engine.create(c)
+        e.set_options(use_graph=1)
+        e.step(60)
+        a, b = e.get_state(), bat.get_state(i)
+        keep = np.ones(c.n, bool)
+        if i == 0:
+            keep[f] = False  # the particle that left (frozen where it crossed)
+        assert np.abs(a["pos"][keep] - b["pos"][keep]).max() < 0.05 * c.params["dp"], i
+        assert abs(a["t"] - b["t"]) < 1e-3 * a["t"]
+        e.destroy()
+    bat.destroy()
+    if wide:
+        runs = []
+        for w in (0, 1):
+            bw = sph.Engine.batch(cs)
+            bw.set_options(use_graph=1, wide_records=w)
+            bw.step(60)
+            runs.append([bw.get_state(i) for i in range(len(cs))])
+            bw.destroy()
+        for a, b in zip(*runs):
+            for k in ("pos", "vel", "rho"):
+                assert np.array_equal(a[k], b[k]), k
+
+
 def test_kept_list_steps_do_not_depend_on_calls(c0):
     """Splitting steps into calls changes nothing on the kept list: a call
     continues the list of the previous one (eager launches and graph replay
