@@ -736,8 +736,11 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
   const float Pa = has ? press[i] * va.w : 0.f;  // press holds P / rho
   const float kv = C.kvisc * va.w;
   const bool ddt_on = C.ddt != 0;
-  // boundary targets of an mDBC case take their density from Eq 38, not Eq 36
-  const bool work = has && (afluid || C.bmode == 0) && lmode != 0;
+  // boundary targets of an mDBC case take their density from Eq 38, not Eq 36;
+  // a half list (every boundary index above every fluid one) leaves boundary
+  // targets without candidates
+  constexpr bool HALF = (LIST & 3) == 3;
+  const bool work = has && (afluid || C.bmode == 0) && lmode != 0 && (!HALF || afluid);
   Ext X;
   X.C = &C;
   X.hyd = EXT >= 1 && C.ddt == 2;
@@ -795,8 +798,13 @@ k_interact(int n, const int *__restrict__ nvalid_p, const uint32_t *__restrict__
       }
       const int c0 = gc + dz * nxy + dy * nx + kx0;
       const int c1 = gc + dz * nxy + dy * nx + kx1 + 1;
-      loF = (int)cstart[c0];
-      hiF = (int)cstart[c1];
+      // half list: the fluid particles of the rows below the target's and of
+      // the cells before its own in its row have smaller indices (cell order)
+      const bool below = HALF && (dz < 0 || (dz == 0 && dy < 0));
+      if (!below) {
+        loF = (int)cstart[HALF && dz == 0 && dy == 0 ? gc + max(kx0, 0) : c0];
+        hiF = (int)cstart[c1];
+      }
       if (afluid) {
         loB = (int)cstart[cap1 + c0];
         hiB = (int)cstart[cap1 + c1];
