@@ -289,7 +289,8 @@ def measure_batched(ncases, steps, warmup, tune, clock_index=0, pair_once=0, fix
         cm, var, block = fixed
     elif tune:
         mk = lambda cc: sph.Engine.batch(cc, stream=stream)
-        (cm, var, block), tune_ms = autotune.tune(cs, mk, torch.cuda.get_device_name(0))
+        (cm, var, block), tune_ms = autotune.tune(cs, mk, torch.cuda.get_device_name(0),
+                                                  pair_once=pair_once)
     for c in cs:
         c.params["cell_mode"] = cm
     eng = sph.Engine.batch(cs, stream=stream)

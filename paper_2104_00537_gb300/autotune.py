@@ -26,10 +26,11 @@ def cache_path() -> str:
     return base
 
 
-def bucket_key(gpu_name: str, cases) -> str:
+def bucket_key(gpu_name: str, cases, pair_once=0) -> str:
     n = sum(c.n for c in cases)
-    return "%s|cases~2^%d|particles~2^%d" % (gpu_name, int(math.log2(max(1, len(cases)))),
-                                            int(math.log2(max(1, n))))
+    return "%s|cases~2^%d|particles~2^%d%s" % (gpu_name, int(math.log2(max(1, len(cases)))),
+                                              int(math.log2(max(1, n))),
+                                              "|pair_once" if pair_once else "")
 
 
 def _load():
@@ -52,7 +53,7 @@ def _store(d):
         pass
 
 
-def _time(cases, make_engine, cm, var, block, steps, warmup):
+def _time(cases, make_engine, cm, var, block, steps, warmup, pair_once=0):
     """ms per step of one configuration; inf if it cannot run (for instance a
     neighbour list that overflows at this cell size: the library reports it)."""
     for c in cases:
@@ -62,9 +63,9 @@ def _time(cases, make_engine, cm, var, block, steps, warmup):
     except RuntimeError:
         return float("inf")
     try:
-        e.set_options(pi_variant=var, pi_block=block)
+        e.set_options(pi_variant=var, pi_block=block, pair_once=pair_once)
         e.step(warmup)
-        e.set_options(pi_variant=var, pi_block=block, timing=1)
+        e.set_options(pi_variant=var, pi_block=block, timing=1, pair_once=pair_once)
         e.timing(reset=True)
         e.step(steps)
         t = e.timing(reset=True)
@@ -76,13 +77,14 @@ def _time(cases, make_engine, cm, var, block, steps, warmup):
 
 
 def tune(cases, make_engine, gpu_name: str, steps=3, warmup=2, candidates=CANDIDATES,
-         blocks=BLOCKS, use_cache=True):
+         blocks=BLOCKS, use_cache=True, pair_once=0):
     """Return ((cell_mode, pi_variant, pi_block), {config: ms_per_step}).
 
     make_engine(cases) must build an engine from the cases (whose params carry
     cell_mode); the engine's timing option gives the device time per step.
-    The cases' cell_mode is restored afterwards."""
-    key = bucket_key(gpu_name, cases)
+    pair_once: the candidates are timed with each pair evaluated once (where a
+    list walk applies).  The cases' cell_mode is restored afterwards."""
+    key = bucket_key(gpu_name, cases, pair_once)
     cache = _load() if use_cache else {}
     if key in cache and len(cache[key].get("best", ())) == 3:
         return tuple(cache[key]["best"]), cache[key].get("times", {})
@@ -90,14 +92,15 @@ def tune(cases, make_engine, gpu_name: str, steps=3, warmup=2, candidates=CANDID
     saved = [c.params.get("cell_mode", 0) for c in cases]
     try:
         for cm, var in candidates:
-            times["%d,%d,128" % (cm, var)] = _time(cases, make_engine, cm, var, 0, steps, warmup)
+            times["%d,%d,128" % (cm, var)] = _time(cases, make_engine, cm, var, 0, steps, warmup,
+                                                   pair_once)
         best_s = min(times, key=times.get)
         cm, var, _ = (int(x) for x in best_s.split(","))
         if var in (3, 4, 5):
             for b in blocks:
                 k = "%d,%d,%d" % (cm, var, b)
                 if k not in times:
-                    times[k] = _time(cases, make_engine, cm, var, b, steps, warmup)
+                    times[k] = _time(cases, make_engine, cm, var, b, steps, warmup, pair_once)
     finally:
         for c, cm0 in zip(cases, saved):
             c.params["cell_mode"] = cm0
