@@ -172,7 +172,7 @@ def dam_break(dp: float = 0.02, seed: int = 0, column=(0.4, 0.4, 0.4),
     """3-D dam break: fluid column in the x=0, y=0 corner of an open tank.
 
     dp = 0.02 gives 8,000 fluid + 20,062 boundary particles; dp = 0.004
-    gives 1,000,000 fluid + 482,638 boundary particles."""
+    gives 1,000,000 fluid + 479,826 boundary particles."""
     NX, NY, NZ = (int(round(L / dp)) for L in tank)
     nfx, nfy, nfz = (int(round(L / dp)) for L in column)
     r = lambda a, b: np.arange(a, b + 1)
