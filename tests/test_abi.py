@@ -66,6 +66,33 @@ int main(void) {
         sph.CaseParams.cell_mode.offset, sph.Particles.n_motions.offset, sph.Stats.n.offset]
 
 
+def test_every_field_offset_matches_c():
+    """Every field of every struct the binding passes, at the offset the C
+    compiler gives it (a field added, dropped or reordered on one side only
+    fails here)."""
+    structs = {"sph_case_params": sph.CaseParams, "sph_particles": sph.Particles,
+               "sph_motion": sph.Motion, "sph_stats": sph.Stats, "sph_options": sph.Options}
+    lines = []
+    for cname, cls in structs.items():
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%%s %%s %%zu\\n", "%s", "%s", offsetof(%s, %s));'
+                         % (cname, fname, cname, fname))
+    prog = ("#include <stdio.h>\n#include <stddef.h>\n#include \"sph.h\"\n"
+            "int main(void) {\n" + "\n".join(lines) + "\n  return 0;\n}\n")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(src, "w").write(prog)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        out = subprocess.check_output([exe], text=True).split("\n")
+    got = {(c, f): int(o) for c, f, o in (x.split() for x in out if x.strip())}
+    for cname, cls in structs.items():
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+        # the last field ends where the C struct (with its tail padding) allows
+        assert C.sizeof(cls) >= max(getattr(cls, f).offset for f, _ in cls._fields_)
+
+
 def test_calls_without_gpu_fail_loudly():
     import torch
     if torch.cuda.is_available():
