@@ -294,7 +294,9 @@ int sph_eval_forces(sph_engine e, int32_t icase, float *acc, float *drho,
  * [0, cs)).  The part of the next step before its first evaluation runs for
  * real -- a pending rebuild of the kept list, or the sort of a per-step list
  * or cell walk -- and everything else the next step reads is restored, so
- * sph_step afterwards takes the steps it would have taken (bit for bit).
+ * sph_step afterwards takes the steps it would have taken (bit for bit with
+ * each target's own sums; with pair_once the evaluations take the pair-once
+ * walk, whose atomic sums vary in their last bits from run to run).
  * Outputs, caller-owned host buffers in the caller's particle order, any may
  * be NULL: pos [3n] (FP64, from the evaluated cell + offset), vel [3n], rho [n]
  * the evaluated state; acc [3n] dv/dt of Eq 22 + f (zero for B), drho [n]
